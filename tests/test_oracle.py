@@ -1,0 +1,320 @@
+"""Pins of the CPU oracle against facts fixed outside it (arXiv 2312.14832, Section 2).
+
+Each test checks the oracle against something it does not compute itself: a library
+routine (scipy.sparse products, numpy SVD, HiGHS), brute-force vertex enumeration,
+closed forms (box-only LPs), planted optima built to satisfy complementarity,
+or theorems about PDHG (fixed point, Fejer monotonicity in the M-norm,
+Pock-Chambolle's norm bound, weak duality, Ruiz equilibration).
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def dense(lp):
+    return sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(lp["m"], lp["n"]))
+
+
+# ---------------------------------------------------------------- products
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_spmv_matches_scipy(seed):
+    lengths = [0, 1, 31, 32, 33, 0, 5, 200, 1, 64] * 3
+    rp, ci, v = lpgen.random_csr(seed, len(lengths), 300, lengths, dist="wide")
+    lp = dict(m=len(lengths), n=300, m1=0, row_ptr=rp, col_idx=ci, val=v)
+    K = dense(lp)
+    x = np.random.default_rng(seed).standard_normal(300)
+    y = np.random.default_rng(seed + 7).standard_normal(len(lengths))
+    np.testing.assert_allclose(oracle.spmv(lp, x), K @ x, rtol=1e-13, atol=1e-10)
+    np.testing.assert_allclose(oracle.spmv_t(lp, y), K.T @ y, rtol=1e-13, atol=1e-10)
+
+
+# ---------------------------------------------------------------- cone and projections
+
+def test_proj_lambda_cases():
+    inf = np.inf
+    # both infinite -> {0}
+    assert oracle.proj_lambda(3.0, -inf, inf) == 0.0
+    assert oracle.proj_lambda(-3.0, -inf, inf) == 0.0
+    # only u finite -> R^-
+    assert oracle.proj_lambda(-2.0, -inf, 1.0) == -2.0
+    assert oracle.proj_lambda(2.0, -inf, 1.0) == 0.0
+    # only l finite -> R^+
+    assert oracle.proj_lambda(2.0, 0.0, inf) == 2.0
+    assert oracle.proj_lambda(-2.0, 0.0, inf) == 0.0
+    # both finite -> R
+    assert oracle.proj_lambda(-2.0, 0.0, 1.0) == -2.0
+    assert oracle.proj_lambda(2.0, 0.0, 1.0) == 2.0
+
+
+# ---------------------------------------------------------------- planted optima
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_planted_optimum_is_kkt_point(seed):
+    lp = lpgen.planted_small(seed)
+    p = oracle.kkt_parts(lp, lp["x_star"], lp["y_star"])
+    scale = 1.0 + np.abs(lp["c"]).max() * 10.0 + np.abs(lp["q"]).max()
+    assert np.sqrt(p["pres2"]) < 1e-11 * scale * np.sqrt(lp["m"])
+    assert np.sqrt(p["dres2"]) < 1e-11 * scale * np.sqrt(lp["n"])
+    assert abs(p["gap"]) < 1e-10 * (1 + abs(lp["obj_star"]))
+    assert abs(p["pobj"] - lp["obj_star"]) < 1e-12 * (1 + abs(lp["obj_star"]))
+    g = dense(lp).T @ lp["y_star"]
+    lam = np.array([oracle.proj_lambda(d, a, b) for d, a, b in zip(lp["c"] - g, lp["l"], lp["u"])])
+    np.testing.assert_allclose(lam, lp["lam_star"], atol=1e-12)
+
+
+def test_planted_zipf_small_is_kkt_point():
+    lp = lpgen.planted_zipf(seed=3, n=4000, m=2000, nnz=40000)
+    p = oracle.kkt_parts(lp, lp["x_star"], lp["y_star"])
+    assert np.sqrt(p["pres2"]) <= 1e-9 * (1 + np.linalg.norm(lp["q"]))
+    assert np.sqrt(p["dres2"]) <= 1e-9 * (1 + np.linalg.norm(lp["c"]))
+    assert abs(p["gap"]) <= 1e-9 * (1 + abs(p["pobj"]))
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_planted_optimum_is_pdhg_fixed_point(seed):
+    lp = lpgen.planted_small(seed)
+    for eta, omega in ((0.05, 1.0), (0.1, 0.3), (0.02, 4.0)):
+        x, y = oracle.pdhg_step(lp, lp["x_star"], lp["y_star"], eta, omega)
+        np.testing.assert_allclose(x, lp["x_star"], rtol=1e-12, atol=1e-11)
+        np.testing.assert_allclose(y, lp["y_star"], rtol=1e-12, atol=1e-11)
+
+
+def test_nonoptimal_point_moves():
+    lp = lpgen.planted_small(0)
+    x0 = lp["x_star"].copy()
+    x0[lp["l"] > -np.inf] = lp["l"][lp["l"] > -np.inf]
+    x, y = oracle.pdhg_step(lp, x0, lp["y_star"], 0.05, 1.0)
+    assert np.linalg.norm(x - x0) > 1e-6
+
+
+# ---------------------------------------------------------------- PDHG theory
+
+def test_fejer_monotone_in_M_norm():
+    """For PDHG on L(x,y) = c'x - y'Kx + q'y with tau = eta/omega, sigma = eta*omega and
+    eta ||K|| < 1, ||z^t - z*||_M is nonincreasing with M = [[I/tau, K'], [K, I/sigma]]."""
+    for seed in (1, 4):
+        lp = lpgen.planted_small(seed)
+        K = dense(lp)
+        s = np.linalg.norm(K.toarray(), 2)
+        for omega in (0.5, 2.0):
+            eta = 0.95 / s
+            tau, sig = eta / omega, eta * omega
+
+            def mnorm(dx, dy):
+                return dx @ dx / tau + dy @ dy / sig + 2.0 * (dy @ (K @ dx))
+
+            rng = np.random.default_rng(seed)
+            x = np.clip(rng.standard_normal(lp["n"]) * 5, lp["l"], lp["u"])
+            y = rng.standard_normal(lp["m"])
+            y[lp["m1"]:] = np.abs(y[lp["m1"]:])
+            prev = mnorm(x - lp["x_star"], y - lp["y_star"])
+            assert prev > 0
+            for _ in range(200):
+                x, y = oracle.pdhg_step(lp, x, y, eta, omega)
+                cur = mnorm(x - lp["x_star"], y - lp["y_star"])
+                assert cur <= prev * (1 + 1e-10) + 1e-10
+                prev = cur
+
+
+def test_weak_duality():
+    """For x primal feasible and y in Y with c - K'y - lambda = 0: dual obj <= primal obj."""
+    for seed in range(5):
+        lp = lpgen.tiny_lp(seed, n=5, m1=1, m2=3)
+        rng = np.random.default_rng(100 + seed)
+        # a primal feasible x from a feasibility LP solved by HiGHS
+        K = lp["K_dense"]
+        from scipy.optimize import linprog
+        res = linprog(np.zeros(lp["n"]), A_ub=-K[lp["m1"]:], b_ub=-lp["q"][lp["m1"]:],
+                      A_eq=K[: lp["m1"]], b_eq=lp["q"][: lp["m1"]],
+                      bounds=list(zip(lp["l"], lp["u"])), method="highs")
+        assert res.status == 0
+        x = res.x
+        for _ in range(10):
+            y = rng.standard_normal(lp["m"])
+            y[lp["m1"]:] = np.abs(y[lp["m1"]:])
+            p = oracle.kkt_parts(lp, x, y)
+            assert p["dres2"] < 1e-20   # all bounds finite: Lambda = R, so lambda = c - K'y
+            assert p["dobj"] <= p["pobj"] + 1e-9
+
+
+# ---------------------------------------------------------------- restart rule
+
+def test_restart_decision_conditions():
+    d = oracle.restart_decision
+    inf = float("inf")
+    # condition 1: sufficient decay, <= is inclusive
+    assert d(0.2, 1.0, inf, 10, 1000) == 1
+    assert d(0.19, 1.0, 0.1, 10, 1000) == 1
+    # condition 2: necessary decay and no local progress (strictly larger than previous)
+    assert d(0.5, 1.0, 0.4, 10, 1000) == 2
+    assert d(0.8, 1.0, 0.4, 10, 1000) == 2
+    assert d(0.5, 1.0, 0.5, 10, 1000) == 0      # equal to previous: progress not lost
+    assert d(0.5, 1.0, inf, 10, 1000) == 0      # first check of an inner loop
+    assert d(0.81, 1.0, 0.4, 10, 1000) == 0     # not enough decay
+    # condition 3: long inner loop t >= 0.36 k
+    assert d(0.9, 1.0, 0.4, 36, 100) == 3
+    assert d(0.9, 1.0, 0.4, 35, 100) == 0
+    assert d(2.0, 1.0, inf, 64, 64) == 3        # first loop: t = k
+
+
+# ---------------------------------------------------------------- scaling
+
+def test_ruiz_equilibrates():
+    """Ruiz passes drive every row and column infinity norm to 1."""
+    rp, ci, v = lpgen.random_csr(5, 60, 80, np.random.default_rng(5).integers(1, 20, 60), dist="wide")
+    lp = dict(m=60, n=80, m1=0, row_ptr=rp, col_idx=ci, val=v)
+    K = dense(lp).toarray()
+    nz_cols = np.abs(K).max(axis=0) > 0
+    vs, Dr, Dc = oracle.scale(lp, ruiz_iters=60, pock_chambolle=False)
+    Ks = dense(dict(lp, val=vs)).toarray()
+    np.testing.assert_allclose(np.abs(Ks).max(axis=1), 1.0, rtol=1e-9)
+    np.testing.assert_allclose(np.abs(Ks).max(axis=0)[nz_cols], 1.0, rtol=1e-9)
+    np.testing.assert_allclose(Ks, Dr[:, None] * K * Dc[None, :], rtol=1e-13, atol=0)
+
+
+def test_pock_chambolle_norm_bound():
+    """After the Pock-Chambolle pass (alpha = 1) the scaled matrix has ||K||_2 <= 1."""
+    for seed in range(3):
+        lp = lpgen.planted_small(seed)
+        K = dense(lp).toarray()
+        for ruiz in (0, 3, 10):
+            vs, Dr, Dc = oracle.scale(lp, ruiz_iters=ruiz)
+            Ks = dense(dict(lp, val=vs)).toarray()
+            assert np.linalg.norm(Ks, 2) <= 1.0 + 1e-12
+            np.testing.assert_allclose(Ks, Dr[:, None] * K * Dc[None, :], rtol=1e-13, atol=0)
+
+
+def test_power_norm_matches_svd():
+    lp = lpgen.planted_small(2)
+    s = np.linalg.norm(dense(lp).toarray(), 2)
+    est = oracle.power_norm(lp, iters=2000)
+    assert est <= s * (1 + 1e-12)
+    assert est >= s * (1 - 1e-6)
+    est100 = oracle.power_norm(lp, iters=100)
+    assert s * 0.9 < est100 <= s * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- whole solves
+
+def _vertex_enumeration(lp):
+    K = lp["K_dense"]
+    n, m1, m = lp["n"], lp["m1"], lp["m"]
+    rows = [(K[i], lp["q"][i]) for i in range(m1, m)]
+    rows += [(np.eye(n)[j], lp["l"][j]) for j in range(n)]
+    rows += [(np.eye(n)[j], lp["u"][j]) for j in range(n)]
+    best = np.inf
+    for comb in itertools.combinations(range(len(rows)), n - m1):
+        M = np.vstack([K[:m1]] + [rows[r][0] for r in comb])
+        rhs = np.concatenate([lp["q"][:m1], [rows[r][1] for r in comb]])
+        if abs(np.linalg.det(M)) < 1e-9:
+            continue
+        x = np.linalg.solve(M, rhs)
+        if np.all(x >= lp["l"] - 1e-9) and np.all(x <= lp["u"] + 1e-9) and \
+                np.all(K[m1:] @ x >= lp["q"][m1:] - 1e-9):
+            best = min(best, float(lp["c"] @ x))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tiny_lp_matches_vertex_enumeration(seed):
+    lp = lpgen.tiny_lp(seed, n=5, m1=1, m2=3)
+    best = _vertex_enumeration(lp)
+    assert np.isfinite(best)
+    r = oracle.solve(lp, tol=1e-8, max_iter=2_000_000)
+    assert r["status"] == oracle.STATUS_OPTIMAL
+    assert abs(r["primal_obj"] - best) <= 1e-6 * (1 + abs(best))
+    from scipy.optimize import linprog
+    K = lp["K_dense"]
+    ref = linprog(lp["c"], A_ub=-K[lp["m1"]:], b_ub=-lp["q"][lp["m1"]:], A_eq=K[: lp["m1"]],
+                  b_eq=lp["q"][: lp["m1"]], bounds=list(zip(lp["l"], lp["u"])), method="highs")
+    assert abs(ref.fun - best) <= 1e-7 * (1 + abs(best))
+
+
+@pytest.mark.parametrize("seed,free_frac", [(0, 0.0), (1, 0.3)])
+def test_box_only_closed_form(seed, free_frac):
+    lp = lpgen.box_only(seed, n=50, free_frac=free_frac)
+    r = oracle.solve(lp, tol=1e-10, max_iter=100000)
+    assert r["status"] == oracle.STATUS_OPTIMAL
+    c, l, u = lp["c"], lp["l"], lp["u"]
+    fin = np.isfinite(l)
+    want = np.where(c > 0, l, u)
+    np.testing.assert_allclose(r["x"][fin & (c != 0)], want[fin & (c != 0)], rtol=0, atol=1e-9)
+    obj = np.sum(np.minimum(c[fin] * l[fin], c[fin] * u[fin]))
+    assert abs(r["primal_obj"] - obj) <= 1e-9 * (1 + abs(obj))
+    assert r["eta"] == 1.0   # ||K|| = 0
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_planted_small_converges_to_planted_objective(scaling):
+    lp = lpgen.planted_small(0)
+    K = dense(lp)
+    for tol in (1e-4, 1e-8):
+        r = oracle.solve(lp, tol=tol, scaling=scaling)
+        assert r["status"] == oracle.STATUS_OPTIMAL
+        # independent evaluation of the three tests of Section 2 with scipy
+        x, y = r["x"], r["y"]
+        # unscaling x = Dc * xt rounds, so bounds hold to a few ulps
+        slack = 1e-15 * (1 + np.abs(x)) * 4
+        assert np.all(x >= lp["l"] - slack) and np.all(x <= lp["u"] + slack)
+        assert np.all(y[lp["m1"]:] >= 0)
+        Kx = K @ x
+        pr = np.concatenate([Kx[: lp["m1"]] - lp["q"][: lp["m1"]],
+                             np.maximum(lp["q"][lp["m1"]:] - Kx[lp["m1"]:], 0)])
+        d = lp["c"] - K.T @ y
+        fl, fu = np.isfinite(lp["l"]), np.isfinite(lp["u"])
+        lam = np.where(fl & fu, d, np.where(fl, np.maximum(d, 0), np.where(fu, np.minimum(d, 0), 0)))
+        dobj = lp["q"] @ y + np.sum(np.where(lam > 0, np.where(fl, lp["l"], 0) * lam, 0)) \
+            + np.sum(np.where(lam < 0, np.where(fu, lp["u"], 0) * lam, 0))
+        pobj = lp["c"] @ x
+        assert np.linalg.norm(pr) <= tol * (1 + np.linalg.norm(lp["q"])) * (1 + 1e-9)
+        assert np.linalg.norm(d - lam) <= tol * (1 + np.linalg.norm(lp["c"])) * (1 + 1e-9)
+        assert abs(dobj - pobj) <= tol * (1 + abs(dobj) + abs(pobj)) * (1 + 1e-9)
+        if tol == 1e-8:
+            assert abs(pobj - lp["obj_star"]) <= 1e-6 * abs(lp["obj_star"])
+
+
+def test_restart_schedule_properties():
+    lp = lpgen.planted_small(1)
+    r = oracle.solve(lp, tol=1e-8, check_every=64)
+    its = r["restart_iters"]
+    assert len(its) == r["restarts"] > 0
+    assert its[0] == 64            # first loop: t = k, so the first check restarts
+    assert np.all(its % 64 == 0)
+    assert np.all(np.diff(its) > 0)
+
+
+def test_max_iter_zero_returns_initial_point():
+    lp = lpgen.planted_small(0)
+    r = oracle.solve(lp, tol=1e-8, max_iter=0)
+    assert r["iters"] == 0 and r["status"] == oracle.STATUS_ITER_LIMIT
+    np.testing.assert_array_equal(r["x"], np.clip(0.0, lp["l"], lp["u"]))
+    np.testing.assert_array_equal(r["y"], 0.0)
+
+
+def test_iteration_limit_not_multiple_of_check():
+    lp = lpgen.planted_small(0)
+    r = oracle.solve(lp, tol=0.0, max_iter=100)
+    assert r["iters"] == 100 and r["status"] == oracle.STATUS_ITER_LIMIT
+
+
+def test_golden_regression():
+    """The oracle reproduces its committed record for the small planted LP (written by
+    tests/golden/make_golden.py from the oracle alone)."""
+    with open(os.path.join(HERE, "golden", "planted_small_seed0.json")) as f:
+        g = json.load(f)
+    lp = lpgen.planted_small(0)
+    for rec in g["solves"]:
+        r = oracle.solve(lp, tol=rec["tol"], scaling=rec["scaling"])
+        assert r["iters"] == rec["iters"]
+        assert list(map(int, r["restart_iters"])) == rec["restart_iters"]
+        assert abs(r["primal_obj"] - rec["primal_obj"]) <= 1e-12 * abs(rec["primal_obj"])
