@@ -1,0 +1,191 @@
+/*
+ * pdlp.h -- C ABI of the B300 restarted-PDHG LP solver.
+ *
+ * The LP is the one of arXiv 2312.14832, Section 2, Eq. (LP):
+ *
+ *     min  c'x   s.t.  A x = b,  G x >= h,  l <= x <= u,
+ *
+ * given stacked as K = [A; G] (rows 0..m1-1 are the equality rows A),
+ * q = [b; h], with l_j = -INFINITY / u_j = +INFINITY for absent bounds.
+ * The dual is  max q'y + l'lambda^+ - u'lambda^-  s.t.  c - K'y = lambda,
+ * y_{m1..m-1} >= 0, lambda in Lambda (the bound-multiplier cone of Section 2).
+ *
+ * The solver runs restarted PDHG (Section 2, "Restarted PDHG"): the primal
+ * step x <- proj_X(x - (eta/omega)(c - K'y)), the dual step
+ * y <- proj_Y(y + eta*omega*(q - K(2x_new - x_old))), uniform averaging inside
+ * each inner loop, and the KKT_omega-based restart rule of Section 2
+ * ("Restart criteria"), with termination by the three relative tests of
+ * Section 2 ("Optimality termination criteria").
+ *
+ * Conventions of every entry point:
+ *  - Return value: 0 on success, a negative PDLP_E* code on failure; the text
+ *    of the last failure is returned by pdlp_last_error(handle) (or
+ *    pdlp_last_error(NULL) for a failed pdlp_setup).  No C++ exception
+ *    crosses this boundary.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Array arguments are plain pointers.  For pdlp_setup / pdlp_solve /
+ *    pdlp_get_iterate / pdlp_spmv they are host pointers unless
+ *    params.inputs_on_device = 1, in which case they are device pointers on
+ *    the current CUDA device.  The library copies what it needs; callers keep
+ *    ownership of their arrays and may free them after the call returns.
+ *  - All vectors the caller sees are in the caller's (original, unscaled)
+ *    row and column order.
+ *  - Work runs on a stream owned by the handle; when params.stream is not
+ *    NULL that stream is ordered before and after each call.
+ */
+#ifndef PDLP_B300_H
+#define PDLP_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes (return values) */
+#define PDLP_OK 0
+#define PDLP_EINVAL (-1)    /* malformed input: CSR not monotone, column out of range,
+                               NaN value, l > u, m1 > m, bad parameter */
+#define PDLP_ENOMEM (-2)    /* device or host allocation failed */
+#define PDLP_ECUDA (-3)     /* a CUDA runtime call failed (message in pdlp_last_error) */
+#define PDLP_EINTERNAL (-5) /* internal consistency check failed */
+
+/* solve outcome (pdlp_result.status) */
+#define PDLP_OPTIMAL 0      /* all three relative tests hold at params.tol */
+#define PDLP_ITER_LIMIT 1   /* max_iter reached */
+#define PDLP_TIME_LIMIT 2   /* time_limit_s reached */
+#define PDLP_NUMERICAL 3    /* a NaN or Inf appeared in the KKT quantities */
+
+typedef struct pdlp_ctx* pdlp_handle;
+
+typedef struct {
+  double tol;            /* epsilon of the three relative tests (default 1e-4)            */
+  int64_t max_iter;      /* PDHG iteration limit (default 1e8)                            */
+  double time_limit_s;   /* wall-clock limit of pdlp_solve (default +inf)                 */
+  int32_t check_every;   /* iterations between restart/termination checks (default 64)    */
+  int32_t scaling;       /* 1: Ruiz + Pock-Chambolle scaling at setup (default 0)         */
+  double beta_suff;      /* restart condition 1 factor (Section 2; default 0.2)           */
+  double beta_nec;       /* restart condition 2 factor (Section 2; default 0.8)           */
+  double beta_art;       /* restart condition 3 factor (Section 2; default 0.36)          */
+  double step_scale;     /* eta = step_scale / ||K||_2 (default 0.9)                      */
+  double omega_theta;    /* primal-weight smoothing at restarts (default 0.5)             */
+  int32_t ruiz_iters;    /* Ruiz passes when scaling (default 10)                         */
+  int32_t power_iters;   /* power iterations for ||K||_2 (default 100)                    */
+  double eta;            /* > 0: fixed step size instead of step_scale/||K||_2 (default 0)*/
+  int32_t tile_slots;    /* SpMV work per warp in 32-row slots; 0 = chosen at setup       */
+  int32_t inputs_on_device; /* 1: array arguments are device pointers (default 0)        */
+  void* stream;          /* cudaStream_t the caller orders with, or NULL                  */
+  int32_t log_capacity;  /* per-check records kept on the device (default 4096)          */
+  int32_t reserved;
+} pdlp_params;
+
+typedef struct {
+  int32_t status;        /* PDLP_OPTIMAL / ITER_LIMIT / TIME_LIMIT / NUMERICAL             */
+  int32_t which;         /* returned point: 0 current iterate, 1 average of the inner loop */
+  int64_t iters;         /* PDHG iterations taken (k)                                      */
+  int64_t restarts;
+  double primal_obj;     /* c'x of the returned point                                      */
+  double dual_obj;       /* q'y + l'lambda^+ - u'lambda^- of the returned point            */
+  double rel_primal;     /* ||(Ax-b, [h-Gx]^+)|| / (1 + ||q||)                             */
+  double rel_dual;       /* ||c - K'y - lambda|| / (1 + ||c||)                             */
+  double rel_gap;        /* |dual - primal| / (1 + |dual| + |primal|)                      */
+  double kkt_omega;      /* KKT_omega of the returned point on the scaled problem          */
+  double omega;          /* final primal weight                                            */
+  double eta;            /* step size                                                      */
+  double solve_s;        /* host wall time of pdlp_solve                                   */
+  double device_ms;      /* device time from the first to the last kernel of the solve     */
+  int64_t launches;      /* kernels launched on the device by this solve                  */
+} pdlp_result;
+
+/* Per-check record (pdlp_get_log). */
+typedef struct {
+  int64_t k;             /* iteration count at the check                                   */
+  int64_t t;             /* inner-loop length at the check                                 */
+  int32_t restart;       /* 0 none, 1 sufficient decay, 2 necessary decay, 3 long loop     */
+  int32_t candidate;     /* 0 current iterate, 1 average                                   */
+  double omega;          /* primal weight used at this check                               */
+  double kkt_cur, kkt_avg, kkt_anchor;
+  double rel_primal, rel_dual, rel_gap;  /* of the better of the two points                */
+} pdlp_check_record;
+
+/* Static description of the device layout (pdlp_get_info). */
+typedef struct {
+  int64_t m, n, m1, nnz;
+  int64_t slots_K, slots_Kt;   /* 32-wide slots stored for K and K' (nnz plus padding)/32 */
+  int64_t tasks_K, tasks_Kt;   /* warp tasks per SpMV                                      */
+  int64_t split_chunks_K, split_chunks_Kt;
+  int32_t tile_slots_K, tile_slots_Kt;
+  double algorithmic_bytes_per_iter; /* unique-bytes model: 24 nnz + 68 (m + n)         */
+  double stored_bytes_per_iter;      /* the same with padding slots counted               */
+  double eta, omega0, norm_K;
+} pdlp_info;
+
+/* Fills p with the defaults listed above. */
+void pdlp_default_params(pdlp_params* p);
+
+/* Builds a solver handle for the LP (K, c, q, l, u, m1).
+ *   m, n     : rows and columns of K (m >= 0, n >= 1), 0 <= m1 <= m.
+ *   row_ptr  : int64[m+1], CSR row offsets, row_ptr[0] = 0, nondecreasing.
+ *   col_idx  : int32[nnz], column of each entry, 0 <= col < n (nnz = row_ptr[m] < 2^31).
+ *   val      : double[nnz], finite.
+ *   c, l, u  : double[n]; l_j <= u_j, l_j in R or -INFINITY, u_j in R or +INFINITY.
+ *   q        : double[m], finite.
+ *   p        : parameters (NULL = defaults).
+ * Copies every input; builds the length-sorted device layout of K and K', scales
+ * (if p->scaling), estimates ||K||_2 and sets eta and the initial primal weight
+ * (Section 2 leaves both open: eta = step_scale/||K||_2, omega0 = ||c||/||q||).
+ * On success *out owns all device memory of the solver.
+ * Errors: PDLP_EINVAL, PDLP_ENOMEM, PDLP_ECUDA; *out is set to NULL on failure. */
+int pdlp_setup(pdlp_handle* out, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr,
+               const int32_t* col_idx, const double* val, const double* c, const double* q,
+               const double* l, const double* u, const pdlp_params* p);
+
+/* Runs restarted PDHG from (x0, y0) (NULL = 0, projected onto X and Y) with initial
+ * primal weight omega0 (<= 0 = the setup value).  tol, max_iter, time_limit_s,
+ * check_every and the restart factors are taken from p (NULL = the setup params).
+ * Writes the result to *res and the returned point to x_out[n], y_out[m] (either may
+ * be NULL).  Each call starts a new solve (iteration count 0).
+ * Errors: PDLP_EINVAL (NULL handle, bad parameter), PDLP_ECUDA. */
+int pdlp_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const double* y0,
+               double omega0, pdlp_result* res, double* x_out, double* y_out);
+
+/* Releases everything the handle owns.  NULL is allowed. */
+void pdlp_free(pdlp_handle h);
+
+/* Text of the handle's last error ("" if none); NULL = last pdlp_setup failure
+ * of this thread.  The string stays valid until the next call on the handle. */
+const char* pdlp_last_error(pdlp_handle h);
+
+/* Copies the solver's state after pdlp_solve: which = 0 current iterate, 1 average of
+ * the current inner loop (the current iterate if it is empty), 2 restart anchor
+ * z^{n,0}.  Unscaled, original order; x[n], y[m] (either may be NULL). */
+int pdlp_get_iterate(pdlp_handle h, int32_t which, double* x, double* y);
+
+/* Iteration counts at which the last solve restarted; returns how many restarts
+ * happened (copies at most cap of them), or a negative error code. */
+int64_t pdlp_get_restarts(pdlp_handle h, int64_t* iters, int64_t cap);
+
+/* Per-check records of the last solve; returns the number of checks made (copies
+ * at most cap, and at most log_capacity were kept), or a negative error code. */
+int64_t pdlp_get_log(pdlp_handle h, pdlp_check_record* rec, int64_t cap);
+
+/* out = K in (transpose = 0: in[n], out[m]) or out = K' in (transpose = 1: in[m],
+ * out[n]) for the ORIGINAL (unscaled) K, computed by the solver's SpMV kernels on its
+ * scaled device copy (in is divided by the scaling on the way in, out multiplied
+ * back on the way out; with scaling off the kernels see the input values as given). */
+int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out);
+
+/* Layout, step size and byte model of the handle. */
+int pdlp_get_info(pdlp_handle h, pdlp_info* info);
+
+/* Runs `iters` plain PDHG iterations (no checks, no restarts) on the handle's current
+ * state and returns, through ms_primal / ms_dual (may be NULL), the average device
+ * time of one primal kernel (K'y SpMV fused with the primal step) and of one dual
+ * kernel (K x SpMV fused with the dual step), each timed with CUDA events recorded
+ * on the handle's stream around every launch. */
+int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

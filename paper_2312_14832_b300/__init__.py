@@ -1,0 +1,179 @@
+"""B300-native restarted PDHG for linear programming (arXiv 2312.14832, Section 2).
+
+The solver is the native library ``libpdlp_b300.so`` (C ABI in include/pdlp.h, CUDA
+kernels for sm_103a).  This module only marshals arguments: numpy arrays are passed
+as host pointers, CUDA torch tensors as device pointers.  There is no CPU path: if
+the library or a GPU is missing, the calls raise.
+
+    lp = dict(m=..., n=..., m1=..., row_ptr=..., col_idx=..., val=..., c=..., q=..., l=..., u=...)
+    with Solver.from_lp(lp, scaling=1) as s:
+        r = s.solve(tol=1e-4)          # dict with status, iters, objectives, x, y, ...
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import ITER_LIMIT, NUMERICAL, OPTIMAL, TIME_LIMIT  # noqa: F401
+
+__all__ = ["Solver", "SolverError", "default_params", "OPTIMAL", "ITER_LIMIT", "TIME_LIMIT",
+           "NUMERICAL"]
+
+
+class SolverError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pdlp error {code}: {msg}")
+        self.code = code
+
+
+def default_params(**kw) -> _lib.Params:
+    p = _lib.Params()
+    _lib.load().pdlp_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+class _Arg:
+    """Keeps a contiguous array alive and exposes its address."""
+
+    def __init__(self, a, dtype, device):
+        if device:
+            import torch
+            tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+            self.obj = a.to(dtype=tdt).contiguous()
+            self.ptr = self.obj.data_ptr() if self.obj.numel() else None
+        else:
+            self.obj = np.ascontiguousarray(a, dtype=dtype)
+            self.ptr = self.obj.ctypes.data if self.obj.size else None
+
+
+class Solver:
+    def __init__(self, m, n, m1, row_ptr, col_idx, val, c, q, l, u, **params):
+        self._lib = _lib.load()
+        self._h = C.c_void_p()
+        self.m, self.n, self.m1 = int(m), int(n), int(m1)
+        self.device = _is_torch_cuda(c)
+        p = default_params(**params)
+        p.inputs_on_device = 1 if self.device else 0
+        if self.device and not p.stream:
+            import torch
+            p.stream = torch.cuda.current_stream().cuda_stream
+        self.params = p
+        args = [_Arg(row_ptr, np.int64, self.device), _Arg(col_idx, np.int32, self.device),
+                _Arg(val, np.float64, self.device), _Arg(c, np.float64, self.device),
+                _Arg(q, np.float64, self.device), _Arg(l, np.float64, self.device),
+                _Arg(u, np.float64, self.device)]
+        rc = self._lib.pdlp_setup(C.byref(self._h), self.m, self.n, self.m1,
+                                  *[a.ptr for a in args], C.byref(p))
+        if rc != 0:
+            raise SolverError(rc, self._lib.pdlp_last_error(None).decode())
+
+    @classmethod
+    def from_lp(cls, lp, **params):
+        return cls(lp["m"], lp["n"], lp["m1"], lp["row_ptr"], lp["col_idx"], lp["val"], lp["c"],
+                   lp["q"], lp["l"], lp["u"], **params)
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, rc):
+        if rc < 0:
+            raise SolverError(rc, self._lib.pdlp_last_error(self._h).decode())
+        return rc
+
+    def _out(self, size):
+        if self.device:
+            import torch
+            return torch.empty(max(size, 0), dtype=torch.float64, device="cuda")
+        return np.empty(max(size, 0), dtype=np.float64)
+
+    @staticmethod
+    def _ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr() if a.numel() else None
+        return a.ctypes.data if a.size else None
+
+    # ------------------------------------------------------------------ API
+    def solve(self, x0=None, y0=None, omega0=0.0, want_point=True, **overrides) -> dict:
+        p = _lib.Params()
+        C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
+        for k, v in overrides.items():
+            if not hasattr(p, k):
+                raise KeyError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        xa = _Arg(x0, np.float64, self.device) if x0 is not None else None
+        ya = _Arg(y0, np.float64, self.device) if y0 is not None else None
+        x = self._out(self.n) if want_point else None
+        y = self._out(self.m) if want_point else None
+        r = _lib.Result()
+        self._check(self._lib.pdlp_solve(self._h, C.byref(p), xa.ptr if xa else None,
+                                         ya.ptr if ya else None, float(omega0), C.byref(r),
+                                         self._ptr(x), self._ptr(y) if y is not None and self.m else None))
+        out = {f: getattr(r, f) for f, _ in _lib.Result._fields_}
+        out["x"], out["y"] = x, y
+        return out
+
+    def iterate(self, which=0):
+        """which: 0 current iterate, 1 average of the inner loop, 2 restart anchor."""
+        x, y = self._out(self.n), self._out(self.m)
+        self._check(self._lib.pdlp_get_iterate(self._h, int(which), self._ptr(x),
+                                               self._ptr(y) if self.m else None))
+        return x, y
+
+    def restarts(self):
+        cnt = self._check(self._lib.pdlp_get_restarts(self._h, None, 0))
+        buf = np.zeros(max(cnt, 1), dtype=np.int64)
+        self._check(self._lib.pdlp_get_restarts(self._h, buf.ctypes.data, cnt))
+        return buf[:cnt]
+
+    def log(self):
+        cnt = self._check(self._lib.pdlp_get_log(self._h, None, 0))
+        recs = (_lib.CheckRecord * max(cnt, 1))()
+        got = min(cnt, self.params.log_capacity)
+        self._check(self._lib.pdlp_get_log(self._h, recs, got))
+        return [{f: getattr(recs[i], f) for f, _ in _lib.CheckRecord._fields_} for i in range(got)]
+
+    def spmv(self, v, transpose=False):
+        """K v (transpose=False, v of length n) or K' v, through the device kernels."""
+        a = _Arg(v, np.float64, self.device)
+        out = self._out(self.n if transpose else self.m)
+        if out.shape[0] == 0:
+            return out
+        self._check(self._lib.pdlp_spmv(self._h, 1 if transpose else 0, a.ptr, self._ptr(out)))
+        return out
+
+    def info(self) -> dict:
+        i = _lib.Info()
+        self._check(self._lib.pdlp_get_info(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in _lib.Info._fields_}
+
+    def time_iterations(self, iters):
+        a, b = C.c_double(), C.c_double()
+        self._check(self._lib.pdlp_time_iterations(self._h, int(iters), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if self._h:
+            self._lib.pdlp_free(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,608 @@
+// Device kernels of the restarted-PDHG hot path (arXiv 2312.14832, Section 2).
+//
+// Everything runs in FP64 on the solver's internal numbering (rows and columns
+// sorted by length, see layout.h) and on the scaled problem
+// Kt = Dr K Dc, ct = Dc c, qt = Dr q, lt = l/Dc, ut = u/Dc.
+//
+// FP64 on this part issues one warp instruction per ~16 SM cycles whatever the
+// number of active lanes, so the kernels keep every lane of every FP64
+// instruction busy (one row per lane) and do comparisons, clamps and sign
+// projections with integer operations on the bit patterns instead of FP64
+// min/max.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "layout.h"
+
+namespace pdlp {
+
+// ------------------------------------------------------------------ state
+
+// Scalars of a solve that live on the device, so that a captured check
+// interval needs no host involvement.
+struct DevState {
+  double tau, sigma, omega, eta;   // tau = eta/omega, sigma = eta*omega
+  double kkt_anchor, kkt_prev;     // KKT_omega(z^{n,0}) and of the previous candidate
+  double inv_t;                    // 1/t at the current check (0 when t = 0)
+  double out_pobj, out_dobj, out_rel_p, out_rel_d, out_rel_g, out_kkt;  // returned point
+  long long k, t, nrestart, ncheck;
+  int done, status, which, restart_flag, cand_avg, final_force;
+};
+
+struct DevParams {
+  double tol, beta_suff, beta_nec, beta_art, theta;
+  double qnorm, cnorm;            // unscaled ||q||_2, ||c||_2
+  long long max_iter;
+  int log_cap, restart_cap;
+};
+
+struct CheckRecord {              // same layout as pdlp_check_record
+  long long k, t;
+  int restart, candidate;
+  double omega, kkt_cur, kkt_avg, kkt_anchor, rel_p, rel_d, rel_g;
+};
+
+// quantities reduced at a check (current point "C", average "A")
+enum {
+  Q_PRS_C = 0, Q_PRU_C, Q_QY_C, Q_DY_C,            // from the rows of K
+  Q_PRS_A, Q_PRU_A, Q_QY_A, Q_DY_A,
+  Q_DRS_C, Q_DRU_C, Q_LT_C, Q_CX_C, Q_DX_C,        // from the columns
+  Q_DRS_A, Q_DRU_A, Q_LT_A, Q_CX_A, Q_DX_A,
+  NQ
+};
+
+// ------------------------------------------------------------------ helpers
+
+// Order-preserving map of a double to int64 (for non-NaN values).
+__device__ __forceinline__ long long okey(double d) {
+  long long b = __double_as_longlong(d);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+// proj onto [l, u] with integer comparisons.
+__device__ __forceinline__ double clamp_box(double x, double l, double u) {
+  long long kx = okey(x);
+  double r = x;
+  if (kx < okey(l)) r = l;
+  if (kx > okey(u)) r = u;
+  return r;
+}
+// max(y, 0) and min(y, 0) by the sign bit.
+__device__ __forceinline__ double max0(double y) { return (__double2hiint(y) < 0) ? 0.0 : y; }
+__device__ __forceinline__ double min0(double y) { return (__double2hiint(y) < 0) ? y : 0.0; }
+__device__ __forceinline__ bool is_neg_inf(double v) {
+  return __double_as_longlong(v) == (long long)0xFFF0000000000000ULL;
+}
+__device__ __forceinline__ bool is_pos_inf(double v) {
+  return __double_as_longlong(v) == (long long)0x7FF0000000000000ULL;
+}
+__device__ __forceinline__ bool is_zero(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) == 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+#define PDLP_GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------ SELL SpMV
+
+struct SellView {
+  const int32_t* __restrict__ chunk_ptr;
+  const int32_t* __restrict__ col;
+  const double* __restrict__ val;
+  const SellTask* __restrict__ tasks;
+  int32_t ntasks;
+  double* gpart;   // ntasks * 32 partial sums of split-chunk pieces
+  int32_t* cnt;    // arrival counters (index: first piece task), zero between launches
+};
+
+// Row-sum operations: SpMV (gathered), and the infinity / 1-norms used by scaling.
+struct OpSpmv {
+  static constexpr bool kGather = true;
+  __device__ static double step(double acc, double v, double x) { return fma(v, x, acc); }
+  __device__ static double join(double a, double b) { return a + b; }
+};
+struct OpMaxAbs {
+  static constexpr bool kGather = false;
+  __device__ static double step(double acc, double v, double) {
+    long long a = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+    long long b = __double_as_longlong(acc);
+    return __longlong_as_double(a > b ? a : b);
+  }
+  __device__ static double join(double a, double b) { return step(a, b, 0.0); }
+};
+struct OpSumAbs {
+  static constexpr bool kGather = false;
+  __device__ static double step(double acc, double v, double) { return acc + fabs(v); }
+  __device__ static double join(double a, double b) { return a + b; }
+};
+
+// One warp per task; lane = row of the chunk.  Epi::apply(row, sum) receives the
+// complete row sum exactly once per row.
+template <class Op, class Epi>
+__global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const double* __restrict__ xg,
+                                                        Epi epi, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (w >= A.ntasks) return;
+  const SellTask T = A.tasks[w];
+  epi.prepare(st);
+  int s = T.s0;
+  int c = T.chunk;
+  while (s < T.s1) {
+    const int e = min(A.chunk_ptr[c + 1], T.s1);
+    const int32_t* cp = A.col + (size_t)s * 32 + lane;
+    const double* vp = A.val + (size_t)s * 32 + lane;
+    const int len = e - s;
+    double acc = 0.0;
+    int k = 0;
+    for (; k + 4 <= len; k += 4) {
+      double v0 = __ldcs(vp), v1 = __ldcs(vp + 32), v2 = __ldcs(vp + 64), v3 = __ldcs(vp + 96);
+      double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+      if (Op::kGather) {
+        int c0 = __ldcs(cp), c1 = __ldcs(cp + 32), c2 = __ldcs(cp + 64), c3 = __ldcs(cp + 96);
+        x0 = __ldg(xg + c0); x1 = __ldg(xg + c1); x2 = __ldg(xg + c2); x3 = __ldg(xg + c3);
+      }
+      acc = Op::step(acc, v0, x0);
+      acc = Op::step(acc, v1, x1);
+      acc = Op::step(acc, v2, x2);
+      acc = Op::step(acc, v3, x3);
+      vp += 128;
+      cp += 128;
+    }
+    for (; k < len; ++k) {
+      double v0 = __ldcs(vp);
+      double x0 = 0.0;
+      if (Op::kGather) x0 = __ldg(xg + __ldcs(cp));
+      acc = Op::step(acc, v0, x0);
+      vp += 32;
+      cp += 32;
+    }
+    s = e;
+    const int row = c * 32 + lane;
+    if (T.np == 0) {
+      epi.apply(row, acc);
+    } else {
+      // piece of a split chunk: publish, count arrivals, the last arrival combines
+      A.gpart[(size_t)w * 32 + lane] = acc;
+      __threadfence();
+      int old = 0;
+      if (lane == 0) old = atomicAdd(A.cnt + T.t0, 1);
+      old = __shfl_sync(0xffffffffu, old, 0);
+      if (old == T.np - 1) {
+        __threadfence();
+        double sum = __ldcg(A.gpart + (size_t)T.t0 * 32 + lane);
+        for (int i = 1; i < T.np; ++i) sum = Op::join(sum, __ldcg(A.gpart + (size_t)(T.t0 + i) * 32 + lane));
+        if (lane == 0) A.cnt[T.t0] = 0;
+        epi.apply(row, sum);
+      }
+    }
+    ++c;
+  }
+}
+
+// out[row] = sum (optionally times the state's 1/t, for products of the average).
+struct EpiStore {
+  double* out;
+  int use_inv_t;
+  double scale;
+  __device__ void prepare(const DevState* st) { scale = (use_inv_t && st) ? st->inv_t : 1.0; }
+  __device__ void apply(int r, double s) { out[r] = use_inv_t ? s * scale : s; }
+};
+
+// Primal step fused on g = (K'y)_j (Section 2, primal update):
+//   x_j <- proj_[l_j,u_j](x_j - tau (c_j - g_j)),  sx_j += x_j.
+struct EpiPrimal {
+  double* __restrict__ x;
+  double* __restrict__ sx;
+  const double* __restrict__ c;
+  const double* __restrict__ l;
+  const double* __restrict__ u;
+  double tau;
+  __device__ void prepare(const DevState* st) { tau = st->tau; }
+  __device__ void apply(int j, double g) {
+    double xo = x[j];
+    double d = c[j] - g;
+    double xn = clamp_box(fma(-tau, d, xo), l[j], u[j]);
+    x[j] = xn;
+    sx[j] = sx[j] + xn;
+  }
+};
+
+// Dual step fused on v = (K x_new)_i (Section 2, dual update with extrapolation,
+// using K(2 x_new - x_old) = 2 v - K x_old):
+//   y_i <- y_i + sigma (q_i - 2 v + (K x_old)_i), projected onto y_i >= 0 for i >= m1;
+//   sy_i += y_i;  (K x_old)_i <- v.
+struct EpiDual {
+  double* __restrict__ y;
+  double* __restrict__ sy;
+  double* __restrict__ kxp;
+  const double* __restrict__ q;
+  int m1;
+  double sigma;
+  __device__ void prepare(const DevState* st) { sigma = st->sigma; }
+  __device__ void apply(int i, double v) {
+    double e = q[i] + kxp[i];
+    double yn = fma(sigma, fma(-2.0, v, e), y[i]);
+    if (i >= m1) yn = max0(yn);
+    y[i] = yn;
+    sy[i] = sy[i] + yn;
+    kxp[i] = v;
+  }
+};
+
+// ------------------------------------------------------------------ vector kernels
+
+__global__ void k_fill(double* a, double v, int64_t n) {
+  PDLP_GRID_STRIDE(i, n) a[i] = v;
+}
+__global__ void k_copy(double* dst, const double* src, int64_t n) {
+  PDLP_GRID_STRIDE(i, n) dst[i] = src[i];
+}
+
+// dst[p] = src[perm[p]] (divided by div[p] if given) for p < n, pad for n <= p < npad.
+__global__ void k_permute_in(double* dst, const double* src, const int32_t* perm, const double* div,
+                             int64_t n, int64_t npad, double pad) {
+  PDLP_GRID_STRIDE(p, npad) {
+    if (p < n) {
+      double v = src[perm[p]];
+      dst[p] = div ? v / div[p] : v;
+    } else {
+      dst[p] = pad;
+    }
+  }
+}
+
+// out[i] = a[pos[i]] * d[pos[i]] (unscale and return to the caller's order)
+__global__ void k_unpermute_scale(double* out, const double* a, const double* d, const int32_t* pos,
+                                  int64_t n) {
+  PDLP_GRID_STRIDE(i, n) {
+    int32_t p = pos[i];
+    out[i] = d[p] * a[p];
+  }
+}
+
+// SELL values from the input CSR values: v[e] = src[e] >= 0 ? csr[src[e]] : 0
+__global__ void k_gather_values(double* v, const int32_t* src, const double* csr, int64_t total) {
+  PDLP_GRID_STRIDE(e, total) {
+    int32_t s = src[e];
+    v[e] = s >= 0 ? csr[s] : 0.0;
+  }
+}
+
+// Scaling factor from a row norm: f = 1/sqrt(norm) (1 for an empty row); D *= f.
+__global__ void k_scale_factor(double* f, double* D, const double* norm, int64_t n) {
+  PDLP_GRID_STRIDE(i, n) {
+    double r = norm[i];
+    double fi = r > 0.0 ? 1.0 / sqrt(r) : 1.0;
+    f[i] = fi;
+    D[i] *= fi;
+  }
+}
+
+// v <- (v * fr[row]) * fc[col] over a SELL matrix (padding entries stay 0); one warp per chunk.
+__global__ void k_scale_sell(double* v, const int32_t* col, const int32_t* chunk_ptr, int64_t nchunks,
+                             const double* frow, const double* fcol) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
+       ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double fr = frow[ch * 32 + lane];
+    for (int64_t s = chunk_ptr[ch]; s < chunk_ptr[ch + 1]; ++s) {
+      size_t e = (size_t)s * 32 + lane;
+      v[e] = (v[e] * fr) * fcol[col[e]];
+    }
+  }
+}
+
+// Problem vectors of the scaled problem: c <- Dc c, l <- l/Dc, u <- u/Dc (columns),
+// q <- Dr q (rows); inverse factors kept for the unscaled residuals.
+__global__ void k_scale_cols(double* c, double* l, double* u, double* invD, const double* D, int64_t n) {
+  PDLP_GRID_STRIDE(j, n) {
+    double d = D[j];
+    c[j] = d * c[j];
+    l[j] = l[j] / d;
+    u[j] = u[j] / d;
+    invD[j] = 1.0 / d;
+  }
+}
+__global__ void k_scale_rows(double* q, double* invD, const double* D, int64_t m) {
+  PDLP_GRID_STRIDE(i, m) {
+    double d = D[i];
+    q[i] = d * q[i];
+    invD[i] = 1.0 / d;
+  }
+}
+
+// Deterministic 2-norm in two levels: per-block partial sums of squares, then one warp.
+__global__ void k_sumsq_partial(double* part, const double* a, int64_t n) {
+  double s = 0.0;
+  PDLP_GRID_STRIDE(i, n) s = fma(a[i], a[i], s);
+  s = warp_sum(s);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+// out[0] = sqrt(sum of part[0..nb)), one warp.
+__global__ void k_sum_sqrt(double* out, const double* part, int nb) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s += part[i];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+// a <- a / s[0] unless s[0] == 0 (power-iteration normalisation).
+__global__ void k_div_by(double* a, const double* s, int64_t n) {
+  const double d = s[0];
+  if (d == 0.0) return;
+  PDLP_GRID_STRIDE(i, n) a[i] = a[i] / d;
+}
+
+// ------------------------------------------------------------------ solve kernels
+
+// Initial point: x = proj_X(x0), y = proj_Y(y0) (x0, y0 already scaled; null = 0).
+__global__ void k_init_point(double* x, const double* x0, const double* l, const double* u, int64_t n,
+                             int64_t npad, double* y, const double* y0, int64_t m, int64_t mpad, int m1) {
+  const int64_t tot = npad > mpad ? npad : mpad;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < npad) x[i] = i < n ? clamp_box(x0 ? x0[i] : 0.0, l[i], u[i]) : 0.0;
+    if (i < mpad) {
+      double yi = (i < m && y0) ? y0[i] : 0.0;
+      y[i] = (i >= m1) ? max0(yi) : yi;
+    }
+  }
+}
+
+// Before a check: advance k and t by the interval just run, 1/t for the average.
+__global__ void k_precheck(DevState* st, int len) {
+  if (st->done) return;
+  st->k += len;
+  st->t += len;
+  st->inv_t = st->t > 0 ? 1.0 / (double)st->t : 0.0;
+}
+
+struct KktInputs {
+  // rows (length m): scaled q, K x (current), K x (average, already times 1/t), y, sy, anchor y, 1/Dr
+  const double *q, *kx_c, *kx_a, *y, *sy, *ya, *invDr;
+  // columns (length n): scaled c, l, u, K'y current and average (times 1/t), x, sx, anchor x, 1/Dc
+  const double *c, *l, *u, *g_c, *g_a, *x, *sx, *xa, *invDc;
+  int64_t m, n;
+  int m1;
+  int rows_blocks;   // blocks [0, rows_blocks) reduce rows, the rest reduce columns
+};
+
+// Per-block partial sums of the NQ check quantities (Section 2: primal residual
+// ||(Ax-b, [h-Gx]^+)||, dual residual ||c - K'y - lambda|| with lambda = proj_Lambda,
+// objectives q'y + l'lambda^+ - u'lambda^- and c'x, and distances to the anchor),
+// residuals both on the scaled problem and on the unscaled one.
+__global__ void __launch_bounds__(256) k_kkt_partials(KktInputs in, const DevState* st, double* part) {
+  if (st->done) return;
+  const bool avg_is_cur = st->t == 0;
+  const double it = st->inv_t;
+  double acc[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) acc[i] = 0.0;
+  const bool rows = (int)blockIdx.x < in.rows_blocks;
+  if (rows) {
+    const int64_t nthr = (int64_t)in.rows_blocks * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < in.m; i += nthr) {
+      const double qi = in.q[i], id = in.invDr[i], yai = in.ya[i];
+      const bool ineq = i >= in.m1;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const bool avg = (p == 1) && !avg_is_cur;
+        const double kx = avg ? in.kx_a[i] : in.kx_c[i];
+        const double yi = avg ? in.sy[i] * it : in.y[i];
+        double r = kx - qi;
+        if (ineq) r = min0(r);   // [h - Gx]^+ enters squared as min(Gx - h, 0)^2
+        const double ru = r * id;
+        acc[4 * p + 0] = fma(r, r, acc[4 * p + 0]);
+        acc[4 * p + 1] = fma(ru, ru, acc[4 * p + 1]);
+        acc[4 * p + 2] = fma(qi, yi, acc[4 * p + 2]);
+        const double dy = yi - yai;
+        acc[4 * p + 3] = fma(dy, dy, acc[4 * p + 3]);
+      }
+    }
+  } else {
+    const int64_t nthr = (int64_t)(gridDim.x - in.rows_blocks) * blockDim.x;
+    for (int64_t j = (blockIdx.x - in.rows_blocks) * (int64_t)blockDim.x + threadIdx.x; j < in.n; j += nthr) {
+      const double cj = in.c[j], lj = in.l[j], uj = in.u[j], id = in.invDc[j], xaj = in.xa[j];
+      const bool lf = !is_neg_inf(lj), uf = !is_pos_inf(uj);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const bool avg = (p == 1) && !avg_is_cur;
+        const double g = avg ? in.g_a[j] : in.g_c[j];
+        const double xj = avg ? in.sx[j] * it : in.x[j];
+        const double d = cj - g;
+        // lambda = proj_Lambda(d): {0}, R^-, R^+ or R by which bounds are finite;
+        // d - lambda is then either 0 or d, so no FP64 subtraction is needed
+        const bool neg = __double2hiint(d) < 0;
+        double lam, rd;
+        if (lf && uf) { lam = d; rd = 0.0; }
+        else if (lf) { lam = neg ? 0.0 : d; rd = neg ? d : 0.0; }
+        else if (uf) { lam = neg ? d : 0.0; rd = neg ? 0.0 : d; }
+        else { lam = 0.0; rd = d; }
+        const double rdu = rd * id;
+        // l'lambda^+ - u'lambda^-: the bound on lambda's side times lambda (0 when lambda = 0)
+        const double bnd = is_zero(lam) ? 0.0 : (__double2hiint(lam) < 0 ? uj : lj);
+        acc[5 * p + 0] = fma(rd, rd, acc[5 * p + 0]);
+        acc[5 * p + 1] = fma(rdu, rdu, acc[5 * p + 1]);
+        acc[5 * p + 2] = fma(bnd, lam, acc[5 * p + 2]);
+        acc[5 * p + 3] = fma(cj, xj, acc[5 * p + 3]);
+        const double dx = xj - xaj;
+        acc[5 * p + 4] = fma(dx, dx, acc[5 * p + 4]);
+      }
+    }
+  }
+  __shared__ double sh[8][10];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    double v = warp_sum(acc[i]);
+    if (lane == 0) sh[wid][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 10) {
+    double v = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sh[w2][threadIdx.x];
+    const int base = rows ? 0 : 8;
+    const int nq = rows ? 8 : 10;
+    if ((int)threadIdx.x < nq) part[(size_t)blockIdx.x * NQ + base + threadIdx.x] = v;
+  }
+}
+
+__device__ __forceinline__ double kkt_w(double prs, double drs, double gap, double w) {
+  return sqrt(w * w * prs + drs / (w * w) + gap * gap);
+}
+
+// Sum the partials (fixed order), then the restart / termination logic of Section 2
+// on one thread.  mode 1: initialisation (KKT_omega of the anchor only).
+// final_check = 1 forces termination at this check (iteration-limit semantics).
+__global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState* st, const DevParams* Pp,
+                         CheckRecord* logbuf, long long* restarts, int mode, int final_check) {
+  if (st->done) return;
+  __shared__ double tot[NQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int qd = wid; qd < NQ; qd += (int)(blockDim.x >> 5)) {
+    const bool rowq = qd < 8;
+    const int b0 = rowq ? 0 : nb_rows, nb = rowq ? nb_rows : nb_cols;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += part[(size_t)(b0 + b) * NQ + qd];
+    s = warp_sum(s);
+    if (lane == 0) tot[qd] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const DevParams P = *Pp;
+
+  const double w = st->omega;
+  const double pobj_c = tot[Q_CX_C], dobj_c = tot[Q_QY_C] + tot[Q_LT_C];
+  const double gap_c = dobj_c - pobj_c;
+  const double pobj_a = tot[Q_CX_A], dobj_a = tot[Q_QY_A] + tot[Q_LT_A];
+  const double gap_a = dobj_a - pobj_a;
+  const double kc = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap_c, w);
+  const double ka = kkt_w(tot[Q_PRS_A], tot[Q_DRS_A], gap_a, w);
+  const double inf = __longlong_as_double(0x7FF0000000000000LL);
+  if (mode == 1) {
+    st->kkt_anchor = kc;
+    st->kkt_prev = inf;
+    return;
+  }
+  const double rp_c = sqrt(tot[Q_PRU_C]) / (1.0 + P.qnorm), rd_c = sqrt(tot[Q_DRU_C]) / (1.0 + P.cnorm);
+  const double rg_c = fabs(gap_c) / (1.0 + fabs(dobj_c) + fabs(pobj_c));
+  const double rp_a = sqrt(tot[Q_PRU_A]) / (1.0 + P.qnorm), rd_a = sqrt(tot[Q_DRU_A]) / (1.0 + P.cnorm);
+  const double rg_a = fabs(gap_a) / (1.0 + fabs(dobj_a) + fabs(pobj_a));
+  const double ec = fmax(rp_c, fmax(rd_c, rg_c)), ea = fmax(rp_a, fmax(rd_a, rg_a));
+  const bool pass_c = ec <= P.tol, pass_a = ea <= P.tol;
+  const bool finite = isfinite(kc) && isfinite(ka) && isfinite(ec) && isfinite(ea);
+  const bool last = final_check || st->k >= P.max_iter || st->final_force;
+  const bool better_c = ec < ea;
+
+  CheckRecord rec;
+  rec.k = st->k;
+  rec.t = st->t;
+  rec.restart = 0;
+  rec.candidate = !(kc < ka);
+  rec.omega = w;
+  rec.kkt_cur = kc;
+  rec.kkt_avg = ka;
+  rec.kkt_anchor = st->kkt_anchor;
+  rec.rel_p = better_c ? rp_c : rp_a;
+  rec.rel_d = better_c ? rd_c : rd_a;
+  rec.rel_g = better_c ? rg_c : rg_a;
+
+  st->restart_flag = 0;
+  if (!finite || pass_c || pass_a || last) {
+    int which;
+    if (pass_c && !pass_a) which = 0;
+    else if (pass_a && !pass_c) which = 1;
+    else which = better_c ? 0 : 1;
+    st->which = which;
+    st->status = !finite ? 3 : ((pass_c || pass_a) ? 0 : 1);
+    st->out_pobj = which ? pobj_a : pobj_c;
+    st->out_dobj = which ? dobj_a : dobj_c;
+    st->out_rel_p = which ? rp_a : rp_c;
+    st->out_rel_d = which ? rd_a : rd_c;
+    st->out_rel_g = which ? rg_a : rg_c;
+    st->out_kkt = which ? ka : kc;
+    st->done = 1;
+  } else {
+    // restart candidate: the current iterate if strictly better, else the average
+    const int cand_avg = !(kc < ka);
+    const double kkt_c = cand_avg ? ka : kc;
+    int why = 0;
+    if (kkt_c <= P.beta_suff * st->kkt_anchor) why = 1;
+    else if (kkt_c <= P.beta_nec * st->kkt_anchor && kkt_c > st->kkt_prev) why = 2;
+    else if ((double)st->t >= P.beta_art * (double)st->k) why = 3;
+    rec.restart = why;
+    if (why) {
+      const double dx = sqrt(cand_avg ? tot[Q_DX_A] : tot[Q_DX_C]);
+      const double dy = sqrt(cand_avg ? tot[Q_DY_A] : tot[Q_DY_C]);
+      double wn = w;
+      if (dx > 1e-10 && dy > 1e-10) wn = exp(P.theta * log(dy / dx) + (1.0 - P.theta) * log(w));
+      st->omega = wn;
+      st->tau = st->eta / wn;
+      st->sigma = st->eta * wn;
+      st->kkt_anchor = cand_avg ? kkt_w(tot[Q_PRS_A], tot[Q_DRS_A], gap_a, wn)
+                                : kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap_c, wn);
+      st->kkt_prev = inf;
+      st->restart_flag = 1;
+      st->cand_avg = cand_avg;
+      if (st->nrestart < P.restart_cap) restarts[st->nrestart] = st->k;
+      st->nrestart += 1;
+    } else {
+      st->kkt_prev = kkt_c;
+    }
+  }
+  if (st->ncheck < P.log_cap) logbuf[st->ncheck] = rec;
+  st->ncheck += 1;
+}
+
+struct RestartArgs {
+  double *x, *sx, *xa, *y, *sy, *ya, *kxp;
+  const double* kx_a;
+  int64_t npad, mpad;
+};
+
+// Restart (Section 2): the next inner loop starts from the candidate; the anchor
+// becomes that point and the running sums are cleared.
+__global__ void k_restart_apply(RestartArgs a, const DevState* st) {
+  if (!st->restart_flag || st->done) return;
+  const bool avg = st->cand_avg;
+  const double it = st->inv_t;
+  const int64_t tot = a.npad > a.mpad ? a.npad : a.mpad;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < a.npad) {
+      double xi = avg ? a.sx[i] * it : a.x[i];
+      a.x[i] = xi;
+      a.xa[i] = xi;
+      a.sx[i] = 0.0;
+    }
+    if (i < a.mpad) {
+      double yi = avg ? a.sy[i] * it : a.y[i];
+      a.y[i] = yi;
+      a.ya[i] = yi;
+      a.sy[i] = 0.0;
+      if (avg) a.kxp[i] = a.kx_a[i];
+    }
+  }
+}
+
+// After the restart kernel: t <- 0 (separate so that every block of the restart
+// kernel reads the same 1/t).
+__global__ void k_post_restart(DevState* st) {
+  if (st->done || !st->restart_flag) return;
+  st->t = 0;
+  st->inv_t = 0.0;
+}
+
+}  // namespace pdlp

@@ -1,0 +1,102 @@
+// Host-side construction of the SELL-32 layout and the warp task plan (see layout.h).
+#include "layout.h"
+
+#include <algorithm>
+
+namespace pdlp {
+
+void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi,
+                         std::vector<int32_t>& perm) {
+  if (hi <= lo) return;
+  int64_t maxlen = 0;
+  for (int64_t i = lo; i < hi; ++i) maxlen = std::max(maxlen, len[(size_t)i]);
+  // counting sort on length, descending, stable in the original index
+  std::vector<int64_t> cnt((size_t)maxlen + 2, 0);
+  for (int64_t i = lo; i < hi; ++i) cnt[(size_t)(maxlen - len[(size_t)i])]++;
+  int64_t acc = lo;
+  for (size_t b = 0; b < cnt.size(); ++b) {
+    int64_t c = cnt[b];
+    cnt[b] = acc;
+    acc += c;
+  }
+  for (int64_t i = lo; i < hi; ++i) perm[(size_t)cnt[(size_t)(maxlen - len[(size_t)i])]++] = (int32_t)i;
+}
+
+SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
+                    const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
+                    const std::vector<int32_t>& esrc) {
+  SellHost S;
+  S.rows = rows;
+  S.rows_pad = std::max<int64_t>(32, (rows + 31) / 32 * 32);
+  S.nchunks = S.rows_pad / 32;
+  S.chunk_ptr.assign((size_t)S.nchunks + 1, 0);
+  for (int64_t ch = 0; ch < S.nchunks; ++ch) {
+    int64_t L = 1;
+    for (int64_t r = ch * 32; r < std::min(rows, ch * 32 + 32); ++r) L = std::max(L, elen[(size_t)r]);
+    S.chunk_ptr[(size_t)ch + 1] = S.chunk_ptr[(size_t)ch] + (int32_t)L;
+  }
+  size_t total = (size_t)S.chunk_ptr.back() * 32;
+  S.col.assign(total, 0);
+  S.src.assign(total, -1);
+  for (int64_t ch = 0; ch < S.nchunks; ++ch) {
+    int64_t base = S.chunk_ptr[(size_t)ch];
+    int64_t clen = S.chunk_ptr[(size_t)ch + 1] - base;
+    for (int64_t lane = 0; lane < 32; ++lane) {
+      int64_t r = ch * 32 + lane;
+      if (r >= rows) break;
+      int64_t st = estart[(size_t)r], L = elen[(size_t)r];
+      for (int64_t k = 0; k < L; ++k) {
+        size_t e = (size_t)(base + k) * 32 + (size_t)lane;
+        S.col[e] = ecol[(size_t)(st + k)];
+        S.src[e] = esrc[(size_t)(st + k)];
+      }
+      // padding slots gather the row's own first column (already in cache), value 0
+      if (L > 0)
+        for (int64_t k = L; k < clen; ++k) S.col[(size_t)(base + k) * 32 + (size_t)lane] = ecol[(size_t)st];
+    }
+  }
+  return S;
+}
+
+TaskPlan plan_tasks(const SellHost& S, int32_t Q) {
+  TaskPlan P;
+  if (Q < 1) Q = 1;
+  int64_t c = 0;
+  while (c < S.nchunks) {
+    int32_t base = S.chunk_ptr[(size_t)c];
+    int32_t len = S.chunk_ptr[(size_t)c + 1] - base;
+    if (len > Q) {
+      int32_t np = (len + Q - 1) / Q;
+      int32_t t0 = (int32_t)P.tasks.size();
+      for (int32_t i = 0; i < np; ++i) {
+        SellTask T{};
+        T.s0 = base + (int32_t)(((int64_t)len * i) / np);
+        T.s1 = base + (int32_t)(((int64_t)len * (i + 1)) / np);
+        T.chunk = (int32_t)c;
+        T.t0 = t0;
+        T.np = np;
+        P.tasks.push_back(T);
+      }
+      P.split_chunks++;
+      ++c;
+    } else {
+      SellTask T{};
+      T.s0 = base;
+      T.chunk = (int32_t)c;
+      T.t0 = -1;
+      T.np = 0;
+      int32_t tot = 0;
+      while (c < S.nchunks) {
+        int32_t l = S.chunk_ptr[(size_t)c + 1] - S.chunk_ptr[(size_t)c];
+        if (l > Q || tot + l > Q) break;
+        tot += l;
+        ++c;
+      }
+      T.s1 = S.chunk_ptr[(size_t)c];
+      P.tasks.push_back(T);
+    }
+  }
+  return P;
+}
+
+}  // namespace pdlp

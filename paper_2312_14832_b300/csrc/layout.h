@@ -1,0 +1,54 @@
+// Host-side construction of the device layout of K and K'.
+//
+// Rows are renumbered in order of decreasing length (equality rows keep the
+// first m1 positions, so the dual sign projection stays "row >= m1"), columns
+// likewise.  Each matrix is stored "SELL-32": 32 consecutive rows form a chunk,
+// and slot k of a chunk holds entry k of each of its 32 rows side by side, so a
+// warp reads one slot with one fully coalesced 256-byte load and every lane owns
+// one row.  A chunk is as long as its longest row (at least one slot); shorter
+// rows are padded with zero values.  Work is cut into warp tasks of about
+// `tile_slots` slots: short chunks are packed whole into a task, a chunk longer
+// than tile_slots is split into pieces whose partial sums are combined, in piece
+// order, by the warp that finishes last.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace pdlp {
+
+struct SellTask {
+  int32_t s0, s1;   // slot range [s0, s1) of this warp task
+  int32_t chunk;    // first chunk the task touches
+  int32_t t0;       // split chunk: index of its first piece task; else -1
+  int32_t np;       // split chunk: number of pieces; else 0
+  int32_t pad[3];
+};
+
+struct SellHost {
+  int64_t rows = 0;       // logical rows
+  int64_t rows_pad = 0;   // rows rounded up to a multiple of 32 (at least 32)
+  int64_t nchunks = 0;
+  std::vector<int32_t> chunk_ptr;  // nchunks + 1, in slots
+  std::vector<int32_t> col;        // slots * 32, internal column index
+  std::vector<int32_t> src;        // slots * 32, position in the input CSR (-1 in padding)
+  int64_t slots() const { return chunk_ptr.empty() ? 0 : chunk_ptr.back(); }
+};
+
+struct TaskPlan {
+  std::vector<SellTask> tasks;
+  int64_t split_chunks = 0;
+};
+
+// Permutation by decreasing length (stable) of the indices [lo, hi), written to perm[lo..hi).
+void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi,
+                         std::vector<int32_t>& perm);
+
+// Builds the SELL-32 arrays of a matrix whose internal row p (0 <= p < rows) has the
+// entries estart[p] .. estart[p] + elen[p] - 1 of the entry arrays ecol / esrc.
+SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
+                    const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
+                    const std::vector<int32_t>& esrc);
+
+TaskPlan plan_tasks(const SellHost& S, int32_t tile_slots);
+
+}  // namespace pdlp

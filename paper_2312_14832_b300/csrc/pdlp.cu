@@ -1,0 +1,943 @@
+// Host driver and C ABI of the restarted-PDHG solver (declarations and contract in
+// include/pdlp.h; method: arXiv 2312.14832, Section 2).
+//
+// pdlp_setup builds the length-sorted SELL-32 layout of K and K' on the host,
+// moves it to the device, scales (Ruiz + Pock-Chambolle) and estimates ||K||_2
+// with device kernels.  pdlp_solve runs the iteration as CUDA graphs, one graph
+// per check interval: check_every x (primal kernel, dual kernel) followed by the
+// check (three SpMVs, the KKT reductions, the restart decision and the restart
+// itself), all state on the device.  The host only launches graphs and reads a
+// small status record a few intervals behind the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "layout.h"
+#include "pdlp.h"
+
+namespace pdlp {
+
+static thread_local std::string g_setup_error;
+
+struct Failure {
+  int code;
+  std::string msg;
+};
+
+static void check_cuda(cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess) return;
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed (line %d): %s", what, line, cudaGetErrorString(e));
+  throw Failure{e == cudaErrorMemoryAllocation ? PDLP_ENOMEM : PDLP_ECUDA, buf};
+}
+#define CK(call) check_cuda((call), #call, __LINE__)
+#define CKL(what) check_cuda(cudaGetLastError(), what, __LINE__)
+
+static void invalid(const std::string& msg) { throw Failure{PDLP_EINVAL, msg}; }
+
+struct DevSell {
+  int32_t* chunk_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  SellTask* tasks = nullptr;
+  double* gpart = nullptr;
+  int32_t* cnt = nullptr;
+  int32_t ntasks = 0;
+  int32_t tile = 0;
+  int64_t rows = 0, rows_pad = 0, nchunks = 0, slots = 0, split = 0;
+  SellView view() const { return SellView{chunk_ptr, col, val, tasks, ntasks, gpart, cnt}; }
+};
+
+constexpr int kRing = 4;        // pinned status records in flight
+constexpr int kLookahead = 2;   // intervals queued ahead of the one being read
+constexpr int kVecGridMax = 148 * 8;
+
+}  // namespace pdlp
+
+using namespace pdlp;
+
+struct pdlp_ctx {
+  pdlp_params p{};
+  int64_t m = 0, n = 0, m1 = 0, nnz = 0, mpad = 0, npad = 0;
+  int dev = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_user = nullptr, ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  cudaEvent_t ev_ring[kRing] = {};
+  std::vector<void*> allocs;
+  DevSell K, Kt;
+  int32_t *perm_r = nullptr, *pos_r = nullptr, *perm_c = nullptr, *pos_c = nullptr;
+  double *c = nullptr, *l = nullptr, *u = nullptr, *q = nullptr;
+  double *Dr = nullptr, *Dc = nullptr, *invDr = nullptr, *invDc = nullptr;
+  double *x = nullptr, *y = nullptr, *sx = nullptr, *sy = nullptr, *xa = nullptr, *ya = nullptr;
+  double *kxp = nullptr, *g_c = nullptr, *g_a = nullptr, *kx_a = nullptr;
+  double *tn = nullptr, *tm = nullptr, *stage_n = nullptr, *stage_m = nullptr;
+  double* part = nullptr;
+  int nb_rows = 1, nb_cols = 1;
+  double *red_part = nullptr, *red_out = nullptr;
+  int red_blocks = 1;
+  DevState* st = nullptr;
+  DevState* st_tmp = nullptr;
+  DevParams* dp = nullptr;
+  CheckRecord* log = nullptr;
+  long long* restarts = nullptr;
+  int log_cap = 4096, restart_cap = 1 << 16;
+  DevState* st_host = nullptr;   // pinned ring
+  DevState st_init{};
+  DevParams dp_host{};
+  double eta = 1.0, omega0 = 1.0, normK = 0.0, qnorm = 0.0, cnorm = 0.0;
+  std::string err;
+  int64_t last_ncheck = 0, last_nrestart = 0;
+  bool solved = false;
+  cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
+  int g_full_len = -1, g_rem_len = -1;
+  std::vector<cudaEvent_t> timing_events;
+};
+
+namespace pdlp {
+
+static int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > kVecGridMax) g = kVecGridMax;
+  return (int)g;
+}
+
+template <class T>
+static T* dalloc(pdlp_ctx* h, size_t count) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  CK(cudaMalloc(&p, bytes));
+  h->allocs.push_back(p);
+  CK(cudaMemsetAsync(p, 0, bytes, h->s));
+  return (T*)p;
+}
+
+template <class T>
+static T* upload(pdlp_ctx* h, const std::vector<T>& v) {
+  T* d = dalloc<T>(h, v.size());
+  if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->s));
+  CK(cudaStreamSynchronize(h->s));   // host vectors may be released after return
+  return d;
+}
+
+static void dfree(pdlp_ctx* h, void* p) {
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) {
+    cudaFree(p);
+    h->allocs.erase(it);
+  }
+}
+
+template <class Op, class Epi>
+static void launch_rows(pdlp_ctx* h, const DevSell& S, const double* xg, Epi epi, const DevState* st) {
+  const int blocks = (S.ntasks + 7) / 8;
+  sell_rows_kernel<Op, Epi><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
+}
+
+static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const TaskPlan& P,
+                              const double* d_csr_val) {
+  D.rows = S.rows;
+  D.rows_pad = S.rows_pad;
+  D.nchunks = S.nchunks;
+  D.slots = S.slots();
+  D.split = P.split_chunks;
+  D.ntasks = (int32_t)P.tasks.size();
+  D.chunk_ptr = upload(h, S.chunk_ptr);
+  D.col = upload(h, S.col);
+  D.tasks = upload(h, P.tasks);
+  D.gpart = dalloc<double>(h, (size_t)D.ntasks * 32);
+  D.cnt = dalloc<int32_t>(h, (size_t)D.ntasks);
+  D.val = dalloc<double>(h, (size_t)D.slots * 32);
+  int32_t* d_src = upload(h, S.src);
+  k_gather_values<<<grid_for(D.slots * 32), 256, 0, h->s>>>(D.val, d_src, d_csr_val, D.slots * 32);
+  CKL("k_gather_values");
+  CK(cudaStreamSynchronize(h->s));
+  dfree(h, d_src);
+}
+
+static void norm2_dev(pdlp_ctx* h, const double* a, int64_t n) {
+  k_sumsq_partial<<<h->red_blocks, 256, 0, h->s>>>(h->red_part, a, n);
+  k_sum_sqrt<<<1, 32, 0, h->s>>>(h->red_out, h->red_part, h->red_blocks);
+}
+
+static double norm2_host(pdlp_ctx* h, const double* a, int64_t n) {
+  norm2_dev(h, a, n);
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return v;
+}
+
+// k_div_into: a <- w / s[0] when s[0] != 0 (otherwise a keeps the last unit vector)
+__global__ void k_div_into(double* a, const double* w, const double* s, int64_t n) {
+  const double d = s[0];
+  if (d == 0.0) return;
+  PDLP_GRID_STRIDE(i, n) a[i] = w[i] / d;
+}
+
+// v <- (v * fr[i]) * fc[j] for K (transposed = 0: chunk rows are i, columns j) and for
+// K' (transposed = 1: chunk rows are j, columns i), so both copies round identically.
+__global__ void k_scale_sell2(double* v, const int32_t* col, const int32_t* chunk_ptr, int64_t nchunks,
+                              const double* fr, const double* fc, int transposed) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
+       ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t row = ch * 32 + lane;
+    for (int64_t s = chunk_ptr[ch]; s < chunk_ptr[ch + 1]; ++s) {
+      const size_t e = (size_t)s * 32 + lane;
+      const double a = transposed ? fr[col[e]] : fr[row];
+      const double b = transposed ? fc[row] : fc[col[e]];
+      v[e] = (v[e] * a) * b;
+    }
+  }
+}
+
+// dst = average of the inner loop (sum * 1/t), or the current iterate when t = 0
+__global__ void k_average(double* dst, const double* sum, const double* cur, const DevState* st, int64_t n) {
+  const bool empty = st->t == 0;
+  const double it = st->inv_t;
+  PDLP_GRID_STRIDE(i, n) dst[i] = empty ? cur[i] : sum[i] * it;
+}
+
+// copy of the state with done cleared (for pdlp_time_iterations)
+__global__ void k_copy_state(DevState* dst, const DevState* src) {
+  *dst = *src;
+  dst->done = 0;
+}
+
+static void enqueue_iteration(pdlp_ctx* h, const DevState* st) {
+  launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, st);
+  launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, st);
+}
+
+static KktInputs kkt_inputs(pdlp_ctx* h) {
+  KktInputs in;
+  in.q = h->q; in.kx_c = h->kxp; in.kx_a = h->kx_a; in.y = h->y; in.sy = h->sy; in.ya = h->ya;
+  in.invDr = h->invDr;
+  in.c = h->c; in.l = h->l; in.u = h->u; in.g_c = h->g_c; in.g_a = h->g_a; in.x = h->x; in.sx = h->sx;
+  in.xa = h->xa; in.invDc = h->invDc;
+  in.m = h->m; in.n = h->n; in.m1 = (int)h->m1; in.rows_blocks = h->nb_rows;
+  return in;
+}
+
+// The check (launch count: 8).
+static void enqueue_check(pdlp_ctx* h, int len, int final_check) {
+  k_precheck<<<1, 1, 0, h->s>>>(h->st, len);
+  launch_rows<OpSpmv>(h, h->Kt, h->y, EpiStore{h->g_c, 0, 1.0}, h->st);
+  launch_rows<OpSpmv>(h, h->K, h->sx, EpiStore{h->kx_a, 1, 1.0}, h->st);
+  launch_rows<OpSpmv>(h, h->Kt, h->sy, EpiStore{h->g_a, 1, 1.0}, h->st);
+  k_kkt_partials<<<h->nb_rows + h->nb_cols, 256, 0, h->s>>>(kkt_inputs(h), h->st, h->part);
+  k_decide<<<1, 256, 0, h->s>>>(h->part, h->nb_rows, h->nb_cols, h->st, h->dp, h->log, h->restarts, 0,
+                                final_check);
+  RestartArgs ra{h->x, h->sx, h->xa, h->y, h->sy, h->ya, h->kxp, h->kx_a, h->npad, h->mpad};
+  k_restart_apply<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(ra, h->st);
+  k_post_restart<<<1, 1, 0, h->s>>>(h->st);
+}
+
+static cudaGraphExec_t capture_interval(pdlp_ctx* h, int len) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < len; ++i) enqueue_iteration(h, h->st);
+  enqueue_check(h, len, 0);
+  cudaError_t e = cudaStreamEndCapture(h->s, &g);
+  CK(e);
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return ex;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct StreamOrder {
+  pdlp_ctx* h;
+  cudaStream_t user;
+  StreamOrder(pdlp_ctx* h_, void* user_stream) : h(h_), user((cudaStream_t)user_stream) {
+    if (user) {
+      CK(cudaEventRecord(h->ev_user, user));
+      CK(cudaStreamWaitEvent(h->s, h->ev_user, 0));
+    }
+  }
+  ~StreamOrder() {
+    if (user) {
+      cudaEventRecord(h->ev_done, h->s);
+      cudaStreamWaitEvent(user, h->ev_done, 0);
+    }
+  }
+};
+
+static void copy_in(pdlp_ctx* h, double* dst, const double* src, int64_t count) {
+  if (count <= 0) return;
+  CK(cudaMemcpyAsync(dst, src, (size_t)count * sizeof(double),
+                     h->p.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+}
+static void copy_out(pdlp_ctx* h, double* dst, const double* src, int64_t count) {
+  if (count <= 0 || dst == nullptr) return;
+  CK(cudaMemcpyAsync(dst, src, (size_t)count * sizeof(double),
+                     h->p.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+}
+
+// Unscaled, original-order copy of an internal (x, y) pair to caller buffers.
+static void export_point(pdlp_ctx* h, const double* xi, const double* yi, double* x_out, double* y_out) {
+  if (x_out) {
+    k_unpermute_scale<<<grid_for(h->n), 256, 0, h->s>>>(h->stage_n, xi, h->Dc, h->pos_c, h->n);
+    copy_out(h, x_out, h->stage_n, h->n);
+  }
+  if (y_out && h->m > 0) {
+    k_unpermute_scale<<<grid_for(h->m), 256, 0, h->s>>>(h->stage_m, yi, h->Dr, h->pos_r, h->m);
+    copy_out(h, y_out, h->stage_m, h->m);
+  }
+  CK(cudaStreamSynchronize(h->s));
+}
+
+static void destroy(pdlp_ctx* h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  if (h->g_full) cudaGraphExecDestroy(h->g_full);
+  if (h->g_rem) cudaGraphExecDestroy(h->g_rem);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->st_host) cudaFreeHost(h->st_host);
+  for (auto e : h->timing_events) cudaEventDestroy(e);
+  for (auto& e : h->ev_ring)
+    if (e) cudaEventDestroy(e);
+  if (h->ev_user) cudaEventDestroy(h->ev_user);
+  if (h->ev_done) cudaEventDestroy(h->ev_done);
+  if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+  if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+}
+
+// ------------------------------------------------------------------ setup
+
+static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr_in,
+                       const int32_t* col_in, const double* val_in, const double* c_in,
+                       const double* q_in, const double* l_in, const double* u_in) {
+  const pdlp_params& P = h->p;
+  if (m < 0 || n < 1 || m1 < 0 || m1 > m) invalid("sizes must satisfy m >= 0, n >= 1, 0 <= m1 <= m");
+  if (m >= (int64_t)1 << 31 || n >= (int64_t)1 << 31) invalid("m and n must be below 2^31");
+  if (P.check_every < 1) invalid("check_every must be >= 1");
+  if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
+  if (!row_ptr_in || !c_in || !l_in || !u_in || (m > 0 && !q_in)) invalid("null input array");
+  CK(cudaGetDevice(&h->dev));
+  CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+  CK(cudaEventCreate(&h->ev_t0));
+  CK(cudaEventCreate(&h->ev_t1));
+  for (auto& e : h->ev_ring) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CK(cudaMallocHost(&h->st_host, sizeof(DevState) * kRing));
+
+  // ---- host copies of the structure (and, for validation, of the values)
+  const bool dev_in = P.inputs_on_device != 0;
+  std::vector<int64_t> rp((size_t)m + 1);
+  if (dev_in) CK(cudaMemcpy(rp.data(), row_ptr_in, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost));
+  else std::memcpy(rp.data(), row_ptr_in, sizeof(int64_t) * (m + 1));
+  if (rp[0] != 0) invalid("row_ptr[0] must be 0");
+  for (int64_t i = 0; i < m; ++i)
+    if (rp[(size_t)i + 1] < rp[(size_t)i]) invalid("row_ptr must be nondecreasing");
+  const int64_t nnz = rp[(size_t)m];
+  if (nnz >= ((int64_t)1 << 31)) invalid("nnz must be below 2^31");
+  if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
+  std::vector<int32_t> col((size_t)nnz);
+  std::vector<double> val((size_t)nnz), c((size_t)n), l((size_t)n), u((size_t)n), q((size_t)m);
+  auto fetch = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return;
+    if (dev_in) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    else std::memcpy(dst, src, bytes);
+  };
+  fetch(col.data(), col_in, sizeof(int32_t) * nnz);
+  fetch(val.data(), val_in, sizeof(double) * nnz);
+  fetch(c.data(), c_in, sizeof(double) * n);
+  fetch(l.data(), l_in, sizeof(double) * n);
+  fetch(u.data(), u_in, sizeof(double) * n);
+  fetch(q.data(), q_in, sizeof(double) * m);
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (col[(size_t)k] < 0 || col[(size_t)k] >= n) invalid("column index out of range");
+    if (!std::isfinite(val[(size_t)k])) invalid("non-finite matrix value");
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    double a = l[(size_t)j], b = u[(size_t)j];
+    if (!std::isfinite(c[(size_t)j])) invalid("non-finite c");
+    if (std::isnan(a) || std::isnan(b) || a == INFINITY || b == -INFINITY || a > b)
+      invalid("bounds must satisfy l <= u, l < +inf, u > -inf");
+  }
+  for (int64_t i = 0; i < m; ++i)
+    if (!std::isfinite(q[(size_t)i])) invalid("non-finite q");
+  h->m = m;
+  h->n = n;
+  h->m1 = m1;
+  h->nnz = nnz;
+
+  // ---- renumbering by length
+  std::vector<int64_t> rlen((size_t)m), clen((size_t)n, 0);
+  for (int64_t i = 0; i < m; ++i) rlen[(size_t)i] = rp[(size_t)i + 1] - rp[(size_t)i];
+  for (int64_t k = 0; k < nnz; ++k) clen[(size_t)col[(size_t)k]]++;
+  std::vector<int32_t> perm_r((size_t)m), pos_r((size_t)m), perm_c((size_t)n), pos_c((size_t)n);
+  sort_by_length_desc(rlen, 0, m1, perm_r);
+  sort_by_length_desc(rlen, m1, m, perm_r);
+  sort_by_length_desc(clen, 0, n, perm_c);
+  for (int64_t p = 0; p < m; ++p) pos_r[(size_t)perm_r[(size_t)p]] = (int32_t)p;
+  for (int64_t p = 0; p < n; ++p) pos_c[(size_t)perm_c[(size_t)p]] = (int32_t)p;
+
+  // ---- SELL layouts of K (rows) and K' (columns)
+  SellHost SK, SKt;
+  {
+    std::vector<int32_t> ecol((size_t)nnz), esrc((size_t)nnz);
+    for (int64_t k = 0; k < nnz; ++k) {
+      ecol[(size_t)k] = pos_c[(size_t)col[(size_t)k]];
+      esrc[(size_t)k] = (int32_t)k;
+    }
+    std::vector<int64_t> est((size_t)m), eln((size_t)m);
+    for (int64_t p = 0; p < m; ++p) {
+      est[(size_t)p] = rp[(size_t)perm_r[(size_t)p]];
+      eln[(size_t)p] = rlen[(size_t)perm_r[(size_t)p]];
+    }
+    SK = build_sell(m, est, eln, ecol, esrc);
+  }
+  {
+    std::vector<int64_t> tp((size_t)n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) tp[(size_t)j + 1] = tp[(size_t)j] + clen[(size_t)j];
+    std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+    std::vector<int32_t> tcol((size_t)nnz), tsrc((size_t)nnz);
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t k = rp[(size_t)i]; k < rp[(size_t)i + 1]; ++k) {
+        int64_t at = fill[(size_t)col[(size_t)k]]++;
+        tcol[(size_t)at] = pos_r[(size_t)i];
+        tsrc[(size_t)at] = (int32_t)k;
+      }
+    std::vector<int64_t> est((size_t)n), eln((size_t)n);
+    for (int64_t p = 0; p < n; ++p) {
+      est[(size_t)p] = tp[(size_t)perm_c[(size_t)p]];
+      eln[(size_t)p] = clen[(size_t)perm_c[(size_t)p]];
+    }
+    SKt = build_sell(n, est, eln, tcol, tsrc);
+  }
+  h->mpad = SK.rows_pad;
+  h->npad = SKt.rows_pad;
+  const int32_t tile = P.tile_slots > 0 ? P.tile_slots : 32;
+  TaskPlan PK = plan_tasks(SK, tile), PKt = plan_tasks(SKt, tile);
+  h->K.tile = tile;
+  h->Kt.tile = tile;
+
+  double* d_val = upload(h, val);
+  build_device_sell(h, h->K, SK, PK, d_val);
+  build_device_sell(h, h->Kt, SKt, PKt, d_val);
+  dfree(h, d_val);
+
+  h->perm_r = upload(h, perm_r);
+  h->pos_r = upload(h, pos_r);
+  h->perm_c = upload(h, perm_c);
+  h->pos_c = upload(h, pos_c);
+
+  const int64_t mp = h->mpad, np = h->npad;
+  h->c = dalloc<double>(h, np);
+  h->l = dalloc<double>(h, np);
+  h->u = dalloc<double>(h, np);
+  h->q = dalloc<double>(h, mp);
+  h->Dr = dalloc<double>(h, mp);
+  h->Dc = dalloc<double>(h, np);
+  h->invDr = dalloc<double>(h, mp);
+  h->invDc = dalloc<double>(h, np);
+  for (double** v : {&h->x, &h->sx, &h->xa, &h->g_c, &h->g_a, &h->tn}) *v = dalloc<double>(h, np);
+  for (double** v : {&h->y, &h->sy, &h->ya, &h->kxp, &h->kx_a, &h->tm}) *v = dalloc<double>(h, mp);
+  h->stage_n = dalloc<double>(h, n);
+  h->stage_m = dalloc<double>(h, std::max<int64_t>(m, 1));
+  h->red_blocks = grid_for(std::max(np, mp));
+  h->red_part = dalloc<double>(h, h->red_blocks);
+  h->red_out = dalloc<double>(h, 1);
+  h->nb_rows = std::min<int>(296, std::max<int>(1, (int)((m + 255) / 256)));
+  h->nb_cols = std::min<int>(296, std::max<int>(1, (int)((n + 255) / 256)));
+  h->part = dalloc<double>(h, (size_t)(h->nb_rows + h->nb_cols) * NQ);
+  h->st = dalloc<DevState>(h, 1);
+  h->st_tmp = dalloc<DevState>(h, 1);
+  h->dp = dalloc<DevParams>(h, 1);
+  h->log_cap = P.log_capacity > 0 ? P.log_capacity : 1;
+  h->log = dalloc<CheckRecord>(h, (size_t)h->log_cap);
+  h->restarts = dalloc<long long>(h, (size_t)h->restart_cap);
+
+  // ---- problem vectors in internal order; unscaled norms for the termination tests
+  copy_in(h, h->stage_n, c_in, n);
+  h->cnorm = norm2_host(h, h->stage_n, n);
+  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->c, h->stage_n, h->perm_c, nullptr, n, np, 0.0);
+  copy_in(h, h->stage_n, l_in, n);
+  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->l, h->stage_n, h->perm_c, nullptr, n, np, 0.0);
+  copy_in(h, h->stage_n, u_in, n);
+  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->u, h->stage_n, h->perm_c, nullptr, n, np, 0.0);
+  if (m > 0) {
+    copy_in(h, h->stage_m, q_in, m);
+    h->qnorm = norm2_host(h, h->stage_m, m);
+  }
+  k_permute_in<<<grid_for(mp), 256, 0, h->s>>>(h->q, h->stage_m, h->perm_r, nullptr, m, mp, 0.0);
+  k_fill<<<grid_for(mp), 256, 0, h->s>>>(h->Dr, 1.0, mp);
+  k_fill<<<grid_for(np), 256, 0, h->s>>>(h->Dc, 1.0, np);
+  CKL("setup vectors");
+
+  // ---- scaling: ruiz_iters Ruiz passes, then one Pock-Chambolle pass
+  if (P.scaling) {
+    for (int pass = 0; pass <= P.ruiz_iters; ++pass) {
+      const bool pc = pass == P.ruiz_iters;
+      if (pc) {
+        launch_rows<OpSumAbs>(h, h->K, nullptr, EpiStore{h->tm, 0, 1.0}, nullptr);
+        launch_rows<OpSumAbs>(h, h->Kt, nullptr, EpiStore{h->tn, 0, 1.0}, nullptr);
+      } else {
+        launch_rows<OpMaxAbs>(h, h->K, nullptr, EpiStore{h->tm, 0, 1.0}, nullptr);
+        launch_rows<OpMaxAbs>(h, h->Kt, nullptr, EpiStore{h->tn, 0, 1.0}, nullptr);
+      }
+      k_scale_factor<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->Dr, h->tm, mp);
+      k_scale_factor<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->Dc, h->tn, np);
+      k_scale_sell2<<<grid_for(h->K.nchunks * 32), 256, 0, h->s>>>(h->K.val, h->K.col, h->K.chunk_ptr,
+                                                                  h->K.nchunks, h->tm, h->tn, 0);
+      k_scale_sell2<<<grid_for(h->Kt.nchunks * 32), 256, 0, h->s>>>(h->Kt.val, h->Kt.col, h->Kt.chunk_ptr,
+                                                                   h->Kt.nchunks, h->tm, h->tn, 1);
+      CKL("scaling pass");
+    }
+  }
+  k_scale_cols<<<grid_for(np), 256, 0, h->s>>>(h->c, h->l, h->u, h->invDc, h->Dc, np);
+  k_scale_rows<<<grid_for(mp), 256, 0, h->s>>>(h->q, h->invDr, h->Dr, mp);
+  CKL("scale vectors");
+
+  // ---- ||K||_2 by power iteration on K'K (v0 = 1/sqrt(n)), eta, omega0
+  if (P.eta > 0.0) {
+    h->eta = P.eta;
+  } else {
+    double* a = h->tn;
+    double* w = h->g_a;
+    k_fill<<<grid_for(np), 256, 0, h->s>>>(a, 0.0, np);
+    k_fill<<<grid_for(n), 256, 0, h->s>>>(a, 1.0 / std::sqrt((double)n), n);
+    for (int it = 0; it < P.power_iters; ++it) {
+      launch_rows<OpSpmv>(h, h->K, a, EpiStore{h->tm, 0, 1.0}, nullptr);
+      launch_rows<OpSpmv>(h, h->Kt, h->tm, EpiStore{w, 0, 1.0}, nullptr);
+      norm2_dev(h, w, np);
+      k_div_into<<<grid_for(np), 256, 0, h->s>>>(a, w, h->red_out, np);
+    }
+    launch_rows<OpSpmv>(h, h->K, a, EpiStore{h->tm, 0, 1.0}, nullptr);
+    CKL("power iteration");
+    h->normK = m > 0 ? norm2_host(h, h->tm, mp) : 0.0;
+    h->eta = h->normK > 0.0 ? P.step_scale / h->normK : 1.0;
+  }
+  {
+    const double cn = norm2_host(h, h->c, np), qn = norm2_host(h, h->q, mp);
+    h->omega0 = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
+  }
+  CK(cudaStreamSynchronize(h->s));
+}
+
+static void ensure_graphs(pdlp_ctx* h, int full, int rem) {
+  if (h->g_full_len != full) {
+    if (h->g_full) cudaGraphExecDestroy(h->g_full);
+    h->g_full = nullptr;
+    h->g_full_len = -1;
+    if (full > 0) {
+      h->g_full = capture_interval(h, full);
+      h->g_full_len = full;
+    }
+  }
+  if (rem > 0 && h->g_rem_len != rem) {
+    if (h->g_rem) cudaGraphExecDestroy(h->g_rem);
+    h->g_rem = nullptr;
+    h->g_rem_len = -1;
+    h->g_rem = capture_interval(h, rem);
+    h->g_rem_len = rem;
+  }
+}
+
+static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0, double omega0,
+                      pdlp_result* res, double* x_out, double* y_out) {
+  if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
+  auto t_start = std::chrono::steady_clock::now();
+  const int64_t n = h->n, m = h->m, np = h->npad, mp = h->mpad;
+  int64_t launches = 0;
+
+  // device parameters of the decision kernel
+  h->dp_host.tol = sp.tol;
+  h->dp_host.beta_suff = sp.beta_suff;
+  h->dp_host.beta_nec = sp.beta_nec;
+  h->dp_host.beta_art = sp.beta_art;
+  h->dp_host.theta = sp.omega_theta;
+  h->dp_host.qnorm = h->qnorm;
+  h->dp_host.cnorm = h->cnorm;
+  h->dp_host.max_iter = sp.max_iter;
+  h->dp_host.log_cap = h->log_cap;
+  h->dp_host.restart_cap = h->restart_cap;
+  CK(cudaMemcpyAsync(h->dp, &h->dp_host, sizeof(DevParams), cudaMemcpyHostToDevice, h->s));
+
+  // initial point (Section 2: x in X, y in Y), anchor z^{0,0} = (x0, y0)
+  const double* xs = nullptr;
+  const double* ys = nullptr;
+  if (x0) {
+    copy_in(h, h->stage_n, x0, n);
+    k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, n, np, 0.0);
+    xs = h->tn;
+    launches++;
+  }
+  if (y0 && m > 0) {
+    copy_in(h, h->stage_m, y0, m);
+    k_permute_in<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, m, mp, 0.0);
+    ys = h->tm;
+    launches++;
+  }
+  CK(cudaEventRecord(h->ev_t0, h->s));
+  k_init_point<<<grid_for(std::max(np, mp)), 256, 0, h->s>>>(h->x, xs, h->l, h->u, n, np, h->y, ys, m, mp,
+                                                              (int)h->m1);
+  const double w0 = omega0 > 0.0 ? omega0 : h->omega0;
+  DevState& s0 = h->st_init;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.eta = h->eta;
+  s0.omega = w0;
+  s0.tau = h->eta / w0;
+  s0.sigma = h->eta * w0;
+  s0.kkt_prev = std::numeric_limits<double>::infinity();
+  CK(cudaMemcpyAsync(h->st, &s0, sizeof(DevState), cudaMemcpyHostToDevice, h->s));
+  launch_rows<OpSpmv>(h, h->K, h->x, EpiStore{h->kxp, 0, 1.0}, h->st);
+  launch_rows<OpSpmv>(h, h->Kt, h->y, EpiStore{h->g_c, 0, 1.0}, h->st);
+  k_copy<<<grid_for(np), 256, 0, h->s>>>(h->xa, h->x, np);
+  k_copy<<<grid_for(mp), 256, 0, h->s>>>(h->ya, h->y, mp);
+  k_fill<<<grid_for(np), 256, 0, h->s>>>(h->sx, 0.0, np);
+  k_fill<<<grid_for(mp), 256, 0, h->s>>>(h->sy, 0.0, mp);
+  k_kkt_partials<<<h->nb_rows + h->nb_cols, 256, 0, h->s>>>(kkt_inputs(h), h->st, h->part);
+  k_decide<<<1, 256, 0, h->s>>>(h->part, h->nb_rows, h->nb_cols, h->st, h->dp, h->log, h->restarts, 1, 0);
+  launches += 9;
+  CKL("solve init");
+
+  const int L = sp.check_every;
+  const int64_t nfull = sp.max_iter / L;
+  const int rem = (int)(sp.max_iter % L);
+  const int64_t nint = nfull + (rem > 0 ? 1 : 0);
+  bool timed_out = false;
+  DevState fin{};
+  if (nint == 0) {
+    enqueue_check(h, 0, 1);
+    launches += 8;
+    CKL("final check");
+  } else {
+    ensure_graphs(h, nfull > 0 ? L : 0, rem);
+    int64_t issued = 0, read = 0;
+    bool done = false;
+    while (!done && read < nint) {
+      while (issued < nint && issued - read < kLookahead) {
+        cudaGraphExec_t g = (issued < nfull) ? h->g_full : h->g_rem;
+        const int len = (issued < nfull) ? L : rem;
+        CK(cudaGraphLaunch(g, h->s));
+        launches += 2 * len + 8;
+        const int slot = (int)(issued % kRing);
+        CK(cudaMemcpyAsync(h->st_host + slot, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaEventRecord(h->ev_ring[slot], h->s));
+        ++issued;
+      }
+      const int slot = (int)(read % kRing);
+      CK(cudaEventSynchronize(h->ev_ring[slot]));
+      done = h->st_host[slot].done != 0;
+      ++read;
+      if (!done && std::isfinite(sp.time_limit_s)) {
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if (el > sp.time_limit_s) {
+          timed_out = true;
+          break;
+        }
+      }
+    }
+    CK(cudaStreamSynchronize(h->s));
+    CK(cudaMemcpy(&fin, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    if (!fin.done) {
+      // time limit: one more check that must terminate
+      int one = 1;
+      CK(cudaMemcpyAsync(&h->st->final_force, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      enqueue_check(h, 0, 1);
+      launches += 8;
+      CKL("time-limit check");
+    }
+  }
+  CK(cudaEventRecord(h->ev_t1, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaMemcpy(&fin, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  float dev_ms = 0.f;
+  CK(cudaEventElapsedTime(&dev_ms, h->ev_t0, h->ev_t1));
+  h->last_ncheck = fin.ncheck;
+  h->last_nrestart = fin.nrestart;
+  h->solved = true;
+
+  // returned point
+  if (x_out || y_out) {
+    const double* xo = h->x;
+    const double* yo = h->y;
+    if (fin.which == 1) {
+      k_average<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->sx, h->x, h->st, np);
+      k_average<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->sy, h->y, h->st, mp);
+      xo = h->tn;
+      yo = h->tm;
+    }
+    export_point(h, xo, yo, x_out, y_out);
+  }
+  if (res) {
+    res->status = fin.status;
+    if (timed_out && fin.status != PDLP_OPTIMAL && fin.status != PDLP_NUMERICAL) res->status = PDLP_TIME_LIMIT;
+    res->which = fin.which;
+    res->iters = fin.k;
+    res->restarts = fin.nrestart;
+    res->primal_obj = fin.out_pobj;
+    res->dual_obj = fin.out_dobj;
+    res->rel_primal = fin.out_rel_p;
+    res->rel_dual = fin.out_rel_d;
+    res->rel_gap = fin.out_rel_g;
+    res->kkt_omega = fin.out_kkt;
+    res->omega = fin.omega;
+    res->eta = fin.eta;
+    res->device_ms = dev_ms;
+    res->launches = launches;
+    res->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return PDLP_OK;
+}
+
+template <class F>
+static int guarded(pdlp_ctx* h, F&& f) {
+  if (!h) return PDLP_EINVAL;
+  h->err.clear();
+  try {
+    DeviceGuard dg(h->dev);
+    StreamOrder so(h, h->p.stream);
+    return f();
+  } catch (const Failure& e) {
+    h->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return PDLP_ENOMEM;
+  } catch (...) {
+    h->err = "unexpected internal error";
+    return PDLP_EINTERNAL;
+  }
+}
+
+}  // namespace pdlp
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+void pdlp_default_params(pdlp_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tol = 1e-4;
+  p->max_iter = 100000000;
+  p->time_limit_s = INFINITY;
+  p->check_every = 64;
+  p->scaling = 0;
+  p->beta_suff = 0.2;
+  p->beta_nec = 0.8;
+  p->beta_art = 0.36;
+  p->step_scale = 0.9;
+  p->omega_theta = 0.5;
+  p->ruiz_iters = 10;
+  p->power_iters = 100;
+  p->eta = 0.0;
+  p->tile_slots = 0;
+  p->inputs_on_device = 0;
+  p->stream = nullptr;
+  p->log_capacity = 4096;
+}
+
+int pdlp_setup(pdlp_handle* out, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr,
+               const int32_t* col_idx, const double* val, const double* c, const double* q, const double* l,
+               const double* u, const pdlp_params* p) {
+  g_setup_error.clear();
+  if (!out) {
+    g_setup_error = "null output handle";
+    return PDLP_EINVAL;
+  }
+  *out = nullptr;
+  pdlp_ctx* h = nullptr;
+  try {
+    h = new pdlp_ctx();
+    if (p) h->p = *p;
+    else pdlp_default_params(&h->p);
+    setup_impl(h, m, n, m1, row_ptr, col_idx, val, c, q, l, u);
+    if (h->p.stream) {
+      CK(cudaEventRecord(h->ev_done, h->s));
+      CK(cudaStreamWaitEvent((cudaStream_t)h->p.stream, h->ev_done, 0));
+    }
+  } catch (const Failure& e) {
+    g_setup_error = e.msg;
+    destroy(h);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_setup_error = "host allocation failed";
+    destroy(h);
+    return PDLP_ENOMEM;
+  } catch (...) {
+    g_setup_error = "unexpected internal error";
+    destroy(h);
+    return PDLP_EINTERNAL;
+  }
+  *out = h;
+  return PDLP_OK;
+}
+
+int pdlp_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const double* y0, double omega0,
+               pdlp_result* res, double* x_out, double* y_out) {
+  return guarded(h, [&]() {
+    pdlp_params sp = p ? *p : h->p;
+    return solve_impl(h, sp, x0, y0, omega0, res, x_out, y_out);
+  });
+}
+
+void pdlp_free(pdlp_handle h) {
+  if (!h) return;
+  DeviceGuard dg(h->dev);
+  destroy(h);
+}
+
+const char* pdlp_last_error(pdlp_handle h) {
+  if (!h) return g_setup_error.c_str();
+  return h->err.c_str();
+}
+
+int pdlp_get_iterate(pdlp_handle h, int32_t which, double* x, double* y) {
+  return guarded(h, [&]() {
+    if (which < 0 || which > 2) invalid("which must be 0, 1 or 2");
+    if (!h->solved) invalid("no solve has run on this handle");
+    const double* xi = h->x;
+    const double* yi = h->y;
+    if (which == 1) {
+      k_average<<<grid_for(h->npad), 256, 0, h->s>>>(h->tn, h->sx, h->x, h->st, h->npad);
+      k_average<<<grid_for(h->mpad), 256, 0, h->s>>>(h->tm, h->sy, h->y, h->st, h->mpad);
+      xi = h->tn;
+      yi = h->tm;
+    } else if (which == 2) {
+      xi = h->xa;
+      yi = h->ya;
+    }
+    export_point(h, xi, yi, x, y);
+    return PDLP_OK;
+  });
+}
+
+int64_t pdlp_get_restarts(pdlp_handle h, int64_t* iters, int64_t cap) {
+  return guarded(h, [&]() -> int {
+    int64_t nr = h->solved ? h->last_nrestart : 0;
+    int64_t k = std::min<int64_t>({nr, cap, (int64_t)h->restart_cap});
+    if (iters && k > 0) CK(cudaMemcpy(iters, h->restarts, sizeof(long long) * k, cudaMemcpyDeviceToHost));
+    return (int)nr;
+  });
+}
+
+int64_t pdlp_get_log(pdlp_handle h, pdlp_check_record* rec, int64_t cap) {
+  static_assert(sizeof(pdlp_check_record) == sizeof(CheckRecord), "record layout");
+  return guarded(h, [&]() -> int {
+    int64_t nc = h->solved ? h->last_ncheck : 0;
+    int64_t k = std::min<int64_t>({nc, cap, (int64_t)h->log_cap});
+    if (rec && k > 0) CK(cudaMemcpy(rec, h->log, sizeof(CheckRecord) * k, cudaMemcpyDeviceToHost));
+    return (int)nc;
+  });
+}
+
+int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out) {
+  return guarded(h, [&]() {
+    if (!in || !out) invalid("null vector");
+    if (!transpose) {
+      copy_in(h, h->stage_n, in, h->n);
+      k_permute_in<<<grid_for(h->npad), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, h->n, h->npad, 0.0);
+      launch_rows<OpSpmv>(h, h->K, h->tn, EpiStore{h->tm, 0, 1.0}, nullptr);
+      if (h->m > 0) {
+        k_unpermute_scale<<<grid_for(h->m), 256, 0, h->s>>>(h->stage_m, h->tm, h->invDr, h->pos_r, h->m);
+        copy_out(h, out, h->stage_m, h->m);
+      }
+    } else {
+      if (h->m > 0) copy_in(h, h->stage_m, in, h->m);
+      k_permute_in<<<grid_for(h->mpad), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, h->m, h->mpad, 0.0);
+      launch_rows<OpSpmv>(h, h->Kt, h->tm, EpiStore{h->tn, 0, 1.0}, nullptr);
+      k_unpermute_scale<<<grid_for(h->n), 256, 0, h->s>>>(h->stage_n, h->tn, h->invDc, h->pos_c, h->n);
+      copy_out(h, out, h->stage_n, h->n);
+    }
+    CKL("pdlp_spmv");
+    CK(cudaStreamSynchronize(h->s));
+    return PDLP_OK;
+  });
+}
+
+int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
+  return guarded(h, [&]() {
+    if (!info) invalid("null info");
+    std::memset(info, 0, sizeof(*info));
+    info->m = h->m;
+    info->n = h->n;
+    info->m1 = h->m1;
+    info->nnz = h->nnz;
+    info->slots_K = h->K.slots;
+    info->slots_Kt = h->Kt.slots;
+    info->tasks_K = h->K.ntasks;
+    info->tasks_Kt = h->Kt.ntasks;
+    info->split_chunks_K = h->K.split;
+    info->split_chunks_Kt = h->Kt.split;
+    info->tile_slots_K = h->K.tile;
+    info->tile_slots_Kt = h->Kt.tile;
+    info->algorithmic_bytes_per_iter = 24.0 * h->nnz + 68.0 * (h->m + h->n);
+    info->stored_bytes_per_iter = 12.0 * 32.0 * (h->K.slots + h->Kt.slots) + 68.0 * (h->mpad + h->npad);
+    info->eta = h->eta;
+    info->omega0 = h->omega0;
+    info->norm_K = h->normK;
+    return PDLP_OK;
+  });
+}
+
+int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual) {
+  return guarded(h, [&]() {
+    if (iters < 1) invalid("iters must be >= 1");
+    if (!h->solved) invalid("no solve has run on this handle");
+    k_copy_state<<<1, 1, 0, h->s>>>(h->st_tmp, h->st);
+    const int64_t chunk = 512;
+    while ((int64_t)h->timing_events.size() < 2 * chunk + 1) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->timing_events.push_back(e);
+    }
+    double tp = 0.0, td = 0.0;
+    for (int64_t done = 0; done < iters; done += chunk) {
+      const int64_t cnt = std::min(chunk, iters - done);
+      auto& ev = h->timing_events;
+      CK(cudaEventRecord(ev[0], h->s));
+      for (int64_t i = 0; i < cnt; ++i) {
+        launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
+        CK(cudaEventRecord(ev[2 * i + 1], h->s));
+        launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, h->st_tmp);
+        CK(cudaEventRecord(ev[2 * i + 2], h->s));
+      }
+      CKL("timed iterations");
+      CK(cudaStreamSynchronize(h->s));
+      for (int64_t i = 0; i < cnt; ++i) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, ev[2 * i], ev[2 * i + 1]));
+        CK(cudaEventElapsedTime(&b, ev[2 * i + 1], ev[2 * i + 2]));
+        tp += a;
+        td += b;
+      }
+    }
+    if (ms_primal) *ms_primal = tp / (double)iters;
+    if (ms_dual) *ms_dual = td / (double)iters;
+    return PDLP_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+  * SpMV: |gpu - oracle| <= 1e-13 * sum_j |K_ij x_j| per row (different summation
+    order only; FP64 rounding is ~1e-16 per term).
+  * iterates after a fixed number of PDHG iterations: relative 1e-10 in the 2-norm
+    and elementwise against 1e-10 * max |reference|.
+  * objectives at a tolerance: relative 1e-6.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_2312_14832_b300 import build
+    build.build()
+    import paper_2312_14832_b300 as pk
+    return pk
+
+
+def dense(lp):
+    return sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(lp["m"], lp["n"]))
+
+
+def close_rel(a, b, rel):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if b.size == 0:
+        return
+    scale = max(np.abs(b).max(), 1e-300)
+    err = np.abs(a - b).max()
+    assert err <= rel * scale, f"max abs err {err:.3e} > {rel:.1e} * {scale:.3e}"
+    assert np.linalg.norm(a - b) <= rel * max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- SpMV
+
+LENGTH_REGIMES = {
+    "mixed": [0, 1, 31, 32, 33, 0, 5, 200, 1, 64] * 7 + [3],
+    "long": [10000, 1, 2, 4500, 0, 33, 700, 65, 64, 63] * 4,
+    "uniform": [7] * 1000 + [0] * 17,
+    "empty_rows": [0] * 50,
+}
+
+
+@pytest.mark.parametrize("regime", list(LENGTH_REGIMES))
+@pytest.mark.parametrize("tile", [0, 8, 64])
+def test_spmv_matches_oracle(pk, regime, tile):
+    lengths = LENGTH_REGIMES[regime]
+    n = 12000
+    rp, ci, v = lpgen.random_csr(11, len(lengths), n, lengths, dist="wide")
+    m = len(lengths)
+    lp = dict(m=m, n=n, m1=m // 3, row_ptr=rp, col_idx=ci, val=v, c=np.zeros(n), q=np.zeros(m),
+              l=np.full(n, -np.inf), u=np.full(n, np.inf))
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(n)
+    y = rng.standard_normal(m)
+    K = dense(lp)
+    with pk.Solver.from_lp(lp, tile_slots=tile) as s:
+        for _ in range(2):   # twice: split-chunk counters must be back at zero
+            gx = s.spmv(x)
+            gy = s.spmv(y, transpose=True)
+            ref_x = oracle.spmv(lp, x)
+            ref_y = oracle.spmv_t(lp, y)
+            bx = abs(K) @ np.abs(x)
+            by = abs(K).T @ np.abs(y)
+            assert np.all(np.abs(gx - ref_x) <= 1e-13 * bx + 1e-300)
+            assert np.all(np.abs(gy - ref_y) <= 1e-13 * by + 1e-300)
+
+
+def test_spmv_scaled_roundtrip(pk):
+    lp = lpgen.planted_zipf(seed=5, n=6000, m=3000, nnz=60000)
+    x = np.random.default_rng(1).standard_normal(lp["n"])
+    K = dense(lp)
+    with pk.Solver.from_lp(lp, scaling=1) as s:
+        gx = s.spmv(x)
+    bx = abs(K) @ np.abs(x)
+    assert np.all(np.abs(gx - K @ x) <= 1e-12 * bx + 1e-300)
+
+
+# ---------------------------------------------------------------- iterates
+
+def _compare_iterates(pk, lp, iters, **params):
+    ref = oracle.solve(lp, tol=0.0, max_iter=iters, **params)
+    with pk.Solver.from_lp(lp, scaling=params.get("scaling", 0)) as s:
+        r = s.solve(tol=0.0, max_iter=iters)
+        assert r["iters"] == ref["iters"] == iters
+        assert r["status"] == pk.ITER_LIMIT
+        np.testing.assert_array_equal(s.restarts(), ref["restart_iters"])
+        xc, yc = s.iterate(0)
+        xa, ya = s.iterate(1)
+        close_rel(xc, ref["x_cur"], 1e-10)
+        close_rel(yc, ref["y_cur"], 1e-10)
+        close_rel(xa, ref["x_avg"], 1e-10)
+        close_rel(ya, ref["y_avg"], 1e-10)
+        assert abs(r["omega"] - ref["omega"]) <= 1e-10 * ref["omega"]
+        assert abs(r["eta"] - ref["eta"]) <= 1e-12 * ref["eta"]
+        assert r["which"] == ref["which"]
+        close_rel(r["x"], ref["x"], 1e-10)
+    return r, ref
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_iterates_after_1000_small_planted(pk, seed, scaling):
+    _compare_iterates(pk, lpgen.planted_small(seed), 1000, scaling=scaling)
+
+
+def test_iterates_after_1000_zipf(pk):
+    lp = lpgen.planted_zipf(seed=2, n=20000, m=10000, nnz=200000)
+    _compare_iterates(pk, lp, 1000, scaling=1)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 63, 64, 100])
+def test_iteration_counts_and_ragged_intervals(pk, iters):
+    _compare_iterates(pk, lpgen.planted_small(4), iters)
+
+
+def test_box_only_lp(pk):
+    lp = lpgen.box_only(3, n=100, free_frac=0.2)
+    ref = oracle.solve(lp, tol=1e-10, max_iter=100000)
+    with pk.Solver.from_lp(lp) as s:
+        r = s.solve(tol=1e-10, max_iter=100000)
+    assert r["status"] == pk.OPTIMAL and r["iters"] == ref["iters"]
+    close_rel(r["x"], ref["x"], 1e-12)
+    assert r["eta"] == 1.0
+
+
+def test_warm_start_matches_oracle(pk):
+    lp = lpgen.planted_small(6)
+    rng = np.random.default_rng(0)
+    x0 = lp["x_star"] + 0.1 * rng.standard_normal(lp["n"])
+    y0 = lp["y_star"] + 0.1 * rng.standard_normal(lp["m"])
+    ref = oracle.solve(lp, tol=0.0, max_iter=500, x0=x0, y0=y0)
+    with pk.Solver.from_lp(lp) as s:
+        r = s.solve(x0=x0, y0=y0, tol=0.0, max_iter=500)
+        xc, yc = s.iterate(0)
+    close_rel(xc, ref["x_cur"], 1e-10)
+    close_rel(yc, ref["y_cur"], 1e-10)
+
+
+# ---------------------------------------------------------------- solves to tolerance
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8])
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_objective_at_tolerance(pk, tol, scaling):
+    lp = lpgen.planted_small(0)
+    ref = oracle.solve(lp, tol=tol, scaling=scaling)
+    with pk.Solver.from_lp(lp, scaling=scaling) as s:
+        r = s.solve(tol=tol)
+    assert r["status"] == pk.OPTIMAL
+    assert r["iters"] == ref["iters"]
+    assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * abs(ref["primal_obj"])
+    assert abs(r["dual_obj"] - ref["dual_obj"]) <= 1e-6 * abs(ref["dual_obj"])
+    assert max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) <= tol
+    if tol == 1e-8:
+        assert abs(r["primal_obj"] - lp["obj_star"]) <= 1e-6 * abs(lp["obj_star"])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_lp_objective(pk, seed):
+    lp = lpgen.tiny_lp(seed, n=5, m1=1, m2=3)
+    ref = oracle.solve(lp, tol=1e-8, max_iter=2_000_000)
+    with pk.Solver.from_lp(lp) as s:
+        r = s.solve(tol=1e-8, max_iter=2_000_000)
+    assert r["status"] == pk.OPTIMAL
+    assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
+
+
+def test_solves_are_deterministic(pk):
+    lp = lpgen.planted_zipf(seed=7, n=8000, m=4000, nnz=80000)
+    with pk.Solver.from_lp(lp, scaling=1) as s:
+        a = s.solve(tol=0.0, max_iter=700)
+        b = s.solve(tol=0.0, max_iter=700)
+        np.testing.assert_array_equal(a["x"], b["x"])
+        np.testing.assert_array_equal(a["y"], b["y"])
+
+
+def test_invalid_inputs_are_rejected(pk):
+    lp = lpgen.planted_small(0)
+    bad = dict(lp, col_idx=lp["col_idx"].copy())
+    bad["col_idx"][3] = lp["n"]
+    with pytest.raises(pk.SolverError):
+        pk.Solver.from_lp(bad)
+    bad = dict(lp, l=lp["l"].copy())
+    bad["l"][0] = 20.0   # l > u
+    with pytest.raises(pk.SolverError):
+        pk.Solver.from_lp(bad)
+    bad = dict(lp, val=lp["val"].copy())
+    bad["val"][0] = np.nan
+    with pytest.raises(pk.SolverError):
+        pk.Solver.from_lp(bad)
