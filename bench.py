@@ -1,0 +1,303 @@
+"""Benchmark of the restarted-PDHG hot path on one B300 (or N independent replicas).
+
+Workload (default): the large planted sparse LP -- n = 2e6 columns, m = 1e6 rows (40 %
+equalities), nnz ~ 2e7 with Zipf(1.5) row lengths, values +-10^U(-3,3), mixed bounds,
+Ruiz + Pock-Chambolle scaling (lpgen.planted_zipf, seed 0 + rank).
+
+A step is one check interval: check_every (64) PDHG iterations -- each one the fused
+K'y SpMV + primal step kernel and the fused K x SpMV + dual step kernel -- followed by
+the restart/termination check (three SpMVs, the KKT and duality-gap reductions, the
+restart decision and the restart).  `value` is PDHG iterations per second of the whole
+job (all ranks), timed with CUDA events on the current stream around one pdlp_solve of
+steps * 64 iterations (tolerance 0, so every step runs), inputs resident in HBM.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--workload large|small]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-4 KKT & PDHG iter/s (HBM GB/s vs peak); batched & warm-start vs plain"
+CHECK_EVERY = 64
+
+
+def workload(name, rank):
+    import lpgen
+    if name == "large":
+        lp = lpgen.planted_zipf(seed=rank, n=2_000_000, m=1_000_000, nnz=20_000_000)
+        desc = ("planted sparse LP, n=2e6, m=1e6 (m1=4e5), nnz~2e7, Zipf(1.5) row lengths capped 1e4, "
+                "values +-10^U(-3,3), bounds 25% free / 50% [0,U(1,100)] / 25% [0,inf), "
+                "Ruiz(10)+Pock-Chambolle scaling")
+    elif name == "medium":
+        lp = lpgen.planted_zipf(seed=rank, n=500_000, m=250_000, nnz=5_000_000)
+        desc = ("planted sparse LP, n=5e5, m=2.5e5, nnz~5e6, the large recipe at a quarter of the size, "
+                "Ruiz(10)+Pock-Chambolle scaling")
+    elif name == "small":
+        lp = lpgen.planted_small(seed=rank)
+        desc = "planted LP m1=200, m2=300, n=1000, nnz=5000, N(0,1) values"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return lp, desc
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def kernel_bytes(lp):
+    """Algorithmic bytes per launch of the two fused iteration kernels (unique-bytes model:
+    FP64 values, int32 indices, each array touched once, the gathered vector once)."""
+    nnz, m, n = lp["val"].shape[0], lp["m"], lp["n"]
+    primal = 12 * nnz + 4 * (n + 1) + 8 * m + 56 * n   # K' CSR, y gather, x c l u sx read, x sx written
+    dual = 12 * nnz + 4 * (m + 1) + 8 * n + 56 * m     # K CSR, x gather, y q Kx sy read, y Kx sy written
+    return primal, dual
+
+
+def stored_traffic(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_2312_14832_b300", "csrc", "kernels.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    k = rec.get("kernels", {}).get(kernel)
+    if not k or rec.get("source_sha") != h or rec.get("workload") != workload_name:
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi during the timed region."""
+
+    def __init__(self, dev):
+        self.p = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(dev)
+            sel = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        except Exception:
+            sel = str(dev)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", sel, f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(lp, seconds=12.0):
+    """The oracle's PDHG step (oracle.pdhg_step, single thread) on the same LP."""
+    import oracle
+    x = np.clip(np.zeros(lp["n"]), lp["l"], lp["u"])
+    y = np.zeros(lp["m"])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        x, y = oracle.pdhg_step(lp, x, y, 1e-3, 1.0)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 200:
+            break
+    return {"value": steps / el, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle PDHG steps (orc_pdhg_step: K'y, primal step, K(2x+-x), dual step) "
+                      f"on the full workload, {el:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
+    ap.add_argument("--ttt-budget", type=float, default=60.0, help="seconds for the time-to-1e-4 solve")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # the reference arm is the CPU oracle, on rank 0 only
+        if rank != 0:
+            return
+        lp, desc = workload(args.workload, 0)
+        base = cpu_baseline(lp, seconds=max(3.0, 1.0 * (args.steps + args.warmup)))
+        out = {"metric": METRIC, "value": base["value"], "unit": base["unit"], "n_gpus": 0,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * CHECK_EVERY / base["value"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "impl": "reference",
+               "config": {"workload": desc, "check_every": CHECK_EVERY},
+               "cpu_baseline": base,
+               "e2e": {"value": base["value"], "unit": base["unit"], "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    import torch
+    import paper_2312_14832_b300 as pk
+    from paper_2312_14832_b300 import build as pkbuild
+    pkbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    lp, desc = workload(args.workload, rank)
+    stream = torch.cuda.current_stream()
+    s = pk.Solver.from_lp(lp, scaling=1, stream=stream.cuda_stream)
+    info = s.info()
+    iters = args.steps * CHECK_EVERY
+    s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clk = Clocks(local)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = s.solve(tol=0.0, max_iter=iters, want_point=False)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * iters / (ms * 1e-3)
+
+    # dominant kernel, timed live with CUDA events on the solver's stream
+    ms_p, ms_d = s.time_iterations(200)
+    bp, bd = kernel_bytes(lp)
+    pk_, peak_kind = peaks()
+    if ms_p >= ms_d:
+        kname, kb, kms = "primal (K'y SpMV + primal step)", bp, ms_p
+        kkey = "sell_rows_kernel<OpSpmv,EpiPrimal>"
+    else:
+        kname, kb, kms = "dual (K x SpMV + dual step)", bd, ms_d
+        kkey = "sell_rows_kernel<OpSpmv,EpiDual>"
+    achieved = kb / (kms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": pk_["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk_["hbm_gbs"], "peak_kind": peak_kind,
+                "traffic": stored_traffic(kkey, args.workload),
+                "bytes_per_launch": kb, "ms_per_launch": kms,
+                "other_kernel_ms": ms_d if kms == ms_p else ms_p}
+    iter_bytes = info["algorithmic_bytes_per_iter"]
+    whole_iter_gbs = iter_bytes * (iters / (ms * 1e-3)) / 1e9
+
+    # time to 1e-4 relative KKT (cold start)
+    ttt = None
+    if args.ttt_budget > 0:
+        rt = s.solve(tol=1e-4, time_limit_s=args.ttt_budget, want_point=False)
+        ttt = {"tol": 1e-4, "status": ["optimal", "iter_limit", "time_limit", "numerical"][rt["status"]],
+               "iters": rt["iters"], "restarts": rt["restarts"], "device_s": rt["device_ms"] * 1e-3,
+               "wall_s": rt["solve_s"], "rel_primal": rt["rel_primal"], "rel_dual": rt["rel_dual"],
+               "rel_gap": rt["rel_gap"], "primal_obj": rt["primal_obj"], "obj_star": lp.get("obj_star")}
+    s.close()
+
+    # end to end through the public API with host buffers: setup (H2D, layout), solve, D2H
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        s2 = pk.Solver.from_lp(lp, scaling=1)
+        r2 = s2.solve(tol=0.0, max_iter=iters)
+        _ = (r2["x"], r2["y"])
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s2.close()
+        if dist is not None:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nnz = lp["val"].shape[0]
+        h2d = 8 * (lp["m"] + 1) + 12 * nnz + 8 * (3 * lp["n"] + lp["m"])
+        d2h = 8 * (lp["n"] + lp["m"])
+        e2e = {"value": world * iters / el, "unit": "PDHG iter/s", "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps, "wall_s": el,
+               "note": "setup (host CSR -> device layout, scaling, ||K|| estimate) + solve + result copy"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    base = None if args.no_cpu or world > 1 else cpu_baseline(lp)
+    out = {"metric": METRIC, "value": value, "unit": "PDHG iter/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": desc, "check_every": CHECK_EVERY,
+                      "step": f"{CHECK_EVERY} PDHG iterations + 1 restart/termination check",
+                      "l2": "inputs larger than L2 (~0.7 GB touched per iteration)",
+                      "parallelism": "replicas only" if world > 1 else "1 GPU",
+                      "m": lp["m"], "n": lp["n"], "nnz": int(lp["val"].shape[0])},
+           "roofline": roofline,
+           "iteration_gbs": whole_iter_gbs, "iteration_frac": whole_iter_gbs / pk_["hbm_gbs"],
+           "algorithmic_bytes_per_iter": iter_bytes, "stored_bytes_per_iter": info["stored_bytes_per_iter"],
+           "time_to_tol": ttt, "cpu_baseline": base, "e2e": e2e, "gpu_launches": int(r["launches"]),
+           "device_ms_library": r["device_ms"], "clocks": clocks,
+           "layout": {k: info[k] for k in ("slots_K", "slots_Kt", "tasks_K", "tasks_Kt", "split_chunks_K",
+                                           "split_chunks_Kt", "tile_slots_K")},
+           "eta": info["eta"], "norm_K": info["norm_K"]}
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
