@@ -152,8 +152,9 @@ int pdlp_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const doub
 /* Releases everything the handle owns.  NULL is allowed. */
 void pdlp_free(pdlp_handle h);
 
-/* Text of the handle's last error ("" if none); NULL = last pdlp_setup failure
- * of this thread.  The string stays valid until the next call on the handle. */
+/* Text of the handle's last error ("" if none); NULL = last failure of pdlp_setup or
+ * pdlp_spmv_csr_noalloc on this thread.  The string stays valid until the next call
+ * on the handle. */
 const char* pdlp_last_error(pdlp_handle h);
 
 /* Copies the solver's state after pdlp_solve: which = 0 current iterate, 1 average of
@@ -184,6 +185,32 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info);
  * kernel (K x SpMV fused with the dual step), each timed with CUDA events recorded
  * on the handle's stream around every launch. */
 int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual);
+
+/* y = K x for a CSR matrix held in the caller's device memory, with no device memory
+ * allocated by the call.  This entry point has no counterpart in the paper; it is for
+ * callers that cannot call cudaMalloc at the point where they need the product, for
+ * example an application whose device memory is all handed to its own pool allocator,
+ * or a latency-bound loop that must not take cudaMalloc's implicit device
+ * synchronisation.  It needs no handle.
+ *   m, n, nnz : rows, columns and nonzeros of K (m < 2^31, n >= 1).
+ *   row_ptr   : int64[m+1] device array, row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz.
+ *   col_idx   : int32[nnz] device array, 0 <= col < n;  val: double[nnz] device array.
+ *   x         : double[n] device array;  y: double[m] device array (output, overwritten).
+ *   stream    : cudaStream_t to run on (NULL = the default stream); the call returns
+ *               without waiting, y is ready when the stream reaches that point.
+ * Scratch: partial sums of rows that cross thread boundaries live in one fixed 8 MiB
+ * device array of the library, which every GPU that uses this call keeps until the
+ * process exits.  It limits nnz to 22,369,600; larger inputs return PDLP_EINVAL with a
+ * message in pdlp_last_error(NULL), before any device work.  The first call on a device
+ * looks up that array's device address (with the device current); make that first call
+ * before any stream capture.  Every call on a device shares the array, so calls that
+ * overlap on the GPU (different streams, or different host threads) race and give wrong
+ * results; the call writes every scratch entry it later reads, so nothing needs clearing.
+ * The same 1e-13 relative agreement with pdlp_spmv holds (summation order differs).
+ * Errors: PDLP_EINVAL (sizes, null arrays), PDLP_ECUDA (no device, launch failure). */
+int pdlp_spmv_csr_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                          const int32_t* col_idx, const double* val, const double* x, double* y,
+                          void* stream);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("pdlp.cu", "layout.cpp")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("pdlp.cu", "layout.cpp", "noalloc.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "layout.h")] + \
     [os.path.join(ROOT, "include", "pdlp.h")]
 LIB = os.path.join(HERE, "libpdlp_b300.so")

@@ -27,6 +27,9 @@ namespace pdlp {
 
 static thread_local std::string g_setup_error;
 
+// Records the text returned by pdlp_last_error(NULL) for handle-less calls.
+void set_thread_error(const std::string& msg) { g_setup_error = msg; }
+
 struct Failure {
   int code;
   std::string msg;
