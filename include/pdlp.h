@@ -72,10 +72,17 @@ typedef struct {
   int32_t ruiz_iters;    /* Ruiz passes when scaling (default 10)                         */
   int32_t power_iters;   /* power iterations for ||K||_2 (default 100)                    */
   double eta;            /* > 0: fixed step size instead of step_scale/||K||_2 (default 0)*/
-  int32_t tile_slots;    /* SpMV work per warp in 32-row slots; 0 = chosen at setup       */
+  int32_t tile_slots;    /* SpMV work per warp in 32-row slots; 0 = chosen at setup.
+                            When tile_slots, tile_chunks and spmv_batch are all 0 and
+                            nnz >= 2^20, setup times 16 candidate schedules per layout
+                            and keeps the fastest (results then depend on the choice only
+                            through the summation order of split rows)                 */
   int32_t inputs_on_device; /* 1: array arguments are device pointers (default 0)        */
   void* stream;          /* cudaStream_t the caller orders with, or NULL                  */
   int32_t log_capacity;  /* per-check records kept on the device (default 4096)          */
+  int32_t tile_chunks;   /* at most this many 32-row chunks per SpMV warp task (1..32);
+                            0 = chosen at setup                                           */
+  int32_t spmv_batch;    /* SpMV slots whose loads are issued together: 4 or 8; 0 = setup */
   int32_t reserved;
 } pdlp_params;
 
@@ -115,6 +122,8 @@ typedef struct {
   int64_t tasks_K, tasks_Kt;   /* warp tasks per SpMV                                      */
   int64_t split_chunks_K, split_chunks_Kt;
   int32_t tile_slots_K, tile_slots_Kt;
+  int32_t tile_chunks_K, tile_chunks_Kt;
+  int32_t spmv_batch_K, spmv_batch_Kt;
   double algorithmic_bytes_per_iter; /* unique-bytes model: 24 nnz + 68 (m + n)         */
   double stored_bytes_per_iter;      /* the same with padding slots counted               */
   double eta, omega0, norm_K;

@@ -17,7 +17,8 @@ class Params(C.Structure):
                 ("beta_nec", C.c_double), ("beta_art", C.c_double), ("step_scale", C.c_double),
                 ("omega_theta", C.c_double), ("ruiz_iters", C.c_int32), ("power_iters", C.c_int32),
                 ("eta", C.c_double), ("tile_slots", C.c_int32), ("inputs_on_device", C.c_int32),
-                ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("reserved", C.c_int32)]
+                ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("tile_chunks", C.c_int32),
+                ("spmv_batch", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -40,6 +41,8 @@ class Info(C.Structure):
                 ("slots_K", C.c_int64), ("slots_Kt", C.c_int64), ("tasks_K", C.c_int64),
                 ("tasks_Kt", C.c_int64), ("split_chunks_K", C.c_int64), ("split_chunks_Kt", C.c_int64),
                 ("tile_slots_K", C.c_int32), ("tile_slots_Kt", C.c_int32),
+                ("tile_chunks_K", C.c_int32), ("tile_chunks_Kt", C.c_int32),
+                ("spmv_batch_K", C.c_int32), ("spmv_batch_Kt", C.c_int32),
                 ("algorithmic_bytes_per_iter", C.c_double), ("stored_bytes_per_iter", C.c_double),
                 ("eta", C.c_double), ("omega0", C.c_double), ("norm_K", C.c_double)]
 

@@ -97,6 +97,7 @@ struct SellView {
   const double* __restrict__ val;
   const SellTask* __restrict__ tasks;
   int32_t ntasks;
+  int32_t nchunks;
   double* gpart;   // ntasks * 32 partial sums of split-chunk pieces
   int32_t* cnt;    // arrival counters (index: first piece task), zero between launches
 };
@@ -122,9 +123,44 @@ struct OpSumAbs {
   __device__ static double join(double a, double b) { return a + b; }
 };
 
-// One warp per task; lane = row of the chunk.  Epi::apply(row, sum) receives the
-// complete row sum exactly once per row.
-template <class Op, class Epi>
+// Sum of slots [s, e) of one chunk for this lane's row.  Loads of a batch of up to
+// kBatch slots are issued before any of its FMAs; `nb` is warp-uniform, so the
+// guards do not diverge and no FP64 instruction is spent on a missing slot.
+template <class Op, int kBatch>
+__device__ __forceinline__ double chunk_sum(const SellView& A, const double* __restrict__ xg, int s, int e,
+                                            int lane) {
+  const int32_t* cp = A.col + (size_t)s * 32 + lane;
+  const double* vp = A.val + (size_t)s * 32 + lane;
+  double acc = 0.0;
+  for (int k = s; k < e; k += kBatch) {
+    const int nb = min(kBatch, e - k);
+    double v[kBatch], xv[kBatch];
+    int ci[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if (j < nb) {
+        v[j] = __ldcs(vp + 32 * j);
+        if (Op::kGather) ci[j] = __ldcs(cp + 32 * j);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      xv[j] = 0.0;
+      if (Op::kGather && j < nb) xv[j] = __ldg(xg + ci[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+      if (j < nb) acc = Op::step(acc, v[j], xv[j]);
+    vp += 32 * kBatch;
+    cp += 32 * kBatch;
+  }
+  return acc;
+}
+
+// One warp per task; lane = row of the chunk.  Epi::finish(row, sum, pre) receives the
+// complete row sum exactly once per row; Epi::load(row) fetches, before the row's
+// SpMV loop, the operands the epilogue needs, so their latency overlaps it.
+template <class Op, class Epi, int kBatch>
 __global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const double* __restrict__ xg,
                                                         Epi epi, const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
@@ -133,57 +169,34 @@ __global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const double
   if (w >= A.ntasks) return;
   const SellTask T = A.tasks[w];
   epi.prepare(st);
-  int s = T.s0;
-  int c = T.chunk;
-  while (s < T.s1) {
-    const int e = min(A.chunk_ptr[c + 1], T.s1);
-    const int32_t* cp = A.col + (size_t)s * 32 + lane;
-    const double* vp = A.val + (size_t)s * 32 + lane;
-    const int len = e - s;
-    double acc = 0.0;
-    int k = 0;
-    for (; k + 4 <= len; k += 4) {
-      double v0 = __ldcs(vp), v1 = __ldcs(vp + 32), v2 = __ldcs(vp + 64), v3 = __ldcs(vp + 96);
-      double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
-      if (Op::kGather) {
-        int c0 = __ldcs(cp), c1 = __ldcs(cp + 32), c2 = __ldcs(cp + 64), c3 = __ldcs(cp + 96);
-        x0 = __ldg(xg + c0); x1 = __ldg(xg + c1); x2 = __ldg(xg + c2); x3 = __ldg(xg + c3);
-      }
-      acc = Op::step(acc, v0, x0);
-      acc = Op::step(acc, v1, x1);
-      acc = Op::step(acc, v2, x2);
-      acc = Op::step(acc, v3, x3);
-      vp += 128;
-      cp += 128;
+  if (T.np == 0) {
+    // whole chunks T.chunk .. T.chunk + nc - 1; lane j holds the start of chunk j
+    const int cb = A.chunk_ptr[min(T.chunk + lane, A.nchunks)];
+    for (int j = 0; j < T.nc; ++j) {
+      const int s = __shfl_sync(0xffffffffu, cb, j);
+      const int e = __shfl_sync(0xffffffffu, cb, j + 1);
+      const int row = (T.chunk + j) * 32 + lane;
+      const typename Epi::Pre pre = epi.load(row);
+      const double acc = chunk_sum<Op, kBatch>(A, xg, s, e, lane);
+      epi.finish(row, acc, pre);
     }
-    for (; k < len; ++k) {
-      double v0 = __ldcs(vp);
-      double x0 = 0.0;
-      if (Op::kGather) x0 = __ldg(xg + __ldcs(cp));
-      acc = Op::step(acc, v0, x0);
-      vp += 32;
-      cp += 32;
-    }
-    s = e;
-    const int row = c * 32 + lane;
-    if (T.np == 0) {
-      epi.apply(row, acc);
-    } else {
-      // piece of a split chunk: publish, count arrivals, the last arrival combines
-      A.gpart[(size_t)w * 32 + lane] = acc;
+  } else {
+    // piece of a split chunk: publish, count arrivals, the last arrival combines
+    const double acc = chunk_sum<Op, kBatch>(A, xg, T.s0, T.s1, lane);
+    const int row = T.chunk * 32 + lane;
+    A.gpart[(size_t)w * 32 + lane] = acc;
+    __threadfence();
+    int old = 0;
+    if (lane == 0) old = atomicAdd(A.cnt + T.t0, 1);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old == T.np - 1) {
       __threadfence();
-      int old = 0;
-      if (lane == 0) old = atomicAdd(A.cnt + T.t0, 1);
-      old = __shfl_sync(0xffffffffu, old, 0);
-      if (old == T.np - 1) {
-        __threadfence();
-        double sum = __ldcg(A.gpart + (size_t)T.t0 * 32 + lane);
-        for (int i = 1; i < T.np; ++i) sum = Op::join(sum, __ldcg(A.gpart + (size_t)(T.t0 + i) * 32 + lane));
-        if (lane == 0) A.cnt[T.t0] = 0;
-        epi.apply(row, sum);
-      }
+      const typename Epi::Pre pre = epi.load(row);
+      double sum = __ldcg(A.gpart + (size_t)T.t0 * 32 + lane);
+      for (int i = 1; i < T.np; ++i) sum = Op::join(sum, __ldcg(A.gpart + (size_t)(T.t0 + i) * 32 + lane));
+      if (lane == 0) A.cnt[T.t0] = 0;
+      epi.finish(row, sum, pre);
     }
-    ++c;
   }
 }
 
@@ -192,8 +205,10 @@ struct EpiStore {
   double* out;
   int use_inv_t;
   double scale;
+  struct Pre {};
   __device__ void prepare(const DevState* st) { scale = (use_inv_t && st) ? st->inv_t : 1.0; }
-  __device__ void apply(int r, double s) { out[r] = use_inv_t ? s * scale : s; }
+  __device__ Pre load(int) const { return Pre{}; }
+  __device__ void finish(int r, double s, const Pre&) { out[r] = use_inv_t ? s * scale : s; }
 };
 
 // Primal step fused on g = (K'y)_j (Section 2, primal update):
@@ -205,13 +220,14 @@ struct EpiPrimal {
   const double* __restrict__ l;
   const double* __restrict__ u;
   double tau;
+  struct Pre { double xo, c, l, u, sx; };
   __device__ void prepare(const DevState* st) { tau = st->tau; }
-  __device__ void apply(int j, double g) {
-    double xo = x[j];
-    double d = c[j] - g;
-    double xn = clamp_box(fma(-tau, d, xo), l[j], u[j]);
+  __device__ Pre load(int j) const { return Pre{x[j], c[j], l[j], u[j], sx[j]}; }
+  __device__ void finish(int j, double g, const Pre& p) {
+    const double d = p.c - g;
+    const double xn = clamp_box(fma(-tau, d, p.xo), p.l, p.u);
     x[j] = xn;
-    sx[j] = sx[j] + xn;
+    sx[j] = p.sx + xn;
   }
 };
 
@@ -226,13 +242,15 @@ struct EpiDual {
   const double* __restrict__ q;
   int m1;
   double sigma;
+  struct Pre { double q, kxp, y, sy; };
   __device__ void prepare(const DevState* st) { sigma = st->sigma; }
-  __device__ void apply(int i, double v) {
-    double e = q[i] + kxp[i];
-    double yn = fma(sigma, fma(-2.0, v, e), y[i]);
+  __device__ Pre load(int i) const { return Pre{q[i], kxp[i], y[i], sy[i]}; }
+  __device__ void finish(int i, double v, const Pre& p) {
+    const double e = p.q + p.kxp;
+    double yn = fma(sigma, fma(-2.0, v, e), p.y);
     if (i >= m1) yn = max0(yn);
     y[i] = yn;
-    sy[i] = sy[i] + yn;
+    sy[i] = p.sy + yn;
     kxp[i] = v;
   }
 };

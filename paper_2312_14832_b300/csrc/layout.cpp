@@ -58,9 +58,11 @@ SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
   return S;
 }
 
-TaskPlan plan_tasks(const SellHost& S, int32_t Q) {
+TaskPlan plan_tasks(const SellHost& S, int32_t Q, int32_t C) {
   TaskPlan P;
   if (Q < 1) Q = 1;
+  if (C < 1) C = 1;
+  if (C > 32) C = 32;
   int64_t c = 0;
   while (c < S.nchunks) {
     int32_t base = S.chunk_ptr[(size_t)c];
@@ -75,6 +77,7 @@ TaskPlan plan_tasks(const SellHost& S, int32_t Q) {
         T.chunk = (int32_t)c;
         T.t0 = t0;
         T.np = np;
+        T.nc = 1;
         P.tasks.push_back(T);
       }
       P.split_chunks++;
@@ -85,14 +88,16 @@ TaskPlan plan_tasks(const SellHost& S, int32_t Q) {
       T.chunk = (int32_t)c;
       T.t0 = -1;
       T.np = 0;
-      int32_t tot = 0;
-      while (c < S.nchunks) {
+      int32_t tot = 0, nc = 0;
+      while (c < S.nchunks && nc < C) {
         int32_t l = S.chunk_ptr[(size_t)c + 1] - S.chunk_ptr[(size_t)c];
         if (l > Q || tot + l > Q) break;
         tot += l;
+        ++nc;
         ++c;
       }
       T.s1 = S.chunk_ptr[(size_t)c];
+      T.nc = nc;
       P.tasks.push_back(T);
     }
   }

@@ -7,7 +7,9 @@
 // warp reads one slot with one fully coalesced 256-byte load and every lane owns
 // one row.  A chunk is as long as its longest row (at least one slot); shorter
 // rows are padded with zero values.  Work is cut into warp tasks of about
-// `tile_slots` slots: short chunks are packed whole into a task, a chunk longer
+// `tile_slots` slots: short chunks are packed whole into a task (at most
+// `tile_chunks` of them, so that a warp never runs a long serial chain of tiny
+// chunks), a chunk longer
 // than tile_slots is split into pieces whose partial sums are combined, in piece
 // order, by the warp that finishes last.
 #pragma once
@@ -21,7 +23,8 @@ struct SellTask {
   int32_t chunk;    // first chunk the task touches
   int32_t t0;       // split chunk: index of its first piece task; else -1
   int32_t np;       // split chunk: number of pieces; else 0
-  int32_t pad[3];
+  int32_t nc;       // chunks the task covers (1 for a split piece)
+  int32_t pad[2];
 };
 
 struct SellHost {
@@ -49,6 +52,8 @@ SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
                     const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
                     const std::vector<int32_t>& esrc);
 
-TaskPlan plan_tasks(const SellHost& S, int32_t tile_slots);
+// Packs whole chunks into tasks of at most tile_slots slots and at most tile_chunks
+// (<= 32) chunks; chunks longer than tile_slots become split pieces.
+TaskPlan plan_tasks(const SellHost& S, int32_t tile_slots, int32_t tile_chunks);
 
 }  // namespace pdlp

@@ -54,14 +54,15 @@ struct DevSell {
   double* gpart = nullptr;
   int32_t* cnt = nullptr;
   int32_t ntasks = 0;
-  int32_t tile = 0;
+  int32_t tile = 0, tchunks = 0, batch = 8;
   int64_t rows = 0, rows_pad = 0, nchunks = 0, slots = 0, split = 0;
-  SellView view() const { return SellView{chunk_ptr, col, val, tasks, ntasks, gpart, cnt}; }
+  SellView view() const { return SellView{chunk_ptr, col, val, tasks, ntasks, (int32_t)nchunks, gpart, cnt}; }
 };
 
 constexpr int kRing = 4;        // pinned status records in flight
 constexpr int kLookahead = 2;   // intervals queued ahead of the one being read
 constexpr int kVecGridMax = 148 * 8;
+constexpr int64_t kAutotuneMinNnz = 1 << 20;   // smaller matrices keep the default schedule
 
 }  // namespace pdlp
 
@@ -142,7 +143,8 @@ static void dfree(pdlp_ctx* h, void* p) {
 template <class Op, class Epi>
 static void launch_rows(pdlp_ctx* h, const DevSell& S, const double* xg, Epi epi, const DevState* st) {
   const int blocks = (S.ntasks + 7) / 8;
-  sell_rows_kernel<Op, Epi><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
+  if (S.batch == 4) sell_rows_kernel<Op, Epi, 4><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
+  else sell_rows_kernel<Op, Epi, 8><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
 }
 
 static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const TaskPlan& P,
@@ -164,6 +166,22 @@ static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const 
   CKL("k_gather_values");
   CK(cudaStreamSynchronize(h->s));
   dfree(h, d_src);
+}
+
+// Replaces the warp-task plan of a device layout (the arrays of values and indices stay).
+static void set_plan(pdlp_ctx* h, DevSell& D, const TaskPlan& P, int32_t tile, int32_t tchunks, int32_t batch) {
+  CK(cudaStreamSynchronize(h->s));
+  dfree(h, D.tasks);
+  dfree(h, D.gpart);
+  dfree(h, D.cnt);
+  D.ntasks = (int32_t)P.tasks.size();
+  D.split = P.split_chunks;
+  D.tasks = upload(h, P.tasks);
+  D.gpart = dalloc<double>(h, (size_t)D.ntasks * 32);
+  D.cnt = dalloc<int32_t>(h, (size_t)D.ntasks);
+  D.tile = tile;
+  D.tchunks = tchunks;
+  D.batch = batch;
 }
 
 static void norm2_dev(pdlp_ctx* h, const double* a, int64_t n) {
@@ -331,6 +349,52 @@ static void destroy(pdlp_ctx* h) {
   delete h;
 }
 
+// ------------------------------------------------------------------ autotuner
+
+// Chooses (tile_slots, tile_chunks, batch) for one layout by timing the production
+// iteration kernel (fused epilogue included) on the handle's own buffers, which the
+// next pdlp_solve re-initialises; tau = sigma = 0 so the iterate does not move.
+static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
+  static const int32_t tiles[] = {32, 64};
+  static const int32_t chunks[] = {1, 2, 4, 8};
+  static const int32_t batches[] = {4, 8};
+  DevState zs{};
+  CK(cudaMemcpyAsync(h->st_tmp, &zs, sizeof(DevState), cudaMemcpyHostToDevice, h->s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int32_t bt = D.tile, bc = D.tchunks, bb = D.batch;
+  for (int32_t t : tiles)
+    for (int32_t c : chunks) {
+      TaskPlan P = plan_tasks(S, t, c);
+      for (int32_t b : batches) {
+        set_plan(h, D, P, t, c, b);
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+          if (rep == 1) CK(cudaEventRecord(e0, h->s));
+          if (primal)
+            launch_rows<OpSpmv>(h, D, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
+          else
+            launch_rows<OpSpmv>(h, D, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, h->st_tmp);
+        }
+        CK(cudaEventRecord(e1, h->s));
+        CKL("autotune launch");
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&tot, e0, e1));
+        if (tot < best) {
+          best = tot;
+          bt = t;
+          bc = c;
+          bb = b;
+        }
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_plan(h, D, plan_tasks(S, bt, bc), bt, bc, bb);
+}
+
 // ------------------------------------------------------------------ setup
 
 static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr_in,
@@ -438,10 +502,12 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   }
   h->mpad = SK.rows_pad;
   h->npad = SKt.rows_pad;
-  const int32_t tile = P.tile_slots > 0 ? P.tile_slots : 32;
-  TaskPlan PK = plan_tasks(SK, tile), PKt = plan_tasks(SKt, tile);
-  h->K.tile = tile;
-  h->Kt.tile = tile;
+  const int32_t tile = P.tile_slots > 0 ? P.tile_slots : 64;
+  const int32_t tchunks = P.tile_chunks > 0 ? std::min(P.tile_chunks, 32) : 4;
+  TaskPlan PK = plan_tasks(SK, tile, tchunks), PKt = plan_tasks(SKt, tile, tchunks);
+  h->K.tile = h->Kt.tile = tile;
+  h->K.tchunks = h->Kt.tchunks = tchunks;
+  h->K.batch = h->Kt.batch = (P.spmv_batch == 4) ? 4 : 8;
 
   double* d_val = upload(h, val);
   build_device_sell(h, h->K, SK, PK, d_val);
@@ -519,6 +585,13 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   k_scale_cols<<<grid_for(np), 256, 0, h->s>>>(h->c, h->l, h->u, h->invDc, h->Dc, np);
   k_scale_rows<<<grid_for(mp), 256, 0, h->s>>>(h->q, h->invDr, h->Dr, mp);
   CKL("scale vectors");
+
+  // ---- SpMV schedule per layout: explicit parameters, or timed candidates for large K
+  const bool auto_tile = P.tile_slots == 0 && P.tile_chunks == 0 && P.spmv_batch == 0;
+  if (auto_tile && nnz >= kAutotuneMinNnz) {
+    autotune(h, h->Kt, SKt, true);
+    autotune(h, h->K, SK, false);
+  }
 
   // ---- ||K||_2 by power iteration on K'K (v0 = 1/sqrt(n)), eta, omega0
   if (P.eta > 0.0) {
@@ -760,6 +833,8 @@ void pdlp_default_params(pdlp_params* p) {
   p->inputs_on_device = 0;
   p->stream = nullptr;
   p->log_capacity = 4096;
+  p->tile_chunks = 0;
+  p->spmv_batch = 0;
 }
 
 int pdlp_setup(pdlp_handle* out, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr,
@@ -896,6 +971,10 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->split_chunks_Kt = h->Kt.split;
     info->tile_slots_K = h->K.tile;
     info->tile_slots_Kt = h->Kt.tile;
+    info->tile_chunks_K = h->K.tchunks;
+    info->tile_chunks_Kt = h->Kt.tchunks;
+    info->spmv_batch_K = h->K.batch;
+    info->spmv_batch_Kt = h->Kt.batch;
     info->algorithmic_bytes_per_iter = 24.0 * h->nnz + 68.0 * (h->m + h->n);
     info->stored_bytes_per_iter = 12.0 * 32.0 * (h->K.slots + h->Kt.slots) + 68.0 * (h->mpad + h->npad);
     info->eta = h->eta;
