@@ -24,7 +24,22 @@ def stale() -> bool:
     return any(os.path.getmtime(d) > t for d in DEPS)
 
 
+CEIL_SRC = os.path.join(HERE, "csrc", "gather_ceiling.cu")
+CEIL_BIN = os.path.join(HERE, "gather_ceiling")
+
+
+def build_ceiling(force: bool = False) -> str:
+    """The gather/stream throughput microbenchmark used by bench.py for the roofline."""
+    if force or not os.path.exists(CEIL_BIN) or os.path.getmtime(CEIL_BIN) < os.path.getmtime(CEIL_SRC):
+        tmp = CEIL_BIN + f".tmp{os.getpid()}"
+        subprocess.check_call([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
+                               "-o", tmp, CEIL_SRC])
+        os.replace(tmp, CEIL_BIN)
+    return CEIL_BIN
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    build_ceiling(force)
     if force or stale():
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [NVCC, *FLAGS, "-o", tmp, *SRC]
