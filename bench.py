@@ -186,18 +186,79 @@ def cpu_baseline(lp, seconds=12.0):
                       f"on the full workload, {el:.1f} s"}
 
 
+FP64_FMA_PER_S = 5.66e11   # measured DFMA rate of this GPU (lane-ops/s), see the design doc
+
+
+def bench_batched(args):
+    """Batched workload: `count` independent planted LPs (lpgen.batch_planted, seed 0),
+    n ~ U(50, 5000), m ~ U(0.3, 0.8) n, density U(0.5%, 5%), N(0,1) values; solved to
+    1e-4 relative KKT by one persistent launch, against the same LPs solved one after
+    the other by the single-LP solver (a sample of them, scaled to the full count)."""
+    import torch
+    import lpgen
+    import paper_2312_14832_b300 as pk
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    lps = lpgen.batch_planted(args.count, seed=0)
+    gen_s = time.perf_counter() - t0
+    nnz = [int(lp["val"].shape[0]) for lp in lps]
+    t0 = time.perf_counter()
+    b = pk.BatchSolver.from_lps(lps, scaling=args.batch_scaling)
+    setup_s = time.perf_counter() - t0
+    b.solve(tol=1e-4, max_iter=64, want_points=False)      # warm-up launch
+    clk = Clocks(0)
+    res = b.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False)
+    clocks = clk.stop()
+    dev_s = res[0]["device_ms"] * 1e-3
+    iters = np.array([r["iters"] for r in res])
+    status = np.array([r["status"] for r in res])
+    fma = float(np.sum(2.0 * np.array(nnz) * iters))
+    b.close()
+    # sequential single-LP solves on a sample
+    stride = max(1, args.count // args.seq_sample)
+    sample = list(range(0, args.count, stride))
+    seq_s, seq_it = 0.0, 0
+    for i in sample:
+        with pk.Solver.from_lp(lps[i], scaling=args.batch_scaling) as s1:
+            r1 = s1.solve(tol=1e-4, max_iter=args.batch_max_iter, want_point=False)
+        seq_s += r1["solve_s"]
+        seq_it += r1["iters"]
+    seq_total = seq_s * args.count / len(sample)
+    out = {"metric": METRIC, "value": args.count / dev_s, "unit": "LPs/s to 1e-4", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f64", "data": "synthetic", "impl": "ours-batched",
+           "config": {"workload": f"{args.count} planted LPs, n~U(50,5000), m~U(0.3,0.8)n, density U(0.5%,5%), "
+                                  "N(0,1) values (lpgen.batch_planted seed 0)",
+                      "scaling": args.batch_scaling, "total_nnz": int(np.sum(nnz))},
+           "batch_device_s": dev_s, "optimal": int(np.sum(status == 0)), "iters_mean": float(iters.mean()),
+           "iters_max": int(iters.max()),
+           "roofline": {"bound": "alu", "unit": "FMA/s", "achieved": fma / dev_s, "peak": FP64_FMA_PER_S,
+                        "frac": fma / dev_s / FP64_FMA_PER_S, "note": "FP64 FMAs of both SpMVs per iteration"},
+           "sequential": {"sample": len(sample), "sample_s": seq_s, "sample_iters": seq_it,
+                          "estimated_total_s": seq_total, "lps_per_s": args.count / seq_total},
+           "speedup_vs_sequential": seq_total / dev_s, "setup_s": setup_s, "generate_s": gen_s,
+           "clocks": clocks}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batched"])
     ap.add_argument("--ttt-budget", type=float, default=0.0,
                     help="seconds for a cold time-to-1e-4 solve of the bench workload (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--count", type=int, default=4096, help="LPs in the batched workload")
+    ap.add_argument("--batch-max-iter", type=int, default=200000)
+    ap.add_argument("--batch-scaling", type=int, default=0)
+    ap.add_argument("--seq-sample", type=int, default=32)
     args = ap.parse_args()
+    if args.workload == "batched":
+        bench_batched(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -195,6 +195,37 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info);
  * on the handle's stream around every launch. */
 int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent LPs solved by one persistent kernel launch: each CTA of the launch
+ * takes LPs from a queue (largest first) and runs the whole restarted PDHG of one LP
+ * (power iteration for eta, iterations, checks, restarts, termination) with that
+ * LP's x and y in shared memory.  Each LP must satisfy (n + m, each rounded up to a
+ * multiple of 32) * 8 bytes + 5 KB <= the per-block shared-memory limit (about
+ * 28,000 rows plus columns on this GPU). */
+
+/* Sets up a batch of `count` LPs given back to back:
+ *   m[count], n[count], m1[count] : host arrays of each LP's sizes (m1 <= m, n >= 1).
+ *   row_ptr : the LPs' CSR row pointers one after the other, each starting at 0
+ *             (sum of (m_b + 1) entries);
+ *   col_idx, val : their entries one after the other (sum of nnz_b), columns local to the LP;
+ *   c, l, u : sum of n_b entries;  q : sum of m_b entries.
+ * Scaling (Ruiz + Pock-Chambolle per LP when params.scaling) runs at setup; eta and
+ * omega0 are computed per LP inside the solve.  The same handle type as pdlp_setup;
+ * free it with pdlp_free.  Single-LP calls on it (pdlp_solve, pdlp_get_iterate,
+ * pdlp_time_iterations) return PDLP_EINVAL; pdlp_spmv applies the block-diagonal K.
+ * Errors: PDLP_EINVAL (sizes, CSR, bounds; an LP too large for one CTA), PDLP_ENOMEM,
+ * PDLP_ECUDA. */
+int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const int64_t* n, const int64_t* m1,
+                     const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* c,
+                     const double* q, const double* l, const double* u, const pdlp_params* p);
+
+/* Solves every LP of the batch from a cold start (x = proj_X(0), y = 0) with the
+ * tolerance, iteration limit, check interval and restart factors of p (NULL = setup
+ * params; time_limit_s is not used).  res[count] receives one result per LP (solve_s
+ * and device_ms are those of the whole batch); x_out (sum n_b) and y_out (sum m_b),
+ * either may be NULL, receive the returned points back to back in the caller's order. */
+int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, pdlp_result* res, double* x_out, double* y_out);
+
 /* y = K x for a CSR matrix held in the caller's device memory, with no device memory
  * allocated by the call.  This entry point has no counterpart in the paper; it is for
  * callers that cannot call cudaMalloc at the point where they need the product, for

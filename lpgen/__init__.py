@@ -31,6 +31,8 @@ __all__ = [
     "csr_from_coo",
     "planted_from_structure",
     "planted_small",
+    "planted_random",
+    "batch_planted",
     "planted_zipf",
     "box_only",
     "tiny_lp",
@@ -125,15 +127,14 @@ def planted_from_structure(rng, m, n, m1, row_ptr, col_idx, val, bound_class,
                 obj_star=float(c @ x))
 
 
-def planted_small(seed=0, m1=200, m2=300, n=1000, nnz=5000):
-    """The small planted-optimum LP: m1 equality rows, m2 inequality rows, n columns,
-    exactly ``nnz`` distinct positions drawn uniformly without replacement, values
-    N(0,1).  Columns (random permutation): a quarter at l=0, a quarter at u=10, a
-    quarter interior of [0,10], a quarter free.  Half of the inequality rows tight.
-    """
-    rng = np.random.default_rng(seed)
+def planted_random(rng, m1, m2, n, nnz, box_u=10.0):
+    """A planted-optimum LP with ``nnz`` distinct positions drawn uniformly without
+    replacement and N(0,1) values.  Columns (random permutation): a quarter at l=0
+    (bounds [0, box_u], lambda* > 0), a quarter at u=box_u (lambda* < 0), a quarter
+    interior of [0, box_u], the rest free.  Half of the inequality rows are tight."""
     m = m1 + m2
-    pos = rng.choice(m * n, size=nnz, replace=False)
+    nnz = min(int(nnz), m * n)
+    pos = rng.choice(m * n, size=nnz, replace=False) if m > 0 else np.zeros(0, dtype=np.int64)
     rows, cols = pos // n, pos % n
     vals = rng.standard_normal(nnz)
     row_ptr, col_idx, val = csr_from_coo(m, n, rows, cols, vals)
@@ -142,15 +143,15 @@ def planted_small(seed=0, m1=200, m2=300, n=1000, nnz=5000):
     x = np.zeros(n)
     lam = np.zeros(n)
     l = np.zeros(n)
-    u = np.full(n, 10.0)
+    u = np.full(n, box_u)
     at_l, at_u, inner, free = perm[:q4], perm[q4:2 * q4], perm[2 * q4:3 * q4], perm[3 * q4:]
     lam[at_l] = np.abs(rng.standard_normal(at_l.shape[0]))
-    x[at_u] = 10.0
+    x[at_u] = box_u
     lam[at_u] = -np.abs(rng.standard_normal(at_u.shape[0]))
-    x[inner] = rng.uniform(1.0, 9.0, inner.shape[0])
+    x[inner] = rng.uniform(0.1 * box_u, 0.9 * box_u, inner.shape[0])
     l[free] = -np.inf
     u[free] = np.inf
-    x[free] = rng.uniform(-10.0, 10.0, free.shape[0])
+    x[free] = rng.uniform(-box_u, box_u, free.shape[0])
     y = np.zeros(m)
     y[:m1] = rng.standard_normal(m1)
     act = rng.permutation(m2)[: m2 // 2]
@@ -163,6 +164,29 @@ def planted_small(seed=0, m1=200, m2=300, n=1000, nnz=5000):
     return dict(m=m, n=n, m1=m1, row_ptr=row_ptr, col_idx=col_idx, val=val,
                 c=c, q=q, l=l, u=u, x_star=x, y_star=y, lam_star=lam,
                 obj_star=float(c @ x))
+
+
+def planted_small(seed=0, m1=200, m2=300, n=1000, nnz=5000):
+    """The small planted-optimum LP: m1 equality rows, m2 inequality rows, n columns,
+    exactly ``nnz`` distinct positions (see ``planted_random``)."""
+    return planted_random(np.random.default_rng(seed), m1, m2, n, nnz)
+
+
+def batch_planted(count, seed=0, n_lo=50, n_hi=5000, m_ratio=(0.3, 0.8), density=(0.005, 0.05),
+                  eq_frac=0.4):
+    """The batched workload: ``count`` independent planted LPs, LP i drawn with seed
+    ``seed + i``: n ~ U(n_lo, n_hi) (integer), m = round(U(m_ratio) n), m1 = round(eq_frac m),
+    density ~ U(density) of the m x n positions, values N(0,1), bounds as planted_random."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        n = int(rng.integers(n_lo, n_hi + 1))
+        m = int(round(rng.uniform(*m_ratio) * n))
+        m1 = int(round(eq_frac * m))
+        d = rng.uniform(*density)
+        nnz = max(1, int(round(d * m * n))) if m > 0 else 0
+        out.append(planted_random(rng, m1, m - m1, n, nnz))
+    return out
 
 
 def _zipf_lengths(rng, m, target_nnz, n, a=1.5, cap=10000):

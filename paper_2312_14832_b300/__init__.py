@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import ITER_LIMIT, NUMERICAL, OPTIMAL, TIME_LIMIT  # noqa: F401
 
-__all__ = ["Solver", "SolverError", "default_params", "OPTIMAL", "ITER_LIMIT", "TIME_LIMIT",
+__all__ = ["Solver", "BatchSolver", "SolverError", "default_params", "OPTIMAL", "ITER_LIMIT", "TIME_LIMIT",
            "NUMERICAL"]
 
 
@@ -160,6 +160,92 @@ class Solver:
         a, b = C.c_double(), C.c_double()
         self._check(self._lib.pdlp_time_iterations(self._h, int(iters), C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def close(self):
+        if self._h:
+            self._lib.pdlp_free(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Many independent LPs solved by one persistent kernel (pdlp_batch_setup/solve).
+
+        with BatchSolver.from_lps([lp0, lp1, ...], scaling=1) as b:
+            results = b.solve(tol=1e-4)     # one dict per LP, with x and y
+    """
+
+    def __init__(self, lps, **params):
+        self._lib = _lib.load()
+        self._h = C.c_void_p()
+        self.count = len(lps)
+        if self.count == 0:
+            raise ValueError("empty batch")
+        self.m = np.array([lp["m"] for lp in lps], dtype=np.int64)
+        self.n = np.array([lp["n"] for lp in lps], dtype=np.int64)
+        self.m1 = np.array([lp["m1"] for lp in lps], dtype=np.int64)
+        cat = lambda key, dt: np.ascontiguousarray(np.concatenate([np.asarray(lp[key], dtype=dt) for lp in lps]))
+        self._arrays = [cat("row_ptr", np.int64), cat("col_idx", np.int32), cat("val", np.float64),
+                        cat("c", np.float64), cat("q", np.float64), cat("l", np.float64), cat("u", np.float64)]
+        p = default_params(**params)
+        p.inputs_on_device = 0
+        self.params = p
+        ptr = lambda a: a.ctypes.data if a.size else None
+        rc = self._lib.pdlp_batch_setup(C.byref(self._h), self.count, self.m.ctypes.data, self.n.ctypes.data,
+                                        self.m1.ctypes.data, *[ptr(a) for a in self._arrays], C.byref(p))
+        if rc != 0:
+            raise SolverError(rc, self._lib.pdlp_last_error(None).decode())
+        self._arrays = None
+
+    @classmethod
+    def from_lps(cls, lps, **params):
+        return cls(lps, **params)
+
+    def solve(self, want_points=True, **overrides):
+        p = _lib.Params()
+        C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
+        for k, v in overrides.items():
+            if not hasattr(p, k):
+                raise KeyError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        res = (_lib.Result * self.count)()
+        x = np.empty(int(self.n.sum())) if want_points else None
+        y = np.empty(int(self.m.sum())) if want_points else None
+        rc = self._lib.pdlp_batch_solve(self._h, C.byref(p), res, x.ctypes.data if want_points else None,
+                                        y.ctypes.data if (want_points and y.size) else None)
+        if rc < 0:
+            raise SolverError(rc, self._lib.pdlp_last_error(self._h).decode())
+        out = []
+        xo = np.concatenate([[0], np.cumsum(self.n)])
+        yo = np.concatenate([[0], np.cumsum(self.m)])
+        for b in range(self.count):
+            d = {f: getattr(res[b], f) for f, _ in _lib.Result._fields_}
+            if want_points:
+                d["x"] = x[xo[b]:xo[b + 1]].copy()
+                d["y"] = y[yo[b]:yo[b + 1]].copy()
+            out.append(d)
+        return out
+
+    def spmv(self, v, transpose=False):
+        """Block-diagonal K v (or K' v) of the whole batch."""
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.empty(int(self.n.sum() if transpose else self.m.sum()))
+        if out.size:
+            rc = self._lib.pdlp_spmv(self._h, 1 if transpose else 0, a.ctypes.data, out.ctypes.data)
+            if rc < 0:
+                raise SolverError(rc, self._lib.pdlp_last_error(self._h).decode())
+        return out
 
     def close(self):
         if self._h:

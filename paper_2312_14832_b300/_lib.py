@@ -63,6 +63,9 @@ SIGNATURES = {
     "pdlp_get_info": (C.c_int, [_vp, C.POINTER(Info)]),
     "pdlp_time_iterations": (C.c_int, [_vp, _i64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pdlp_spmv_csr_noalloc": (C.c_int, [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pdlp_batch_setup": (C.c_int, [C.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   C.POINTER(Params)]),
+    "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp]),
 }
 
 _lib = None

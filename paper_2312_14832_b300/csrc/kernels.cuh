@@ -264,12 +264,13 @@ __global__ void k_copy(double* dst, const double* src, int64_t n) {
   PDLP_GRID_STRIDE(i, n) dst[i] = src[i];
 }
 
-// dst[p] = src[perm[p]] (divided by div[p] if given) for p < n, pad for n <= p < npad.
-__global__ void k_permute_in(double* dst, const double* src, const int32_t* perm, const double* div,
-                             int64_t n, int64_t npad, double pad) {
+// dst[p] = src[perm[p]] (divided by div[p] if given); pad where perm[p] < 0 (padding).
+__global__ void k_permute_in(double* dst, const double* src, const int32_t* perm, const double* div, int64_t npad,
+                             double pad) {
   PDLP_GRID_STRIDE(p, npad) {
-    if (p < n) {
-      double v = src[perm[p]];
+    const int32_t q = perm[p];
+    if (q >= 0) {
+      const double v = src[q];
       dst[p] = div ? v / div[p] : v;
     } else {
       dst[p] = pad;
@@ -482,26 +483,15 @@ __device__ __forceinline__ double kkt_w(double prs, double drs, double gap, doub
   return sqrt(w * w * prs + drs / (w * w) + gap * gap);
 }
 
-// Sum the partials (fixed order), then the restart / termination logic of Section 2
-// on one thread.  mode 1: initialisation (KKT_omega of the anchor only).
-// final_check = 1 forces termination at this check (iteration-limit semantics).
-__global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState* st, const DevParams* Pp,
-                         CheckRecord* logbuf, long long* restarts, int mode, int final_check) {
-  if (st->done) return;
-  __shared__ double tot[NQ];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int qd = wid; qd < NQ; qd += (int)(blockDim.x >> 5)) {
-    const bool rowq = qd < 8;
-    const int b0 = rowq ? 0 : nb_rows, nb = rowq ? nb_rows : nb_cols;
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += part[(size_t)(b0 + b) * NQ + qd];
-    s = warp_sum(s);
-    if (lane == 0) tot[qd] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  const DevParams P = *Pp;
-
+// The restart / termination logic of Section 2 on the reduced totals of one check,
+// run by one thread.  Termination (the three relative tests, or the iteration limit
+// when `last`) is tested first; otherwise the candidate (Section 2: the current
+// iterate if its KKT_omega is strictly smaller, else the average) is checked against
+// restart conditions 1-3; on a restart omega, tau, sigma and the KKT anchor are
+// updated and st->restart_flag / st->cand_avg tell the caller what to copy.
+// `restarts` (may be null) receives the iteration count of each restart.
+__device__ inline CheckRecord decide_core(const double* tot, DevState* st, const DevParams& P, bool last,
+                                          long long* restarts) {
   const double w = st->omega;
   const double pobj_c = tot[Q_CX_C], dobj_c = tot[Q_QY_C] + tot[Q_LT_C];
   const double gap_c = dobj_c - pobj_c;
@@ -510,11 +500,6 @@ __global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState*
   const double kc = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap_c, w);
   const double ka = kkt_w(tot[Q_PRS_A], tot[Q_DRS_A], gap_a, w);
   const double inf = __longlong_as_double(0x7FF0000000000000LL);
-  if (mode == 1) {
-    st->kkt_anchor = kc;
-    st->kkt_prev = inf;
-    return;
-  }
   const double rp_c = sqrt(tot[Q_PRU_C]) / (1.0 + P.qnorm), rd_c = sqrt(tot[Q_DRU_C]) / (1.0 + P.cnorm);
   const double rg_c = fabs(gap_c) / (1.0 + fabs(dobj_c) + fabs(pobj_c));
   const double rp_a = sqrt(tot[Q_PRU_A]) / (1.0 + P.qnorm), rd_a = sqrt(tot[Q_DRU_A]) / (1.0 + P.cnorm);
@@ -522,7 +507,6 @@ __global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState*
   const double ec = fmax(rp_c, fmax(rd_c, rg_c)), ea = fmax(rp_a, fmax(rd_a, rg_a));
   const bool pass_c = ec <= P.tol, pass_a = ea <= P.tol;
   const bool finite = isfinite(kc) && isfinite(ka) && isfinite(ec) && isfinite(ea);
-  const bool last = final_check || st->k >= P.max_iter || st->final_force;
   const bool better_c = ec < ea;
 
   CheckRecord rec;
@@ -554,7 +538,6 @@ __global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState*
     st->out_kkt = which ? ka : kc;
     st->done = 1;
   } else {
-    // restart candidate: the current iterate if strictly better, else the average
     const int cand_avg = !(kc < ka);
     const double kkt_c = cand_avg ? ka : kc;
     int why = 0;
@@ -575,14 +558,45 @@ __global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState*
       st->kkt_prev = inf;
       st->restart_flag = 1;
       st->cand_avg = cand_avg;
-      if (st->nrestart < P.restart_cap) restarts[st->nrestart] = st->k;
+      if (restarts != nullptr && st->nrestart < P.restart_cap) restarts[st->nrestart] = st->k;
       st->nrestart += 1;
     } else {
       st->kkt_prev = kkt_c;
     }
   }
-  if (st->ncheck < P.log_cap) logbuf[st->ncheck] = rec;
   st->ncheck += 1;
+  return rec;
+}
+
+// Sum the partials (fixed order), then decide_core on one thread.
+// mode 1: initialisation (KKT_omega of the anchor only).  final_check = 1 forces
+// termination at this check (iteration-limit semantics).
+__global__ void k_decide(const double* part, int nb_rows, int nb_cols, DevState* st, const DevParams* Pp,
+                         CheckRecord* logbuf, long long* restarts, int mode, int final_check) {
+  if (st->done) return;
+  __shared__ double tot[NQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int qd = wid; qd < NQ; qd += (int)(blockDim.x >> 5)) {
+    const bool rowq = qd < 8;
+    const int b0 = rowq ? 0 : nb_rows, nb = rowq ? nb_rows : nb_cols;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += part[(size_t)(b0 + b) * NQ + qd];
+    s = warp_sum(s);
+    if (lane == 0) tot[qd] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const DevParams P = *Pp;
+  if (mode == 1) {
+    const double gap_c = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
+    st->kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap_c, st->omega);
+    st->kkt_prev = __longlong_as_double(0x7FF0000000000000LL);
+    return;
+  }
+  const long long ncheck = st->ncheck;
+  const bool last = final_check || st->k >= P.max_iter || st->final_force;
+  const CheckRecord rec = decide_core(tot, st, P, last, restarts);
+  if (ncheck < P.log_cap) logbuf[ncheck] = rec;
 }
 
 struct RestartArgs {

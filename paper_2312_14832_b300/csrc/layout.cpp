@@ -24,7 +24,7 @@ void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi
 
 SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
                     const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
-                    const std::vector<int32_t>& esrc) {
+                    const std::vector<int32_t>& esrc, int32_t pad_col) {
   SellHost S;
   S.rows = rows;
   S.rows_pad = std::max<int64_t>(32, (rows + 31) / 32 * 32);
@@ -36,7 +36,7 @@ SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
     S.chunk_ptr[(size_t)ch + 1] = S.chunk_ptr[(size_t)ch] + (int32_t)L;
   }
   size_t total = (size_t)S.chunk_ptr.back() * 32;
-  S.col.assign(total, 0);
+  S.col.assign(total, pad_col);
   S.src.assign(total, -1);
   for (int64_t ch = 0; ch < S.nchunks; ++ch) {
     int64_t base = S.chunk_ptr[(size_t)ch];
@@ -56,6 +56,17 @@ SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
     }
   }
   return S;
+}
+
+void append_sell(SellHost& G, const SellHost& S) {
+  if (G.chunk_ptr.empty()) G.chunk_ptr.push_back(0);
+  const int32_t base = G.chunk_ptr.back();
+  for (int64_t ch = 0; ch < S.nchunks; ++ch) G.chunk_ptr.push_back(base + S.chunk_ptr[(size_t)ch + 1]);
+  G.col.insert(G.col.end(), S.col.begin(), S.col.end());
+  G.src.insert(G.src.end(), S.src.begin(), S.src.end());
+  G.rows += S.rows_pad;
+  G.rows_pad = G.rows;
+  G.nchunks += S.nchunks;
 }
 
 TaskPlan plan_tasks(const SellHost& S, int32_t Q, int32_t C) {

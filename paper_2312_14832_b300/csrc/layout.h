@@ -48,9 +48,14 @@ void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi
 
 // Builds the SELL-32 arrays of a matrix whose internal row p (0 <= p < rows) has the
 // entries estart[p] .. estart[p] + elen[p] - 1 of the entry arrays ecol / esrc.
+// Padding slots of empty rows point at column pad_col.
 SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
                     const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
-                    const std::vector<int32_t>& esrc);
+                    const std::vector<int32_t>& esrc, int32_t pad_col = 0);
+
+// Appends the chunks of S after those of G (block-diagonal concatenation; the column
+// indices of S must already be in G's numbering).
+void append_sell(SellHost& G, const SellHost& S);
 
 // Packs whole chunks into tasks of at most tile_slots slots and at most tile_chunks
 // (<= 32) chunks; chunks longer than tile_slots become split pieces.

@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 
+#include "batch_kernel.cuh"
 #include "kernels.cuh"
 #include "layout.h"
 #include "pdlp.h"
@@ -103,6 +104,19 @@ struct pdlp_ctx {
   cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
   int g_full_len = -1, g_rem_len = -1;
   std::vector<cudaEvent_t> timing_events;
+  // batch handles (pdlp_batch_setup): one block-diagonal layout, one LP per CTA
+  bool is_batch = false;
+  int64_t count = 0;
+  LpDesc* desc = nullptr;
+  int32_t* order = nullptr;
+  int32_t* next = nullptr;
+  DevState* bstate = nullptr;
+  double *bx = nullptr, *by = nullptr;
+  int batch_grid = 0;
+  size_t batch_smem = 0;
+  int xs_off = 0, ys_off = 0, red_off = 0;
+  std::vector<LpDesc> hdesc;
+  std::vector<DevState> hstate;
 };
 
 namespace pdlp {
@@ -397,15 +411,14 @@ static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
 
 // ------------------------------------------------------------------ setup
 
-static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr_in,
-                       const int32_t* col_in, const double* val_in, const double* c_in,
-                       const double* q_in, const double* l_in, const double* u_in) {
-  const pdlp_params& P = h->p;
-  if (m < 0 || n < 1 || m1 < 0 || m1 > m) invalid("sizes must satisfy m >= 0, n >= 1, 0 <= m1 <= m");
-  if (m >= (int64_t)1 << 31 || n >= (int64_t)1 << 31) invalid("m and n must be below 2^31");
-  if (P.check_every < 1) invalid("check_every must be >= 1");
-  if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
-  if (!row_ptr_in || !c_in || !l_in || !u_in || (m > 0 && !q_in)) invalid("null input array");
+// Validated host copy of an LP (one LP, or the concatenation of a batch).
+struct HostLP {
+  std::vector<int64_t> rp;   // row pointers (per LP restarting at 0 for a batch)
+  std::vector<int32_t> col;
+  std::vector<double> val, c, l, u, q;
+};
+
+static void init_handle_resources(pdlp_ctx* h) {
   CK(cudaGetDevice(&h->dev));
   CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming));
@@ -414,110 +427,219 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   CK(cudaEventCreate(&h->ev_t1));
   for (auto& e : h->ev_ring) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CK(cudaMallocHost(&h->st_host, sizeof(DevState) * kRing));
+}
 
-  // ---- host copies of the structure (and, for validation, of the values)
-  const bool dev_in = P.inputs_on_device != 0;
-  std::vector<int64_t> rp((size_t)m + 1);
-  if (dev_in) CK(cudaMemcpy(rp.data(), row_ptr_in, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost));
-  else std::memcpy(rp.data(), row_ptr_in, sizeof(int64_t) * (m + 1));
-  if (rp[0] != 0) invalid("row_ptr[0] must be 0");
-  for (int64_t i = 0; i < m; ++i)
-    if (rp[(size_t)i + 1] < rp[(size_t)i]) invalid("row_ptr must be nondecreasing");
-  const int64_t nnz = rp[(size_t)m];
-  if (nnz >= ((int64_t)1 << 31)) invalid("nnz must be below 2^31");
-  if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
-  std::vector<int32_t> col((size_t)nnz);
-  std::vector<double> val((size_t)nnz), c((size_t)n), l((size_t)n), u((size_t)n), q((size_t)m);
+static void check_params(const pdlp_params& P) {
+  if (P.check_every < 1) invalid("check_every must be >= 1");
+  if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
+}
+
+// Copies (from host or device) and validates one LP in CSR form; rows_total and the
+// sizes of the arrays are given by the caller (a batch validates each LP's rows and
+// columns against its own n through col_limit).
+static void fetch_and_validate(pdlp_ctx* h, int64_t rows, int64_t cols, const int64_t* row_ptr_in,
+                               const int32_t* col_in, const double* val_in, const double* c_in,
+                               const double* q_in, const double* l_in, const double* u_in, HostLP& H,
+                               int64_t rp_count) {
+  const bool dev_in = h->p.inputs_on_device != 0;
   auto fetch = [&](void* dst, const void* src, size_t bytes) {
     if (bytes == 0) return;
     if (dev_in) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
     else std::memcpy(dst, src, bytes);
   };
-  fetch(col.data(), col_in, sizeof(int32_t) * nnz);
-  fetch(val.data(), val_in, sizeof(double) * nnz);
-  fetch(c.data(), c_in, sizeof(double) * n);
-  fetch(l.data(), l_in, sizeof(double) * n);
-  fetch(u.data(), u_in, sizeof(double) * n);
-  fetch(q.data(), q_in, sizeof(double) * m);
-  for (int64_t k = 0; k < nnz; ++k) {
-    if (col[(size_t)k] < 0 || col[(size_t)k] >= n) invalid("column index out of range");
-    if (!std::isfinite(val[(size_t)k])) invalid("non-finite matrix value");
-  }
-  for (int64_t j = 0; j < n; ++j) {
-    double a = l[(size_t)j], b = u[(size_t)j];
-    if (!std::isfinite(c[(size_t)j])) invalid("non-finite c");
+  H.rp.resize((size_t)rp_count);
+  fetch(H.rp.data(), row_ptr_in, sizeof(int64_t) * rp_count);
+  (void)rows;
+  int64_t nnz = 0;
+  // the caller checks the row pointers of each LP and sets nnz through H.rp; here only sizes
+  for (int64_t i = 0; i < rp_count; ++i)
+    if (H.rp[(size_t)i] < 0) invalid("negative row pointer");
+  nnz = h->nnz;
+  if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
+  H.col.resize((size_t)nnz);
+  H.val.resize((size_t)nnz);
+  H.c.resize((size_t)cols);
+  H.l.resize((size_t)cols);
+  H.u.resize((size_t)cols);
+  H.q.resize((size_t)h->m);
+  fetch(H.col.data(), col_in, sizeof(int32_t) * nnz);
+  fetch(H.val.data(), val_in, sizeof(double) * nnz);
+  fetch(H.c.data(), c_in, sizeof(double) * cols);
+  fetch(H.l.data(), l_in, sizeof(double) * cols);
+  fetch(H.u.data(), u_in, sizeof(double) * cols);
+  fetch(H.q.data(), q_in, sizeof(double) * h->m);
+  for (int64_t k = 0; k < nnz; ++k)
+    if (!std::isfinite(H.val[(size_t)k])) invalid("non-finite matrix value");
+  for (int64_t j = 0; j < cols; ++j) {
+    const double a = H.l[(size_t)j], b = H.u[(size_t)j];
+    if (!std::isfinite(H.c[(size_t)j])) invalid("non-finite c");
     if (std::isnan(a) || std::isnan(b) || a == INFINITY || b == -INFINITY || a > b)
       invalid("bounds must satisfy l <= u, l < +inf, u > -inf");
   }
+  for (int64_t i = 0; i < h->m; ++i)
+    if (!std::isfinite(H.q[(size_t)i])) invalid("non-finite q");
+}
+
+// Checks row pointers [rp0, rp0 + m] of one LP (starting at 0) and its column indices.
+static int64_t check_csr(const HostLP& H, int64_t rp0, int64_t m, int64_t n, int64_t nnz0) {
+  if (H.rp[(size_t)rp0] != 0) invalid("row_ptr[0] must be 0");
   for (int64_t i = 0; i < m; ++i)
-    if (!std::isfinite(q[(size_t)i])) invalid("non-finite q");
+    if (H.rp[(size_t)(rp0 + i + 1)] < H.rp[(size_t)(rp0 + i)]) invalid("row_ptr must be nondecreasing");
+  const int64_t nnz = H.rp[(size_t)(rp0 + m)];
+  for (int64_t k = 0; k < nnz; ++k) {
+    const int32_t cc = H.col[(size_t)(nnz0 + k)];
+    if (cc < 0 || cc >= n) invalid("column index out of range");
+  }
+  return nnz;
+}
+
+// Internal numbering and SELL layouts.  perm_* have one entry per internal (padded)
+// position: the caller's index, or -1 in padding; pos_* map the caller's index to
+// the internal position.
+struct Layout {
+  SellHost SK, SKt;
+  std::vector<int32_t> perm_r, pos_r, perm_c, pos_c;
+  int64_t mpad = 0, npad = 0;
+};
+
+// Appends the layout of one LP (rows rp[rp0..rp0+m], entries from nnz0, columns
+// [col0, col0 + n) of the caller's concatenated vectors) to L at internal offsets
+// L.mpad / L.npad, and pads both to a multiple of 32 (at least 32).
+static void append_lp_layout(Layout& L, const HostLP& H, int64_t rp0, int64_t nnz0, int64_t out0, int64_t m,
+                             int64_t n, int64_t m1, int64_t row0, int64_t col0, std::vector<int64_t>& k_est,
+                             std::vector<int64_t>& k_eln, std::vector<int32_t>& k_ecol, std::vector<int32_t>& k_esrc,
+                             std::vector<int64_t>& t_est, std::vector<int64_t>& t_eln, std::vector<int32_t>& t_ecol,
+                             std::vector<int32_t>& t_esrc) {
+  const int64_t nnz = H.rp[(size_t)(rp0 + m)];
+  const int64_t mp = std::max<int64_t>(32, (m + 31) / 32 * 32), np = std::max<int64_t>(32, (n + 31) / 32 * 32);
+  const int64_t rbase = L.mpad, cbase = L.npad;
+  std::vector<int64_t> rlen((size_t)m), clen((size_t)n, 0);
+  for (int64_t i = 0; i < m; ++i) rlen[(size_t)i] = H.rp[(size_t)(rp0 + i + 1)] - H.rp[(size_t)(rp0 + i)];
+  for (int64_t k = 0; k < nnz; ++k) clen[(size_t)H.col[(size_t)(nnz0 + k)]]++;
+  std::vector<int32_t> pr((size_t)std::max<int64_t>(m, 1)), pc((size_t)n);
+  sort_by_length_desc(rlen, 0, m1, pr);
+  sort_by_length_desc(rlen, m1, m, pr);
+  sort_by_length_desc(clen, 0, n, pc);
+  std::vector<int32_t> lpos_r((size_t)std::max<int64_t>(m, 1)), lpos_c((size_t)n);
+  for (int64_t p = 0; p < m; ++p) lpos_r[(size_t)pr[(size_t)p]] = (int32_t)p;
+  for (int64_t p = 0; p < n; ++p) lpos_c[(size_t)pc[(size_t)p]] = (int32_t)p;
+  for (int64_t p = 0; p < mp; ++p) L.perm_r.push_back(p < m ? (int32_t)(row0 + pr[(size_t)p]) : -1);
+  for (int64_t p = 0; p < np; ++p) L.perm_c.push_back(p < n ? (int32_t)(col0 + pc[(size_t)p]) : -1);
+  for (int64_t i = 0; i < m; ++i) L.pos_r[(size_t)(row0 + i)] = (int32_t)(rbase + lpos_r[(size_t)i]);
+  for (int64_t j = 0; j < n; ++j) L.pos_c[(size_t)(col0 + j)] = (int32_t)(cbase + lpos_c[(size_t)j]);
+  // K rows: entries in CSR order, columns renumbered
+  for (int64_t p = 0; p < mp; ++p) {
+    if (p < m) {
+      const int64_t i = pr[(size_t)p];
+      k_est.push_back(out0 + H.rp[(size_t)(rp0 + i)]);
+      k_eln.push_back(rlen[(size_t)i]);
+    } else {
+      k_est.push_back(0);
+      k_eln.push_back(0);
+    }
+  }
+  for (int64_t k = 0; k < nnz; ++k) {
+    k_ecol[(size_t)(out0 + k)] = (int32_t)(cbase + lpos_c[(size_t)H.col[(size_t)(nnz0 + k)]]);
+    k_esrc[(size_t)(out0 + k)] = (int32_t)(nnz0 + k);
+  }
+  // K' rows (columns of K): entries in increasing row order
+  std::vector<int64_t> tp((size_t)n + 1, 0);
+  for (int64_t j = 0; j < n; ++j) tp[(size_t)j + 1] = tp[(size_t)j] + clen[(size_t)j];
+  std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t k = H.rp[(size_t)(rp0 + i)]; k < H.rp[(size_t)(rp0 + i + 1)]; ++k) {
+      const int64_t at = out0 + fill[(size_t)H.col[(size_t)(nnz0 + k)]]++;
+      t_ecol[(size_t)at] = (int32_t)(rbase + lpos_r[(size_t)i]);
+      t_esrc[(size_t)at] = (int32_t)(nnz0 + k);
+    }
+  for (int64_t p = 0; p < np; ++p) {
+    if (p < n) {
+      const int64_t j = pc[(size_t)p];
+      t_est.push_back(out0 + tp[(size_t)j]);
+      t_eln.push_back(clen[(size_t)j]);
+    } else {
+      t_est.push_back(0);
+      t_eln.push_back(0);
+    }
+  }
+  L.mpad += mp;
+  L.npad += np;
+}
+
+// Upload of the layouts and values, problem vectors in internal order, unscaled norms,
+// scaling and the scaled problem vectors: everything both handle kinds share.
+static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const double* c_in, const double* q_in,
+                                const double* l_in, const double* u_in);
+static void estimate_step_and_weight(pdlp_ctx* h);
+
+static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr_in,
+                       const int32_t* col_in, const double* val_in, const double* c_in,
+                       const double* q_in, const double* l_in, const double* u_in) {
+  const pdlp_params& P = h->p;
+  if (m < 0 || n < 1 || m1 < 0 || m1 > m) invalid("sizes must satisfy m >= 0, n >= 1, 0 <= m1 <= m");
+  if (m >= (int64_t)1 << 31 || n >= (int64_t)1 << 31) invalid("m and n must be below 2^31");
+  check_params(P);
+  if (!row_ptr_in || !c_in || !l_in || !u_in || (m > 0 && !q_in)) invalid("null input array");
+  init_handle_resources(h);
   h->m = m;
   h->n = n;
   h->m1 = m1;
-  h->nnz = nnz;
-
-  // ---- renumbering by length
-  std::vector<int64_t> rlen((size_t)m), clen((size_t)n, 0);
-  for (int64_t i = 0; i < m; ++i) rlen[(size_t)i] = rp[(size_t)i + 1] - rp[(size_t)i];
-  for (int64_t k = 0; k < nnz; ++k) clen[(size_t)col[(size_t)k]]++;
-  std::vector<int32_t> perm_r((size_t)m), pos_r((size_t)m), perm_c((size_t)n), pos_c((size_t)n);
-  sort_by_length_desc(rlen, 0, m1, perm_r);
-  sort_by_length_desc(rlen, m1, m, perm_r);
-  sort_by_length_desc(clen, 0, n, perm_c);
-  for (int64_t p = 0; p < m; ++p) pos_r[(size_t)perm_r[(size_t)p]] = (int32_t)p;
-  for (int64_t p = 0; p < n; ++p) pos_c[(size_t)perm_c[(size_t)p]] = (int32_t)p;
-
-  // ---- SELL layouts of K (rows) and K' (columns)
-  SellHost SK, SKt;
+  // nnz from the last row pointer
   {
-    std::vector<int32_t> ecol((size_t)nnz), esrc((size_t)nnz);
-    for (int64_t k = 0; k < nnz; ++k) {
-      ecol[(size_t)k] = pos_c[(size_t)col[(size_t)k]];
-      esrc[(size_t)k] = (int32_t)k;
-    }
-    std::vector<int64_t> est((size_t)m), eln((size_t)m);
-    for (int64_t p = 0; p < m; ++p) {
-      est[(size_t)p] = rp[(size_t)perm_r[(size_t)p]];
-      eln[(size_t)p] = rlen[(size_t)perm_r[(size_t)p]];
-    }
-    SK = build_sell(m, est, eln, ecol, esrc);
+    int64_t last = 0;
+    if (P.inputs_on_device) CK(cudaMemcpy(&last, row_ptr_in + m, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    else last = row_ptr_in[m];
+    if (last < 0 || last >= ((int64_t)1 << 31)) invalid("nnz must be in [0, 2^31)");
+    h->nnz = last;
   }
+  HostLP H;
+  fetch_and_validate(h, m, n, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, m + 1);
+  check_csr(H, 0, m, n, 0);
+
+  Layout Lo;
+  Lo.pos_r.assign((size_t)m, 0);
+  Lo.pos_c.assign((size_t)n, 0);
   {
-    std::vector<int64_t> tp((size_t)n + 1, 0);
-    for (int64_t j = 0; j < n; ++j) tp[(size_t)j + 1] = tp[(size_t)j] + clen[(size_t)j];
-    std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
-    std::vector<int32_t> tcol((size_t)nnz), tsrc((size_t)nnz);
-    for (int64_t i = 0; i < m; ++i)
-      for (int64_t k = rp[(size_t)i]; k < rp[(size_t)i + 1]; ++k) {
-        int64_t at = fill[(size_t)col[(size_t)k]]++;
-        tcol[(size_t)at] = pos_r[(size_t)i];
-        tsrc[(size_t)at] = (int32_t)k;
-      }
-    std::vector<int64_t> est((size_t)n), eln((size_t)n);
-    for (int64_t p = 0; p < n; ++p) {
-      est[(size_t)p] = tp[(size_t)perm_c[(size_t)p]];
-      eln[(size_t)p] = clen[(size_t)perm_c[(size_t)p]];
-    }
-    SKt = build_sell(n, est, eln, tcol, tsrc);
+    std::vector<int64_t> k_est, k_eln, t_est, t_eln;
+    std::vector<int32_t> k_ecol((size_t)h->nnz), k_esrc((size_t)h->nnz), t_ecol((size_t)h->nnz),
+        t_esrc((size_t)h->nnz);
+    append_lp_layout(Lo, H, 0, 0, 0, m, n, m1, 0, 0, k_est, k_eln, k_ecol, k_esrc, t_est, t_eln, t_ecol, t_esrc);
+    Lo.SK = build_sell(Lo.mpad, k_est, k_eln, k_ecol, k_esrc);
+    Lo.SKt = build_sell(Lo.npad, t_est, t_eln, t_ecol, t_esrc);
   }
-  h->mpad = SK.rows_pad;
-  h->npad = SKt.rows_pad;
+  device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
+
+  // ---- SpMV schedule per layout: explicit parameters, or timed candidates for large K
+  const bool auto_tile = P.tile_slots == 0 && P.tile_chunks == 0 && P.spmv_batch == 0;
+  if (auto_tile && h->nnz >= kAutotuneMinNnz) {
+    autotune(h, h->Kt, Lo.SKt, true);
+    autotune(h, h->K, Lo.SK, false);
+  }
+  estimate_step_and_weight(h);
+}
+
+static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const double* c_in, const double* q_in,
+                                const double* l_in, const double* u_in) {
+  const pdlp_params& P = h->p;
+  const int64_t m = h->m, n = h->n;
+  h->mpad = Lo.mpad;
+  h->npad = Lo.npad;
   const int32_t tile = P.tile_slots > 0 ? P.tile_slots : 64;
   const int32_t tchunks = P.tile_chunks > 0 ? std::min(P.tile_chunks, 32) : 4;
-  TaskPlan PK = plan_tasks(SK, tile, tchunks), PKt = plan_tasks(SKt, tile, tchunks);
+  TaskPlan PK = plan_tasks(Lo.SK, tile, tchunks), PKt = plan_tasks(Lo.SKt, tile, tchunks);
   h->K.tile = h->Kt.tile = tile;
   h->K.tchunks = h->Kt.tchunks = tchunks;
   h->K.batch = h->Kt.batch = (P.spmv_batch == 4) ? 4 : 8;
 
-  double* d_val = upload(h, val);
-  build_device_sell(h, h->K, SK, PK, d_val);
-  build_device_sell(h, h->Kt, SKt, PKt, d_val);
+  double* d_val = upload(h, H.val);
+  build_device_sell(h, h->K, Lo.SK, PK, d_val);
+  build_device_sell(h, h->Kt, Lo.SKt, PKt, d_val);
   dfree(h, d_val);
 
-  h->perm_r = upload(h, perm_r);
-  h->pos_r = upload(h, pos_r);
-  h->perm_c = upload(h, perm_c);
-  h->pos_c = upload(h, pos_c);
+  h->perm_r = upload(h, Lo.perm_r);
+  h->pos_r = upload(h, Lo.pos_r);
+  h->perm_c = upload(h, Lo.perm_c);
+  h->pos_c = upload(h, Lo.pos_c);
 
   const int64_t mp = h->mpad, np = h->npad;
   h->c = dalloc<double>(h, np);
@@ -548,16 +670,16 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   // ---- problem vectors in internal order; unscaled norms for the termination tests
   copy_in(h, h->stage_n, c_in, n);
   h->cnorm = norm2_host(h, h->stage_n, n);
-  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->c, h->stage_n, h->perm_c, nullptr, n, np, 0.0);
+  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->c, h->stage_n, h->perm_c, nullptr, np, 0.0);
   copy_in(h, h->stage_n, l_in, n);
-  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->l, h->stage_n, h->perm_c, nullptr, n, np, 0.0);
+  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->l, h->stage_n, h->perm_c, nullptr, np, 0.0);
   copy_in(h, h->stage_n, u_in, n);
-  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->u, h->stage_n, h->perm_c, nullptr, n, np, 0.0);
+  k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->u, h->stage_n, h->perm_c, nullptr, np, 0.0);
   if (m > 0) {
     copy_in(h, h->stage_m, q_in, m);
     h->qnorm = norm2_host(h, h->stage_m, m);
   }
-  k_permute_in<<<grid_for(mp), 256, 0, h->s>>>(h->q, h->stage_m, h->perm_r, nullptr, m, mp, 0.0);
+  k_permute_in<<<grid_for(mp), 256, 0, h->s>>>(h->q, h->stage_m, h->perm_r, nullptr, mp, 0.0);
   k_fill<<<grid_for(mp), 256, 0, h->s>>>(h->Dr, 1.0, mp);
   k_fill<<<grid_for(np), 256, 0, h->s>>>(h->Dc, 1.0, np);
   CKL("setup vectors");
@@ -586,14 +708,13 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   k_scale_rows<<<grid_for(mp), 256, 0, h->s>>>(h->q, h->invDr, h->Dr, mp);
   CKL("scale vectors");
 
-  // ---- SpMV schedule per layout: explicit parameters, or timed candidates for large K
-  const bool auto_tile = P.tile_slots == 0 && P.tile_chunks == 0 && P.spmv_batch == 0;
-  if (auto_tile && nnz >= kAutotuneMinNnz) {
-    autotune(h, h->Kt, SKt, true);
-    autotune(h, h->K, SK, false);
-  }
+  CK(cudaStreamSynchronize(h->s));
+}
 
-  // ---- ||K||_2 by power iteration on K'K (v0 = 1/sqrt(n)), eta, omega0
+// ||K||_2 by power iteration on K'K (v0 = 1/sqrt(n)) -> eta; omega0 = ||c||/||q||.
+static void estimate_step_and_weight(pdlp_ctx* h) {
+  const pdlp_params& P = h->p;
+  const int64_t m = h->m, n = h->n, mp = h->mpad, np = h->npad;
   if (P.eta > 0.0) {
     h->eta = P.eta;
   } else {
@@ -663,13 +784,13 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   const double* ys = nullptr;
   if (x0) {
     copy_in(h, h->stage_n, x0, n);
-    k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, n, np, 0.0);
+    k_permute_in<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, np, 0.0);
     xs = h->tn;
     launches++;
   }
   if (y0 && m > 0) {
     copy_in(h, h->stage_m, y0, m);
-    k_permute_in<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, m, mp, 0.0);
+    k_permute_in<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, mp, 0.0);
     ys = h->tm;
     launches++;
   }
@@ -809,6 +930,211 @@ static int guarded(pdlp_ctx* h, F&& f) {
 
 }  // namespace pdlp
 
+// ------------------------------------------------------------------ batches
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchRed = NQ * (1 + kBatchThreads / 32);   // block_sum scratch (doubles)
+
+static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, const int64_t* n_in,
+                             const int64_t* m1_in, const int64_t* row_ptr_in, const int32_t* col_in,
+                             const double* val_in, const double* c_in, const double* q_in, const double* l_in,
+                             const double* u_in) {
+  const pdlp_params& P = h->p;
+  check_params(P);
+  if (count < 1 || count >= ((int64_t)1 << 31)) invalid("batch count must be in [1, 2^31)");
+  if (!m_in || !n_in || !m1_in || !row_ptr_in || !c_in || !l_in || !u_in) invalid("null input array");
+  std::vector<int64_t> lm((size_t)count), ln((size_t)count), lm1((size_t)count);
+  std::memcpy(lm.data(), m_in, sizeof(int64_t) * count);   // sizes are host arrays
+  std::memcpy(ln.data(), n_in, sizeof(int64_t) * count);
+  std::memcpy(lm1.data(), m1_in, sizeof(int64_t) * count);
+  int64_t M = 0, N = 0, R = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    if (lm[(size_t)b] < 0 || ln[(size_t)b] < 1 || lm1[(size_t)b] < 0 || lm1[(size_t)b] > lm[(size_t)b])
+      invalid("each LP needs m >= 0, n >= 1, 0 <= m1 <= m");
+    M += lm[(size_t)b];
+    N += ln[(size_t)b];
+    R += lm[(size_t)b] + 1;
+  }
+  if (M >= ((int64_t)1 << 31) || N >= ((int64_t)1 << 31)) invalid("total rows and columns must be below 2^31");
+  if (M > 0 && !q_in) invalid("null q");
+  init_handle_resources(h);
+  h->is_batch = true;
+  h->count = count;
+  h->m = M;
+  h->n = N;
+  h->m1 = 0;
+  // total nonzeros from each LP's last row pointer
+  std::vector<int64_t> rp((size_t)R);
+  if (P.inputs_on_device) CK(cudaMemcpy(rp.data(), row_ptr_in, sizeof(int64_t) * R, cudaMemcpyDeviceToHost));
+  else std::memcpy(rp.data(), row_ptr_in, sizeof(int64_t) * R);
+  int64_t nnz = 0;
+  for (int64_t b = 0, r = 0; b < count; ++b) {
+    r += lm[(size_t)b];
+    if (rp[(size_t)r] < 0) invalid("negative row pointer");
+    nnz += rp[(size_t)r];
+    r += 1;
+  }
+  if (nnz >= ((int64_t)1 << 31)) invalid("total nnz must be below 2^31");
+  h->nnz = nnz;
+  HostLP H;
+  fetch_and_validate(h, M, N, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, R);
+
+  Layout Lo;
+  Lo.pos_r.assign((size_t)M, 0);
+  Lo.pos_c.assign((size_t)N, 0);
+  h->hdesc.resize((size_t)count);
+  int64_t rp0 = 0, nnz0 = 0, row0 = 0, col0 = 0, npad_max = 0, mpad_max = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    const int64_t m = lm[(size_t)b], n = ln[(size_t)b];
+    const int64_t lnnz = check_csr(H, rp0, m, n, nnz0);
+    std::vector<int64_t> k_est, k_eln, t_est, t_eln;
+    std::vector<int32_t> k_ecol((size_t)lnnz), k_esrc((size_t)lnnz), t_ecol((size_t)lnnz), t_esrc((size_t)lnnz);
+    const int64_t rbase = Lo.mpad, cbase = Lo.npad;
+    append_lp_layout(Lo, H, rp0, nnz0, 0, m, n, lm1[(size_t)b], row0, col0, k_est, k_eln, k_ecol, k_esrc, t_est,
+                     t_eln, t_ecol, t_esrc);
+    const int64_t mp = Lo.mpad - rbase, np = Lo.npad - cbase;
+    SellHost sk = build_sell(mp, k_est, k_eln, k_ecol, k_esrc, (int32_t)cbase);
+    SellHost stt = build_sell(np, t_est, t_eln, t_ecol, t_esrc, (int32_t)rbase);
+    LpDesc& D = h->hdesc[(size_t)b];
+    D.m = (int32_t)m;
+    D.n = (int32_t)n;
+    D.m1 = (int32_t)lm1[(size_t)b];
+    D.pad0 = 0;
+    D.kc0 = (int32_t)Lo.SK.nchunks;
+    append_sell(Lo.SK, sk);
+    D.kc1 = (int32_t)Lo.SK.nchunks;
+    D.tc0 = (int32_t)Lo.SKt.nchunks;
+    append_sell(Lo.SKt, stt);
+    D.tc1 = (int32_t)Lo.SKt.nchunks;
+    D.r0 = rbase;
+    D.c0 = cbase;
+    D.mpad = (int32_t)mp;
+    D.npad = (int32_t)np;
+    npad_max = std::max(npad_max, np);
+    mpad_max = std::max(mpad_max, mp);
+    rp0 += m + 1;
+    nnz0 += lnnz;
+    row0 += m;
+    col0 += n;
+  }
+  device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
+
+  // shared memory per CTA: x and y of the largest LP plus the reduction scratch
+  h->xs_off = 0;
+  h->ys_off = (int)npad_max;
+  h->red_off = (int)(npad_max + mpad_max);
+  h->batch_smem = (size_t)(npad_max + mpad_max + kBatchRed) * sizeof(double);
+  int dev_smem = 0;
+  CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+  const size_t static_smem = sizeof(DevState) + (NQ + 8) * sizeof(double) + 64;
+  if (h->batch_smem + static_smem > (size_t)dev_smem)
+    invalid("an LP of the batch is too large for one CTA's shared memory (needs (n + m) padded doubles)");
+  CK(cudaFuncSetAttribute(k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->batch_smem));
+  int per_sm = 0, sms = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve, kBatchThreads, h->batch_smem));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+  if (per_sm < 1) invalid("batched kernel does not fit on an SM");
+  h->batch_grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
+
+  // queue order: largest LP (most nonzeros) first
+  std::vector<int32_t> ord((size_t)count);
+  for (int64_t b = 0; b < count; ++b) ord[(size_t)b] = (int32_t)b;
+  std::vector<int64_t> work((size_t)count);
+  for (int64_t b = 0; b < count; ++b) {
+    const LpDesc& D = h->hdesc[(size_t)b];
+    std::vector<int32_t> dummy;
+    work[(size_t)b] = (int64_t)(Lo.SK.chunk_ptr[(size_t)D.kc1] - Lo.SK.chunk_ptr[(size_t)D.kc0]) + D.mpad + D.npad;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b2) { return work[(size_t)a] > work[(size_t)b2]; });
+  h->desc = upload(h, h->hdesc);
+  h->order = upload(h, ord);
+  h->next = dalloc<int32_t>(h, 1);
+  h->bstate = dalloc<DevState>(h, (size_t)count);
+  h->bx = dalloc<double>(h, h->npad);
+  h->by = dalloc<double>(h, h->mpad);
+  h->hstate.resize((size_t)count);
+  CK(cudaStreamSynchronize(h->s));
+}
+
+static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, pdlp_result* res, double* x_out, double* y_out) {
+  if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
+  auto t_start = std::chrono::steady_clock::now();
+  BatchArgs A;
+  A.desc = h->desc;
+  A.order = h->order;
+  A.count = (int32_t)h->count;
+  A.next = h->next;
+  A.k_cptr = h->K.chunk_ptr;
+  A.k_col = h->K.col;
+  A.k_val = h->K.val;
+  A.t_cptr = h->Kt.chunk_ptr;
+  A.t_col = h->Kt.col;
+  A.t_val = h->Kt.val;
+  A.c = h->c; A.l = h->l; A.u = h->u; A.q = h->q; A.invDr = h->invDr; A.invDc = h->invDc;
+  A.sx = h->sx; A.sy = h->sy; A.xa = h->xa; A.ya = h->ya; A.kxp = h->kxp; A.g = h->g_c; A.kx_a = h->kx_a;
+  A.g_a = h->g_a;
+  A.xout = h->bx;
+  A.yout = h->by;
+  A.st = h->bstate;
+  A.P = DevParams{};
+  A.P.tol = sp.tol;
+  A.P.beta_suff = sp.beta_suff;
+  A.P.beta_nec = sp.beta_nec;
+  A.P.beta_art = sp.beta_art;
+  A.P.theta = sp.omega_theta;
+  A.P.max_iter = sp.max_iter;
+  A.check_every = sp.check_every;
+  A.max_iter = sp.max_iter;
+  A.power_iters = h->p.power_iters;
+  A.step_scale = h->p.step_scale;
+  A.eta_fixed = h->p.eta;
+  A.omega_fixed = 0.0;
+  A.xs_off = h->xs_off;
+  A.ys_off = h->ys_off;
+  A.red_off = h->red_off;
+  CK(cudaEventRecord(h->ev_t0, h->s));
+  k_batch_solve<<<h->batch_grid, kBatchThreads, h->batch_smem, h->s>>>(A);
+  CKL("k_batch_solve");
+  CK(cudaEventRecord(h->ev_t1, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  float dev_ms = 0.f;
+  CK(cudaEventElapsedTime(&dev_ms, h->ev_t0, h->ev_t1));
+  CK(cudaMemcpy(h->hstate.data(), h->bstate, sizeof(DevState) * h->count, cudaMemcpyDeviceToHost));
+  if (x_out) {
+    k_unpermute_scale<<<grid_for(h->n), 256, 0, h->s>>>(h->stage_n, h->bx, h->Dc, h->pos_c, h->n);
+    copy_out(h, x_out, h->stage_n, h->n);
+  }
+  if (y_out && h->m > 0) {
+    k_unpermute_scale<<<grid_for(h->m), 256, 0, h->s>>>(h->stage_m, h->by, h->Dr, h->pos_r, h->m);
+    copy_out(h, y_out, h->stage_m, h->m);
+  }
+  CK(cudaStreamSynchronize(h->s));
+  const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (res) {
+    for (int64_t b = 0; b < h->count; ++b) {
+      const DevState& S = h->hstate[(size_t)b];
+      pdlp_result& r = res[b];
+      r.status = S.status;
+      r.which = S.which;
+      r.iters = S.k;
+      r.restarts = S.nrestart;
+      r.primal_obj = S.out_pobj;
+      r.dual_obj = S.out_dobj;
+      r.rel_primal = S.out_rel_p;
+      r.rel_dual = S.out_rel_d;
+      r.rel_gap = S.out_rel_g;
+      r.kkt_omega = S.out_kkt;
+      r.omega = S.omega;
+      r.eta = S.eta;
+      r.solve_s = wall;
+      r.device_ms = dev_ms;
+      r.launches = 1;
+    }
+  }
+  h->solved = true;
+  return PDLP_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -876,6 +1202,7 @@ int pdlp_setup(pdlp_handle* out, int64_t m, int64_t n, int64_t m1, const int64_t
 int pdlp_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const double* y0, double omega0,
                pdlp_result* res, double* x_out, double* y_out) {
   return guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle: use pdlp_batch_solve");
     pdlp_params sp = p ? *p : h->p;
     return solve_impl(h, sp, x0, y0, omega0, res, x_out, y_out);
   });
@@ -894,6 +1221,7 @@ const char* pdlp_last_error(pdlp_handle h) {
 
 int pdlp_get_iterate(pdlp_handle h, int32_t which, double* x, double* y) {
   return guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle: use pdlp_batch_solve outputs");
     if (which < 0 || which > 2) invalid("which must be 0, 1 or 2");
     if (!h->solved) invalid("no solve has run on this handle");
     const double* xi = h->x;
@@ -936,7 +1264,7 @@ int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out) {
     if (!in || !out) invalid("null vector");
     if (!transpose) {
       copy_in(h, h->stage_n, in, h->n);
-      k_permute_in<<<grid_for(h->npad), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, h->n, h->npad, 0.0);
+      k_permute_in<<<grid_for(h->npad), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, h->npad, 0.0);
       launch_rows<OpSpmv>(h, h->K, h->tn, EpiStore{h->tm, 0, 1.0}, nullptr);
       if (h->m > 0) {
         k_unpermute_scale<<<grid_for(h->m), 256, 0, h->s>>>(h->stage_m, h->tm, h->invDr, h->pos_r, h->m);
@@ -944,7 +1272,7 @@ int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out) {
       }
     } else {
       if (h->m > 0) copy_in(h, h->stage_m, in, h->m);
-      k_permute_in<<<grid_for(h->mpad), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, h->m, h->mpad, 0.0);
+      k_permute_in<<<grid_for(h->mpad), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, h->mpad, 0.0);
       launch_rows<OpSpmv>(h, h->Kt, h->tm, EpiStore{h->tn, 0, 1.0}, nullptr);
       k_unpermute_scale<<<grid_for(h->n), 256, 0, h->s>>>(h->stage_n, h->tn, h->invDc, h->pos_c, h->n);
       copy_out(h, out, h->stage_n, h->n);
@@ -986,6 +1314,7 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
 
 int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual) {
   return guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle");
     if (iters < 1) invalid("iters must be >= 1");
     if (!h->solved) invalid("no solve has run on this handle");
     k_copy_state<<<1, 1, 0, h->s>>>(h->st_tmp, h->st);
@@ -1019,6 +1348,50 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
     if (ms_primal) *ms_primal = tp / (double)iters;
     if (ms_dual) *ms_dual = td / (double)iters;
     return PDLP_OK;
+  });
+}
+
+int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const int64_t* n, const int64_t* m1,
+                     const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* c,
+                     const double* q, const double* l, const double* u, const pdlp_params* p) {
+  g_setup_error.clear();
+  if (!out) {
+    g_setup_error = "null output handle";
+    return PDLP_EINVAL;
+  }
+  *out = nullptr;
+  pdlp_ctx* h = nullptr;
+  try {
+    h = new pdlp_ctx();
+    if (p) h->p = *p;
+    else pdlp_default_params(&h->p);
+    batch_setup_impl(h, count, m, n, m1, row_ptr, col_idx, val, c, q, l, u);
+    if (h->p.stream) {
+      CK(cudaEventRecord(h->ev_done, h->s));
+      CK(cudaStreamWaitEvent((cudaStream_t)h->p.stream, h->ev_done, 0));
+    }
+  } catch (const Failure& e) {
+    g_setup_error = e.msg;
+    destroy(h);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_setup_error = "host allocation failed";
+    destroy(h);
+    return PDLP_ENOMEM;
+  } catch (...) {
+    g_setup_error = "unexpected internal error";
+    destroy(h);
+    return PDLP_EINTERNAL;
+  }
+  *out = h;
+  return PDLP_OK;
+}
+
+int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, pdlp_result* res, double* x_out, double* y_out) {
+  return guarded(h, [&]() {
+    if (!h->is_batch) invalid("not a batch handle (use pdlp_solve)");
+    pdlp_params sp = p ? *p : h->p;
+    return batch_solve_impl(h, sp, res, x_out, y_out);
   });
 }
 

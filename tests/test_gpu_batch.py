@@ -1,0 +1,116 @@
+"""Parity of the batched persistent solver (pdlp_batch_setup / pdlp_batch_solve) with
+the CPU oracle, LP by LP.  Same tolerances as test_gpu_parity: relative 1e-10 on the
+returned point after a fixed number of iterations (with the same restart count and
+returned-point choice), relative 1e-6 on objectives at a tolerance (same iteration
+count), 1e-13 * sum |K_ij x_j| on SpMV rows."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_2312_14832_b300 import build
+    build.build()
+    import paper_2312_14832_b300 as pk
+    return pk
+
+
+def mixed_batch():
+    lps = lpgen.batch_planted(6, seed=100, n_lo=50, n_hi=1200)
+    lps.append(lpgen.planted_small(3))
+    lps.append(lpgen.box_only(4, n=70, free_frac=0.2))          # no rows at all
+    lps.append(lpgen.planted_random(np.random.default_rng(9), 3, 4, 40, 60))   # tiny
+    lps.append(lpgen.tiny_lp(2, n=5, m1=1, m2=3))
+    return lps
+
+
+def close_rel(a, b, rel):
+    a, b = np.asarray(a), np.asarray(b)
+    if b.size == 0:
+        return
+    scale = max(np.abs(b).max(), 1e-300)
+    assert np.abs(a - b).max() <= rel * scale
+    assert np.linalg.norm(a - b) <= rel * max(np.linalg.norm(b), 1e-300)
+
+
+def fixed_iteration_batch():
+    # the box-only LP is left out here: its residuals reach exactly zero, so a
+    # tolerance of 0 is a tie that FP rounding may decide either way; it is covered
+    # at nonzero tolerances below
+    return [lp for lp in mixed_batch() if lp["m"] > 0]
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_batch_iterates_after_1000(pk, scaling):
+    lps = fixed_iteration_batch()
+    with pk.BatchSolver.from_lps(lps, scaling=scaling) as b:
+        res = b.solve(tol=0.0, max_iter=1000)
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=0.0, max_iter=1000, scaling=scaling)
+        assert r["iters"] == ref["iters"] == 1000
+        assert r["status"] == pk.ITER_LIMIT
+        assert r["restarts"] == ref["restarts"]
+        assert r["which"] == ref["which"]
+        assert abs(r["eta"] - ref["eta"]) <= 1e-12 * ref["eta"]
+        # omega is a function of ||x_c - x_anchor|| between nearly equal iterates, whose
+        # relative rounding grows as the iterates settle; the iterates themselves are
+        # held to 1e-10 below
+        assert abs(r["omega"] - ref["omega"]) <= 1e-6 * ref["omega"]
+        close_rel(r["x"], ref["x"], 1e-10)
+        close_rel(r["y"], ref["y"], 1e-10)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8])
+def test_batch_objectives_at_tolerance(pk, tol):
+    lps = mixed_batch()
+    with pk.BatchSolver.from_lps(lps) as b:
+        res = b.solve(tol=tol, max_iter=500_000)
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=tol, max_iter=500_000)
+        assert r["status"] == ref["status"] == pk.OPTIMAL
+        assert r["iters"] == ref["iters"]
+        assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
+        assert max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) <= tol
+
+
+def test_batch_ragged_iteration_limit_and_zero(pk):
+    lps = fixed_iteration_batch()[:4]
+    with pk.BatchSolver.from_lps(lps) as b:
+        for iters in (0, 1, 100):
+            res = b.solve(tol=0.0, max_iter=iters)
+            for lp, r in zip(lps, res):
+                ref = oracle.solve(lp, tol=0.0, max_iter=iters)
+                assert r["iters"] == iters
+                close_rel(r["x"], ref["x"], 1e-10)
+                close_rel(r["y"], ref["y"], 1e-10)
+
+
+def test_batch_block_diagonal_spmv(pk):
+    lps = mixed_batch()
+    x = [np.random.default_rng(i).standard_normal(lp["n"]) for i, lp in enumerate(lps)]
+    with pk.BatchSolver.from_lps(lps) as b:
+        got = b.spmv(np.concatenate(x))
+    off = 0
+    for lp, xi in zip(lps, x):
+        K = sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(lp["m"], lp["n"]))
+        want = oracle.spmv(lp, xi)
+        bound = 1e-13 * (abs(K) @ np.abs(xi)) + 1e-300
+        assert np.all(np.abs(got[off:off + lp["m"]] - want) <= bound)
+        off += lp["m"]
+
+
+def test_batch_matches_single_solver(pk):
+    lps = lpgen.batch_planted(3, seed=7, n_lo=200, n_hi=600)
+    with pk.BatchSolver.from_lps(lps) as b:
+        res = b.solve(tol=1e-6)
+    for lp, r in zip(lps, res):
+        with pk.Solver.from_lp(lp) as s:
+            r1 = s.solve(tol=1e-6)
+        assert r1["iters"] == r["iters"]
+        close_rel(r["x"], r1["x"], 1e-10)
