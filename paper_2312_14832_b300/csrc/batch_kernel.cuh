@@ -50,7 +50,8 @@ enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
 
 // Rows in chunks [c0, c1) of a SELL matrix; warp w of the CTA takes chunks c0+w,
 // c0+w+nw, ...  Each lane sums its row, gathering src[col - base], then calls
-// epi(local_row, sum).  Loads of 4 slots are issued together.
+// epi(local_row, sum).  Loads of kBB slots are issued together.
+constexpr int kBB = 4;
 template <int SRC, class F>
 __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
                                            const double* __restrict__ val, int c0, int c1, int64_t base,
@@ -62,18 +63,18 @@ __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, con
   for (int ch = c0 + wid; ch < c1; ch += nw) {
     const int s0 = cptr[ch], s1 = cptr[ch + 1];
     double acc = 0.0;
-    for (int s = s0; s < s1; s += 4) {
-      const int nb = min(4, s1 - s);
-      double v[4], xv[4];
-      int ci[4];
+    for (int s = s0; s < s1; s += kBB) {
+      const int nb = min(kBB, s1 - s);
+      double v[kBB], xv[kBB];
+      int ci[kBB];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < kBB; ++j)
         if (j < nb) {
           v[j] = __ldcs(val + (size_t)(s + j) * 32 + lane);
           ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
         }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kBB; ++j) {
         xv[j] = 0.0;
         if (j < nb) {
           if (SRC == kSrcSmemX) xv[j] = xs[ci[j]];
@@ -82,7 +83,7 @@ __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, con
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < kBB; ++j)
         if (j < nb) acc = fma(v[j], xv[j], acc);
     }
     epi((ch - c0) * 32 + lane, acc);
