@@ -240,13 +240,66 @@ def bench_batched(args):
     print(json.dumps(out))
 
 
+def bench_mcf(args):
+    """Mixed precision on the multicommodity-flow LP (lpgen.mcf: 8 commodities, 2e5 nodes,
+    1e6 arcs, n = 8e6, m = 2.6e6, nnz = 2.4e7, Ruiz + Pock-Chambolle scaling): PDHG
+    iterations/s and time to 1e-4 for FP64 and for MIXED (FP32 iterations, FP64
+    checks and refinement), and the relative objective difference between the two."""
+    import torch
+    import lpgen
+    import paper_2312_14832_b300 as pk
+    torch.cuda.set_device(0)
+    lp = lpgen.mcf(0)
+    stream = torch.cuda.current_stream()
+    out = {"metric": METRIC, "unit": "PDHG iter/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "impl": "ours-mcf",
+           "config": {"workload": "multicommodity flow: 8 commodities, 2e5 nodes, 1e6 arcs (with a Hamiltonian "
+                                  "cycle), n=8e6, m=2.6e6, nnz=2.4e7, +-1 entries, costs U(1,10), cap U(5,50), "
+                                  "planted feasible flow; Ruiz(10)+Pock-Chambolle scaling",
+                      "check_every": CHECK_EVERY}}
+    iters = args.steps * CHECK_EVERY
+    for name, prec in (("fp64", pk.FP64), ("mixed", pk.MIXED)):
+        s = pk.Solver.from_lp(lp, scaling=1, precision=prec, stream=stream.cuda_stream)
+        s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False,
+                mixed_switch_tol=1e-30)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        # tol 0 and a switch tolerance that is never reached: every interval in this precision
+        r = s.solve(tol=0.0, max_iter=iters, want_point=False, mixed_switch_tol=1e-30)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        mp, md = s.time_iterations(100)
+        rt = s.solve(tol=1e-4, time_limit_s=args.mcf_budget)
+        out[name] = {"iter_per_s": iters / (ms * 1e-3), "ms_primal": mp, "ms_dual": md,
+                     "fp32_iters_in_timed": r["fp32_iters"],
+                     "time_to_1e-4": {"status": ["optimal", "iter_limit", "time_limit", "numerical"][rt["status"]],
+                                      "iters": rt["iters"], "fp32_iters": rt["fp32_iters"],
+                                      "device_s": rt["device_ms"] * 1e-3, "primal_obj": rt["primal_obj"],
+                                      "rel_primal": rt["rel_primal"], "rel_dual": rt["rel_dual"],
+                                      "rel_gap": rt["rel_gap"]}}
+        out[name + "_x"] = rt["x"]
+        s.close()
+    a, b = out["fp64"]["time_to_1e-4"], out["mixed"]["time_to_1e-4"]
+    out["mixed_vs_fp64"] = {"iter_speedup": out["mixed"]["iter_per_s"] / out["fp64"]["iter_per_s"],
+                            "time_to_1e-4_speedup": a["device_s"] / max(b["device_s"], 1e-9),
+                            "rel_obj_diff": abs(a["primal_obj"] - b["primal_obj"]) / abs(a["primal_obj"]),
+                            "rel_x_diff": float(np.linalg.norm(out["fp64_x"] - out["mixed_x"]) /
+                                                np.linalg.norm(out["fp64_x"]))}
+    del out["fp64_x"], out["mixed_x"]
+    out["value"] = out["mixed"]["iter_per_s"]
+    out["dtype"] = "f32 iterations / f64 checks"
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batched"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batched", "mcf"])
     ap.add_argument("--ttt-budget", type=float, default=0.0,
                     help="seconds for a cold time-to-1e-4 solve of the bench workload (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -255,9 +308,13 @@ def main():
     ap.add_argument("--batch-max-iter", type=int, default=200000)
     ap.add_argument("--batch-scaling", type=int, default=0)
     ap.add_argument("--seq-sample", type=int, default=32)
+    ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-1e-4 solve (mcf)")
     args = ap.parse_args()
     if args.workload == "batched":
         bench_batched(args)
+        return
+    if args.workload == "mcf":
+        bench_mcf(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

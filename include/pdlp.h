@@ -56,6 +56,14 @@ extern "C" {
 #define PDLP_TIME_LIMIT 2   /* time_limit_s reached */
 #define PDLP_NUMERICAL 3    /* a NaN or Inf appeared in the KKT quantities */
 
+/* precision (pdlp_params.precision) */
+#define PDLP_FP64 0         /* every iteration in FP64 */
+#define PDLP_MIXED 1        /* FP32 SpMVs and vector updates with FP32 iterates; the checks
+                               (K x, K'y, KKT, restarts, termination) in FP64 on FP64 copies;
+                               FP64 iterations after the switch (refinement).  This
+                               precision split is an extension of this library, not the
+                               paper's (the paper is FP64 throughout). */
+
 typedef struct pdlp_ctx* pdlp_handle;
 
 typedef struct {
@@ -83,7 +91,10 @@ typedef struct {
   int32_t tile_chunks;   /* at most this many 32-row chunks per SpMV warp task (1..32);
                             0 = chosen at setup                                           */
   int32_t spmv_batch;    /* SpMV slots whose loads are issued together: 4 or 8; 0 = setup */
-  int32_t reserved;
+  int32_t precision;     /* PDLP_FP64 (default) or PDLP_MIXED (single-LP handles only)    */
+  double mixed_switch_tol; /* PDLP_MIXED: FP32 iterations until the FP64-measured largest
+                            relative error is <= this (or stops improving for 16 checks),
+                            then FP64 iterations; 0 = max(tol, 1e-5)                      */
 } pdlp_params;
 
 typedef struct {
@@ -102,6 +113,7 @@ typedef struct {
   double solve_s;        /* host wall time of pdlp_solve                                   */
   double device_ms;      /* device time from the first to the last kernel of the solve     */
   int64_t launches;      /* kernels launched on the device by this solve                  */
+  int64_t fp32_iters;    /* PDLP_MIXED: iterations run in FP32 (the rest ran in FP64)     */
 } pdlp_result;
 
 /* Per-check record (pdlp_get_log). */

@@ -33,6 +33,7 @@ __all__ = [
     "planted_small",
     "planted_random",
     "batch_planted",
+    "mcf",
     "planted_zipf",
     "box_only",
     "tiny_lp",
@@ -286,3 +287,66 @@ def random_csr(seed, m, n, lengths, dist="normal"):
     else:
         vals = np.where(rng.random(rows.shape[0]) < 0.5, -1.0, 1.0) * 10.0 ** rng.uniform(-3, 3, rows.shape[0])
     return csr_from_coo(m, n, rows, cols, vals)
+
+
+def mcf(seed=0, nodes=200_000, arcs=1_000_000, commodities=8, walk_len=20, fill=0.5):
+    """Multicommodity-flow LP: a random directed graph on ``nodes`` nodes with ``arcs``
+    arcs, the first ``nodes`` of which form a random Hamiltonian cycle (so every node
+    has an out-arc), and ``commodities`` commodities.  Columns x_{k,a} >= 0 in
+    commodity-major order (k * arcs + a), costs U(1, 10).
+    Rows: conservation, one equality per (k, v) with +1 on the arcs leaving v and -1 on
+    the arcs entering v (m1 = commodities * nodes), then one capacity row per arc,
+    -sum_k x_{k,a} >= -cap_a with cap_a ~ U(5, 50).
+    A feasible flow is planted: each commodity routes random walks of ``walk_len`` arcs
+    with flow U(0.1, 1) each until the commodities together use about ``fill`` of the
+    total capacity; b is its net flow, and an arc whose planted load exceeds 90 % of its
+    capacity gets capacity load / 0.9 (so the planted flow stays strictly feasible)."""
+    rng = np.random.default_rng(seed)
+    V, A, Kc = nodes, arcs, commodities
+    perm = rng.permutation(V)
+    tail = np.empty(A, dtype=np.int64)
+    head = np.empty(A, dtype=np.int64)
+    tail[:V] = perm
+    head[:V] = np.roll(perm, -1)
+    t = rng.integers(0, V, A - V)
+    h = rng.integers(0, V - 1, A - V)
+    h = h + (h >= t)                      # no self-loops
+    tail[V:], head[V:] = t, h
+    cap = rng.uniform(5.0, 50.0, A)
+    cost = rng.uniform(1.0, 10.0, Kc * A)
+    # out-arc lists for the random walks
+    order = np.argsort(tail, kind="stable")
+    out_ptr = np.zeros(V + 1, dtype=np.int64)
+    np.cumsum(np.bincount(tail, minlength=V), out=out_ptr[1:])
+    out_arcs = order
+    walks_per_k = max(1, int(fill * cap.sum() / (Kc * walk_len * 0.55)))
+    flow = np.zeros((Kc, A))
+    for k in range(Kc):
+        cur = rng.integers(0, V, walks_per_k)
+        amount = rng.uniform(0.1, 1.0, walks_per_k)
+        for _ in range(walk_len):
+            deg = out_ptr[cur + 1] - out_ptr[cur]
+            pick = out_arcs[out_ptr[cur] + (rng.random(walks_per_k) * deg).astype(np.int64)]
+            np.add.at(flow[k], pick, amount)
+            cur = head[pick]
+    load = flow.sum(axis=0)
+    cap = np.maximum(cap, load / 0.9)
+    x = flow.reshape(-1)                  # commodity-major, matches the columns
+    # conservation rows (k, v): +1 at the tail node, -1 at the head node of each arc
+    m1 = Kc * V
+    cols = np.arange(Kc * A, dtype=np.int64)
+    kk = cols // A
+    aa = cols % A
+    r_out = kk * V + tail[aa]
+    r_in = kk * V + head[aa]
+    r_cap = m1 + aa
+    rows = np.concatenate([r_out, r_in, r_cap])
+    cc = np.concatenate([cols, cols, cols])
+    vals = np.concatenate([np.ones(Kc * A), -np.ones(Kc * A), -np.ones(Kc * A)])
+    m = m1 + A
+    row_ptr, col_idx, val = csr_from_coo(m, Kc * A, rows, cc, vals)
+    b = np.bincount(r_out, weights=x, minlength=m1) - np.bincount(r_in, weights=x, minlength=m1)
+    q = np.concatenate([b[:m1], -cap])
+    n = Kc * A
+    return dict(m=m, n=n, m1=m1, row_ptr=row_ptr, col_idx=col_idx, val=val, c=cost, q=q,
+                l=np.zeros(n), u=np.full(n, np.inf), x_feasible=x)

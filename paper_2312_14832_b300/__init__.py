@@ -16,10 +16,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import ITER_LIMIT, NUMERICAL, OPTIMAL, TIME_LIMIT  # noqa: F401
+from ._lib import FP64, ITER_LIMIT, MIXED, NUMERICAL, OPTIMAL, TIME_LIMIT  # noqa: F401
 
 __all__ = ["Solver", "BatchSolver", "SolverError", "default_params", "OPTIMAL", "ITER_LIMIT", "TIME_LIMIT",
-           "NUMERICAL"]
+           "NUMERICAL", "FP64", "MIXED"]
 
 
 class SolverError(RuntimeError):

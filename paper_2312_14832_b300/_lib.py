@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(_HERE, "libpdlp_b300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EINTERNAL = 0, -1, -2, -3, -5
 OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL = 0, 1, 2, 3
+FP64, MIXED = 0, 1
 
 
 class Params(C.Structure):
@@ -18,7 +19,8 @@ class Params(C.Structure):
                 ("omega_theta", C.c_double), ("ruiz_iters", C.c_int32), ("power_iters", C.c_int32),
                 ("eta", C.c_double), ("tile_slots", C.c_int32), ("inputs_on_device", C.c_int32),
                 ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("tile_chunks", C.c_int32),
-                ("spmv_batch", C.c_int32), ("reserved", C.c_int32)]
+                ("spmv_batch", C.c_int32), ("precision", C.c_int32),
+                ("mixed_switch_tol", C.c_double)]
 
 
 class Result(C.Structure):
@@ -26,7 +28,8 @@ class Result(C.Structure):
                 ("restarts", C.c_int64), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("rel_primal", C.c_double), ("rel_dual", C.c_double), ("rel_gap", C.c_double),
                 ("kkt_omega", C.c_double), ("omega", C.c_double), ("eta", C.c_double),
-                ("solve_s", C.c_double), ("device_ms", C.c_double), ("launches", C.c_int64)]
+                ("solve_s", C.c_double), ("device_ms", C.c_double), ("launches", C.c_int64),
+                ("fp32_iters", C.c_int64)]
 
 
 class CheckRecord(C.Structure):

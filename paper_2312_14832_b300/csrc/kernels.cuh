@@ -26,6 +26,7 @@ struct DevState {
   double kkt_anchor, kkt_prev;     // KKT_omega(z^{n,0}) and of the previous candidate
   double inv_t;                    // 1/t at the current check (0 when t = 0)
   double out_pobj, out_dobj, out_rel_p, out_rel_d, out_rel_g, out_kkt;  // returned point
+  double last_err;                 // largest relative error of the better point at the last check
   long long k, t, nrestart, ncheck;
   int done, status, which, restart_flag, cand_avg, final_force;
 };
@@ -95,6 +96,7 @@ struct SellView {
   const int32_t* __restrict__ chunk_ptr;
   const int32_t* __restrict__ col;
   const double* __restrict__ val;
+  const float* __restrict__ val32;   // FP32 copy of val (mixed precision), or null
   const SellTask* __restrict__ tasks;
   int32_t ntasks;
   int32_t nchunks;
@@ -122,19 +124,31 @@ struct OpSumAbs {
   __device__ static double step(double acc, double v, double) { return acc + fabs(v); }
   __device__ static double join(double a, double b) { return a + b; }
 };
+// FP32 SpMV (mixed precision iterations).
+struct OpSpmvF {
+  static constexpr bool kGather = true;
+  __device__ static float step(float acc, float v, float x) { return fmaf(v, x, acc); }
+};
+
+// Combination of split-chunk partial sums (kept in FP64 for every value type).
+template <class Op> __device__ __forceinline__ double join_of(double a, double b) { return a + b; }
+template <> __device__ __forceinline__ double join_of<OpMaxAbs>(double a, double b) { return OpMaxAbs::join(a, b); }
+
+template <class T> __device__ __forceinline__ const T* sell_values(const SellView& A);
+template <> __device__ __forceinline__ const double* sell_values<double>(const SellView& A) { return A.val; }
+template <> __device__ __forceinline__ const float* sell_values<float>(const SellView& A) { return A.val32; }
 
 // Sum of slots [s, e) of one chunk for this lane's row.  Loads of a batch of up to
 // kBatch slots are issued before any of its FMAs; `nb` is warp-uniform, so the
 // guards do not diverge and no FP64 instruction is spent on a missing slot.
-template <class Op, int kBatch>
-__device__ __forceinline__ double chunk_sum(const SellView& A, const double* __restrict__ xg, int s, int e,
-                                            int lane) {
+template <class T, class Op, int kBatch>
+__device__ __forceinline__ T chunk_sum(const SellView& A, const T* __restrict__ xg, int s, int e, int lane) {
   const int32_t* cp = A.col + (size_t)s * 32 + lane;
-  const double* vp = A.val + (size_t)s * 32 + lane;
-  double acc = 0.0;
+  const T* vp = sell_values<T>(A) + (size_t)s * 32 + lane;
+  T acc = T(0);
   for (int k = s; k < e; k += kBatch) {
     const int nb = min(kBatch, e - k);
-    double v[kBatch], xv[kBatch];
+    T v[kBatch], xv[kBatch];
     int ci[kBatch];
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
@@ -145,7 +159,7 @@ __device__ __forceinline__ double chunk_sum(const SellView& A, const double* __r
     }
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
-      xv[j] = 0.0;
+      xv[j] = T(0);
       if (Op::kGather && j < nb) xv[j] = __ldg(xg + ci[j]);
     }
 #pragma unroll
@@ -161,47 +175,49 @@ __device__ __forceinline__ double chunk_sum(const SellView& A, const double* __r
 // complete row sum exactly once per row; Epi::load(row) fetches, before the row's
 // SpMV loop, the operands the epilogue needs, so their latency overlaps it.
 template <class Op, class Epi, int kBatch>
-__global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const double* __restrict__ xg,
+__global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const typename Epi::T* __restrict__ xg,
                                                         Epi epi, const DevState* __restrict__ st) {
+  using T = typename Epi::T;
   if (st != nullptr && st->done) return;
   const int lane = threadIdx.x & 31;
   const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   if (w >= A.ntasks) return;
-  const SellTask T = A.tasks[w];
+  const SellTask Tk = A.tasks[w];
   epi.prepare(st);
-  if (T.np == 0) {
+  if (Tk.np == 0) {
     // whole chunks T.chunk .. T.chunk + nc - 1; lane j holds the start of chunk j
-    const int cb = A.chunk_ptr[min(T.chunk + lane, A.nchunks)];
-    for (int j = 0; j < T.nc; ++j) {
+    const int cb = A.chunk_ptr[min(Tk.chunk + lane, A.nchunks)];
+    for (int j = 0; j < Tk.nc; ++j) {
       const int s = __shfl_sync(0xffffffffu, cb, j);
       const int e = __shfl_sync(0xffffffffu, cb, j + 1);
-      const int row = (T.chunk + j) * 32 + lane;
+      const int row = (Tk.chunk + j) * 32 + lane;
       const typename Epi::Pre pre = epi.load(row);
-      const double acc = chunk_sum<Op, kBatch>(A, xg, s, e, lane);
+      const T acc = chunk_sum<T, Op, kBatch>(A, xg, s, e, lane);
       epi.finish(row, acc, pre);
     }
   } else {
     // piece of a split chunk: publish, count arrivals, the last arrival combines
-    const double acc = chunk_sum<Op, kBatch>(A, xg, T.s0, T.s1, lane);
-    const int row = T.chunk * 32 + lane;
-    A.gpart[(size_t)w * 32 + lane] = acc;
+    const T acc = chunk_sum<T, Op, kBatch>(A, xg, Tk.s0, Tk.s1, lane);
+    const int row = Tk.chunk * 32 + lane;
+    A.gpart[(size_t)w * 32 + lane] = (double)acc;
     __threadfence();
     int old = 0;
-    if (lane == 0) old = atomicAdd(A.cnt + T.t0, 1);
+    if (lane == 0) old = atomicAdd(A.cnt + Tk.t0, 1);
     old = __shfl_sync(0xffffffffu, old, 0);
-    if (old == T.np - 1) {
+    if (old == Tk.np - 1) {
       __threadfence();
       const typename Epi::Pre pre = epi.load(row);
-      double sum = __ldcg(A.gpart + (size_t)T.t0 * 32 + lane);
-      for (int i = 1; i < T.np; ++i) sum = Op::join(sum, __ldcg(A.gpart + (size_t)(T.t0 + i) * 32 + lane));
-      if (lane == 0) A.cnt[T.t0] = 0;
-      epi.finish(row, sum, pre);
+      double sum = __ldcg(A.gpart + (size_t)Tk.t0 * 32 + lane);
+      for (int i = 1; i < Tk.np; ++i) sum = join_of<Op>(sum, __ldcg(A.gpart + (size_t)(Tk.t0 + i) * 32 + lane));
+      if (lane == 0) A.cnt[Tk.t0] = 0;
+      epi.finish(row, (T)sum, pre);
     }
   }
 }
 
 // out[row] = sum (optionally times the state's 1/t, for products of the average).
 struct EpiStore {
+  using T = double;
   double* out;
   int use_inv_t;
   double scale;
@@ -214,6 +230,7 @@ struct EpiStore {
 // Primal step fused on g = (K'y)_j (Section 2, primal update):
 //   x_j <- proj_[l_j,u_j](x_j - tau (c_j - g_j)),  sx_j += x_j.
 struct EpiPrimal {
+  using T = double;
   double* __restrict__ x;
   double* __restrict__ sx;
   const double* __restrict__ c;
@@ -236,6 +253,7 @@ struct EpiPrimal {
 //   y_i <- y_i + sigma (q_i - 2 v + (K x_old)_i), projected onto y_i >= 0 for i >= m1;
 //   sy_i += y_i;  (K x_old)_i <- v.
 struct EpiDual {
+  using T = double;
   double* __restrict__ y;
   double* __restrict__ sy;
   double* __restrict__ kxp;
@@ -254,6 +272,83 @@ struct EpiDual {
     kxp[i] = v;
   }
 };
+
+// Mixed precision (spec extension, not in the paper): the same primal and dual
+// steps with FP32 iterates and FP32 arithmetic; the running sums of the inner loop
+// are FP32 over one check interval and folded into FP64 at every check.
+struct EpiPrimal32 {
+  using T = float;
+  float* __restrict__ x;
+  float* __restrict__ sx;
+  const float* __restrict__ c;
+  const float* __restrict__ l;
+  const float* __restrict__ u;
+  float tau;
+  struct Pre { float xo, c, l, u, sx; };
+  __device__ void prepare(const DevState* st) { tau = (float)st->tau; }
+  __device__ Pre load(int j) const { return Pre{x[j], c[j], l[j], u[j], sx[j]}; }
+  __device__ void finish(int j, float g, const Pre& p) {
+    float xn = fmaf(-tau, p.c - g, p.xo);
+    xn = fminf(fmaxf(xn, p.l), p.u);
+    x[j] = xn;
+    sx[j] = p.sx + xn;
+  }
+};
+struct EpiDual32 {
+  using T = float;
+  float* __restrict__ y;
+  float* __restrict__ sy;
+  float* __restrict__ kxp;
+  const float* __restrict__ q;
+  int m1;
+  float sigma;
+  struct Pre { float q, kxp, y, sy; };
+  __device__ void prepare(const DevState* st) { sigma = (float)st->sigma; }
+  __device__ Pre load(int i) const { return Pre{q[i], kxp[i], y[i], sy[i]}; }
+  __device__ void finish(int i, float v, const Pre& p) {
+    float yn = fmaf(sigma, fmaf(-2.0f, v, p.q + p.kxp), p.y);
+    if (i >= m1) yn = fmaxf(yn, 0.0f);
+    y[i] = yn;
+    sy[i] = p.sy + yn;
+    kxp[i] = v;
+  }
+};
+
+// Check in mixed precision: FP64 copies of the FP32 iterates, interval sums folded
+// into the FP64 sums and cleared.
+__global__ void k_mixed_to64(double* x, double* sx, const float* x32, float* sx32, int64_t npad, double* y,
+                             double* sy, const float* y32, float* sy32, int64_t mpad, const DevState* st) {
+  if (st->done) return;
+  const int64_t tot = npad > mpad ? npad : mpad;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < npad) {
+      x[i] = (double)x32[i];
+      sx[i] += (double)sx32[i];
+      sx32[i] = 0.0f;
+    }
+    if (i < mpad) {
+      y[i] = (double)y32[i];
+      sy[i] += (double)sy32[i];
+      sy32[i] = 0.0f;
+    }
+  }
+}
+// After the check (and a restart, if one happened): FP32 iterates from the FP64 ones.
+__global__ void k_mixed_to32(float* x32, const double* x, int64_t npad, float* y32, const double* y,
+                             float* kxp32, const double* kxp, int64_t mpad, const DevState* st) {
+  if (st->done) return;
+  const int64_t tot = npad > mpad ? npad : mpad;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < npad) x32[i] = (float)x[i];
+    if (i < mpad) {
+      y32[i] = (float)y[i];
+      kxp32[i] = (float)kxp[i];
+    }
+  }
+}
+__global__ void k_to_float(float* dst, const double* src, int64_t n) {
+  PDLP_GRID_STRIDE(i, n) dst[i] = (float)src[i];
+}
 
 // ------------------------------------------------------------------ vector kernels
 
@@ -521,6 +616,7 @@ __device__ inline CheckRecord decide_core(const double* tot, DevState* st, const
   rec.rel_p = better_c ? rp_c : rp_a;
   rec.rel_d = better_c ? rd_c : rd_a;
   rec.rel_g = better_c ? rg_c : rg_a;
+  st->last_err = fmin(ec, ea);
 
   st->restart_flag = 0;
   if (!finite || pass_c || pass_a || last) {

@@ -51,13 +51,14 @@ struct DevSell {
   int32_t* chunk_ptr = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
+  float* val32 = nullptr;   // mixed precision only
   SellTask* tasks = nullptr;
   double* gpart = nullptr;
   int32_t* cnt = nullptr;
   int32_t ntasks = 0;
   int32_t tile = 0, tchunks = 0, batch = 8;
   int64_t rows = 0, rows_pad = 0, nchunks = 0, slots = 0, split = 0;
-  SellView view() const { return SellView{chunk_ptr, col, val, tasks, ntasks, (int32_t)nchunks, gpart, cnt}; }
+  SellView view() const { return SellView{chunk_ptr, col, val, val32, tasks, ntasks, (int32_t)nchunks, gpart, cnt}; }
 };
 
 constexpr int kRing = 4;        // pinned status records in flight
@@ -117,6 +118,12 @@ struct pdlp_ctx {
   int xs_off = 0, ys_off = 0, red_off = 0;
   std::vector<LpDesc> hdesc;
   std::vector<DevState> hstate;
+  // mixed precision (params.precision = 1): FP32 iterates, values and problem vectors
+  float *x32 = nullptr, *y32 = nullptr, *sx32 = nullptr, *sy32 = nullptr, *kxp32 = nullptr;
+  float *c32 = nullptr, *l32 = nullptr, *u32 = nullptr, *q32 = nullptr;
+  cudaGraphExec_t gm_full = nullptr, gm_rem = nullptr;
+  int gm_full_len = -1, gm_rem_len = -1;
+  int64_t fp32_iters = 0;   // iterations of the last solve run in FP32
 };
 
 namespace pdlp {
@@ -155,7 +162,7 @@ static void dfree(pdlp_ctx* h, void* p) {
 }
 
 template <class Op, class Epi>
-static void launch_rows(pdlp_ctx* h, const DevSell& S, const double* xg, Epi epi, const DevState* st) {
+static void launch_rows(pdlp_ctx* h, const DevSell& S, const typename Epi::T* xg, Epi epi, const DevState* st) {
   const int blocks = (S.ntasks + 7) / 8;
   if (S.batch == 4) sell_rows_kernel<Op, Epi, 4><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
   else sell_rows_kernel<Op, Epi, 8><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
@@ -253,6 +260,11 @@ static void enqueue_iteration(pdlp_ctx* h, const DevState* st) {
   launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, st);
 }
 
+static void enqueue_iteration32(pdlp_ctx* h, const DevState* st) {
+  launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, st);
+  launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1, 0.f}, st);
+}
+
 static KktInputs kkt_inputs(pdlp_ctx* h) {
   KktInputs in;
   in.q = h->q; in.kx_c = h->kxp; in.kx_a = h->kx_a; in.y = h->y; in.sy = h->sy; in.ya = h->ya;
@@ -277,12 +289,28 @@ static void enqueue_check(pdlp_ctx* h, int len, int final_check) {
   k_post_restart<<<1, 1, 0, h->s>>>(h->st);
 }
 
-static cudaGraphExec_t capture_interval(pdlp_ctx* h, int len) {
+// Mixed-precision check: FP64 copies of the FP32 iterates and sums, K x in FP64, the
+// FP64 check, FP32 iterates back from the (possibly restarted) FP64 ones (launches: 12).
+static void enqueue_check_mixed(pdlp_ctx* h, int len, int final_check) {
+  k_mixed_to64<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x, h->sx, h->x32, h->sx32, h->npad, h->y,
+                                                                       h->sy, h->y32, h->sy32, h->mpad, h->st);
+  launch_rows<OpSpmv>(h, h->K, h->x, EpiStore{h->kxp, 0, 1.0}, h->st);
+  enqueue_check(h, len, final_check);
+  k_mixed_to32<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x32, h->x, h->npad, h->y32, h->y,
+                                                                       h->kxp32, h->kxp, h->mpad, h->st);
+}
+
+static cudaGraphExec_t capture_interval(pdlp_ctx* h, int len, bool mixed = false) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < len; ++i) enqueue_iteration(h, h->st);
-  enqueue_check(h, len, 0);
+  if (mixed) {
+    for (int i = 0; i < len; ++i) enqueue_iteration32(h, h->st);
+    enqueue_check_mixed(h, len, 0);
+  } else {
+    for (int i = 0; i < len; ++i) enqueue_iteration(h, h->st);
+    enqueue_check(h, len, 0);
+  }
   cudaError_t e = cudaStreamEndCapture(h->s, &g);
   CK(e);
   e = cudaGraphInstantiate(&ex, g, 0);
@@ -349,6 +377,8 @@ static void destroy(pdlp_ctx* h) {
   if (h->s) cudaStreamSynchronize(h->s);
   if (h->g_full) cudaGraphExecDestroy(h->g_full);
   if (h->g_rem) cudaGraphExecDestroy(h->g_rem);
+  if (h->gm_full) cudaGraphExecDestroy(h->gm_full);
+  if (h->gm_rem) cudaGraphExecDestroy(h->gm_rem);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -571,6 +601,7 @@ static void append_lp_layout(Layout& L, const HostLP& H, int64_t rp0, int64_t nn
 static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const double* c_in, const double* q_in,
                                 const double* l_in, const double* u_in);
 static void estimate_step_and_weight(pdlp_ctx* h);
+static void setup_mixed(pdlp_ctx* h);
 
 static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr_in,
                        const int32_t* col_in, const double* val_in, const double* c_in,
@@ -616,6 +647,25 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
     autotune(h, h->K, Lo.SK, false);
   }
   estimate_step_and_weight(h);
+  if (P.precision == PDLP_MIXED) setup_mixed(h);
+  else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
+}
+
+// FP32 copies of the scaled matrix values and problem vectors, FP32 iterates.
+static void setup_mixed(pdlp_ctx* h) {
+  const int64_t np = h->npad, mp = h->mpad;
+  for (DevSell* S : {&h->K, &h->Kt}) {
+    S->val32 = dalloc<float>(h, (size_t)S->slots * 32);
+    k_to_float<<<grid_for(S->slots * 32), 256, 0, h->s>>>(S->val32, S->val, S->slots * 32);
+  }
+  for (float** v : {&h->x32, &h->sx32, &h->c32, &h->l32, &h->u32}) *v = dalloc<float>(h, np);
+  for (float** v : {&h->y32, &h->sy32, &h->kxp32, &h->q32}) *v = dalloc<float>(h, mp);
+  k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->c32, h->c, np);
+  k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->l32, h->l, np);
+  k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->u32, h->u, np);
+  k_to_float<<<grid_for(mp), 256, 0, h->s>>>(h->q32, h->q, mp);
+  CKL("mixed setup");
+  CK(cudaStreamSynchronize(h->s));
 }
 
 static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const double* c_in, const double* q_in,
@@ -759,12 +809,32 @@ static void ensure_graphs(pdlp_ctx* h, int full, int rem) {
   }
 }
 
+static void ensure_graphs_mixed(pdlp_ctx* h, int full, int rem) {
+  if (h->gm_full_len != full) {
+    if (h->gm_full) cudaGraphExecDestroy(h->gm_full);
+    h->gm_full = nullptr;
+    h->gm_full_len = -1;
+    if (full > 0) {
+      h->gm_full = capture_interval(h, full, true);
+      h->gm_full_len = full;
+    }
+  }
+  if (rem > 0 && h->gm_rem_len != rem) {
+    if (h->gm_rem) cudaGraphExecDestroy(h->gm_rem);
+    h->gm_rem = nullptr;
+    h->gm_rem_len = -1;
+    h->gm_rem = capture_interval(h, rem, true);
+    h->gm_rem_len = rem;
+  }
+}
+
 static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0, double omega0,
                       pdlp_result* res, double* x_out, double* y_out) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   auto t_start = std::chrono::steady_clock::now();
   const int64_t n = h->n, m = h->m, np = h->npad, mp = h->mpad;
   int64_t launches = 0;
+  h->fp32_iters = 0;
 
   // device parameters of the decision kernel
   h->dp_host.tol = sp.tol;
@@ -815,6 +885,14 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   k_kkt_partials<<<h->nb_rows + h->nb_cols, 256, 0, h->s>>>(kkt_inputs(h), h->st, h->part);
   k_decide<<<1, 256, 0, h->s>>>(h->part, h->nb_rows, h->nb_cols, h->st, h->dp, h->log, h->restarts, 1, 0);
   launches += 9;
+  const bool mixed = h->p.precision == PDLP_MIXED;
+  if (mixed) {
+    CK(cudaMemsetAsync(h->sx32, 0, sizeof(float) * np, h->s));
+    CK(cudaMemsetAsync(h->sy32, 0, sizeof(float) * mp, h->s));
+    k_mixed_to32<<<grid_for(std::max(np, mp)), 256, 0, h->s>>>(h->x32, h->x, np, h->y32, h->y, h->kxp32, h->kxp, mp,
+                                                                 h->st);
+    launches += 1;
+  }
   CKL("solve init");
 
   const int L = sp.check_every;
@@ -829,14 +907,25 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     CKL("final check");
   } else {
     ensure_graphs(h, nfull > 0 ? L : 0, rem);
-    int64_t issued = 0, read = 0;
+    if (mixed) ensure_graphs_mixed(h, nfull > 0 ? L : 0, rem);
+    // mixed precision: FP32 intervals until the FP64-measured relative error reaches
+    // the switch tolerance or stops improving, then FP64 intervals (refinement)
+    bool phase32 = mixed;
+    const double switch_tol = sp.mixed_switch_tol > 0.0 ? sp.mixed_switch_tol : std::max(sp.tol, 1e-5);
+    double best_err = INFINITY;
+    int since_best = 0;
+    int64_t issued = 0, read = 0, issued_k = 0;
+    std::vector<std::pair<int64_t, int>> fp32_intervals;   // (first iteration, length) of FP32 intervals
     bool done = false;
     while (!done && read < nint) {
       while (issued < nint && issued - read < kLookahead) {
-        cudaGraphExec_t g = (issued < nfull) ? h->g_full : h->g_rem;
-        const int len = (issued < nfull) ? L : rem;
+        const bool fullint = issued < nfull;
+        cudaGraphExec_t g = phase32 ? (fullint ? h->gm_full : h->gm_rem) : (fullint ? h->g_full : h->g_rem);
+        const int len = fullint ? L : rem;
         CK(cudaGraphLaunch(g, h->s));
-        launches += 2 * len + 8;
+        launches += 2 * len + (phase32 ? 12 : 8);
+        if (phase32) fp32_intervals.emplace_back(issued_k, len);
+        issued_k += len;
         const int slot = (int)(issued % kRing);
         CK(cudaMemcpyAsync(h->st_host + slot, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
         CK(cudaEventRecord(h->ev_ring[slot], h->s));
@@ -846,6 +935,16 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
       CK(cudaEventSynchronize(h->ev_ring[slot]));
       done = h->st_host[slot].done != 0;
       ++read;
+      if (phase32 && !done) {
+        const double e = h->st_host[slot].last_err;
+        if (e < 0.9 * best_err) {
+          best_err = e;
+          since_best = 0;
+        } else {
+          ++since_best;
+        }
+        if (e <= switch_tol || since_best >= 16) phase32 = false;
+      }
       if (!done && std::isfinite(sp.time_limit_s)) {
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (el > sp.time_limit_s) {
@@ -856,6 +955,8 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     }
     CK(cudaStreamSynchronize(h->s));
     CK(cudaMemcpy(&fin, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    // intervals queued after the solve finished did nothing
+    for (const auto& iv : fp32_intervals) h->fp32_iters += std::max<int64_t>(0, std::min<int64_t>(iv.second, fin.k - iv.first));
     if (!fin.done) {
       // time limit: one more check that must terminate
       int one = 1;
@@ -903,6 +1004,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     res->eta = fin.eta;
     res->device_ms = dev_ms;
     res->launches = launches;
+    res->fp32_iters = h->fp32_iters;
     res->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   }
   return PDLP_OK;
@@ -1161,6 +1263,8 @@ void pdlp_default_params(pdlp_params* p) {
   p->log_capacity = 4096;
   p->tile_chunks = 0;
   p->spmv_batch = 0;
+  p->precision = PDLP_FP64;
+  p->mixed_switch_tol = 0.0;
 }
 
 int pdlp_setup(pdlp_handle* out, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr,
@@ -1330,9 +1434,15 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
       auto& ev = h->timing_events;
       CK(cudaEventRecord(ev[0], h->s));
       for (int64_t i = 0; i < cnt; ++i) {
-        launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
+        if (h->p.precision == PDLP_MIXED)
+          launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, h->st_tmp);
+        else
+          launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
         CK(cudaEventRecord(ev[2 * i + 1], h->s));
-        launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, h->st_tmp);
+        if (h->p.precision == PDLP_MIXED)
+          launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1, 0.f}, h->st_tmp);
+        else
+          launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, h->st_tmp);
         CK(cudaEventRecord(ev[2 * i + 2], h->s));
       }
       CKL("timed iterations");
