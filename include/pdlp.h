@@ -238,6 +238,17 @@ int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const in
  * either may be NULL, receive the returned points back to back in the caller's order. */
 int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, pdlp_result* res, double* x_out, double* y_out);
 
+/* ---------------------------------------------------------------- dense kernels
+ * C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then max(., 0) if relu) on the tcgen05
+ * tensor cores: A and B BF16 row-major (K contiguous) device arrays, C FP32 row-major
+ * device array, bias FP32 device array or NULL.  M and N multiples of 128, K a multiple
+ * of 64.  Used by the learned warm start (a spec extension: the paper has no
+ * learned component); exposed for testing.  Runs on `stream` (NULL = default) and
+ * waits for it.  Errors: PDLP_EINVAL (shapes), PDLP_ECUDA, PDLP_EINTERNAL (an internal
+ * wait gave up). */
+int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
+                 int32_t relu, void* stream);
+
 /* y = K x for a CSR matrix held in the caller's device memory, with no device memory
  * allocated by the call.  This entry point has no counterpart in the paper; it is for
  * callers that cannot call cudaMalloc at the point where they need the product, for

@@ -69,6 +69,7 @@ SIGNATURES = {
     "pdlp_batch_setup": (C.c_int, [C.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                    C.POINTER(Params)]),
     "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp]),
+    "pdlp_tc_gemm": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
 }
 
 _lib = None

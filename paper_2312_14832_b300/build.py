@@ -8,7 +8,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("pdlp.cu", "layout.cpp", "noalloc.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("pdlp.cu", "layout.cpp", "noalloc.cu", "mlp.cu")]
 DEPS = [os.path.join(HERE, "csrc", f) for f in sorted(os.listdir(os.path.join(HERE, "csrc")))
         if f.endswith((".cu", ".cuh", ".h", ".cpp"))] + [os.path.join(ROOT, "include", "pdlp.h"), __file__]
 LIB = os.path.join(HERE, "libpdlp_b300.so")
