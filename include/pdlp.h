@@ -249,6 +249,40 @@ int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, pdlp_result* res, doub
 int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
                  int32_t relu, void* stream);
 
+/* ---------------------------------------------------------------- warm-start network
+ * A 3-layer MLP for learned warm starts (a spec extension; the paper has no
+ * learned component):  Y = relu(relu(X W1' + b1) W2' + b2) W3' + b3,
+ * W1 [hidden x n_in], W2 [hidden x hidden], W3 [n_out x hidden], row-major FP32 masters.
+ * Every product runs on the tcgen05 tensor cores with BF16 operands and FP32
+ * accumulation (pdlp_tc_gemm's kernel); the BF16 points are X, W1..W3 and the hidden
+ * activations.  Training minimises the mean squared error
+ *   L = sum over rows r and outputs o of (Y_ro - T_ro)^2 / (2 rows n_out)
+ * with AdamW (beta 0.9, 0.999, eps 1e-8, weight decay on the weights only).
+ * All arrays of these calls are host arrays; data rows are selected by index. */
+typedef struct pdlp_mlp_ctx* pdlp_mlp;
+
+/* hidden: a multiple of 128; max_batch: the most rows one call handles. */
+int pdlp_mlp_create(pdlp_mlp* out, int32_t n_in, int32_t hidden, int32_t n_out, int32_t max_batch);
+void pdlp_mlp_free(pdlp_mlp h);
+const char* pdlp_mlp_last_error(pdlp_mlp h);
+/* Sets the parameters (unpadded shapes as above) and clears the optimiser state. */
+int pdlp_mlp_set_params(pdlp_mlp h, const float* W1, const float* b1, const float* W2, const float* b2,
+                        const float* W3, const float* b3);
+int pdlp_mlp_get_params(pdlp_mlp h, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3);
+/* Copies a dataset to the device: X [count x n_in], T [count x n_out] (T may be NULL
+ * for inference only). */
+int pdlp_mlp_load_data(pdlp_mlp h, int64_t count, const float* X, const float* T);
+/* Y [rows x n_out] = network(X[idx[r]]), rows <= max_batch. */
+int pdlp_mlp_forward(pdlp_mlp h, int32_t rows, const int32_t* idx, float* Y);
+/* Loss and gradients of L on the rows idx (no update); any output may be NULL. */
+int pdlp_mlp_gradients(pdlp_mlp h, int32_t rows, const int32_t* idx, double* loss, float* gW1, float* gb1,
+                       float* gW2, float* gb2, float* gW3, float* gb3);
+/* `epochs` passes over the loaded data in minibatches of `batch` rows (order shuffled
+ * per epoch from `seed`; a last partial batch is skipped); epoch_loss[epochs] receives
+ * the mean minibatch loss, train_ms the device time. */
+int pdlp_mlp_train(pdlp_mlp h, int32_t epochs, int32_t batch, float lr, float weight_decay, uint64_t seed,
+                   double* epoch_loss, double* train_ms);
+
 /* y = K x for a CSR matrix held in the caller's device memory, with no device memory
  * allocated by the call.  This entry point has no counterpart in the paper; it is for
  * callers that cannot call cudaMalloc at the point where they need the product, for

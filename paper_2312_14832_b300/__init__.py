@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import FP64, ITER_LIMIT, MIXED, NUMERICAL, OPTIMAL, TIME_LIMIT  # noqa: F401
 
-__all__ = ["Solver", "BatchSolver", "SolverError", "default_params", "OPTIMAL", "ITER_LIMIT", "TIME_LIMIT",
+__all__ = ["Solver", "BatchSolver", "MLP", "SolverError", "default_params", "OPTIMAL", "ITER_LIMIT", "TIME_LIMIT",
            "NUMERICAL", "FP64", "MIXED"]
 
 
@@ -250,6 +250,89 @@ class BatchSolver:
     def close(self):
         if self._h:
             self._lib.pdlp_free(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The warm-start network (pdlp_mlp_*): 3 linear layers with ReLU, BF16 tensor-core
+    products, FP32 masters, AdamW.  Parameters are numpy float32 arrays
+    W1 [hidden x n_in], b1, W2 [hidden x hidden], b2, W3 [n_out x hidden], b3."""
+
+    def __init__(self, n_in, hidden, n_out, max_batch):
+        self._lib = _lib.load()
+        self._h = C.c_void_p()
+        self.n_in, self.hidden, self.n_out, self.max_batch = n_in, hidden, n_out, max_batch
+        rc = self._lib.pdlp_mlp_create(C.byref(self._h), n_in, hidden, n_out, max_batch)
+        if rc != 0:
+            raise SolverError(rc, self._lib.pdlp_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc < 0:
+            raise SolverError(rc, self._lib.pdlp_mlp_last_error(self._h).decode())
+
+    def shapes(self):
+        return [(self.hidden, self.n_in), (self.hidden,), (self.hidden, self.hidden), (self.hidden,),
+                (self.n_out, self.hidden), (self.n_out,)]
+
+    def set_params(self, params):
+        arrs = [np.ascontiguousarray(p, dtype=np.float32) for p in params]
+        for a, shp in zip(arrs, self.shapes()):
+            if a.shape != shp:
+                raise ValueError(f"parameter shape {a.shape} != {shp}")
+        self._check(self._lib.pdlp_mlp_set_params(self._h, *[a.ctypes.data for a in arrs]))
+
+    def get_params(self):
+        arrs = [np.empty(shp, dtype=np.float32) for shp in self.shapes()]
+        self._check(self._lib.pdlp_mlp_get_params(self._h, *[a.ctypes.data for a in arrs]))
+        return arrs
+
+    def load_data(self, X, T=None):
+        self._X = np.ascontiguousarray(X, dtype=np.float32)
+        self._T = None if T is None else np.ascontiguousarray(T, dtype=np.float32)
+        self._check(self._lib.pdlp_mlp_load_data(self._h, self._X.shape[0], self._X.ctypes.data,
+                                                 None if self._T is None else self._T.ctypes.data))
+        self.count = self._X.shape[0]
+
+    def forward(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        Y = np.empty((idx.shape[0], self.n_out), dtype=np.float32)
+        for s in range(0, idx.shape[0], self.max_batch):
+            part = np.ascontiguousarray(idx[s:s + self.max_batch])
+            out = np.empty((part.shape[0], self.n_out), dtype=np.float32)
+            self._check(self._lib.pdlp_mlp_forward(self._h, part.shape[0], part.ctypes.data, out.ctypes.data))
+            Y[s:s + part.shape[0]] = out
+        return Y
+
+    def gradients(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        grads = [np.empty(shp, dtype=np.float32) for shp in self.shapes()]
+        loss = C.c_double()
+        self._check(self._lib.pdlp_mlp_gradients(self._h, idx.shape[0], idx.ctypes.data, C.byref(loss),
+                                                 *[g.ctypes.data for g in grads]))
+        return loss.value, grads
+
+    def train(self, epochs, batch, lr, weight_decay=0.0, seed=0):
+        losses = np.zeros(epochs)
+        ms = C.c_double()
+        self._check(self._lib.pdlp_mlp_train(self._h, epochs, batch, lr, weight_decay, seed, losses.ctypes.data,
+                                             C.byref(ms)))
+        return losses, ms.value
+
+    def close(self):
+        if self._h:
+            self._lib.pdlp_mlp_free(self._h)
             self._h = C.c_void_p()
 
     def __enter__(self):

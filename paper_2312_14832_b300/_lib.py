@@ -70,6 +70,15 @@ SIGNATURES = {
                                    C.POINTER(Params)]),
     "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp]),
     "pdlp_tc_gemm": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "pdlp_mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _i32, _i32, _i32]),
+    "pdlp_mlp_free": (None, [_vp]),
+    "pdlp_mlp_last_error": (C.c_char_p, [_vp]),
+    "pdlp_mlp_set_params": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pdlp_mlp_get_params": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pdlp_mlp_load_data": (C.c_int, [_vp, _i64, _vp, _vp]),
+    "pdlp_mlp_forward": (C.c_int, [_vp, _i32, _vp, _vp]),
+    "pdlp_mlp_gradients": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pdlp_mlp_train": (C.c_int, [_vp, _i32, _i32, C.c_float, C.c_float, C.c_uint64, _vp, _vp]),
 }
 
 _lib = None

@@ -1,9 +1,16 @@
-// Dense kernels of the learned warm start: the tcgen05 BF16 GEMM launcher and its
-// C ABI test entry point.
+// The learned warm start's network (a spec extension; the paper has no learned
+// component): a 3-layer MLP  X -> relu(X W1' + b1) -> relu(. W2' + b2) -> . W3' + b3,
+// BF16 operands on the tcgen05 tensor cores (tc_gemm.cuh) with FP32 accumulation,
+// FP32 master weights, MSE loss and AdamW, forward and backward all on the device.
+// Backward products use explicit BF16 transposes so that every GEMM is A * B'.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <string>
+#include <vector>
 
 #include "pdlp.h"
 #include "tc_gemm.cuh"
@@ -59,3 +66,456 @@ extern "C" int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, cons
   }
   return PDLP_OK;
 }
+
+// ------------------------------------------------------------------ MLP kernels
+
+namespace pdlp {
+
+__global__ void k_mlp_fill_bf16_from_f32(__nv_bfloat16* dst, const float* src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// dst[R x Cp] (bf16) = src rows[idx[r]] (fp32, r < rows, c < cols), zero elsewhere.
+__global__ void k_mlp_gather_rows(__nv_bfloat16* dst, int R, int Cp, const float* src, int cols, const int* idx,
+                                  int rows) {
+  const int64_t tot = (int64_t)R * Cp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / Cp), c = (int)(i % Cp);
+    float v = 0.f;
+    if (r < rows && c < cols) v = src[(int64_t)idx[r] * cols + c];
+    dst[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// dst[C x R] = src[R x C]^T, 32x32 tiles through shared memory.
+__global__ void k_mlp_transpose_bf16(__nv_bfloat16* dst, const __nv_bfloat16* src, int R, int C) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < R && c < C) t[j][threadIdx.x] = src[(int64_t)r * C + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = bx + j, r = by + threadIdx.x;
+    if (r < R && c < C) dst[(int64_t)c * R + r] = t[threadIdx.x][j];
+  }
+}
+
+// dY = (Y - T) / (rows * n_out) on the valid block, 0 elsewhere; BF16 copy; per-block
+// partial sums of (Y - T)^2 for the loss.
+__global__ void k_mlp_loss_grad(const float* Y, int Bp, int Op, const float* T, int n_out, const int* idx, int rows,
+                                float* dY, __nv_bfloat16* dYb, double* part) {
+  const double inv = 1.0 / ((double)rows * n_out);
+  double acc = 0.0;
+  const int64_t tot = (int64_t)Bp * Op;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / Op), c = (int)(i % Op);
+    float g = 0.f;
+    if (r < rows && c < n_out) {
+      const float d = Y[i] - T[(int64_t)idx[r] * n_out + c];
+      acc += (double)d * d;
+      g = (float)(d * inv);
+    }
+    dY[i] = g;
+    dYb[i] = __float2bfloat16_rn(g);
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// dZ = dH * (H > 0), FP32 and BF16.
+__global__ void k_mlp_relu_back(float* dZ, __nv_bfloat16* dZb, const float* dH, const float* H, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = H[i] > 0.f ? dH[i] : 0.f;
+    dZ[i] = g;
+    dZb[i] = __float2bfloat16_rn(g);
+  }
+}
+
+// db[c] = sum over rows r < R of dZ[r][c] (fixed row order).
+__global__ void k_mlp_colsum(float* db, const float* dZ, int R, int C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float s = 0.f;
+  for (int r = 0; r < R; ++r) s += dZ[(int64_t)r * C + c];
+  db[c] = s;
+}
+
+// AdamW on one tensor: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// w -= lr (m_hat / (sqrt(v_hat) + eps) + wd w).
+__global__ void k_mlp_adamw(float* w, float* m, float* v, const float* g, int64_t n, float lr, float wd, float b1,
+                            float b2, float c1, float c2, float eps) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+  }
+}
+
+}  // namespace pdlp
+
+using namespace pdlp;
+
+struct pdlp_mlp_ctx {
+  int n_in, hid, n_out, in_p, out_p, maxb, bp;
+  cudaStream_t s = nullptr;
+  std::vector<void*> allocs;
+  // parameters (FP32 masters), gradients, Adam moments: W1 [hid x in_p], W2 [hid x hid], W3 [out_p x hid]
+  float *W[3], *b[3], *gW[3], *gb[3], *mW[3], *vW[3], *mb[3], *vb[3];
+  int64_t wsz[3];
+  int bsz[3];
+  __nv_bfloat16 *Wb[3], *WTb[3];
+  // activations for one batch
+  __nv_bfloat16 *Xb, *XTb, *H1b, *H1Tb, *H2b, *H2Tb, *dYb, *dYTb, *dZ2b, *dZ2Tb, *dZ1Tb, *dZ1b;
+  float *H1, *H2, *Y, *dY, *dH2, *dZ2, *dH1, *dZ1;
+  double* part;
+  int* err;
+  int* idx;          // batch row indices into the dataset
+  float *dataX = nullptr, *dataT = nullptr;
+  int64_t ndata = 0;
+  int64_t step = 0;
+  std::string msg;
+};
+
+namespace pdlp {
+
+static int ceil_to(int v, int q) { return (v + q - 1) / q * q; }
+
+template <class T>
+static T* mlp_alloc(pdlp_mlp_ctx* h, size_t n) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) throw std::string("cudaMalloc: ") + cudaGetErrorString(e);
+  h->allocs.push_back(p);
+  cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(T), h->s);
+  return (T*)p;
+}
+
+static void mlp_ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 148 * 8); }
+
+static void gemm(pdlp_mlp_ctx* h, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, __nv_bfloat16* Cb,
+                 const float* bias, int M, int N, int K, int relu) {
+  mlp_ck(tc_gemm_launch(A, B, C, Cb, bias, M, N, K, relu, h->err, h->s), "tc_gemm");
+}
+
+static void transpose(pdlp_mlp_ctx* h, __nv_bfloat16* dst, const __nv_bfloat16* src, int R, int C) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+  k_mlp_transpose_bf16<<<grid, block, 0, h->s>>>(dst, src, R, C);
+}
+
+// BF16 copies of the weights (and transposes of W2, W3 for the backward products).
+static void refresh_bf16(pdlp_mlp_ctx* h) {
+  for (int l = 0; l < 3; ++l) k_mlp_fill_bf16_from_f32<<<gridn(h->wsz[l]), 256, 0, h->s>>>(h->Wb[l], h->W[l], h->wsz[l]);
+  transpose(h, h->WTb[1], h->Wb[1], h->hid, h->hid);
+  transpose(h, h->WTb[2], h->Wb[2], h->out_p, h->hid);
+}
+
+// Forward on rows idx[0..rows) of X (device, n_in columns), outputs in h->Y.
+static void forward(pdlp_mlp_ctx* h, const float* X, const int* idx, int rows) {
+  k_mlp_gather_rows<<<gridn((int64_t)h->bp * h->in_p), 256, 0, h->s>>>(h->Xb, h->bp, h->in_p, X, h->n_in, idx, rows);
+  gemm(h, h->Xb, h->Wb[0], h->H1, h->H1b, h->b[0], h->bp, h->hid, h->in_p, 1);
+  gemm(h, h->H1b, h->Wb[1], h->H2, h->H2b, h->b[1], h->bp, h->hid, h->hid, 1);
+  gemm(h, h->H2b, h->Wb[2], h->Y, nullptr, h->b[2], h->bp, h->out_p, h->hid, 0);
+}
+
+// Backward of the MSE loss against rows idx of T (device, n_out columns); gradients
+// in h->gW / h->gb; returns the loss (sum of squares / (2 rows n_out)).
+static double backward(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows) {
+  const int nb = 148;
+  k_mlp_loss_grad<<<nb, 256, 0, h->s>>>(h->Y, h->bp, h->out_p, T, h->n_out, idx, rows, h->dY, h->dYb, h->part);
+  transpose(h, h->dYTb, h->dYb, h->bp, h->out_p);
+  transpose(h, h->H2Tb, h->H2b, h->bp, h->hid);
+  transpose(h, h->H1Tb, h->H1b, h->bp, h->hid);
+  transpose(h, h->XTb, h->Xb, h->bp, h->in_p);
+  // layer 3
+  gemm(h, h->dYTb, h->H2Tb, h->gW[2], nullptr, nullptr, h->out_p, h->hid, h->bp, 0);
+  k_mlp_colsum<<<(h->out_p + 255) / 256, 256, 0, h->s>>>(h->gb[2], h->dY, h->bp, h->out_p);
+  gemm(h, h->dYb, h->WTb[2], h->dH2, nullptr, nullptr, h->bp, h->hid, h->out_p, 0);
+  k_mlp_relu_back<<<gridn((int64_t)h->bp * h->hid), 256, 0, h->s>>>(h->dZ2, h->dZ2b, h->dH2, h->H2,
+                                                                    (int64_t)h->bp * h->hid);
+  // layer 2
+  transpose(h, h->dZ2Tb, h->dZ2b, h->bp, h->hid);
+  gemm(h, h->dZ2Tb, h->H1Tb, h->gW[1], nullptr, nullptr, h->hid, h->hid, h->bp, 0);
+  k_mlp_colsum<<<(h->hid + 255) / 256, 256, 0, h->s>>>(h->gb[1], h->dZ2, h->bp, h->hid);
+  gemm(h, h->dZ2b, h->WTb[1], h->dH1, nullptr, nullptr, h->bp, h->hid, h->hid, 0);
+  k_mlp_relu_back<<<gridn((int64_t)h->bp * h->hid), 256, 0, h->s>>>(h->dZ1, h->dZ1b, h->dH1, h->H1,
+                                                                    (int64_t)h->bp * h->hid);
+  // layer 1
+  transpose(h, h->dZ1Tb, h->dZ1b, h->bp, h->hid);
+  gemm(h, h->dZ1Tb, h->XTb, h->gW[0], nullptr, nullptr, h->hid, h->in_p, h->bp, 0);
+  k_mlp_colsum<<<(h->hid + 255) / 256, 256, 0, h->s>>>(h->gb[0], h->dZ1, h->bp, h->hid);
+  mlp_ck(cudaGetLastError(), "backward");
+  std::vector<double> part(nb);
+  mlp_ck(cudaMemcpyAsync(part.data(), h->part, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->s), "loss copy");
+  mlp_ck(cudaStreamSynchronize(h->s), "backward sync");
+  double s = 0.0;
+  for (double v : part) s += v;
+  return s / (2.0 * rows * h->n_out);
+}
+
+static void check_err(pdlp_mlp_ctx* h) {
+  int e = 0;
+  mlp_ck(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->s), "err copy");
+  mlp_ck(cudaStreamSynchronize(h->s), "sync");
+  if (e) throw std::string("tensor-core GEMM: an internal wait gave up");
+}
+
+template <class F>
+static int mlp_guard(pdlp_mlp_ctx* h, F&& f) {
+  if (!h) return PDLP_EINVAL;
+  h->msg.clear();
+  try {
+    f();
+    return PDLP_OK;
+  } catch (const std::string& m) {
+    h->msg = m;
+    return m.rfind("bad", 0) == 0 ? PDLP_EINVAL : PDLP_ECUDA;
+  } catch (...) {
+    h->msg = "unexpected internal error";
+    return PDLP_EINTERNAL;
+  }
+}
+
+}  // namespace pdlp
+
+extern "C" {
+
+int pdlp_mlp_create(pdlp_mlp* out, int32_t n_in, int32_t hidden, int32_t n_out, int32_t max_batch) {
+  if (!out) return PDLP_EINVAL;
+  *out = nullptr;
+  if (n_in < 1 || n_out < 1 || hidden < 128 || hidden % 128 || max_batch < 1) {
+    set_thread_error("pdlp_mlp_create: need n_in, n_out >= 1, hidden a multiple of 128, max_batch >= 1");
+    return PDLP_EINVAL;
+  }
+  pdlp_mlp_ctx* h = new pdlp_mlp_ctx();
+  try {
+    h->n_in = n_in;
+    h->hid = hidden;
+    h->n_out = n_out;
+    h->in_p = ceil_to(n_in, 128);
+    h->out_p = ceil_to(n_out, 128);
+    h->maxb = max_batch;
+    h->bp = ceil_to(max_batch, 128);
+    mlp_ck(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream");
+    const int rows_of[3] = {h->hid, h->hid, h->out_p}, cols_of[3] = {h->in_p, h->hid, h->hid};
+    for (int l = 0; l < 3; ++l) {
+      h->wsz[l] = (int64_t)rows_of[l] * cols_of[l];
+      h->bsz[l] = rows_of[l];
+      for (float** p : {&h->W[l], &h->gW[l], &h->mW[l], &h->vW[l]}) *p = mlp_alloc<float>(h, h->wsz[l]);
+      for (float** p : {&h->b[l], &h->gb[l], &h->mb[l], &h->vb[l]}) *p = mlp_alloc<float>(h, h->bsz[l]);
+      h->Wb[l] = mlp_alloc<__nv_bfloat16>(h, h->wsz[l]);
+      h->WTb[l] = mlp_alloc<__nv_bfloat16>(h, h->wsz[l]);
+    }
+    const int64_t bh = (int64_t)h->bp * h->hid;
+    h->Xb = mlp_alloc<__nv_bfloat16>(h, (int64_t)h->bp * h->in_p);
+    h->XTb = mlp_alloc<__nv_bfloat16>(h, (int64_t)h->bp * h->in_p);
+    for (__nv_bfloat16** p : {&h->H1b, &h->H1Tb, &h->H2b, &h->H2Tb, &h->dZ2b, &h->dZ2Tb, &h->dZ1Tb, &h->dZ1b})
+      *p = mlp_alloc<__nv_bfloat16>(h, bh);
+    h->dYb = mlp_alloc<__nv_bfloat16>(h, (int64_t)h->bp * h->out_p);
+    h->dYTb = mlp_alloc<__nv_bfloat16>(h, (int64_t)h->bp * h->out_p);
+    for (float** p : {&h->H1, &h->H2, &h->dH2, &h->dZ2, &h->dH1, &h->dZ1}) *p = mlp_alloc<float>(h, bh);
+    h->Y = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
+    h->dY = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
+    h->part = mlp_alloc<double>(h, 148);
+    h->err = mlp_alloc<int>(h, 1);
+    h->idx = mlp_alloc<int>(h, h->bp);
+    mlp_ck(cudaStreamSynchronize(h->s), "create");
+  } catch (const std::string& m) {
+    set_thread_error("pdlp_mlp_create: " + m);
+    pdlp_mlp_free(h);
+    return PDLP_ECUDA;
+  }
+  *out = h;
+  return PDLP_OK;
+}
+
+void pdlp_mlp_free(pdlp_mlp h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+}
+
+const char* pdlp_mlp_last_error(pdlp_mlp h) { return h ? h->msg.c_str() : ""; }
+
+int pdlp_mlp_set_params(pdlp_mlp h, const float* W1, const float* b1, const float* W2, const float* b2,
+                        const float* W3, const float* b3) {
+  return mlp_guard(h, [&]() {
+    const float* Ws[3] = {W1, W2, W3};
+    const float* bs[3] = {b1, b2, b3};
+    const int rows[3] = {h->hid, h->hid, h->n_out}, cols[3] = {h->n_in, h->hid, h->hid};
+    const int ldp[3] = {h->in_p, h->hid, h->hid};
+    for (int l = 0; l < 3; ++l) {
+      if (!Ws[l] || !bs[l]) throw std::string("bad: null parameter array");
+      std::vector<float> w((size_t)h->wsz[l], 0.f), bb((size_t)h->bsz[l], 0.f);
+      for (int r = 0; r < rows[l]; ++r)
+        for (int c = 0; c < cols[l]; ++c) w[(size_t)r * ldp[l] + c] = Ws[l][(size_t)r * cols[l] + c];
+      for (int r = 0; r < rows[l]; ++r) bb[(size_t)r] = bs[l][r];
+      mlp_ck(cudaMemcpyAsync(h->W[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice, h->s), "set W");
+      mlp_ck(cudaMemcpyAsync(h->b[l], bb.data(), bb.size() * 4, cudaMemcpyHostToDevice, h->s), "set b");
+      mlp_ck(cudaMemsetAsync(h->mW[l], 0, h->wsz[l] * 4, h->s), "zero m");
+      mlp_ck(cudaMemsetAsync(h->vW[l], 0, h->wsz[l] * 4, h->s), "zero v");
+      mlp_ck(cudaMemsetAsync(h->mb[l], 0, h->bsz[l] * 4, h->s), "zero m");
+      mlp_ck(cudaMemsetAsync(h->vb[l], 0, h->bsz[l] * 4, h->s), "zero v");
+      mlp_ck(cudaStreamSynchronize(h->s), "set params");
+    }
+    h->step = 0;
+    refresh_bf16(h);
+    mlp_ck(cudaStreamSynchronize(h->s), "set params");
+  });
+}
+
+int pdlp_mlp_get_params(pdlp_mlp h, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3) {
+  return mlp_guard(h, [&]() {
+    float* Ws[3] = {W1, W2, W3};
+    float* bs[3] = {b1, b2, b3};
+    const int rows[3] = {h->hid, h->hid, h->n_out}, cols[3] = {h->n_in, h->hid, h->hid};
+    const int ldp[3] = {h->in_p, h->hid, h->hid};
+    for (int l = 0; l < 3; ++l) {
+      std::vector<float> w((size_t)h->wsz[l]), bb((size_t)h->bsz[l]);
+      mlp_ck(cudaMemcpyAsync(w.data(), h->W[l], w.size() * 4, cudaMemcpyDeviceToHost, h->s), "get W");
+      mlp_ck(cudaMemcpyAsync(bb.data(), h->b[l], bb.size() * 4, cudaMemcpyDeviceToHost, h->s), "get b");
+      mlp_ck(cudaStreamSynchronize(h->s), "get params");
+      if (Ws[l])
+        for (int r = 0; r < rows[l]; ++r)
+          for (int c = 0; c < cols[l]; ++c) Ws[l][(size_t)r * cols[l] + c] = w[(size_t)r * ldp[l] + c];
+      if (bs[l])
+        for (int r = 0; r < rows[l]; ++r) bs[l][r] = bb[(size_t)r];
+    }
+  });
+}
+
+int pdlp_mlp_load_data(pdlp_mlp h, int64_t count, const float* X, const float* T) {
+  return mlp_guard(h, [&]() {
+    if (count < 1 || !X) throw std::string("bad: empty data");
+    if (h->dataX) {
+      for (void* p : {(void*)h->dataX, (void*)h->dataT}) {
+        auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+        if (it != h->allocs.end()) {
+          cudaFree(p);
+          h->allocs.erase(it);
+        }
+      }
+    }
+    h->dataX = mlp_alloc<float>(h, (size_t)count * h->n_in);
+    h->dataT = mlp_alloc<float>(h, (size_t)count * h->n_out);
+    mlp_ck(cudaMemcpyAsync(h->dataX, X, (size_t)count * h->n_in * 4, cudaMemcpyHostToDevice, h->s), "data X");
+    if (T) mlp_ck(cudaMemcpyAsync(h->dataT, T, (size_t)count * h->n_out * 4, cudaMemcpyHostToDevice, h->s), "data T");
+    mlp_ck(cudaStreamSynchronize(h->s), "load data");
+    h->ndata = count;
+  });
+}
+
+int pdlp_mlp_forward(pdlp_mlp h, int32_t rows, const int32_t* idx, float* Y) {
+  return mlp_guard(h, [&]() {
+    if (!h->dataX || rows < 1 || rows > h->maxb || !idx || !Y) throw std::string("bad: forward arguments");
+    for (int r = 0; r < rows; ++r)
+      if (idx[r] < 0 || idx[r] >= h->ndata) throw std::string("bad: row index out of range");
+    mlp_ck(cudaMemcpyAsync(h->idx, idx, sizeof(int) * rows, cudaMemcpyHostToDevice, h->s), "idx");
+    forward(h, h->dataX, h->idx, rows);
+    check_err(h);
+    std::vector<float> y((size_t)h->bp * h->out_p);
+    mlp_ck(cudaMemcpyAsync(y.data(), h->Y, y.size() * 4, cudaMemcpyDeviceToHost, h->s), "Y");
+    mlp_ck(cudaStreamSynchronize(h->s), "forward");
+    for (int r = 0; r < rows; ++r) std::memcpy(Y + (size_t)r * h->n_out, y.data() + (size_t)r * h->out_p, 4 * h->n_out);
+  });
+}
+
+int pdlp_mlp_gradients(pdlp_mlp h, int32_t rows, const int32_t* idx, double* loss, float* gW1, float* gb1,
+                       float* gW2, float* gb2, float* gW3, float* gb3) {
+  return mlp_guard(h, [&]() {
+    if (!h->dataX || rows < 1 || rows > h->maxb || !idx) throw std::string("bad: gradient arguments");
+    for (int r = 0; r < rows; ++r)
+      if (idx[r] < 0 || idx[r] >= h->ndata) throw std::string("bad: row index out of range");
+    mlp_ck(cudaMemcpyAsync(h->idx, idx, sizeof(int) * rows, cudaMemcpyHostToDevice, h->s), "idx");
+    forward(h, h->dataX, h->idx, rows);
+    const double L = backward(h, h->dataT, h->idx, rows);
+    check_err(h);
+    if (loss) *loss = L;
+    float* Ws[3] = {gW1, gW2, gW3};
+    float* bs[3] = {gb1, gb2, gb3};
+    const int nrows[3] = {h->hid, h->hid, h->n_out}, cols[3] = {h->n_in, h->hid, h->hid};
+    const int ldp[3] = {h->in_p, h->hid, h->hid};
+    for (int l = 0; l < 3; ++l) {
+      std::vector<float> w((size_t)h->wsz[l]), bb((size_t)h->bsz[l]);
+      mlp_ck(cudaMemcpyAsync(w.data(), h->gW[l], w.size() * 4, cudaMemcpyDeviceToHost, h->s), "gW");
+      mlp_ck(cudaMemcpyAsync(bb.data(), h->gb[l], bb.size() * 4, cudaMemcpyDeviceToHost, h->s), "gb");
+      mlp_ck(cudaStreamSynchronize(h->s), "gradients");
+      if (Ws[l])
+        for (int r = 0; r < nrows[l]; ++r)
+          for (int c = 0; c < cols[l]; ++c) Ws[l][(size_t)r * cols[l] + c] = w[(size_t)r * ldp[l] + c];
+      if (bs[l])
+        for (int r = 0; r < nrows[l]; ++r) bs[l][r] = bb[(size_t)r];
+    }
+  });
+}
+
+int pdlp_mlp_train(pdlp_mlp h, int32_t epochs, int32_t batch, float lr, float weight_decay, uint64_t seed,
+                   double* epoch_loss, double* train_ms) {
+  return mlp_guard(h, [&]() {
+    if (!h->dataX || epochs < 1 || batch < 1 || batch > h->maxb) throw std::string("bad: train arguments");
+    const int64_t N = h->ndata;
+    std::vector<int> perm((size_t)N);
+    uint64_t st = seed * 0x9E3779B97F4A7C15ULL + 1;
+    auto rnd = [&]() {
+      st ^= st << 13;
+      st ^= st >> 7;
+      st ^= st << 17;
+      return st;
+    };
+    cudaEvent_t e0, e1;
+    mlp_ck(cudaEventCreate(&e0), "event");
+    mlp_ck(cudaEventCreate(&e1), "event");
+    float total_ms = 0.f;
+    for (int ep = 0; ep < epochs; ++ep) {
+      for (int64_t i = 0; i < N; ++i) perm[(size_t)i] = (int)i;
+      for (int64_t i = N - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(rnd() % (uint64_t)(i + 1))]);
+      double lsum = 0.0;
+      int64_t nb = 0;
+      mlp_ck(cudaEventRecord(e0, h->s), "event");
+      for (int64_t off = 0; off + batch <= N; off += batch, ++nb) {
+        mlp_ck(cudaMemcpyAsync(h->idx, perm.data() + off, sizeof(int) * batch, cudaMemcpyHostToDevice, h->s), "idx");
+        forward(h, h->dataX, h->idx, batch);
+        lsum += backward(h, h->dataT, h->idx, batch);
+        h->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+        for (int l = 0; l < 3; ++l) {
+          k_mlp_adamw<<<gridn(h->wsz[l]), 256, 0, h->s>>>(h->W[l], h->mW[l], h->vW[l], h->gW[l], h->wsz[l], lr,
+                                                           weight_decay, b1, b2, c1, c2, 1e-8f);
+          k_mlp_adamw<<<gridn(h->bsz[l]), 256, 0, h->s>>>(h->b[l], h->mb[l], h->vb[l], h->gb[l], h->bsz[l], lr, 0.f,
+                                                           b1, b2, c1, c2, 1e-8f);
+        }
+        refresh_bf16(h);
+      }
+      mlp_ck(cudaEventRecord(e1, h->s), "event");
+      mlp_ck(cudaEventSynchronize(e1), "event");
+      float ms = 0.f;
+      mlp_ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+      total_ms += ms;
+      if (epoch_loss) epoch_loss[ep] = nb ? lsum / nb : 0.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    check_err(h);
+    if (train_ms) *train_ms = total_ms;
+  });
+}
+
+}  // extern "C"

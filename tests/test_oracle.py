@@ -318,3 +318,37 @@ def test_golden_regression():
         assert r["iters"] == rec["iters"]
         assert list(map(int, r["restart_iters"])) == rec["restart_iters"]
         assert abs(r["primal_obj"] - rec["primal_obj"]) <= 1e-12 * abs(rec["primal_obj"])
+
+
+# ---------------------------------------------------------------- warm-start network (oracle)
+
+def test_mlp_oracle_gradients_match_finite_differences():
+    """The plain (float64, no BF16) network's backward pass against central differences."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    params = [p.astype(np.float64) for p in mlp.init_params(5, 7, 3, seed=1)]
+    X = rng.standard_normal((4, 5))
+    T = rng.standard_normal((4, 3))
+    loss, grads = mlp.loss_and_grads(params, X, T, use_bf16=False)
+    h = 1e-6
+    for p, g in zip(params, grads):
+        flat = p.reshape(-1)
+        gf = g.reshape(-1)
+        for i in range(0, flat.shape[0], max(1, flat.shape[0] // 9)):
+            old = flat[i]
+            flat[i] = old + h
+            lp = mlp.loss_and_grads(params, X, T, use_bf16=False)[0]
+            flat[i] = old - h
+            lm = mlp.loss_and_grads(params, X, T, use_bf16=False)[0]
+            flat[i] = old
+            assert abs((lp - lm) / (2 * h) - gf[i]) <= 1e-6 * (1 + abs(gf[i]))
+
+
+def test_bf16_rounding():
+    from oracle import mlp
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, 3.14159, -2.5e-3, 0.0], dtype=np.float32)
+    r = mlp.bf16(vals)
+    assert r[0] == 1.0 and r[1] == 1.0          # a tie rounds to even
+    assert r[2] == 1.0 + 2 ** -7
+    assert abs(r[3] - 3.140625) < 1e-12
+    assert np.all(np.abs(r - vals) <= np.abs(vals) * 2 ** -8)
