@@ -293,13 +293,53 @@ def bench_mcf(args):
     print(json.dumps(out))
 
 
+def bench_warmstart(args):
+    """Learned warm start on a transportation family (lpgen.transport_family(S, D), seed 0):
+    solutions of args.ws_train instances (seeds 1..) from the batched solver train the
+    3-layer width-1024 BF16 MLP on the device; held-out seeds 100001.. are solved cold and
+    warm-started (KKT fallback) to 1e-4 and 1e-8."""
+    import torch
+    import lpgen
+    from paper_2312_14832_b300 import warmstart as ws
+    torch.cuda.set_device(0)
+    fam = lpgen.transport_family(args.ws_supplies, args.ws_demands, seed=0)
+    t0 = time.perf_counter()
+    train = [lpgen.transport_instance(fam, s) for s in range(1, args.ws_train + 1)]
+    held = [lpgen.transport_instance(fam, s) for s in range(100001, 100001 + args.ws_heldout)]
+    gen_s = time.perf_counter() - t0
+    P = np.array([lp["features"] for lp in train])
+    t0 = time.perf_counter()
+    X, Y, W, its, st, dev = ws.solve_family(train, tol=1e-6)
+    data_s = time.perf_counter() - t0
+    model = ws.WarmStart(P.shape[1], train[0]["n"], train[0]["m"], hidden=1024, max_batch=256, seed=0)
+    fit = model.fit(P, X, Y, W, epochs=args.ws_epochs, batch=256, lr=1e-3)
+    Ph = np.array([lp["features"] for lp in held])
+    ev = ws.evaluate(model, held, Ph, tols=(1e-4, 1e-8))
+    model.close()
+    n_in, hid, n_out = P.shape[1], 1024, train[0]["n"] + train[0]["m"] + 1
+    flop_step = 2 * 256 * (n_in * hid + hid * hid + hid * n_out) * 3
+    steps = args.ws_epochs * (len(train) // 256)
+    out = {"metric": METRIC, "value": ev["1e-04"]["iters_ratio"], "unit": "cold/warm mean iterations to 1e-4",
+           "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "impl": "ours-warmstart", "dtype": "bf16 MLP / f64 LP",
+           "config": {"workload": f"transportation family {args.ws_supplies} x {args.ws_demands} (n="
+                                  f"{train[0]['n']}, m={train[0]['m']}), s,d ~ Gamma(2,50), costs = distance + "
+                                  "N(0,0.05); MLP in -> 1024 -> 1024 -> n+m+1 (BF16, tcgen05)",
+                      "train": len(train), "heldout": len(held), "epochs": args.ws_epochs},
+           "evaluation": ev, "train_loss_first_last": [float(fit["losses"][0]), float(fit["losses"][-1])],
+           "train_device_s": fit["train_device_s"],
+           "train_tflops": flop_step * steps / max(fit["train_device_s"], 1e-9) / 1e12,
+           "data_generation": {"solve_device_s": dev, "wall_s": data_s, "mean_iters": float(its.mean()),
+                               "optimal": int(np.sum(st == 0)), "generate_s": gen_s}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batched", "mcf"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batched", "mcf", "warmstart"])
     ap.add_argument("--ttt-budget", type=float, default=0.0,
                     help="seconds for a cold time-to-1e-4 solve of the bench workload (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -309,12 +349,20 @@ def main():
     ap.add_argument("--batch-scaling", type=int, default=0)
     ap.add_argument("--seq-sample", type=int, default=32)
     ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-1e-4 solve (mcf)")
+    ap.add_argument("--ws-train", type=int, default=50000)
+    ap.add_argument("--ws-heldout", type=int, default=1000)
+    ap.add_argument("--ws-epochs", type=int, default=30)
+    ap.add_argument("--ws-supplies", type=int, default=40)
+    ap.add_argument("--ws-demands", type=int, default=60)
     args = ap.parse_args()
     if args.workload == "batched":
         bench_batched(args)
         return
     if args.workload == "mcf":
         bench_mcf(args)
+        return
+    if args.workload == "warmstart":
+        bench_warmstart(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -231,12 +231,15 @@ int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const in
                      const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* c,
                      const double* q, const double* l, const double* u, const pdlp_params* p);
 
-/* Solves every LP of the batch from a cold start (x = proj_X(0), y = 0) with the
- * tolerance, iteration limit, check interval and restart factors of p (NULL = setup
- * params; time_limit_s is not used).  res[count] receives one result per LP (solve_s
- * and device_ms are those of the whole batch); x_out (sum n_b) and y_out (sum m_b),
- * either may be NULL, receive the returned points back to back in the caller's order. */
-int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, pdlp_result* res, double* x_out, double* y_out);
+/* Solves every LP of the batch from (x0, y0) projected onto X and Y (NULL = 0 for
+ * every LP, the cold start) with initial primal weights omega0[count] (NULL or <= 0 =
+ * ||c||/||q|| of the LP), using the tolerance, iteration limit, check interval and
+ * restart factors of p (NULL = setup params; time_limit_s is not used).  x0 (sum n_b)
+ * and y0 (sum m_b) are back to back in the caller's order, unscaled.  res[count]
+ * receives one result per LP (solve_s and device_ms are those of the whole batch);
+ * x_out and y_out (either may be NULL) receive the returned points, back to back. */
+int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const double* y0, const double* omega0,
+                     pdlp_result* res, double* x_out, double* y_out);
 
 /* ---------------------------------------------------------------- dense kernels
  * C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then max(., 0) if relu) on the tcgen05

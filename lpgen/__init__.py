@@ -34,6 +34,8 @@ __all__ = [
     "planted_random",
     "batch_planted",
     "mcf",
+    "transport_family",
+    "transport_instance",
     "planted_zipf",
     "box_only",
     "tiny_lp",
@@ -350,3 +352,32 @@ def mcf(seed=0, nodes=200_000, arcs=1_000_000, commodities=8, walk_len=20, fill=
     n = Kc * A
     return dict(m=m, n=n, m1=m1, row_ptr=row_ptr, col_idx=col_idx, val=val, c=cost, q=q,
                 l=np.zeros(n), u=np.full(n, np.inf), x_feasible=x)
+
+
+def transport_family(supplies=40, demands=60, seed=0):
+    """A family of transportation LPs sharing one cost matrix: supply and demand points
+    uniform in [0,1]^2, cost = Euclidean distance + N(0, 0.05) (drawn once per family)."""
+    rng = np.random.default_rng(seed)
+    P = rng.random((supplies, 2))
+    Q = rng.random((demands, 2))
+    cost = np.sqrt(((P[:, None, :] - Q[None, :, :]) ** 2).sum(-1)) + rng.normal(0.0, 0.05, (supplies, demands))
+    return dict(S=supplies, D=demands, cost=cost, seed=seed)
+
+
+def transport_instance(family, seed):
+    """One LP of the family: supplies s ~ Gamma(2, 50), demands d ~ Gamma(2, 50) rescaled
+    to the same total; min sum c_ij x_ij  s.t.  sum_j x_ij = s_i, sum_i x_ij = d_j, x >= 0
+    (all rows equalities, one of them redundant).  Column i*D + j is x_ij.  ``features``
+    holds (s, d), the parameters a warm-start model sees."""
+    S, D = family["S"], family["D"]
+    rng = np.random.default_rng(seed)
+    s = rng.gamma(2.0, 50.0, S)
+    d = rng.gamma(2.0, 50.0, D)
+    d *= s.sum() / d.sum()
+    n, m = S * D, S + D
+    cols = np.arange(n, dtype=np.int64)
+    rows = np.concatenate([cols // D, S + cols % D])
+    row_ptr, col_idx, val = csr_from_coo(m, n, rows, np.concatenate([cols, cols]), np.ones(2 * n))
+    return dict(m=m, n=n, m1=m, row_ptr=row_ptr, col_idx=col_idx, val=val,
+                c=family["cost"].reshape(-1).copy(), q=np.concatenate([s, d]), l=np.zeros(n),
+                u=np.full(n, np.inf), features=np.concatenate([s, d]))

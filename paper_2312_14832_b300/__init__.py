@@ -212,7 +212,8 @@ class BatchSolver:
     def from_lps(cls, lps, **params):
         return cls(lps, **params)
 
-    def solve(self, want_points=True, **overrides):
+    def solve(self, want_points=True, x0=None, y0=None, omega0=None, **overrides):
+        """x0, y0: warm starts back to back (sum n, sum m) or per-LP lists; omega0: per LP."""
         p = _lib.Params()
         C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
         for k, v in overrides.items():
@@ -222,7 +223,18 @@ class BatchSolver:
         res = (_lib.Result * self.count)()
         x = np.empty(int(self.n.sum())) if want_points else None
         y = np.empty(int(self.m.sum())) if want_points else None
-        rc = self._lib.pdlp_batch_solve(self._h, C.byref(p), res, x.ctypes.data if want_points else None,
+        cat = lambda v: None if v is None else np.ascontiguousarray(
+            np.concatenate(v) if isinstance(v, (list, tuple)) else v, dtype=np.float64)
+        x0a, y0a, w0a = cat(x0), cat(y0), (None if omega0 is None else np.ascontiguousarray(omega0, np.float64))
+        if x0a is not None and x0a.shape[0] != int(self.n.sum()):
+            raise ValueError("x0 must have sum(n) entries")
+        if y0a is not None and y0a.shape[0] != int(self.m.sum()):
+            raise ValueError("y0 must have sum(m) entries")
+        if w0a is not None and w0a.shape[0] != self.count:
+            raise ValueError("omega0 must have one entry per LP")
+        ptr = lambda a: None if a is None or a.size == 0 else a.ctypes.data
+        rc = self._lib.pdlp_batch_solve(self._h, C.byref(p), ptr(x0a), ptr(y0a), ptr(w0a), res,
+                                        x.ctypes.data if want_points else None,
                                         y.ctypes.data if (want_points and y.size) else None)
         if rc < 0:
             raise SolverError(rc, self._lib.pdlp_last_error(self._h).decode())

@@ -68,7 +68,7 @@ SIGNATURES = {
     "pdlp_spmv_csr_noalloc": (C.c_int, [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pdlp_batch_setup": (C.c_int, [C.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                    C.POINTER(Params)]),
-    "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp]),
+    "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _vp]),
     "pdlp_tc_gemm": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
     "pdlp_mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _i32, _i32, _i32]),
     "pdlp_mlp_free": (None, [_vp]),

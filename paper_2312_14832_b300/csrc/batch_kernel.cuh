@@ -36,6 +36,8 @@ struct BatchArgs {
   const double *c, *l, *u, *q, *invDr, *invDc;   // scaled problem, internal order
   double *sx, *sy, *xa, *ya, *kxp, *g, *kx_a, *g_a;
   double *xout, *yout;       // returned point per LP (scaled, internal order)
+  const double *x0, *y0;     // warm start (scaled, internal order) or null
+  const double* omega0;      // initial primal weight per LP (<= 0: the default) or null
   DevState* st;              // per LP
   DevParams P;
   int check_every;
@@ -251,23 +253,26 @@ __device__ void batch_solve_one(const BatchArgs& A, int b) {
     }
     __syncthreads();
     if (!(omega > 0.0)) omega = scal[0];
+    if (A.omega0 != nullptr && A.omega0[b] > 0.0) omega = A.omega0[b];
   }
   DevParams P = A.P;
   P.cnorm = scal[1];
   P.qnorm = scal[2];
 
-  // ---- initial point and anchor
+  // ---- initial point (the warm start or 0, projected onto X and Y) and anchor
   for (int j = tid; j < D.npad; j += nt) {
     const int64_t gj = D.c0 + j;
-    const double x0 = j < n ? clamp_box(0.0, A.l[gj], A.u[gj]) : 0.0;
+    const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
     xs[j] = x0;
     A.xa[gj] = x0;
     A.sx[gj] = 0.0;
   }
   for (int i = tid; i < D.mpad; i += nt) {
     const int64_t gi = D.r0 + i;
-    ys[i] = 0.0;
-    A.ya[gi] = 0.0;
+    double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
+    if (i >= D.m1) y0 = max0(y0);
+    ys[i] = y0;
+    A.ya[gi] = y0;
     A.sy[gi] = 0.0;
   }
   __syncthreads();

@@ -112,7 +112,7 @@ struct pdlp_ctx {
   int32_t* order = nullptr;
   int32_t* next = nullptr;
   DevState* bstate = nullptr;
-  double *bx = nullptr, *by = nullptr;
+  double *bx = nullptr, *by = nullptr, *bomega = nullptr;
   int batch_grid = 0;
   size_t batch_smem = 0;
   int xs_off = 0, ys_off = 0, red_off = 0;
@@ -1158,10 +1158,29 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   CK(cudaStreamSynchronize(h->s));
 }
 
-static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, pdlp_result* res, double* x_out, double* y_out) {
+static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0,
+                            const double* omega0, pdlp_result* res, double* x_out, double* y_out) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   auto t_start = std::chrono::steady_clock::now();
   BatchArgs A;
+  A.x0 = nullptr;
+  A.y0 = nullptr;
+  A.omega0 = nullptr;
+  if (x0) {
+    copy_in(h, h->stage_n, x0, h->n);
+    k_permute_in<<<grid_for(h->npad), 256, 0, h->s>>>(h->tn, h->stage_n, h->perm_c, h->Dc, h->npad, 0.0);
+    A.x0 = h->tn;
+  }
+  if (y0 && h->m > 0) {
+    copy_in(h, h->stage_m, y0, h->m);
+    k_permute_in<<<grid_for(h->mpad), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, h->mpad, 0.0);
+    A.y0 = h->tm;
+  }
+  if (omega0) {
+    if (!h->bomega) h->bomega = dalloc<double>(h, (size_t)h->count);
+    copy_in(h, h->bomega, omega0, h->count);
+    A.omega0 = h->bomega;
+  }
   A.desc = h->desc;
   A.order = h->order;
   A.count = (int32_t)h->count;
@@ -1497,11 +1516,12 @@ int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const in
   return PDLP_OK;
 }
 
-int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, pdlp_result* res, double* x_out, double* y_out) {
+int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const double* y0, const double* omega0,
+                     pdlp_result* res, double* x_out, double* y_out) {
   return guarded(h, [&]() {
     if (!h->is_batch) invalid("not a batch handle (use pdlp_solve)");
     pdlp_params sp = p ? *p : h->p;
-    return batch_solve_impl(h, sp, res, x_out, y_out);
+    return batch_solve_impl(h, sp, x0, y0, omega0, res, x_out, y_out);
   });
 }
 

@@ -1,0 +1,116 @@
+"""Learned warm start for a family of LPs (an extension of this library; the paper has no
+learned component).
+
+An MLP (``MLP``: three linear layers, ReLU, BF16 tcgen05 products, AdamW on the device)
+maps the parameters of an LP of the family (for the transportation family: supplies
+and demands) to a starting point x0, y0 and an initial primal weight omega0.  It is
+trained on solutions the batched solver computes, and used through the batched
+solver's warm start.  The KKT error decides: for each LP the prediction is used only
+if its largest relative error (the three tests of Section 2, measured by the solver
+at iteration 0) is below the cold start's; otherwise that LP starts cold.
+
+Normalisation is per component: parameters and targets are standardised with the
+training set's mean and standard deviation (floor 1e-6); omega is learned in log
+space.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import MLP, BatchSolver
+
+
+def _init_params(n_in, hidden, n_out, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for fi, fo in ((n_in, hidden), (hidden, hidden), (hidden, n_out)):
+        a = 1.0 / np.sqrt(fi)
+        out.append(rng.uniform(-a, a, (fo, fi)).astype(np.float32))
+        out.append(rng.uniform(-a, a, fo).astype(np.float32))
+    return out
+
+
+def solve_family(lps, tol, chunk=4096, **params):
+    """Solves LPs with the batched solver, `chunk` per launch.  Returns x (N x n),
+    y (N x m), omega (N,), iterations (N,), status (N,) and the device seconds."""
+    xs, ys, ws, its, sts, dev = [], [], [], [], [], 0.0
+    for s in range(0, len(lps), chunk):
+        part = lps[s:s + chunk]
+        with BatchSolver.from_lps(part, **params) as b:
+            res = b.solve(tol=tol)
+        dev += res[0]["device_ms"] * 1e-3
+        for r in res:
+            xs.append(r["x"])
+            ys.append(r["y"])
+            ws.append(r["omega"])
+            its.append(r["iters"])
+            sts.append(r["status"])
+    return (np.array(xs), np.array(ys), np.array(ws), np.array(its), np.array(sts), dev)
+
+
+class WarmStart:
+    def __init__(self, n_params, n, m, hidden=1024, max_batch=256, seed=0):
+        self.n_params, self.n, self.m = n_params, n, m
+        self.net = MLP(n_params, hidden, n + m + 1, max_batch)
+        self.net.set_params(_init_params(n_params, hidden, n + m + 1, seed))
+        self.max_batch = max_batch
+
+    def _targets(self, X, Y, W):
+        return np.concatenate([X, Y, np.log(np.maximum(W, 1e-300))[:, None]], axis=1)
+
+    def fit(self, P, X, Y, W, epochs=30, batch=256, lr=1e-3, weight_decay=0.0, seed=0):
+        T = self._targets(X, Y, W)
+        self.p_mu, self.p_sd = P.mean(0), np.maximum(P.std(0), 1e-6)
+        self.t_mu, self.t_sd = T.mean(0), np.maximum(T.std(0), 1e-6)
+        self.net.load_data((P - self.p_mu) / self.p_sd, (T - self.t_mu) / self.t_sd)
+        t0 = time.perf_counter()
+        losses, ms = self.net.train(epochs, min(batch, self.max_batch), lr, weight_decay, seed)
+        return dict(losses=losses, train_device_s=ms * 1e-3, train_wall_s=time.perf_counter() - t0)
+
+    def predict(self, P):
+        self.net.load_data((np.asarray(P) - self.p_mu) / self.p_sd)
+        Tn = self.net.forward(np.arange(len(P), dtype=np.int32))
+        T = Tn.astype(np.float64) * self.t_sd + self.t_mu
+        x0 = np.maximum(T[:, :self.n], 0.0)
+        y0 = T[:, self.n:self.n + self.m]
+        w0 = np.exp(T[:, -1])
+        return x0, y0, w0
+
+    def close(self):
+        self.net.close()
+
+
+def evaluate(model, lps, P, tols=(1e-4, 1e-8), **params):
+    """Cold start against the learned warm start (with the KKT fallback) on held-out LPs,
+    all in one batched launch per solve.  Returns per tolerance the mean iterations and
+    the batch device time of both, and how many LPs used the prediction."""
+    x0, y0, w0 = model.predict(P)
+    out = {}
+    with BatchSolver.from_lps(lps, **params) as b:
+        c0 = b.solve(tol=0.0, max_iter=0, want_points=False)
+        p0 = b.solve(tol=0.0, max_iter=0, want_points=False, x0=list(x0), y0=list(y0), omega0=w0)
+        e_cold = np.array([max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) for r in c0])
+        e_pred = np.array([max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) for r in p0])
+        use = e_pred < e_cold
+        xs = [x0[i] if use[i] else np.zeros(lp["n"]) for i, lp in enumerate(lps)]
+        ys = [y0[i] if use[i] else np.zeros(lp["m"]) for i, lp in enumerate(lps)]
+        ws = np.where(use, w0, 0.0)
+        for tol in tols:
+            cold = b.solve(tol=tol, want_points=False)
+            warm = b.solve(tol=tol, want_points=False, x0=xs, y0=ys, omega0=ws)
+            ci = np.array([r["iters"] for r in cold])
+            wi = np.array([r["iters"] for r in warm])
+            out[f"{tol:.0e}"] = dict(
+                cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()),
+                iters_ratio=float(ci.mean() / max(wi.mean(), 1e-9)),
+                cold_device_s=cold[0]["device_ms"] * 1e-3, warm_device_s=warm[0]["device_ms"] * 1e-3,
+                time_ratio=cold[0]["device_ms"] / max(warm[0]["device_ms"], 1e-9),
+                cold_optimal=int(sum(r["status"] == 0 for r in cold)),
+                warm_optimal=int(sum(r["status"] == 0 for r in warm)),
+                warm_fewer_iters=int(np.sum(wi < ci)), warm_more_iters=int(np.sum(wi > ci)))
+    out["used_prediction"] = int(use.sum())
+    out["initial_err_cold_median"] = float(np.median(e_cold))
+    out["initial_err_pred_median"] = float(np.median(e_pred))
+    return out

@@ -114,3 +114,19 @@ def test_batch_matches_single_solver(pk):
             r1 = s.solve(tol=1e-6)
         assert r1["iters"] == r["iters"]
         close_rel(r["x"], r1["x"], 1e-10)
+
+
+def test_batch_warm_start_matches_oracle(pk):
+    lps = fixed_iteration_batch()[:5]
+    rng = np.random.default_rng(3)
+    x0 = [lp["x_star"] + 0.1 * rng.standard_normal(lp["n"]) if "x_star" in lp else rng.standard_normal(lp["n"])
+          for lp in lps]
+    y0 = [rng.standard_normal(lp["m"]) for lp in lps]
+    w0 = np.array([0.5, 0.0, 2.0, 1.0, 0.0])
+    with pk.BatchSolver.from_lps(lps) as b:
+        res = b.solve(tol=0.0, max_iter=400, x0=x0, y0=y0, omega0=w0)
+    for i, (lp, r) in enumerate(zip(lps, res)):
+        ref = oracle.solve(lp, tol=0.0, max_iter=400, x0=x0[i], y0=y0[i], omega0=float(w0[i]))
+        assert r["restarts"] == ref["restarts"]
+        close_rel(r["x"], ref["x"], 1e-10)
+        close_rel(r["y"], ref["y"], 1e-10)
