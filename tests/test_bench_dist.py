@@ -1,0 +1,47 @@
+"""Host-side logic of bench.py's multi-GPU (replicas) path on CPU: two gloo ranks each
+time their own replica; the reported time is the maximum over ranks and the value the
+units of all ranks divided by it."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms_local = 100.0 + 50.0 * rank          # rank 1 is slower
+    ms, value = bench.aggregate_ranks(ms_local, units_local=640, world=world, dist_mod=dist)
+    out[rank] = (ms, value)
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        out = man.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        res = dict(out)
+    for r in range(2):
+        ms, value = res[r]
+        assert ms == pytest.approx(150.0)
+        assert value == pytest.approx(2 * 640 / 0.150)
