@@ -95,6 +95,15 @@ typedef struct {
   double mixed_switch_tol; /* PDLP_MIXED: FP32 iterations until the FP64-measured largest
                             relative error is <= this (or stops improving for 16 checks),
                             then FP64 iterations; 0 = max(tol, 1e-5)                      */
+  int32_t cluster_ctas;    /* pdlp_batch_solve: CTAs that share one LP (a thread-block
+                              cluster; each keeps x and y in shared memory and owns a
+                              slice of the rows and columns): 1..16, or 0 = automatic
+                              (one CTA per LP when the batch fills the GPU, else up to
+                              16 per LP)                                                    */
+  int32_t resident;        /* pdlp_batch_solve: copy each CTA's slice of K and K' and the
+                              vectors of its rows and columns into shared memory for the
+                              iterations: 0 = automatic (when every LP's slices fit without
+                              lowering the CTAs per SM), 1 = never, 2 = whenever they fit  */
 } pdlp_params;
 
 typedef struct {
@@ -139,6 +148,8 @@ typedef struct {
   double algorithmic_bytes_per_iter; /* unique-bytes model: 24 nnz + 68 (m + n)         */
   double stored_bytes_per_iter;      /* the same with padding slots counted               */
   double eta, omega0, norm_K;
+  int32_t batch_team;          /* batch handles: CTAs per LP of the last pdlp_batch_solve    */
+  int32_t batch_resident;      /* batch handles: 1 if that launch ran from shared memory      */
 } pdlp_info;
 
 /* Fills p with the defaults listed above. */

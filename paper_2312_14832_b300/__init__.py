@@ -249,6 +249,14 @@ class BatchSolver:
             out.append(d)
         return out
 
+    def info(self) -> dict:
+        """Layout sizes, and the team size and resident mode of the last solve."""
+        i = _lib.Info()
+        rc = self._lib.pdlp_get_info(self._h, C.byref(i))
+        if rc < 0:
+            raise SolverError(rc, self._lib.pdlp_last_error(self._h).decode())
+        return {f: getattr(i, f) for f, _ in _lib.Info._fields_}
+
     def spmv(self, v, transpose=False):
         """Block-diagonal K v (or K' v) of the whole batch."""
         a = np.ascontiguousarray(v, dtype=np.float64)

@@ -20,7 +20,7 @@ class Params(C.Structure):
                 ("eta", C.c_double), ("tile_slots", C.c_int32), ("inputs_on_device", C.c_int32),
                 ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("tile_chunks", C.c_int32),
                 ("spmv_batch", C.c_int32), ("precision", C.c_int32),
-                ("mixed_switch_tol", C.c_double)]
+                ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -47,7 +47,8 @@ class Info(C.Structure):
                 ("tile_chunks_K", C.c_int32), ("tile_chunks_Kt", C.c_int32),
                 ("spmv_batch_K", C.c_int32), ("spmv_batch_Kt", C.c_int32),
                 ("algorithmic_bytes_per_iter", C.c_double), ("stored_bytes_per_iter", C.c_double),
-                ("eta", C.c_double), ("omega0", C.c_double), ("norm_K", C.c_double)]
+                ("eta", C.c_double), ("omega0", C.c_double), ("norm_K", C.c_double),
+                ("batch_team", C.c_int32), ("batch_resident", C.c_int32)]
 
 
 # every function declared in include/pdlp.h: name -> (restype, argtypes)

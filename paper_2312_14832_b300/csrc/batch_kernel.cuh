@@ -7,9 +7,19 @@
 // the PDHG iterations, and the checks with the restart rule and the termination
 // tests, all without leaving the CTA.  The two iterates live in shared memory, so
 // the random gathers of both SpMVs are shared-memory loads; the matrix and the other
-// per-row vectors stream from global memory.  Phases are separated by __syncthreads:
-// the primal phase reads y and writes x, the dual phase reads x and writes y.
+// per-row vectors stream from global memory.  Phases are separated by barriers: the
+// primal phase reads y and writes x, the dual phase reads x and writes y.
+//
+// A team of CTAs can share one LP (k_batch_solve<true>, a thread-block cluster of up
+// to 16 CTAs): CTA r owns a contiguous range of the LP's SELL chunks of K (rows) and
+// of K' (columns), balanced by slot count, and every CTA keeps a full replica of x
+// and y in its shared memory.  An owner writes each new x_j (y_i) into all replicas
+// through distributed shared memory, and a cluster barrier ends each phase, so the
+// gathers of both SpMVs stay local.  Team-wide sums add the CTAs' partial sums in
+// rank order in every CTA, so all CTAs take the same restart decisions and leave the
+// loop together; the cluster barrier is the hardware barrier, not a spin.
 #pragma once
+#include <cooperative_groups.h>
 #include "kernels.cuh"
 
 namespace pdlp {
@@ -45,19 +55,77 @@ struct BatchArgs {
   int power_iters;
   double step_scale, eta_fixed, omega_fixed;
   int xs_off, ys_off, red_off;   // offsets (doubles) of x, y and the reduction area in shared memory
+  int part_off;                  // team partial sums (kPartBuf doubles)
 };
+
+constexpr int kMaxTeam = 16;                         // CTAs per LP (non-portable cluster size)
+constexpr int kPartStride = 16;                      // >= the widest team sum (10 values)
+constexpr int kPartBuf = 2 * kMaxTeam * kPartStride; // two alternating areas
+
+// The CTAs that solve one LP: one CTA (kCl = false) or the CTAs of a cluster.
+template <bool kCl>
+struct Team {
+  int rank = 0, size = 1;
+  __device__ __forceinline__ void init() {
+    if constexpr (kCl) {
+      cooperative_groups::cluster_group c = cooperative_groups::this_cluster();
+      rank = (int)c.block_rank();
+      size = (int)c.num_blocks();
+    }
+  }
+  // barrier of the team (release/acquire at cluster scope for a cluster)
+  __device__ __forceinline__ void sync() const {
+    if constexpr (kCl) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+  }
+  template <class T>
+  __device__ __forceinline__ T* at(T* p, int r) const {
+    if constexpr (kCl) return cooperative_groups::this_cluster().map_shared_rank(p, (unsigned)r);
+    else return p;
+  }
+  // a[i] = v in the replica of every CTA of the team
+  __device__ __forceinline__ void put(double* a, int i, double v) const {
+    if constexpr (kCl) {
+      for (int k = 0; k < size; ++k) {
+        int r = rank + k;
+        if (r >= size) r -= size;
+        *at(a + i, r) = v;
+      }
+    } else {
+      a[i] = v;
+    }
+  }
+};
+
+// First chunk of piece r when chunks [c0, c1) are cut into `size` pieces of about
+// equal slot counts (piece r is [split_point(r), split_point(r + 1))).
+__device__ __forceinline__ int split_point(const int32_t* __restrict__ cptr, int c0, int c1, int r, int size) {
+  if (r <= 0) return c0;
+  if (r >= size) return c1;
+  const long long s0 = cptr[c0], s1 = cptr[c1];
+  const long long target = s0 + (s1 - s0) * r / size;
+  int lo = c0, hi = c1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cptr[mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
 
 // Gather source of a batched SpMV: the shared-memory x or y, or a global vector.
 enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
 
-// Rows in chunks [c0, c1) of a SELL matrix; warp w of the CTA takes chunks c0+w,
+// Rows in chunks [c0, c1) of a SELL matrix (in global memory, or a slice staged in
+// shared memory: kMatS); warp w of the CTA takes chunks c0+w,
 // c0+w+nw, ...  Each lane sums its row, gathering src[col - base], then calls
-// epi(local_row, sum).  Loads of kBB slots are issued together.
+// epi(local_row, sum), local_row counted from chunk cbase (the LP's first chunk).
+// Loads of kBB slots are issued together.
 constexpr int kBB = 4;
-template <int SRC, class F>
+template <int SRC, bool kMatS, class F>
 __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
-                                           const double* __restrict__ val, int c0, int c1, int64_t base,
-                                           const double* gsrc, const BatchArgs& A, F epi) {
+                                           const double* __restrict__ val, int c0, int c1, int cbase,
+                                           int64_t base, const double* gsrc, const BatchArgs& A, F epi) {
   extern __shared__ double bsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* xs = bsm + A.xs_off;
@@ -72,8 +140,13 @@ __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, con
 #pragma unroll
       for (int j = 0; j < kBB; ++j)
         if (j < nb) {
-          v[j] = __ldcs(val + (size_t)(s + j) * 32 + lane);
-          ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
+          if constexpr (kMatS) {
+            v[j] = val[(size_t)(s + j) * 32 + lane];
+            ci[j] = col[(size_t)(s + j) * 32 + lane] - (int)base;
+          } else {
+            v[j] = __ldcs(val + (size_t)(s + j) * 32 + lane);
+            ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
+          }
         }
 #pragma unroll
       for (int j = 0; j < kBB; ++j) {
@@ -88,7 +161,38 @@ __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, con
       for (int j = 0; j < kBB; ++j)
         if (j < nb) acc = fma(v[j], xv[j], acc);
     }
-    epi((ch - c0) * 32 + lane, acc);
+    epi((ch - cbase) * 32 + lane, acc);
+  }
+}
+
+// Rows of this CTA's resident slice of a SELL matrix (shared memory): chunk ch spans
+// elements [cp[ch], cp[ch + 1]) of val / goff (32 per slot, lane = row), goff holds
+// the byte offset of each entry's gathered element within src.  Same summation order
+// per row as batch_rows; epi(row0 + 32 ch + lane, sum).
+template <class F>
+__device__ __forceinline__ void rows_s(const int* __restrict__ cp, const double* __restrict__ val,
+                                       const int* __restrict__ goff, int nch, int row0,
+                                       const double* __restrict__ src, F epi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const char* sb = reinterpret_cast<const char*>(src);
+  for (int ch = wid; ch < nch; ch += nw) {
+    int e = cp[ch] + lane;
+    const int e1 = cp[ch + 1];
+    double acc = 0.0;
+    for (; e + 96 < e1; e += 128) {
+      const double v0 = val[e], v1 = val[e + 32], v2 = val[e + 64], v3 = val[e + 96];
+      const int o0 = goff[e], o1 = goff[e + 32], o2 = goff[e + 64], o3 = goff[e + 96];
+      const double x0 = *reinterpret_cast<const double*>(sb + o0);
+      const double x1 = *reinterpret_cast<const double*>(sb + o1);
+      const double x2 = *reinterpret_cast<const double*>(sb + o2);
+      const double x3 = *reinterpret_cast<const double*>(sb + o3);
+      acc = fma(v0, x0, acc);
+      acc = fma(v1, x1, acc);
+      acc = fma(v2, x2, acc);
+      acc = fma(v3, x3, acc);
+    }
+    for (; e < e1; e += 32) acc = fma(val[e], *reinterpret_cast<const double*>(sb + goff[e]), acc);
+    epi(row0 + ch * 32 + lane, acc);
   }
 }
 
@@ -111,10 +215,49 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   __syncthreads();
 }
 
+// Sum over the team of NV values per thread into red[0..NV) of every CTA: the CTA
+// partials (block_sum) are written into each CTA's partial area, then added in rank
+// order, so every CTA holds the same totals.  The two partial areas alternate
+// (`flip`); the team barrier inside the next sum keeps an area from being reused
+// before every CTA has read it.
+template <int NV, bool kCl>
+__device__ __forceinline__ void team_sum(double (&v)[NV], double* red, double* part, int& flip, const Team<kCl>& T) {
+  block_sum<NV>(v, red);
+  if constexpr (kCl) {
+    double* pa = part + flip * (kMaxTeam * kPartStride);
+    flip ^= 1;
+    const int tid = threadIdx.x;
+    if (tid < NV) {
+      const double s = red[tid];
+      for (int r = 0; r < T.size; ++r) *T.at(pa + T.rank * kPartStride + tid, r) = s;
+    }
+    T.sync();
+    if (tid < NV) {
+      double s = 0.0;
+      for (int r = 0; r < T.size; ++r) s += pa[r * kPartStride + tid];
+      red[tid] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Euclidean norm over the team of v[j0..j1) (each CTA passes its own range).
+template <bool kCl>
+__device__ __forceinline__ double team_norm(const double* v, int j0, int j1, double* red, double* part, int& flip,
+                                            const Team<kCl>& T) {
+  double a[1] = {0.0};
+  for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) a[0] = fma(v[j], v[j], a[0]);
+  team_sum<1>(a, red, part, flip, T);
+  return sqrt(red[0]);
+}
+
 // The 18 check quantities of the LP (same definitions as k_kkt_partials), reduced
-// over the CTA into tot[0..NQ).  avg_is_cur: the average equals the current point.
+// over the team into tot[0..NQ); this CTA adds rows [ir0, ir1) and columns [jc0, jc1).
+// avg_is_cur: the average equals the current point.
+template <bool kCl>
 __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, bool avg_is_cur, double it,
-                                          double* red, double* tot) {
+                                          double* red, double* tot, int ir0, int ir1, int jc0, int jc1,
+                                          double* part, int& flip, const Team<kCl>& T) {
   extern __shared__ double bsm[];
   const double* xs = bsm + A.xs_off;
   const double* ys = bsm + A.ys_off;
@@ -122,7 +265,8 @@ __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, b
     double acc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.0;
-    for (int i = threadIdx.x; i < D.m; i += blockDim.x) {
+    const int i1 = min(ir1, D.m);
+    for (int i = ir0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
       const int64_t gi = D.r0 + i;
       const double qi = A.q[gi], id = A.invDr[gi], yai = A.ya[gi];
       const bool ineq = i >= D.m1;
@@ -141,7 +285,7 @@ __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, b
         acc[4 * p + 3] = fma(dy, dy, acc[4 * p + 3]);
       }
     }
-    block_sum<8>(acc, red);
+    team_sum<8>(acc, red, part, flip, T);
     if ((int)threadIdx.x < 8) tot[threadIdx.x] = red[threadIdx.x];
     __syncthreads();
   }
@@ -149,7 +293,8 @@ __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, b
     double acc[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = 0.0;
-    for (int j = threadIdx.x; j < D.n; j += blockDim.x) {
+    const int j1 = min(jc1, D.n);
+    for (int j = jc0 + (int)threadIdx.x; j < j1; j += blockDim.x) {
       const int64_t gj = D.c0 + j;
       const double cj = A.c[gj], lj = A.l[gj], uj = A.u[gj], id = A.invDc[gj], xaj = A.xa[gj];
       const bool lf = !is_neg_inf(lj), uf = !is_pos_inf(uj);
@@ -175,34 +320,139 @@ __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, b
         acc[5 * p + 4] = fma(dx, dx, acc[5 * p + 4]);
       }
     }
-    block_sum<10>(acc, red);
+    team_sum<10>(acc, red, part, flip, T);
     if ((int)threadIdx.x < 10) tot[8 + threadIdx.x] = red[threadIdx.x];
     __syncthreads();
   }
 }
 
-__device__ __forceinline__ double block_norm(const double* v, int64_t base, int n, double* red, bool smem) {
-  double a[1] = {0.0};
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const double t = smem ? v[j] : v[base + j];
-    a[0] = fma(t, t, a[0]);
-  }
-  block_sum<1>(a, red);
-  return sqrt(red[0]);
+// Shared-memory footprint (bytes) of one CTA's resident slice: its chunks of K and K'
+// (chunk pointers, columns, values) and the per-entry vectors of the rows and columns
+// it owns.  The host sizes the launch with the same formula.
+__host__ __device__ inline long long resident_bytes(long long kch, long long kslots, long long tch, long long tslots,
+                                                    long long rows, long long cols) {
+  const long long dbl = 32 * (kslots + tslots) + 4 * cols + 3 * rows;
+  const long long ints = 32 * (kslots + tslots) + (kch + 1) + (tch + 1);
+  return 8 * dbl + 4 * ints + 16;
 }
 
-// Runs restarted PDHG on LP b with the whole CTA.
-__device__ void batch_solve_one(const BatchArgs& A, int b) {
+// Runs restarted PDHG on LP b with the team T (one CTA, or the CTAs of a cluster).
+// kRes: the CTA's slice of K and K' and the vectors of its rows and columns are copied
+// into shared memory first, so an iteration touches only shared memory (and, in a
+// cluster, the replicas of the other CTAs); the running sums and K x are written back
+// to global memory at every check.
+template <bool kCl, bool kRes>
+__device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   extern __shared__ double bsm[];
   double* xs = bsm + A.xs_off;
   double* ys = bsm + A.ys_off;
   double* red = bsm + A.red_off;
+  double* part = bsm + A.part_off;
   __shared__ DevState S;
   __shared__ double tot[NQ];
   __shared__ double scal[4];
   const LpDesc D = A.desc[b];
   const int n = D.n, m = D.m;
   const int tid = threadIdx.x, nt = blockDim.x;
+  int flip = 0;
+  // this CTA's chunks of K (rows [ir0, ir1)) and of K' (columns [jc0, jc1))
+  const int kr0 = split_point(A.k_cptr, D.kc0, D.kc1, T.rank, T.size);
+  const int kr1 = split_point(A.k_cptr, D.kc0, D.kc1, T.rank + 1, T.size);
+  const int tr0 = split_point(A.t_cptr, D.tc0, D.tc1, T.rank, T.size);
+  const int tr1 = split_point(A.t_cptr, D.tc0, D.tc1, T.rank + 1, T.size);
+  const int ir0 = (kr0 - D.kc0) * 32, ir1 = (kr1 - D.kc0) * 32;
+  const int jc0 = (tr0 - D.tc0) * 32, jc1 = (tr1 - D.tc0) * 32;
+  const int mo1 = min(ir1, m), no1 = min(jc1, n);
+
+  // per-entry vectors as the iterations see them: v[i - ofs]
+  const double* cv = A.c + D.c0;
+  const double* lv = A.l + D.c0;
+  const double* uv = A.u + D.c0;
+  double* sxv = A.sx + D.c0;
+  const double* qv = A.q + D.r0;
+  double* syv = A.sy + D.r0;
+  double* kxv = A.kxp + D.r0;
+  int jofs = 0, iofs = 0;
+  // resident slices (shared memory): chunk pointers in elements, values, gather offsets
+  const int* kpS = nullptr;
+  const double* kvS = nullptr;
+  const int* kgS = nullptr;
+  const int* tpS = nullptr;
+  const double* tvS = nullptr;
+  const int* tgS = nullptr;
+  if constexpr (kRes) {
+    const int ks0 = A.k_cptr[kr0], ks1 = A.k_cptr[kr1], ts0 = A.t_cptr[tr0], ts1 = A.t_cptr[tr1];
+    const int kn = 32 * (ks1 - ks0), tn = 32 * (ts1 - ts0);
+    const int nco = jc1 - jc0, nro = ir1 - ir0;
+    double* p = bsm + A.part_off + kPartBuf;
+    double* kv = p; p += kn;
+    double* tv = p; p += tn;
+    double* cS = p; p += nco;
+    double* lS = p; p += nco;
+    double* uS = p; p += nco;
+    double* sxS = p; p += nco;
+    double* qS = p; p += nro;
+    double* syS = p; p += nro;
+    double* kxS = p; p += nro;
+    int32_t* ip = reinterpret_cast<int32_t*>(p);
+    int32_t* kg = ip; ip += kn;
+    int32_t* tg = ip; ip += tn;
+    int32_t* kp = ip; ip += (kr1 - kr0) + 1;
+    int32_t* tp = ip;
+    for (int e = tid; e < kn; e += nt) {
+      kv[e] = A.k_val[(size_t)ks0 * 32 + e];
+      kg[e] = (int)(A.k_col[(size_t)ks0 * 32 + e] - D.c0) * 8;
+    }
+    for (int e = tid; e < tn; e += nt) {
+      tv[e] = A.t_val[(size_t)ts0 * 32 + e];
+      tg[e] = (int)(A.t_col[(size_t)ts0 * 32 + e] - D.r0) * 8;
+    }
+    for (int e = tid; e <= kr1 - kr0; e += nt) kp[e] = (A.k_cptr[kr0 + e] - ks0) * 32;
+    for (int e = tid; e <= tr1 - tr0; e += nt) tp[e] = (A.t_cptr[tr0 + e] - ts0) * 32;
+    for (int j = tid; j < nco; j += nt) {
+      const int64_t gj = D.c0 + jc0 + j;
+      cS[j] = A.c[gj];
+      lS[j] = A.l[gj];
+      uS[j] = A.u[gj];
+    }
+    for (int i = tid; i < nro; i += nt) qS[i] = A.q[D.r0 + ir0 + i];
+    kpS = kp;
+    kvS = kv;
+    kgS = kg;
+    tpS = tp;
+    tvS = tv;
+    tgS = tg;
+    cv = cS;
+    lv = lS;
+    uv = uS;
+    sxv = sxS;
+    qv = qS;
+    syv = syS;
+    kxv = kxS;
+    jofs = jc0;
+    iofs = ir0;
+    __syncthreads();
+  }
+  // K times a vector over this CTA's rows (gathering x: the replica or a global vector
+  // of the LP's columns), and K' times a vector over its columns
+  auto Kmul = [&](bool from_replica, const double* gsrc, auto&& epi) {
+    if constexpr (kRes) {
+      if (from_replica) rows_s(kpS, kvS, kgS, kr1 - kr0, ir0, xs, epi);
+      else rows_s(kpS, kvS, kgS, kr1 - kr0, ir0, gsrc, epi);
+    } else {
+      if (from_replica) batch_rows<kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A, epi);
+      else batch_rows<kSrcGlobal, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, gsrc, A, epi);
+    }
+  };
+  auto Tmul = [&](bool from_replica, const double* gsrc, auto&& epi) {
+    if constexpr (kRes) {
+      if (from_replica) rows_s(tpS, tvS, tgS, tr1 - tr0, jc0, ys, epi);
+      else rows_s(tpS, tvS, tgS, tr1 - tr0, jc0, gsrc, epi);
+    } else {
+      if (from_replica) batch_rows<kSrcSmemY, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A, epi);
+      else batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, gsrc, A, epi);
+    }
+  };
 
   // ---- step size: power iteration on K'K from v0 = 1/sqrt(n)
   double eta = A.eta_fixed;
@@ -211,40 +461,40 @@ __device__ void batch_solve_one(const BatchArgs& A, int b) {
     for (int j = tid; j < D.npad; j += nt) xs[j] = j < n ? v0 : 0.0;
     __syncthreads();
     for (int it = 0; it < A.power_iters; ++it) {
-      batch_rows<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, D.kc0, D.kc1, D.c0, nullptr, A,
-                            [&](int i, double s) { ys[i] = s; });
+      Kmul(true, nullptr,
+                                  [&](int i, double s) { T.put(ys, i, s); });
+      T.sync();
+      Tmul(true, nullptr,
+                                  [&](int j, double s) { A.g[D.c0 + j] = s; });
       __syncthreads();
-      batch_rows<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, D.tc0, D.tc1, D.r0, nullptr, A,
-                            [&](int j, double s) { A.g[D.c0 + j] = s; });
-      __syncthreads();
-      const double nw = block_norm(A.g, D.c0, D.npad, red, false);
+      const double nw = team_norm(A.g + D.c0, jc0, jc1, red, part, flip, T);
       if (nw != 0.0)
-        for (int j = tid; j < D.npad; j += nt) xs[j] = A.g[D.c0 + j] / nw;
-      __syncthreads();
+        for (int j = jc0 + tid; j < jc1; j += nt) T.put(xs, j, A.g[D.c0 + j] / nw);
+      T.sync();
     }
-    batch_rows<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, D.kc0, D.kc1, D.c0, nullptr, A,
-                          [&](int i, double s) { ys[i] = s; });
-    __syncthreads();
-    const double sn = m > 0 ? block_norm(ys, 0, D.mpad, red, true) : 0.0;
+    Kmul(true, nullptr,
+                                [&](int i, double s) { T.put(ys, i, s); });
+    T.sync();
+    const double sn = m > 0 ? team_norm(ys, ir0, ir1, red, part, flip, T) : 0.0;
     eta = sn > 0.0 ? A.step_scale / sn : 1.0;
   }
   // ---- initial primal weight ||c||/||q|| and the unscaled norms for termination
   double omega = A.omega_fixed;
   {
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < n; j += nt) {
+    for (int j = jc0 + tid; j < no1; j += nt) {
       const double cj = A.c[D.c0 + j];
       const double cu = cj * A.invDc[D.c0 + j];
       a[0] = fma(cj, cj, a[0]);
       a[2] = fma(cu, cu, a[2]);
     }
-    for (int i = tid; i < m; i += nt) {
+    for (int i = ir0 + tid; i < mo1; i += nt) {
       const double qi = A.q[D.r0 + i];
       const double qu = qi * A.invDr[D.r0 + i];
       a[1] = fma(qi, qi, a[1]);
       a[3] = fma(qu, qu, a[3]);
     }
-    block_sum<4>(a, red);
+    team_sum<4>(a, red, part, flip, T);
     if (tid == 0) {
       const double cn = sqrt(red[0]), qn = sqrt(red[1]);
       scal[0] = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
@@ -259,27 +509,36 @@ __device__ void batch_solve_one(const BatchArgs& A, int b) {
   P.cnorm = scal[1];
   P.qnorm = scal[2];
 
-  // ---- initial point (the warm start or 0, projected onto X and Y) and anchor
+  // ---- initial point (the warm start or 0, projected onto X and Y) and anchor; every
+  // CTA fills its own replicas, the owners the per-entry vectors
   for (int j = tid; j < D.npad; j += nt) {
     const int64_t gj = D.c0 + j;
     const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
     xs[j] = x0;
-    A.xa[gj] = x0;
-    A.sx[gj] = 0.0;
+    if (j >= jc0 && j < jc1) {
+      A.xa[gj] = x0;
+      A.sx[gj] = 0.0;
+      sxv[j - jofs] = 0.0;
+    }
   }
   for (int i = tid; i < D.mpad; i += nt) {
     const int64_t gi = D.r0 + i;
     double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
     if (i >= D.m1) y0 = max0(y0);
     ys[i] = y0;
-    A.ya[gi] = y0;
-    A.sy[gi] = 0.0;
+    if (i >= ir0 && i < ir1) {
+      A.ya[gi] = y0;
+      A.sy[gi] = 0.0;
+      syv[i - iofs] = 0.0;
+    }
   }
   __syncthreads();
-  batch_rows<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, D.kc0, D.kc1, D.c0, nullptr, A,
-                        [&](int i, double s) { A.kxp[D.r0 + i] = s; });
-  batch_rows<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, D.tc0, D.tc1, D.r0, nullptr, A,
-                        [&](int j, double s) { A.g[D.c0 + j] = s; });
+  Kmul(true, nullptr, [&](int i, double s) {
+    A.kxp[D.r0 + i] = s;
+    kxv[i - iofs] = s;
+  });
+  Tmul(true, nullptr,
+                              [&](int j, double s) { A.g[D.c0 + j] = s; });
   __syncthreads();
   if (tid == 0) {
     memset(&S, 0, sizeof(S));
@@ -289,7 +548,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b) {
     S.sigma = eta * omega;
   }
   __syncthreads();
-  batch_kkt(A, D, true, 0.0, red, tot);
+  batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T);
   if (tid == 0) {
     const double gap = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
     S.kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap, S.omega);
@@ -299,45 +558,58 @@ __device__ void batch_solve_one(const BatchArgs& A, int b) {
 
   // ---- iterations (Section 2: primal step, dual step with extrapolation) and checks
   long long k = 0, t = 0;
-  const double* c = A.c;
-  const double* l = A.l;
-  const double* u = A.u;
-  const double* q = A.q;
+  int until_check = A.check_every;
   for (;;) {
     const bool at_limit = k >= A.max_iter;
     if (!at_limit) {
       const double tau = S.tau, sigma = S.sigma;
-      batch_rows<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, D.tc0, D.tc1, D.r0, nullptr, A, [&](int j, double gsum) {
-        const int64_t gj = D.c0 + j;
-        const double xn = clamp_box(fma(-tau, c[gj] - gsum, xs[j]), l[gj], u[gj]);
-        xs[j] = xn;
-        A.sx[gj] = A.sx[gj] + xn;
+      Tmul(true, nullptr, [&](int j, double gsum) {
+        const int jl = j - jofs;
+        const double xn = clamp_box(fma(-tau, cv[jl] - gsum, xs[j]), lv[jl], uv[jl]);
+        T.put(xs, j, xn);
+        sxv[jl] = sxv[jl] + xn;
       });
-      __syncthreads();
-      batch_rows<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, D.kc0, D.kc1, D.c0, nullptr, A, [&](int i, double v) {
-        const int64_t gi = D.r0 + i;
-        const double e = q[gi] + A.kxp[gi];
+      T.sync();
+      Kmul(true, nullptr, [&](int i, double v) {
+        const int il = i - iofs;
+        const double e = qv[il] + kxv[il];
         double yn = fma(sigma, fma(-2.0, v, e), ys[i]);
         if (i >= D.m1) yn = max0(yn);
-        ys[i] = yn;
-        A.sy[gi] = A.sy[gi] + yn;
-        A.kxp[gi] = v;
+        T.put(ys, i, yn);
+        syv[il] = syv[il] + yn;
+        kxv[il] = v;
       });
-      __syncthreads();
+      T.sync();
       ++k;
       ++t;
-      if (!(k % A.check_every == 0 || k >= A.max_iter)) continue;
+      if (--until_check > 0 && k < A.max_iter) continue;
+      until_check = A.check_every;
     }
     // ---- check
+    if constexpr (kRes) {
+      // running sums and K x back to global memory, where the check reads them
+      for (int j = jc0 + tid; j < jc1; j += nt) A.sx[D.c0 + j] = sxv[j - jofs];
+      for (int i = ir0 + tid; i < ir1; i += nt) {
+        A.sy[D.r0 + i] = syv[i - iofs];
+        A.kxp[D.r0 + i] = kxv[i - iofs];
+      }
+    }
+    if constexpr (kCl) {
+      // the averages are gathered from the owners' global running sums
+      __threadfence();
+      T.sync();
+    } else if constexpr (kRes) {
+      __syncthreads();
+    }
     const double it = t > 0 ? 1.0 / (double)t : 0.0;
-    batch_rows<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, D.tc0, D.tc1, D.r0, nullptr, A,
-                          [&](int j, double s) { A.g[D.c0 + j] = s; });
-    batch_rows<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, D.kc0, D.kc1, D.c0, A.sx + D.c0, A,
-                           [&](int i, double s) { A.kx_a[D.r0 + i] = s * it; });
-    batch_rows<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, D.tc0, D.tc1, D.r0, A.sy + D.r0, A,
-                           [&](int j, double s) { A.g_a[D.c0 + j] = s * it; });
+    Tmul(true, nullptr,
+                                [&](int j, double s) { A.g[D.c0 + j] = s; });
+    Kmul(false, A.sx + D.c0,
+                                 [&](int i, double s) { A.kx_a[D.r0 + i] = s * it; });
+    Tmul(false, A.sy + D.r0,
+                                 [&](int j, double s) { A.g_a[D.c0 + j] = s * it; });
     __syncthreads();
-    batch_kkt(A, D, t == 0, it, red, tot);
+    batch_kkt(A, D, t == 0, it, red, tot, ir0, ir1, jc0, jc1, part, flip, T);
     if (tid == 0) {
       S.k = k;
       S.t = t;
@@ -348,48 +620,53 @@ __device__ void batch_solve_one(const BatchArgs& A, int b) {
     if (S.done) break;
     if (S.restart_flag) {
       const bool avg = S.cand_avg;
-      for (int j = tid; j < D.npad; j += nt) {
-        const int64_t gj = D.c0 + j;
-        const double xv = avg ? A.sx[gj] * it : xs[j];
-        xs[j] = xv;
-        A.xa[gj] = xv;
-        A.sx[gj] = 0.0;
+      if (avg) {
+        for (int j = tid; j < D.npad; j += nt) xs[j] = A.sx[D.c0 + j] * it;
+        for (int i = tid; i < D.mpad; i += nt) ys[i] = A.sy[D.r0 + i] * it;
       }
-      for (int i = tid; i < D.mpad; i += nt) {
+      T.sync();   // every replica is read before the owners clear the sums
+      for (int j = jc0 + tid; j < jc1; j += nt) {
+        A.xa[D.c0 + j] = xs[j];
+        sxv[j - jofs] = 0.0;
+      }
+      for (int i = ir0 + tid; i < ir1; i += nt) {
         const int64_t gi = D.r0 + i;
-        const double yv = avg ? A.sy[gi] * it : ys[i];
-        ys[i] = yv;
-        A.ya[gi] = yv;
-        A.sy[gi] = 0.0;
-        if (avg) A.kxp[gi] = A.kx_a[gi];
+        A.ya[gi] = ys[i];
+        syv[i - iofs] = 0.0;
+        if (avg) kxv[i - iofs] = A.kx_a[gi];
       }
       t = 0;
       __syncthreads();
     }
   }
-  // ---- returned point and state
+  // ---- returned point and state (the global sums were written at the last check)
   const bool avg = S.which == 1 && t > 0;
   const double it = t > 0 ? 1.0 / (double)t : 0.0;
-  for (int j = tid; j < D.npad; j += nt) A.xout[D.c0 + j] = avg ? A.sx[D.c0 + j] * it : xs[j];
-  for (int i = tid; i < D.mpad; i += nt) A.yout[D.r0 + i] = avg ? A.sy[D.r0 + i] * it : ys[i];
-  if (tid == 0) A.st[b] = S;
-  __syncthreads();
+  for (int j = jc0 + tid; j < jc1; j += nt) A.xout[D.c0 + j] = avg ? A.sx[D.c0 + j] * it : xs[j];
+  for (int i = ir0 + tid; i < ir1; i += nt) A.yout[D.r0 + i] = avg ? A.sy[D.r0 + i] * it : ys[i];
+  if (tid == 0 && T.rank == 0) A.st[b] = S;
+  T.sync();   // no CTA writes the next LP into a replica (or slice) that is still being read
 }
 
+// Persistent solver: teams draw LPs from the queue until it is empty.  The counter
+// resets itself: the last of the failing draws (one per team) stores 0.
+template <bool kCl, bool kRes>
 __global__ void __launch_bounds__(256, 2) k_batch_solve(BatchArgs A) {
   __shared__ int lp;
+  Team<kCl> T;
+  T.init();
+  const int teams = (int)gridDim.x / T.size;
   for (;;) {
-    if (threadIdx.x == 0) {
+    if (T.rank == 0 && threadIdx.x == 0) {
       const int v = atomicAdd(A.next, 1);
-      lp = v;
-      // the last of the gridDim.x failing draws is the last access of this launch
-      if (v == A.count + (int)gridDim.x - 1) *A.next = 0;
+      if (v == A.count + teams - 1) *A.next = 0;
+      for (int r = 0; r < T.size; ++r) *T.at(&lp, r) = v;
     }
-    __syncthreads();
+    T.sync();
     const int v = lp;
-    __syncthreads();
+    T.sync();
     if (v >= A.count) break;
-    batch_solve_one(A, A.order[v]);
+    batch_solve_one<kCl, kRes>(A, A.order[v], T);
   }
 }
 

@@ -113,8 +113,15 @@ struct pdlp_ctx {
   int32_t* next = nullptr;
   DevState* bstate = nullptr;
   double *bx = nullptr, *by = nullptr, *bomega = nullptr;
-  int batch_grid = 0;
+  int batch_grid = 0;        // CTAs of a one-CTA-per-LP launch
+  int batch_resident = 0;    // CTAs of the batched kernel resident on the whole GPU
+  int64_t team_npad_max = 0;
+  int part_off = 0;
   size_t batch_smem = 0;
+  int last_team = 0;         // CTAs per LP and resident mode of the last batched launch
+  bool last_resident = false;
+  std::vector<int32_t> hk_cptr, ht_cptr;  // host copies of the chunk pointers of K and K'
+  int dev_smem_optin = 0;
   int xs_off = 0, ys_off = 0, red_off = 0;
   std::vector<LpDesc> hdesc;
   std::vector<DevState> hstate;
@@ -462,6 +469,8 @@ static void init_handle_resources(pdlp_ctx* h) {
 static void check_params(const pdlp_params& P) {
   if (P.check_every < 1) invalid("check_every must be >= 1");
   if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
+  if (P.cluster_ctas < 0 || P.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
+  if (P.resident < 0 || P.resident > 2) invalid("resident must be 0, 1 or 2");
 }
 
 // Copies (from host or device) and validates one LP in CSR form; rows_total and the
@@ -1125,18 +1134,40 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   h->xs_off = 0;
   h->ys_off = (int)npad_max;
   h->red_off = (int)(npad_max + mpad_max);
-  h->batch_smem = (size_t)(npad_max + mpad_max + kBatchRed) * sizeof(double);
+  h->part_off = h->red_off + kBatchRed;
+  h->batch_smem = (size_t)(npad_max + mpad_max + kBatchRed + kPartBuf) * sizeof(double);
   int dev_smem = 0;
   CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
   const size_t static_smem = sizeof(DevState) + (NQ + 8) * sizeof(double) + 64;
   if (h->batch_smem + static_smem > (size_t)dev_smem)
     invalid("an LP of the batch is too large for one CTA's shared memory (needs (n + m) padded doubles)");
-  CK(cudaFuncSetAttribute(k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->batch_smem));
+  int static_max = 0;
+  for (const void* f : {(const void*)k_batch_solve<false, false>, (const void*)k_batch_solve<false, true>,
+                        (const void*)k_batch_solve<true, false>, (const void*)k_batch_solve<true, true>}) {
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, f));
+    static_max = std::max(static_max, (int)fa.sharedSizeBytes);
+  }
+  const int smem_cap = dev_smem - static_max;
+  if (smem_cap < (int)h->batch_smem)
+    invalid("an LP of the batch is too large for one CTA's shared memory (needs (n + m) padded doubles)");
+  h->dev_smem_optin = smem_cap;
+  CK(cudaFuncSetAttribute(k_batch_solve<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  CK(cudaFuncSetAttribute(k_batch_solve<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  CK(cudaFuncSetAttribute(k_batch_solve<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  CK(cudaFuncSetAttribute(k_batch_solve<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  CK(cudaFuncSetAttribute(k_batch_solve<true, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  CK(cudaFuncSetAttribute(k_batch_solve<true, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  h->hk_cptr = Lo.SK.chunk_ptr;
+  h->ht_cptr = Lo.SKt.chunk_ptr;
   int per_sm = 0, sms = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve, kBatchThreads, h->batch_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<false, false>, kBatchThreads,
+                                                   h->batch_smem));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
   if (per_sm < 1) invalid("batched kernel does not fit on an SM");
+  h->batch_resident = per_sm * sms;
   h->batch_grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
+  h->team_npad_max = npad_max;
 
   // queue order: largest LP (most nonzeros) first
   std::vector<int32_t> ord((size_t)count);
@@ -1158,9 +1189,55 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   CK(cudaStreamSynchronize(h->s));
 }
 
+// CTAs per LP: the requested count, else one CTA per LP when the batch has enough LPs
+// to fill the GPU, else the largest power of two <= 16 that the LP count leaves room
+// for, with at least 64 columns of the largest LP per CTA.
+// The same cut of chunks [c0, c1) into `size` pieces as split_point on the device.
+static int host_split_point(const std::vector<int32_t>& cptr, int c0, int c1, int r, int size) {
+  if (r <= 0) return c0;
+  if (r >= size) return c1;
+  const long long s0 = cptr[(size_t)c0], s1 = cptr[(size_t)c1];
+  const long long target = s0 + (s1 - s0) * r / size;
+  int lo = c0, hi = c1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cptr[(size_t)mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Largest resident slice (bytes) over the LPs of the batch and the CTAs of a team.
+static long long resident_need(const pdlp_ctx* h, int team) {
+  long long need = 0;
+  for (const LpDesc& D : h->hdesc) {
+    for (int r = 0; r < team; ++r) {
+      const int k0 = host_split_point(h->hk_cptr, D.kc0, D.kc1, r, team);
+      const int k1 = host_split_point(h->hk_cptr, D.kc0, D.kc1, r + 1, team);
+      const int t0 = host_split_point(h->ht_cptr, D.tc0, D.tc1, r, team);
+      const int t1 = host_split_point(h->ht_cptr, D.tc0, D.tc1, r + 1, team);
+      const long long ks = h->hk_cptr[(size_t)k1] - h->hk_cptr[(size_t)k0];
+      const long long ts = h->ht_cptr[(size_t)t1] - h->ht_cptr[(size_t)t0];
+      need = std::max(need, resident_bytes(k1 - k0, ks, t1 - t0, ts, 32LL * (k1 - k0), 32LL * (t1 - t0)));
+    }
+  }
+  return need;
+}
+
+static int batch_team_size(const pdlp_ctx* h, const pdlp_params& sp) {
+  if (sp.cluster_ctas > 0) return sp.cluster_ctas;
+  int team = 1;
+  while (team < kMaxTeam && h->count * (int64_t)(team * 2) <= (int64_t)h->batch_resident &&
+         h->team_npad_max >= (int64_t)(team * 2) * 64)
+    team *= 2;
+  return team;
+}
+
 static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0,
                             const double* omega0, pdlp_result* res, double* x_out, double* y_out) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
+  if (sp.cluster_ctas < 0 || sp.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
+  if (sp.resident < 0 || sp.resident > 2) invalid("resident must be 0, 1 or 2");
   auto t_start = std::chrono::steady_clock::now();
   BatchArgs A;
   A.x0 = nullptr;
@@ -1213,8 +1290,65 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.xs_off = h->xs_off;
   A.ys_off = h->ys_off;
   A.red_off = h->red_off;
+  A.part_off = h->part_off;
+  const int team = batch_team_size(h, sp);
+  // resident slices: the largest one of any LP and CTA decides the launch's shared memory
+  const long long res_bytes = resident_need(h, team);
+  const size_t res_smem = h->batch_smem + (size_t)((res_bytes + 7) / 8 * 8);
+  bool resident = false;
+  if (sp.resident != 1 && res_smem <= (size_t)h->dev_smem_optin) {
+    if (sp.resident == 2) {
+      resident = true;
+    } else {
+      // automatic: only while it keeps as many CTAs per SM as the streaming kernel
+      int a = 0, r = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<false, false>, kBatchThreads,
+                                                       h->batch_smem));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_batch_solve<false, true>, kBatchThreads, res_smem));
+      resident = r >= a;
+    }
+  }
+  const size_t smem = resident ? res_smem : h->batch_smem;
+  int grid = 0;
+  if (team == 1) {
+    int per_sm = 0, sms = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, resident ? (const void*)k_batch_solve<false, true> : (const void*)k_batch_solve<false, false>,
+        kBatchThreads, smem));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    if (per_sm < 1) invalid("batched kernel does not fit on an SM");
+    grid = (int)std::min<int64_t>((int64_t)per_sm * sms, h->count);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)team;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h->s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (team > 1) {
+    cfg.gridDim = dim3((unsigned)team);
+    int nc = 0;
+    CK(cudaOccupancyMaxActiveClusters(
+        &nc, resident ? (const void*)k_batch_solve<true, true> : (const void*)k_batch_solve<true, false>, &cfg));
+    if (nc < 1) invalid("a cluster of this many CTAs does not fit on the GPU");
+    grid = (int)std::min<int64_t>((int64_t)nc, h->count) * team;
+  }
+  cfg.gridDim = dim3((unsigned)grid);
+  h->last_team = team;
+  h->last_resident = resident;
   CK(cudaEventRecord(h->ev_t0, h->s));
-  k_batch_solve<<<h->batch_grid, kBatchThreads, h->batch_smem, h->s>>>(A);
+  if (team == 1) {
+    if (resident) k_batch_solve<false, true><<<grid, kBatchThreads, smem, h->s>>>(A);
+    else k_batch_solve<false, false><<<grid, kBatchThreads, smem, h->s>>>(A);
+  } else {
+    if (resident) CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, true>, A));
+    else CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, false>, A));
+  }
   CKL("k_batch_solve");
   CK(cudaEventRecord(h->ev_t1, h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -1431,6 +1565,8 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->eta = h->eta;
     info->omega0 = h->omega0;
     info->norm_K = h->normK;
+    info->batch_team = h->last_team;
+    info->batch_resident = h->last_resident ? 1 : 0;
     return PDLP_OK;
   });
 }

@@ -130,3 +130,70 @@ def test_batch_warm_start_matches_oracle(pk):
         assert r["restarts"] == ref["restarts"]
         close_rel(r["x"], ref["x"], 1e-10)
         close_rel(r["y"], ref["y"], 1e-10)
+
+
+@pytest.mark.parametrize("team,resident", [(2, 1), (2, 2), (8, 1), (8, 2), (16, 2)])
+def test_cluster_team_iterates_after_1000(pk, team, resident):
+    """Several CTAs (a thread-block cluster) share each LP, with the matrix streamed from
+    global memory (resident=1) or staged in shared memory (2): same iterates as the oracle."""
+    lps = fixed_iteration_batch()
+    with pk.BatchSolver.from_lps(lps, scaling=1) as b:
+        res = b.solve(tol=0.0, max_iter=1000, cluster_ctas=team, resident=resident)
+        info = b.info()
+        assert info["batch_team"] == team
+        if resident == 1:
+            assert info["batch_resident"] == 0
+        if team >= 8 and resident == 2:   # every slice fits once the LPs are cut 8 ways
+            assert info["batch_resident"] == 1
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=0.0, max_iter=1000, scaling=1)
+        assert r["iters"] == 1000 and r["status"] == pk.ITER_LIMIT
+        assert r["restarts"] == ref["restarts"]
+        assert r["which"] == ref["which"]
+        assert abs(r["eta"] - ref["eta"]) <= 1e-12 * ref["eta"]
+        assert abs(r["omega"] - ref["omega"]) <= 1e-6 * ref["omega"]
+        close_rel(r["x"], ref["x"], 1e-10)
+        close_rel(r["y"], ref["y"], 1e-10)
+
+
+def test_resident_one_cta_per_lp(pk):
+    """Small LPs whose whole matrix fits in one CTA's shared memory, one CTA each."""
+    lps = [lp for lp in lpgen.batch_planted(8, seed=21, n_lo=40, n_hi=300) if lp["m"] > 0]
+    lps.append(lpgen.tiny_lp(5, n=6, m1=2, m2=2))
+    with pk.BatchSolver.from_lps(lps) as b:
+        res = b.solve(tol=0.0, max_iter=700, cluster_ctas=1, resident=2)
+        assert b.info()["batch_team"] == 1 and b.info()["batch_resident"] == 1
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=0.0, max_iter=700)
+        assert r["restarts"] == ref["restarts"]
+        close_rel(r["x"], ref["x"], 1e-10)
+        close_rel(r["y"], ref["y"], 1e-10)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8])
+def test_cluster_single_small_lp_at_tolerance(pk, tol):
+    """One LP, automatic team size (the whole cluster on one LP), against the oracle."""
+    lp = lpgen.planted_small(0)
+    ref = oracle.solve(lp, tol=tol)
+    with pk.BatchSolver.from_lps([lp]) as b:
+        for team, resident in ((0, 0), (4, 1), (1, 2)):
+            r = b.solve(tol=tol, cluster_ctas=team, resident=resident)[0]
+            assert r["status"] == ref["status"] == pk.OPTIMAL
+            assert r["iters"] == ref["iters"]
+            assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * abs(ref["primal_obj"])
+            assert abs(r["primal_obj"] - lp["obj_star"]) <= 10 * tol * abs(lp["obj_star"])
+
+
+def test_cluster_warm_start_and_rerun(pk):
+    lps = fixed_iteration_batch()[:5]
+    rng = np.random.default_rng(5)
+    x0 = [rng.standard_normal(lp["n"]) for lp in lps]
+    y0 = [rng.standard_normal(lp["m"]) for lp in lps]
+    w0 = np.array([0.0, 1.5, 0.0, 0.7, 2.0])
+    with pk.BatchSolver.from_lps(lps) as b:
+        for _ in range(2):   # the queue counter resets itself between launches
+            res = b.solve(tol=0.0, max_iter=300, x0=x0, y0=y0, omega0=w0, cluster_ctas=4, resident=2)
+            for i, (lp, r) in enumerate(zip(lps, res)):
+                ref = oracle.solve(lp, tol=0.0, max_iter=300, x0=x0[i], y0=y0[i], omega0=float(w0[i]))
+                close_rel(r["x"], ref["x"], 1e-10)
+                close_rel(r["y"], ref["y"], 1e-10)
