@@ -40,14 +40,15 @@ class Params(C.Structure):
                 ("scaling", C.c_int32), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
                 ("beta_art", C.c_double), ("step_scale", C.c_double), ("omega_theta", C.c_double),
                 ("ruiz_iters", C.c_int32), ("power_iters", C.c_int32), ("eta", C.c_double),
-                ("omega0", C.c_double)]
+                ("omega0", C.c_double), ("step_rule", C.c_int32), ("pad0", C.c_int32)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("which", C.c_int32), ("iters", C.c_int64),
                 ("restarts", C.c_int64), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("rel_primal", C.c_double), ("rel_dual", C.c_double), ("rel_gap", C.c_double),
-                ("kkt_omega", C.c_double), ("omega", C.c_double), ("eta", C.c_double)]
+                ("kkt_omega", C.c_double), ("omega", C.c_double), ("eta", C.c_double),
+                ("accepted", C.c_int64)]
 
 
 class KKT(C.Structure):

@@ -23,6 +23,17 @@
  *    multiplier and an infinite bound is 0 (Lambda makes these the only cases).
  *  - Step size eta is constant: step_scale / ||K||_2, ||K||_2 from power_iters
  *    power iterations on K'K from v0 = 1/sqrt(n); eta = 1 when ||K||_2 = 0.
+ *  - step_rule = 1 replaces it by the adaptive rule of the cited PDLP paper
+ *    (Applegate et al., "Practical large-scale linear programming using
+ *    primal-dual hybrid gradient"): a step with eta is accepted when
+ *      eta <= eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy' K dx|)
+ *    (eta_max = +inf when dy' K dx = 0), and either way the next eta is
+ *      min((1 - (s+1)^-0.3) eta_max, (1 + (s+1)^-0.6) eta),
+ *    s = 1 + the number of steps accepted so far.  A rejected attempt leaves the
+ *    point unchanged; after 64 rejections in a row the attempt is accepted.  The
+ *    first eta is 1 / max_ij |K_ij| (of the scaled K; 1 when K = 0).  The average
+ *    of an inner loop is weighted by the accepted steps' eta.  Iteration counts
+ *    (k, t, max_iter, check_every) count attempts.
  *  - Initial primal weight omega0 = ||c||/||q|| when both exceed 1e-10, else 1.
  *  - At a restart the primal weight becomes
  *      omega <- exp(theta log(dy/dx) + (1-theta) log omega),
@@ -62,6 +73,8 @@ typedef struct {
   int32_t power_iters;
   double eta;          /* > 0: use this step size instead of the power-iteration rule */
   double omega0;       /* > 0: use this initial primal weight */
+  int32_t step_rule;   /* 0 constant eta, 1 adaptive (PDLP) */
+  int32_t pad0;
 } orc_params;
 
 typedef struct {
@@ -69,6 +82,7 @@ typedef struct {
   int32_t which;       /* returned point: 0 current iterate, 1 average */
   int64_t iters, restarts;
   double primal_obj, dual_obj, rel_primal, rel_dual, rel_gap, kkt_omega, omega, eta;
+  int64_t accepted;    /* steps accepted (= iters with the constant rule) */
 } orc_result;
 
 typedef struct {
@@ -271,6 +285,32 @@ void orc_pdhg_step(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const in
   free(g); free(w); free(Kw);
 }
 
+/* ---------- the adaptive step (step_rule = 1) ---------- */
+
+/* One attempt of the adaptive rule from (x, y) with step eta: the candidate goes to
+ * (xn, yn); returns eta_max of the candidate (+inf when dy' K dx = 0). */
+static double adaptive_attempt(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t* ci,
+                               const double* v, const double* c, const double* q, const double* l,
+                               const double* u, double eta, double omega, const double* x, const double* y,
+                               double* xn, double* yn) {
+  memcpy(xn, x, sizeof(double) * (size_t)n);
+  memcpy(yn, y, sizeof(double) * (size_t)m);
+  orc_pdhg_step(m, n, m1, rp, ci, v, c, q, l, u, eta, omega, xn, yn);
+  double* dx = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double* Kdx = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
+  for (int64_t j = 0; j < n; ++j) { dx[j] = xn[j] - x[j]; dx2 += dx[j] * dx[j]; }
+  orc_spmv(m, rp, ci, v, dx, Kdx);
+  for (int64_t i = 0; i < m; ++i) {
+    double dy = yn[i] - y[i];
+    dy2 += dy * dy;
+    inter += dy * Kdx[i];
+  }
+  free(dx); free(Kdx);
+  if (inter == 0.0) return INFINITY;
+  return (omega * dx2 + dy2 / omega) / (2.0 * fabs(inter));
+}
+
 /* ---------- the restarted PDHG solve ---------- */
 
 static void unscale(int64_t len, const double* d, const double* a, double* out) {
@@ -312,7 +352,11 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
   double qnorm = norm2(m, q), cnorm = norm2(n, c);  /* unscaled, for termination */
   double eta;
   if (P->eta > 0.0) eta = P->eta;
-  else {
+  else if (P->step_rule == 1) {
+    double mx = 0.0;
+    for (int64_t e = 0; e < nnz; ++e) if (fabs(vt[e]) > mx) mx = fabs(vt[e]);
+    eta = mx > 0.0 ? 1.0 / mx : 1.0;
+  } else {
     double s = orc_power_norm(m, n, rp, ci, vt, P->power_iters);
     eta = s > 0.0 ? P->step_scale / s : 1.0;
   }
@@ -336,7 +380,10 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
   orc_kkt pa = orc_kkt_parts(m, n, m1, rp, ci, vt, ct, qt, lt, ut, x, y);
   double kkt_anchor = orc_kkt_omega(pa, omega);
   double kkt_prev_c = INFINITY;
-  int64_t k = 0, t = 0, nrestart = 0;
+  int64_t k = 0, t = 0, nrestart = 0, accepted = 0;
+  int rejects = 0;
+  double wsum = 0.0;   /* sum of the weights of the iterates in sx, sy */
+  double *xn = (double*)malloc(nb), *yn = (double*)malloc(mb);
   int status = 1, which = 0;
   orc_kkt fin = pa;
   double frp = 0, frd = 0, frg = 0;
@@ -344,18 +391,39 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
   for (;;) {
     int final_check = (k >= P->max_iter);
     if (!final_check) {
-      orc_pdhg_step(m, n, m1, rp, ci, vt, ct, qt, lt, ut, eta, omega, x, y);
-      for (int64_t j = 0; j < n; ++j) sx[j] += x[j];
-      for (int64_t i = 0; i < m; ++i) sy[i] += y[i];
+      if (P->step_rule == 1) {
+        double emax = adaptive_attempt(m, n, m1, rp, ci, vt, ct, qt, lt, ut, eta, omega, x, y, xn, yn);
+        double sidx = (double)(accepted + 2);   /* s + 1, s = accepted + 1 */
+        double e1 = (1.0 - pow(sidx, -0.3)) * emax, e2 = (1.0 + pow(sidx, -0.6)) * eta;
+        double enext = e1 < e2 ? e1 : e2;
+        if (eta <= emax || rejects >= 64) {
+          memcpy(x, xn, nb);
+          memcpy(y, yn, mb);
+          for (int64_t j = 0; j < n; ++j) sx[j] += eta * x[j];
+          for (int64_t i = 0; i < m; ++i) sy[i] += eta * y[i];
+          wsum += eta;
+          ++accepted;
+          rejects = 0;
+        } else {
+          ++rejects;
+        }
+        eta = enext;
+      } else {
+        orc_pdhg_step(m, n, m1, rp, ci, vt, ct, qt, lt, ut, eta, omega, x, y);
+        for (int64_t j = 0; j < n; ++j) sx[j] += x[j];
+        for (int64_t i = 0; i < m; ++i) sy[i] += y[i];
+        wsum += 1.0;
+        ++accepted;
+      }
       ++t;
       ++k;
       final_check = (k >= P->max_iter);
       if (!(k % P->check_every == 0 || final_check)) continue;
     }
     /* ---- check ---- */
-    if (t > 0) {
-      for (int64_t j = 0; j < n; ++j) xa[j] = sx[j] / (double)t;
-      for (int64_t i = 0; i < m; ++i) ya[i] = sy[i] / (double)t;
+    if (wsum > 0.0) {
+      for (int64_t j = 0; j < n; ++j) xa[j] = sx[j] / wsum;
+      for (int64_t i = 0; i < m; ++i) ya[i] = sy[i] / wsum;
     } else {
       memcpy(xa, x, nb);
       memcpy(ya, y, mb);
@@ -399,6 +467,7 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
       memset(sx, 0, nb);
       memset(sy, 0, mb);
       t = 0;
+      wsum = 0.0;
       kkt_anchor = orc_kkt_omega(pc, omega);
       kkt_prev_c = INFINITY;
       if (nrestart < restart_cap && restart_iters) restart_iters[nrestart] = k;
@@ -408,9 +477,9 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
     }
   }
 
-  if (t > 0) {
-    for (int64_t j = 0; j < n; ++j) xa[j] = sx[j] / (double)t;
-    for (int64_t i = 0; i < m; ++i) ya[i] = sy[i] / (double)t;
+  if (wsum > 0.0) {
+    for (int64_t j = 0; j < n; ++j) xa[j] = sx[j] / wsum;
+    for (int64_t i = 0; i < m; ++i) ya[i] = sy[i] / wsum;
   } else {
     memcpy(xa, x, nb);
     memcpy(ya, y, mb);
@@ -435,9 +504,10 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
     R->kkt_omega = orc_kkt_omega(sfin, omega);
     R->omega = omega;
     R->eta = eta;
+    R->accepted = accepted;
   }
   free(vt); free(Dr); free(Dc); free(ct); free(lt); free(ut); free(qt);
   free(x); free(y); free(sx); free(sy); free(xa); free(ya); free(x0a); free(y0a);
-  free(xu); free(yu);
+  free(xu); free(yu); free(xn); free(yn);
   return 0;
 }

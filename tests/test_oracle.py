@@ -352,3 +352,71 @@ def test_bf16_rounding():
     assert r[2] == 1.0 + 2 ** -7
     assert abs(r[3] - 3.140625) < 1e-12
     assert np.all(np.abs(r - vals) <= np.abs(vals) * 2 ** -8)
+
+
+# ---------------------------------------------------------------- adaptive step rule
+# (step_rule = 1: the rule of the cited PDLP paper, an option beside the constant eta)
+
+def _norm_K(lp):
+    K = dense(lp).toarray()
+    return np.linalg.svd(K, compute_uv=False)[0] if K.size else 0.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adaptive_step_below_one_over_norm_is_accepted(seed):
+    """2|dy'K dx| <= 2||K|| ||dx|| ||dy|| <= ||K|| (omega ||dx||^2 + ||dy||^2/omega), so
+    eta_max >= 1/||K||_2 for every attempt: a first step with eta < 1/||K||_2 is
+    accepted from any point and any primal weight."""
+    lp = lpgen.planted_small(seed)
+    nk = _norm_K(lp)
+    rng = np.random.default_rng(seed)
+    for trial in range(3):
+        x0 = rng.standard_normal(lp["n"]) * 3
+        y0 = rng.standard_normal(lp["m"]) * 3
+        w0 = float(np.exp(rng.uniform(-2, 2)))
+        r = oracle.solve(lp, tol=0.0, max_iter=1, step_rule=1, eta=0.999 / nk, omega0=w0, x0=x0, y0=y0)
+        assert r["iters"] == 1 and r["accepted"] == 1
+        # the accepted step is the plain PDHG step of Section 2 with that eta
+        xs, ys = oracle.pdhg_step(lp, np.clip(x0, lp["l"], lp["u"]),
+                                  np.where(np.arange(lp["m"]) >= lp["m1"], np.maximum(y0, 0), y0),
+                                  0.999 / nk, w0)
+        np.testing.assert_allclose(r["x_cur"], xs, rtol=0, atol=1e-12 * (1 + np.abs(xs).max()))
+        np.testing.assert_allclose(r["y_cur"], ys, rtol=0, atol=1e-12 * (1 + np.abs(ys).max()))
+
+
+def test_adaptive_step_without_rows_grows_by_the_closed_form():
+    """With no rows dy'K dx = 0, so every attempt is accepted and eta only grows:
+    eta_s = eta_0 prod_{i=1..s} (1 + (i+1)^-0.6), eta_0 = 1 (K = 0).  The point still
+    reaches the box optimum of the closed form."""
+    lp = lpgen.box_only(3, n=40)
+    r = oracle.solve(lp, tol=0.0, max_iter=10, step_rule=1)
+    assert r["accepted"] == 10
+    want = np.prod([1.0 + (i + 1.0) ** -0.6 for i in range(1, 11)])
+    assert abs(r["eta"] - want) <= 1e-13 * want
+    r = oracle.solve(lp, tol=1e-10, max_iter=100000, step_rule=1)
+    assert r["status"] == oracle.STATUS_OPTIMAL
+    c, l, u = lp["c"], lp["l"], lp["u"]
+    np.testing.assert_allclose(r["x"], np.where(c > 0, l, u), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adaptive_tiny_lp_matches_vertex_enumeration(seed):
+    lp = lpgen.tiny_lp(seed, n=5, m1=1, m2=3)
+    best = _vertex_enumeration(lp)
+    r = oracle.solve(lp, tol=1e-8, max_iter=2_000_000, step_rule=1)
+    assert r["status"] == oracle.STATUS_OPTIMAL
+    assert r["accepted"] <= r["iters"]
+    assert abs(r["primal_obj"] - best) <= 1e-6 * (1 + abs(best))
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_adaptive_planted_small_reaches_planted_objective(scaling):
+    lp = lpgen.planted_small(0)
+    r = oracle.solve(lp, tol=1e-8, scaling=scaling, step_rule=1)
+    assert r["status"] == oracle.STATUS_OPTIMAL
+    assert 0 < r["accepted"] <= r["iters"]
+    assert abs(r["primal_obj"] - lp["obj_star"]) <= 1e-6 * abs(lp["obj_star"])
+    x = r["x"]
+    Kx = dense(lp) @ x
+    pr = np.concatenate([Kx[: lp["m1"]] - lp["q"][: lp["m1"]], np.maximum(lp["q"][lp["m1"]:] - Kx[lp["m1"]:], 0)])
+    assert np.linalg.norm(pr) <= 1e-8 * (1 + np.linalg.norm(lp["q"])) * (1 + 1e-9)
