@@ -104,6 +104,18 @@ typedef struct {
                               vectors of its rows and columns into shared memory for the
                               iterations: 0 = automatic (when every LP's slices fit without
                               lowering the CTAs per SM), 1 = never, 2 = whenever they fit  */
+  int32_t step_rule;       /* pdlp_solve: 0 = the constant step eta of Section 2;
+                              1 = the adaptive step rule of the cited PDLP paper
+                              (Applegate et al. 2021): an attempt with step eta is kept when
+                              eta <= (omega |dx|^2 + |dy|^2 / omega) / (2 |dy' K dx|), and
+                              the next eta is min((1 - (s+1)^-0.3) eta_max,
+                              (1 + (s+1)^-0.6) eta), s = 1 + steps accepted; a rejected
+                              attempt leaves the point unchanged (after 64 rejections in a
+                              row the attempt is kept); first eta = 1 / max |K_ij| of the
+                              scaled K (or params.eta); averages are weighted by the kept
+                              steps' eta; iteration counts (max_iter, check_every, iters)
+                              count attempts.  Not with PDLP_MIXED; not for batches.       */
+  int32_t reserved1;       /* must be 0                                                     */
 } pdlp_params;
 
 typedef struct {
@@ -123,6 +135,7 @@ typedef struct {
   double device_ms;      /* device time from the first to the last kernel of the solve     */
   int64_t launches;      /* kernels launched on the device by this solve                  */
   int64_t fp32_iters;    /* PDLP_MIXED: iterations run in FP32 (the rest ran in FP64)     */
+  int64_t accepted;      /* steps kept (step_rule 1; equals iters with the constant step) */
 } pdlp_result;
 
 /* Per-check record (pdlp_get_log). */

@@ -20,7 +20,8 @@ class Params(C.Structure):
                 ("eta", C.c_double), ("tile_slots", C.c_int32), ("inputs_on_device", C.c_int32),
                 ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("tile_chunks", C.c_int32),
                 ("spmv_batch", C.c_int32), ("precision", C.c_int32),
-                ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32)]
+                ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32),
+                ("step_rule", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -29,7 +30,7 @@ class Result(C.Structure):
                 ("rel_primal", C.c_double), ("rel_dual", C.c_double), ("rel_gap", C.c_double),
                 ("kkt_omega", C.c_double), ("omega", C.c_double), ("eta", C.c_double),
                 ("solve_s", C.c_double), ("device_ms", C.c_double), ("launches", C.c_int64),
-                ("fp32_iters", C.c_int64)]
+                ("fp32_iters", C.c_int64), ("accepted", C.c_int64)]
 
 
 class CheckRecord(C.Structure):

@@ -29,6 +29,11 @@ struct DevState {
   double last_err;                 // largest relative error of the better point at the last check
   long long k, t, nrestart, ncheck;
   int done, status, which, restart_flag, cand_avg, final_force;
+  // adaptive step rule: weight sum of the running sums, weight of the current iterate
+  // not yet added to them, steps accepted, rejections in a row, last attempt accepted
+  double wsum, pw;
+  long long accepted;
+  int rejects, accept;
 };
 
 struct DevParams {
@@ -195,6 +200,7 @@ __global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const typena
       const T acc = chunk_sum<T, Op, kBatch>(A, xg, s, e, lane);
       epi.finish(row, acc, pre);
     }
+    epi.task_end(w, lane);
   } else {
     // piece of a split chunk: publish, count arrivals, the last arrival combines
     const T acc = chunk_sum<T, Op, kBatch>(A, xg, Tk.s0, Tk.s1, lane);
@@ -212,6 +218,7 @@ __global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const typena
       if (lane == 0) A.cnt[Tk.t0] = 0;
       epi.finish(row, (T)sum, pre);
     }
+    epi.task_end(w, lane);
   }
 }
 
@@ -225,6 +232,7 @@ struct EpiStore {
   __device__ void prepare(const DevState* st) { scale = (use_inv_t && st) ? st->inv_t : 1.0; }
   __device__ Pre load(int) const { return Pre{}; }
   __device__ void finish(int r, double s, const Pre&) { out[r] = use_inv_t ? s * scale : s; }
+  __device__ void task_end(int, int) {}
 };
 
 // Primal step fused on g = (K'y)_j (Section 2, primal update):
@@ -246,6 +254,7 @@ struct EpiPrimal {
     x[j] = xn;
     sx[j] = p.sx + xn;
   }
+  __device__ void task_end(int, int) {}
 };
 
 // Dual step fused on v = (K x_new)_i (Section 2, dual update with extrapolation,
@@ -271,7 +280,176 @@ struct EpiDual {
     sy[i] = p.sy + yn;
     kxp[i] = v;
   }
+  __device__ void task_end(int, int) {}
 };
+
+// Adaptive step rule (the cited PDLP paper; an option beside the constant eta of
+// Section 2).  One attempt is the primal and dual step of Section 2 computed in place,
+// with the previous point kept in backups (xb, yb, kxb) for a rejected attempt, and
+// per-warp-task partial sums of ||dx||^2, ||dy||^2 and dy'(K dx) for the acceptance
+// test.  The running sums receive the previous point with its pending weight pw (the
+// step size that produced it; 0 once added or after a rejection).
+struct EpiPrimalA {
+  using T = double;
+  double* __restrict__ x;
+  double* __restrict__ xb;
+  double* __restrict__ sx;
+  const double* __restrict__ c;
+  const double* __restrict__ l;
+  const double* __restrict__ u;
+  double* __restrict__ part;   // ||dx||^2 per warp task
+  double tau, pw, acc;
+  struct Pre { double xo, c, l, u, sx; };
+  __device__ void prepare(const DevState* st) {
+    tau = st->tau;
+    pw = st->pw;
+    acc = 0.0;
+  }
+  __device__ Pre load(int j) const { return Pre{x[j], c[j], l[j], u[j], sx[j]}; }
+  __device__ void finish(int j, double g, const Pre& p) {
+    const double xn = clamp_box(fma(-tau, p.c - g, p.xo), p.l, p.u);
+    x[j] = xn;
+    xb[j] = p.xo;
+    sx[j] = fma(pw, p.xo, p.sx);
+    const double d = xn - p.xo;
+    acc = fma(d, d, acc);
+  }
+  __device__ void task_end(int w, int lane) {
+    const double s = warp_sum(acc);
+    if (lane == 0) part[w] = s;
+  }
+};
+
+struct EpiDualA {
+  using T = double;
+  double* __restrict__ y;
+  double* __restrict__ yb;
+  double* __restrict__ sy;
+  double* __restrict__ kxp;
+  double* __restrict__ kxb;
+  const double* __restrict__ q;
+  double* __restrict__ part;   // ||dy||^2 and dy'(K dx) per warp task
+  int m1;
+  double sigma, pw, a2, ai;
+  struct Pre { double q, kxp, y, sy; };
+  __device__ void prepare(const DevState* st) {
+    sigma = st->sigma;
+    pw = st->pw;
+    a2 = 0.0;
+    ai = 0.0;
+  }
+  __device__ Pre load(int i) const { return Pre{q[i], kxp[i], y[i], sy[i]}; }
+  __device__ void finish(int i, double v, const Pre& p) {
+    double yn = fma(sigma, fma(-2.0, v, p.q + p.kxp), p.y);
+    if (i >= m1) yn = max0(yn);
+    y[i] = yn;
+    yb[i] = p.y;
+    sy[i] = fma(pw, p.y, p.sy);
+    kxp[i] = v;
+    kxb[i] = p.kxp;
+    const double dy = yn - p.y;
+    a2 = fma(dy, dy, a2);
+    ai = fma(dy, v - p.kxp, ai);
+  }
+  __device__ void task_end(int w, int lane) {
+    const double s2 = warp_sum(a2), si = warp_sum(ai);
+    if (lane == 0) {
+      part[2 * w] = s2;
+      part[2 * w + 1] = si;
+    }
+  }
+};
+
+// Acceptance test and next step size of the adaptive rule, after one attempt:
+//   eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy'K dx|)   (+inf when 0),
+//   accept when eta <= eta_max (or after 64 rejections in a row),
+//   next eta = min((1 - (s+1)^-0.3) eta_max, (1 + (s+1)^-0.6) eta), s = accepted + 1.
+// The partials are added in a fixed order (thread-strided, warps in order).
+__global__ void __launch_bounds__(1024) k_step_decide(const double* __restrict__ px, int ntx,
+                                                      const double* __restrict__ py, int nty, DevState* st) {
+  if (st->done) return;
+  __shared__ double red[3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < ntx; i += blockDim.x) a += px[i];
+  for (int i = threadIdx.x; i < nty; i += blockDim.x) {
+    b += py[2 * i];
+    c += py[2 * i + 1];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
+  for (int w = 0; w < nw; ++w) {
+    dx2 += red[0][w];
+    dy2 += red[1][w];
+    inter += red[2][w];
+  }
+  st->wsum += st->pw;   // the pending weight went into the sums in this attempt
+  const double eta = st->eta, w = st->omega;
+  const double emax = inter == 0.0 ? __longlong_as_double(0x7FF0000000000000LL)
+                                   : (w * dx2 + dy2 / w) / (2.0 * fabs(inter));
+  const double sidx = (double)(st->accepted + 2);
+  const double e1 = (1.0 - pow(sidx, -0.3)) * emax, e2 = (1.0 + pow(sidx, -0.6)) * eta;
+  const double enext = e1 < e2 ? e1 : e2;
+  const bool acc = eta <= emax || st->rejects >= 64;
+  st->accept = acc ? 1 : 0;
+  if (acc) {
+    st->pw = eta;
+    st->accepted += 1;
+    st->rejects = 0;
+  } else {
+    st->pw = 0.0;
+    st->rejects += 1;
+  }
+  st->eta = enext;
+  st->tau = enext / w;
+  st->sigma = enext * w;
+}
+
+// A rejected attempt: back to the previous point (and its K x).
+__global__ void k_step_restore(double* __restrict__ x, const double* __restrict__ xb, int64_t npad,
+                               double* __restrict__ y, const double* __restrict__ yb, double* __restrict__ kxp,
+                               const double* __restrict__ kxb, int64_t mpad, const DevState* st) {
+  if (st->done || st->accept) return;
+  const int64_t tot = npad > mpad ? npad : mpad;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < npad) x[i] = xb[i];
+    if (i < mpad) {
+      y[i] = yb[i];
+      kxp[i] = kxb[i];
+    }
+  }
+}
+
+// Before a check: the pending weight of the current iterate goes into the sums.
+__global__ void k_flush_pending(double* __restrict__ sx, const double* __restrict__ x, int64_t npad,
+                                double* __restrict__ sy, const double* __restrict__ y, int64_t mpad,
+                                const DevState* st) {
+  if (st->done) return;
+  const double pw = st->pw;
+  if (pw == 0.0) return;
+  const int64_t tot = npad > mpad ? npad : mpad;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < npad) sx[i] = fma(pw, x[i], sx[i]);
+    if (i < mpad) sy[i] = fma(pw, y[i], sy[i]);
+  }
+}
+
+// Largest |K_ij| (bit patterns of non-negative doubles order like the values).
+__global__ void k_absmax(const double* __restrict__ v, int64_t len, unsigned long long* out) {
+  double mx = 0.0;
+  PDLP_GRID_STRIDE(i, len) mx = fmax(mx, fabs(v[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
 
 // Mixed precision (spec extension, not in the paper): the same primal and dual
 // steps with FP32 iterates and FP32 arithmetic; the running sums of the inner loop
@@ -293,6 +471,7 @@ struct EpiPrimal32 {
     x[j] = xn;
     sx[j] = p.sx + xn;
   }
+  __device__ void task_end(int, int) {}
 };
 struct EpiDual32 {
   using T = float;
@@ -312,6 +491,7 @@ struct EpiDual32 {
     sy[i] = p.sy + yn;
     kxp[i] = v;
   }
+  __device__ void task_end(int, int) {}
 };
 
 // Check in mixed precision: FP64 copies of the FP32 iterates, interval sums folded
@@ -477,11 +657,19 @@ __global__ void k_init_point(double* x, const double* x0, const double* l, const
 }
 
 // Before a check: advance k and t by the interval just run, 1/t for the average.
-__global__ void k_precheck(DevState* st, int len) {
+// adaptive: the average is weighted by the step sizes (weight sum wsum, after the
+// pending weight has been flushed into the sums)
+__global__ void k_precheck(DevState* st, int len, int adaptive) {
   if (st->done) return;
   st->k += len;
   st->t += len;
-  st->inv_t = st->t > 0 ? 1.0 / (double)st->t : 0.0;
+  if (adaptive) {
+    st->wsum += st->pw;
+    st->pw = 0.0;
+    st->inv_t = st->wsum > 0.0 ? 1.0 / st->wsum : 0.0;
+  } else {
+    st->inv_t = st->t > 0 ? 1.0 / (double)st->t : 0.0;
+  }
 }
 
 struct KktInputs {
@@ -731,6 +919,8 @@ __global__ void k_post_restart(DevState* st) {
   if (st->done || !st->restart_flag) return;
   st->t = 0;
   st->inv_t = 0.0;
+  st->wsum = 0.0;
+  st->pw = 0.0;
 }
 
 }  // namespace pdlp

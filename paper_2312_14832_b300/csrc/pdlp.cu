@@ -131,6 +131,12 @@ struct pdlp_ctx {
   cudaGraphExec_t gm_full = nullptr, gm_rem = nullptr;
   int gm_full_len = -1, gm_rem_len = -1;
   int64_t fp32_iters = 0;   // iterations of the last solve run in FP32
+  // adaptive step rule (params.step_rule = 1): backups of the point, per-task partials
+  double *xb = nullptr, *yb = nullptr, *kxb = nullptr, *part_x = nullptr, *part_y = nullptr;
+  double eta_adapt0 = 1.0;   // 1 / max |K_ij| of the scaled K
+  bool power_done = false;   // the power-iteration step size has been computed
+  cudaGraphExec_t ga_full = nullptr, ga_rem = nullptr;
+  int ga_full_len = -1, ga_rem_len = -1;
 };
 
 namespace pdlp {
@@ -267,6 +273,17 @@ static void enqueue_iteration(pdlp_ctx* h, const DevState* st) {
   launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, st);
 }
 
+// One attempt of the adaptive step rule (launch count: 4).
+static void enqueue_attempt(pdlp_ctx* h, DevState* st) {
+  launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimalA{h->x, h->xb, h->sx, h->c, h->l, h->u, h->part_x, 0.0, 0.0, 0.0}, st);
+  launch_rows<OpSpmv>(h, h->K, h->x,
+                      EpiDualA{h->y, h->yb, h->sy, h->kxp, h->kxb, h->q, h->part_y, (int)h->m1, 0.0, 0.0, 0.0, 0.0},
+                      st);
+  k_step_decide<<<1, 1024, 0, h->s>>>(h->part_x, h->Kt.ntasks, h->part_y, h->K.ntasks, st);
+  k_step_restore<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x, h->xb, h->npad, h->y, h->yb, h->kxp,
+                                                                         h->kxb, h->mpad, st);
+}
+
 static void enqueue_iteration32(pdlp_ctx* h, const DevState* st) {
   launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, st);
   launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1, 0.f}, st);
@@ -282,9 +299,13 @@ static KktInputs kkt_inputs(pdlp_ctx* h) {
   return in;
 }
 
-// The check (launch count: 8).
-static void enqueue_check(pdlp_ctx* h, int len, int final_check) {
-  k_precheck<<<1, 1, 0, h->s>>>(h->st, len);
+// The check (launch count: 8; 9 with the adaptive rule, whose pending weight goes
+// into the running sums first).
+static void enqueue_check(pdlp_ctx* h, int len, int final_check, bool adaptive = false) {
+  if (adaptive)
+    k_flush_pending<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->sx, h->x, h->npad, h->sy, h->y,
+                                                                            h->mpad, h->st);
+  k_precheck<<<1, 1, 0, h->s>>>(h->st, len, adaptive ? 1 : 0);
   launch_rows<OpSpmv>(h, h->Kt, h->y, EpiStore{h->g_c, 0, 1.0}, h->st);
   launch_rows<OpSpmv>(h, h->K, h->sx, EpiStore{h->kx_a, 1, 1.0}, h->st);
   launch_rows<OpSpmv>(h, h->Kt, h->sy, EpiStore{h->g_a, 1, 1.0}, h->st);
@@ -307,13 +328,18 @@ static void enqueue_check_mixed(pdlp_ctx* h, int len, int final_check) {
                                                                        h->kxp32, h->kxp, h->mpad, h->st);
 }
 
-static cudaGraphExec_t capture_interval(pdlp_ctx* h, int len, bool mixed = false) {
+enum { kModeFp64 = 0, kModeMixed = 1, kModeAdaptive = 2 };
+
+static cudaGraphExec_t capture_interval(pdlp_ctx* h, int len, int mode = kModeFp64) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-  if (mixed) {
+  if (mode == kModeMixed) {
     for (int i = 0; i < len; ++i) enqueue_iteration32(h, h->st);
     enqueue_check_mixed(h, len, 0);
+  } else if (mode == kModeAdaptive) {
+    for (int i = 0; i < len; ++i) enqueue_attempt(h, h->st);
+    enqueue_check(h, len, 0, true);
   } else {
     for (int i = 0; i < len; ++i) enqueue_iteration(h, h->st);
     enqueue_check(h, len, 0);
@@ -386,6 +412,8 @@ static void destroy(pdlp_ctx* h) {
   if (h->g_rem) cudaGraphExecDestroy(h->g_rem);
   if (h->gm_full) cudaGraphExecDestroy(h->gm_full);
   if (h->gm_rem) cudaGraphExecDestroy(h->gm_rem);
+  if (h->ga_full) cudaGraphExecDestroy(h->ga_full);
+  if (h->ga_rem) cudaGraphExecDestroy(h->ga_rem);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -471,6 +499,8 @@ static void check_params(const pdlp_params& P) {
   if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
   if (P.cluster_ctas < 0 || P.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
   if (P.resident < 0 || P.resident > 2) invalid("resident must be 0, 1 or 2");
+  if (P.step_rule < 0 || P.step_rule > 1) invalid("step_rule must be 0 or 1");
+  if (P.reserved1 != 0) invalid("reserved1 must be 0");
 }
 
 // Copies (from host or device) and validates one LP in CSR form; rows_total and the
@@ -771,7 +801,8 @@ static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const 
 }
 
 // ||K||_2 by power iteration on K'K (v0 = 1/sqrt(n)) -> eta; omega0 = ||c||/||q||.
-static void estimate_step_and_weight(pdlp_ctx* h) {
+// Power-iteration step size eta = step_scale / ||K||_2 (Section 2, constant step).
+static void power_step(pdlp_ctx* h) {
   const pdlp_params& P = h->p;
   const int64_t m = h->m, n = h->n, mp = h->mpad, np = h->npad;
   if (P.eta > 0.0) {
@@ -791,6 +822,28 @@ static void estimate_step_and_weight(pdlp_ctx* h) {
     CKL("power iteration");
     h->normK = m > 0 ? norm2_host(h, h->tm, mp) : 0.0;
     h->eta = h->normK > 0.0 ? P.step_scale / h->normK : 1.0;
+  }
+  h->power_done = true;
+}
+
+static void estimate_step_and_weight(pdlp_ctx* h) {
+  const pdlp_params& P = h->p;
+  const int64_t mp = h->mpad, np = h->npad;
+  // the power iteration is skipped for a handle set up for the adaptive rule (it runs
+  // on the first constant-step solve instead)
+  if (P.step_rule != 1) power_step(h);
+  {
+    // first step of the adaptive rule: 1 / max |K_ij| (1 when K = 0)
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(h->red_out);
+    CK(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), h->s));
+    const int64_t len = h->K.slots * 32;
+    if (len > 0) k_absmax<<<std::max(1, std::min(grid_for(len), 1184)), 256, 0, h->s>>>(h->K.val, len, mx);
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    double v;
+    std::memcpy(&v, &bits, sizeof(v));
+    h->eta_adapt0 = v > 0.0 ? 1.0 / v : 1.0;
   }
   {
     const double cn = norm2_host(h, h->c, np), qn = norm2_host(h, h->q, mp);
@@ -824,7 +877,7 @@ static void ensure_graphs_mixed(pdlp_ctx* h, int full, int rem) {
     h->gm_full = nullptr;
     h->gm_full_len = -1;
     if (full > 0) {
-      h->gm_full = capture_interval(h, full, true);
+      h->gm_full = capture_interval(h, full, kModeMixed);
       h->gm_full_len = full;
     }
   }
@@ -832,14 +885,48 @@ static void ensure_graphs_mixed(pdlp_ctx* h, int full, int rem) {
     if (h->gm_rem) cudaGraphExecDestroy(h->gm_rem);
     h->gm_rem = nullptr;
     h->gm_rem_len = -1;
-    h->gm_rem = capture_interval(h, rem, true);
+    h->gm_rem = capture_interval(h, rem, kModeMixed);
     h->gm_rem_len = rem;
   }
+}
+
+static void ensure_graphs_adaptive(pdlp_ctx* h, int full, int rem) {
+  if (h->ga_full_len != full) {
+    if (h->ga_full) cudaGraphExecDestroy(h->ga_full);
+    h->ga_full = nullptr;
+    h->ga_full_len = -1;
+    if (full > 0) {
+      h->ga_full = capture_interval(h, full, kModeAdaptive);
+      h->ga_full_len = full;
+    }
+  }
+  if (rem > 0 && h->ga_rem_len != rem) {
+    if (h->ga_rem) cudaGraphExecDestroy(h->ga_rem);
+    h->ga_rem = nullptr;
+    h->ga_rem_len = -1;
+    h->ga_rem = capture_interval(h, rem, kModeAdaptive);
+    h->ga_rem_len = rem;
+  }
+}
+
+// Buffers of the adaptive rule, allocated on its first use.
+static void ensure_adaptive_buffers(pdlp_ctx* h) {
+  if (h->xb) return;
+  h->xb = dalloc<double>(h, h->npad);
+  h->yb = dalloc<double>(h, h->mpad);
+  h->kxb = dalloc<double>(h, h->mpad);
+  h->part_x = dalloc<double>(h, std::max<int64_t>(1, h->Kt.ntasks));
+  h->part_y = dalloc<double>(h, 2 * std::max<int64_t>(1, h->K.ntasks));
 }
 
 static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0, double omega0,
                       pdlp_result* res, double* x_out, double* y_out) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
+  if (sp.step_rule < 0 || sp.step_rule > 1) invalid("step_rule must be 0 or 1");
+  const bool adaptive = sp.step_rule == 1;
+  if (adaptive && h->p.precision == PDLP_MIXED) invalid("the adaptive step rule runs in FP64 only");
+  if (adaptive) ensure_adaptive_buffers(h);
+  if (!adaptive && !h->power_done) power_step(h);
   auto t_start = std::chrono::steady_clock::now();
   const int64_t n = h->n, m = h->m, np = h->npad, mp = h->mpad;
   int64_t launches = 0;
@@ -879,10 +966,11 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   const double w0 = omega0 > 0.0 ? omega0 : h->omega0;
   DevState& s0 = h->st_init;
   std::memset(&s0, 0, sizeof(s0));
-  s0.eta = h->eta;
+  const double eta0 = adaptive ? (sp.eta > 0.0 ? sp.eta : h->eta_adapt0) : h->eta;
+  s0.eta = eta0;
   s0.omega = w0;
-  s0.tau = h->eta / w0;
-  s0.sigma = h->eta * w0;
+  s0.tau = eta0 / w0;
+  s0.sigma = eta0 * w0;
   s0.kkt_prev = std::numeric_limits<double>::infinity();
   CK(cudaMemcpyAsync(h->st, &s0, sizeof(DevState), cudaMemcpyHostToDevice, h->s));
   launch_rows<OpSpmv>(h, h->K, h->x, EpiStore{h->kxp, 0, 1.0}, h->st);
@@ -911,11 +999,12 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   bool timed_out = false;
   DevState fin{};
   if (nint == 0) {
-    enqueue_check(h, 0, 1);
-    launches += 8;
+    enqueue_check(h, 0, 1, adaptive);
+    launches += adaptive ? 9 : 8;
     CKL("final check");
   } else {
-    ensure_graphs(h, nfull > 0 ? L : 0, rem);
+    if (adaptive) ensure_graphs_adaptive(h, nfull > 0 ? L : 0, rem);
+    else ensure_graphs(h, nfull > 0 ? L : 0, rem);
     if (mixed) ensure_graphs_mixed(h, nfull > 0 ? L : 0, rem);
     // mixed precision: FP32 intervals until the FP64-measured relative error reaches
     // the switch tolerance or stops improving, then FP64 intervals (refinement)
@@ -929,10 +1018,12 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     while (!done && read < nint) {
       while (issued < nint && issued - read < kLookahead) {
         const bool fullint = issued < nfull;
-        cudaGraphExec_t g = phase32 ? (fullint ? h->gm_full : h->gm_rem) : (fullint ? h->g_full : h->g_rem);
+        cudaGraphExec_t g = phase32    ? (fullint ? h->gm_full : h->gm_rem)
+                            : adaptive ? (fullint ? h->ga_full : h->ga_rem)
+                                       : (fullint ? h->g_full : h->g_rem);
         const int len = fullint ? L : rem;
         CK(cudaGraphLaunch(g, h->s));
-        launches += 2 * len + (phase32 ? 12 : 8);
+        launches += adaptive ? 4 * len + 9 : 2 * len + (phase32 ? 12 : 8);
         if (phase32) fp32_intervals.emplace_back(issued_k, len);
         issued_k += len;
         const int slot = (int)(issued % kRing);
@@ -971,8 +1062,8 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
       int one = 1;
       CK(cudaMemcpyAsync(&h->st->final_force, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
       CK(cudaStreamSynchronize(h->s));
-      enqueue_check(h, 0, 1);
-      launches += 8;
+      enqueue_check(h, 0, 1, adaptive);
+      launches += adaptive ? 9 : 8;
       CKL("time-limit check");
     }
   }
@@ -1013,6 +1104,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     res->eta = fin.eta;
     res->device_ms = dev_ms;
     res->launches = launches;
+    res->accepted = adaptive ? fin.accepted : fin.k;
     res->fp32_iters = h->fp32_iters;
     res->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   }
@@ -1238,6 +1330,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   if (sp.cluster_ctas < 0 || sp.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
   if (sp.resident < 0 || sp.resident > 2) invalid("resident must be 0, 1 or 2");
+  if (sp.step_rule != 0) invalid("batches use the constant step (step_rule 0)");
   auto t_start = std::chrono::steady_clock::now();
   BatchArgs A;
   A.x0 = nullptr;
