@@ -163,6 +163,8 @@ typedef struct {
   double eta, omega0, norm_K;
   int32_t batch_team;          /* batch handles: CTAs per LP of the last pdlp_batch_solve    */
   int32_t batch_resident;      /* batch handles: 1 if that launch ran from shared memory      */
+  int32_t wide_rows_K;         /* rows of K stored spread over a chunk's lanes (dense rows)   */
+  int32_t reserved;
 } pdlp_info;
 
 /* Fills p with the defaults listed above. */

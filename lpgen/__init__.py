@@ -381,3 +381,58 @@ def transport_instance(family, seed):
     return dict(m=m, n=n, m1=m, row_ptr=row_ptr, col_idx=col_idx, val=val,
                 c=family["cost"].reshape(-1).copy(), q=np.concatenate([s, d]), l=np.zeros(n),
                 u=np.full(n, np.inf), features=np.concatenate([s, d]))
+
+
+def pagerank(n, seed=0, out_degree=6, damping=0.85, dense_ineq_row=False):
+    """A PageRank-shaped LP (the LP form of the PageRank problem, here on a random graph;
+    only the shape of the paper's rand_1m / rand_10m instances is reproduced: n columns,
+    n + 1 rows, about 8 nonzeros per column).
+
+    Graph: node j links to ``out_degree`` distinct random nodes other than itself, so the
+    link matrix S (S_ij = 1 / out_degree for a link j -> i) is column-stochastic.
+    LP over x >= 0 with c = 0:
+        row 0 (equality):        sum_j x_j = 1          (a dense row)
+        rows 1..n (inequality):  x_i - damping (S x)_i >= (1 - damping) / n
+    Summing the inequality rows gives (1 - damping) sum x >= 1 - damping, an equality
+    once sum x = 1, so every row is tight and the only feasible point is the PageRank
+    vector x* = (1 - damping)/n (I - damping S)^-1 1 (returned as x_star; obj_star = 0).
+    dense_ineq_row adds the redundant inequality sum_j x_j >= 1/2 (a second dense row,
+    in the inequality block)."""
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(seed)
+    d = int(out_degree)
+    src = np.repeat(np.arange(n), d)
+    # d distinct targets per node, none equal to the node: uniform draws from the other
+    # n - 1 nodes, rows with a repeated target drawn again
+    t = rng.integers(0, n - 1, size=(n, d))
+    while True:
+        ts = np.sort(t, axis=1)
+        bad = np.nonzero((ts[:, 1:] == ts[:, :-1]).any(axis=1))[0]
+        if bad.size == 0:
+            break
+        t[bad] = rng.integers(0, n - 1, size=(bad.size, d))
+    t = t + (t >= np.arange(n)[:, None])
+    dst = t.reshape(-1)
+    S = sps.csr_matrix((np.full(n * d, 1.0 / d), (dst, src)), shape=(n, n))
+    Gm = (sps.identity(n, format="csr") - damping * S).tocsr()
+    rows = [sps.csr_matrix(np.ones((1, n)))]
+    m1 = 1
+    q = [1.0]
+    rows.append(Gm)
+    q.extend([(1.0 - damping) / n] * n)
+    if dense_ineq_row:
+        rows.append(sps.csr_matrix(np.ones((1, n))))
+        q.append(0.5)
+    K = sps.vstack(rows, format="csr")
+    K.sort_indices()
+    if n <= 20000:
+        x_star = spla.spsolve(Gm.tocsc(), np.full(n, (1.0 - damping) / n))
+    else:   # power iteration: the error shrinks by the damping factor per step
+        x_star = np.full(n, 1.0 / n)
+        for _ in range(250):
+            x_star = damping * (S @ x_star) + (1.0 - damping) / n
+    m = K.shape[0]
+    return dict(m=m, n=n, m1=m1, row_ptr=K.indptr.astype(np.int64), col_idx=K.indices.astype(np.int32),
+                val=K.data.astype(np.float64), c=np.zeros(n), q=np.asarray(q, dtype=np.float64),
+                l=np.zeros(n), u=np.full(n, np.inf), x_star=x_star, obj_star=0.0)

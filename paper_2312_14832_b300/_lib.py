@@ -49,7 +49,8 @@ class Info(C.Structure):
                 ("spmv_batch_K", C.c_int32), ("spmv_batch_Kt", C.c_int32),
                 ("algorithmic_bytes_per_iter", C.c_double), ("stored_bytes_per_iter", C.c_double),
                 ("eta", C.c_double), ("omega0", C.c_double), ("norm_K", C.c_double),
-                ("batch_team", C.c_int32), ("batch_resident", C.c_int32)]
+                ("batch_team", C.c_int32), ("batch_resident", C.c_int32),
+                ("wide_rows_K", C.c_int32), ("reserved", C.c_int32)]
 
 
 # every function declared in include/pdlp.h: name -> (restype, argtypes)

@@ -176,6 +176,16 @@ __device__ __forceinline__ T chunk_sum(const SellView& A, const T* __restrict__ 
   return acc;
 }
 
+// A wide chunk's row sum: the lanes' partial sums combined by a fixed butterfly, the
+// total in lane 0 (the row), 0 in the padding rows of lanes 1..31.
+template <class Op, class T>
+__device__ __forceinline__ T wide_total(T part, int lane) {
+  double v = (double)part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = join_of<Op>(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return lane == 0 ? (T)v : T(0);
+}
+
 // One warp per task; lane = row of the chunk.  Epi::finish(row, sum, pre) receives the
 // complete row sum exactly once per row; Epi::load(row) fetches, before the row's
 // SpMV loop, the operands the epilogue needs, so their latency overlaps it.
@@ -197,7 +207,8 @@ __global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const typena
       const int e = __shfl_sync(0xffffffffu, cb, j + 1);
       const int row = (Tk.chunk + j) * 32 + lane;
       const typename Epi::Pre pre = epi.load(row);
-      const T acc = chunk_sum<T, Op, kBatch>(A, xg, s, e, lane);
+      T acc = chunk_sum<T, Op, kBatch>(A, xg, s, e, lane);
+      if (Tk.wide) acc = wide_total<Op>(acc, lane);
       epi.finish(row, acc, pre);
     }
     epi.task_end(w, lane);
@@ -216,6 +227,7 @@ __global__ void __launch_bounds__(256) sell_rows_kernel(SellView A, const typena
       double sum = __ldcg(A.gpart + (size_t)Tk.t0 * 32 + lane);
       for (int i = 1; i < Tk.np; ++i) sum = join_of<Op>(sum, __ldcg(A.gpart + (size_t)(Tk.t0 + i) * 32 + lane));
       if (lane == 0) A.cnt[Tk.t0] = 0;
+      if (Tk.wide) sum = wide_total<Op>(sum, lane);
       epi.finish(row, (T)sum, pre);
     }
     epi.task_end(w, lane);
@@ -650,7 +662,7 @@ __global__ void k_init_point(double* x, const double* x0, const double* l, const
   PDLP_GRID_STRIDE(i, tot) {
     if (i < npad) x[i] = i < n ? clamp_box(x0 ? x0[i] : 0.0, l[i], u[i]) : 0.0;
     if (i < mpad) {
-      double yi = (i < m && y0) ? y0[i] : 0.0;
+      double yi = y0 ? y0[i] : 0.0;   // y0 is in internal order, zero in padding rows
       y[i] = (i >= m1) ? max0(yi) : yi;
     }
   }

@@ -24,15 +24,21 @@ void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi
 
 SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
                     const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
-                    const std::vector<int32_t>& esrc, int32_t pad_col) {
+                    const std::vector<int32_t>& esrc, int32_t pad_col, const std::vector<uint8_t>* wide_row) {
   SellHost S;
   S.rows = rows;
   S.rows_pad = std::max<int64_t>(32, (rows + 31) / 32 * 32);
   S.nchunks = S.rows_pad / 32;
   S.chunk_ptr.assign((size_t)S.nchunks + 1, 0);
+  S.wide.assign((size_t)S.nchunks, 0);
   for (int64_t ch = 0; ch < S.nchunks; ++ch) {
     int64_t L = 1;
-    for (int64_t r = ch * 32; r < std::min(rows, ch * 32 + 32); ++r) L = std::max(L, elen[(size_t)r]);
+    if (wide_row && ch * 32 < rows && (*wide_row)[(size_t)(ch * 32)]) {
+      S.wide[(size_t)ch] = 1;
+      L = std::max<int64_t>(1, (elen[(size_t)(ch * 32)] + 31) / 32);
+    } else {
+      for (int64_t r = ch * 32; r < std::min(rows, ch * 32 + 32); ++r) L = std::max(L, elen[(size_t)r]);
+    }
     S.chunk_ptr[(size_t)ch + 1] = S.chunk_ptr[(size_t)ch] + (int32_t)L;
   }
   size_t total = (size_t)S.chunk_ptr.back() * 32;
@@ -41,6 +47,20 @@ SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
   for (int64_t ch = 0; ch < S.nchunks; ++ch) {
     int64_t base = S.chunk_ptr[(size_t)ch];
     int64_t clen = S.chunk_ptr[(size_t)ch + 1] - base;
+    if (S.wide[(size_t)ch]) {
+      // entry k of the row in slot k / 32, lane k % 32; padding gathers its first column
+      const int64_t r = ch * 32, st = estart[(size_t)r], L = elen[(size_t)r];
+      for (int64_t k = 0; k < clen * 32; ++k) {
+        const size_t e = (size_t)base * 32 + (size_t)k;
+        if (k < L) {
+          S.col[e] = ecol[(size_t)(st + k)];
+          S.src[e] = esrc[(size_t)(st + k)];
+        } else if (L > 0) {
+          S.col[e] = ecol[(size_t)st];
+        }
+      }
+      continue;
+    }
     for (int64_t lane = 0; lane < 32; ++lane) {
       int64_t r = ch * 32 + lane;
       if (r >= rows) break;
@@ -64,6 +84,7 @@ void append_sell(SellHost& G, const SellHost& S) {
   for (int64_t ch = 0; ch < S.nchunks; ++ch) G.chunk_ptr.push_back(base + S.chunk_ptr[(size_t)ch + 1]);
   G.col.insert(G.col.end(), S.col.begin(), S.col.end());
   G.src.insert(G.src.end(), S.src.begin(), S.src.end());
+  G.wide.insert(G.wide.end(), S.wide.begin(), S.wide.end());
   G.rows += S.rows_pad;
   G.rows_pad = G.rows;
   G.nchunks += S.nchunks;
@@ -75,10 +96,22 @@ TaskPlan plan_tasks(const SellHost& S, int32_t Q, int32_t C) {
   if (C < 1) C = 1;
   if (C > 32) C = 32;
   int64_t c = 0;
+  auto is_wide = [&](int64_t ch) { return !S.wide.empty() && S.wide[(size_t)ch] != 0; };
   while (c < S.nchunks) {
     int32_t base = S.chunk_ptr[(size_t)c];
     int32_t len = S.chunk_ptr[(size_t)c + 1] - base;
-    if (len > Q) {
+    if (is_wide(c) && len <= Q) {
+      SellTask T{};
+      T.s0 = base;
+      T.s1 = base + len;
+      T.chunk = (int32_t)c;
+      T.t0 = -1;
+      T.np = 0;
+      T.nc = 1;
+      T.wide = 1;
+      P.tasks.push_back(T);
+      ++c;
+    } else if (len > Q) {
       int32_t np = (len + Q - 1) / Q;
       int32_t t0 = (int32_t)P.tasks.size();
       for (int32_t i = 0; i < np; ++i) {
@@ -89,6 +122,7 @@ TaskPlan plan_tasks(const SellHost& S, int32_t Q, int32_t C) {
         T.t0 = t0;
         T.np = np;
         T.nc = 1;
+        T.wide = is_wide(c) ? 1 : 0;
         P.tasks.push_back(T);
       }
       P.split_chunks++;
@@ -102,7 +136,7 @@ TaskPlan plan_tasks(const SellHost& S, int32_t Q, int32_t C) {
       int32_t tot = 0, nc = 0;
       while (c < S.nchunks && nc < C) {
         int32_t l = S.chunk_ptr[(size_t)c + 1] - S.chunk_ptr[(size_t)c];
-        if (l > Q || tot + l > Q) break;
+        if (l > Q || tot + l > Q || is_wide(c)) break;
         tot += l;
         ++nc;
         ++c;

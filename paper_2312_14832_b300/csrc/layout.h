@@ -12,6 +12,12 @@
 // chunks), a chunk longer
 // than tile_slots is split into pieces whose partial sums are combined, in piece
 // order, by the warp that finishes last.
+//
+// A "wide" row (one far longer than the rows next to it in length order, such as a
+// dense row) gets a chunk of its own, whose other 31 rows are empty padding rows: its
+// entries are spread over the 32 lanes (entry k in slot k / 32, lane k % 32), and the
+// lanes' partial sums are combined by a fixed warp reduction.  So the row costs its own
+// length / 32 slots instead of its length times 32.
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -24,7 +30,8 @@ struct SellTask {
   int32_t t0;       // split chunk: index of its first piece task; else -1
   int32_t np;       // split chunk: number of pieces; else 0
   int32_t nc;       // chunks the task covers (1 for a split piece)
-  int32_t pad[2];
+  int32_t wide;     // 1: the task's chunk holds one wide row spread over the lanes
+  int32_t pad;
 };
 
 struct SellHost {
@@ -34,6 +41,7 @@ struct SellHost {
   std::vector<int32_t> chunk_ptr;  // nchunks + 1, in slots
   std::vector<int32_t> col;        // slots * 32, internal column index
   std::vector<int32_t> src;        // slots * 32, position in the input CSR (-1 in padding)
+  std::vector<uint8_t> wide;       // nchunks: 1 when the chunk holds one wide row
   int64_t slots() const { return chunk_ptr.empty() ? 0 : chunk_ptr.back(); }
 };
 
@@ -48,17 +56,21 @@ void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi
 
 // Builds the SELL-32 arrays of a matrix whose internal row p (0 <= p < rows) has the
 // entries estart[p] .. estart[p] + elen[p] - 1 of the entry arrays ecol / esrc.
-// Padding slots of empty rows point at column pad_col.
+// Padding slots of empty rows point at column pad_col.  wide_row (optional, per row):
+// rows stored spread over their chunk's lanes; such a row is the first of its chunk and
+// the other 31 rows of the chunk are empty.
 SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
                     const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
-                    const std::vector<int32_t>& esrc, int32_t pad_col = 0);
+                    const std::vector<int32_t>& esrc, int32_t pad_col = 0,
+                    const std::vector<uint8_t>* wide_row = nullptr);
 
 // Appends the chunks of S after those of G (block-diagonal concatenation; the column
 // indices of S must already be in G's numbering).
 void append_sell(SellHost& G, const SellHost& S);
 
 // Packs whole chunks into tasks of at most tile_slots slots and at most tile_chunks
-// (<= 32) chunks; chunks longer than tile_slots become split pieces.
+// (<= 32) chunks; chunks longer than tile_slots become split pieces; a wide chunk is
+// never packed with another.
 TaskPlan plan_tasks(const SellHost& S, int32_t tile_slots, int32_t tile_chunks);
 
 }  // namespace pdlp

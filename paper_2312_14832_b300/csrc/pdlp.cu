@@ -55,6 +55,8 @@ struct DevSell {
   SellTask* tasks = nullptr;
   double* gpart = nullptr;
   int32_t* cnt = nullptr;
+  uint8_t* wide = nullptr;   // per chunk, or null when no chunk is wide
+  int32_t nwide = 0;
   int32_t ntasks = 0;
   int32_t tile = 0, tchunks = 0, batch = 8;
   int64_t rows = 0, rows_pad = 0, nchunks = 0, slots = 0, split = 0;
@@ -73,6 +75,7 @@ using namespace pdlp;
 struct pdlp_ctx {
   pdlp_params p{};
   int64_t m = 0, n = 0, m1 = 0, nnz = 0, mpad = 0, npad = 0;
+  int64_t m1_int = 0;   // internal rows [0, m1_int) are equality rows (padding rows included)
   int dev = 0;
   cudaStream_t s = nullptr;
   cudaEvent_t ev_user = nullptr, ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
@@ -195,6 +198,9 @@ static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const 
   D.gpart = dalloc<double>(h, (size_t)D.ntasks * 32);
   D.cnt = dalloc<int32_t>(h, (size_t)D.ntasks);
   D.val = dalloc<double>(h, (size_t)D.slots * 32);
+  D.nwide = 0;
+  for (uint8_t f : S.wide) D.nwide += f != 0;
+  D.wide = D.nwide > 0 ? upload(h, S.wide) : nullptr;
   int32_t* d_src = upload(h, S.src);
   k_gather_values<<<grid_for(D.slots * 32), 256, 0, h->s>>>(D.val, d_src, d_csr_val, D.slots * 32);
   CKL("k_gather_values");
@@ -240,12 +246,13 @@ __global__ void k_div_into(double* a, const double* w, const double* s, int64_t 
 
 // v <- (v * fr[i]) * fc[j] for K (transposed = 0: chunk rows are i, columns j) and for
 // K' (transposed = 1: chunk rows are j, columns i), so both copies round identically.
+// A wide chunk (wide[ch] != 0) holds one row, the chunk's first.
 __global__ void k_scale_sell2(double* v, const int32_t* col, const int32_t* chunk_ptr, int64_t nchunks,
-                              const double* fr, const double* fc, int transposed) {
+                              const double* fr, const double* fc, int transposed, const uint8_t* wide) {
   const int lane = threadIdx.x & 31;
   for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
        ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t row = ch * 32 + lane;
+    const int64_t row = ch * 32 + ((wide != nullptr && wide[ch]) ? 0 : lane);
     for (int64_t s = chunk_ptr[ch]; s < chunk_ptr[ch + 1]; ++s) {
       const size_t e = (size_t)s * 32 + lane;
       const double a = transposed ? fr[col[e]] : fr[row];
@@ -270,14 +277,14 @@ __global__ void k_copy_state(DevState* dst, const DevState* src) {
 
 static void enqueue_iteration(pdlp_ctx* h, const DevState* st) {
   launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, st);
-  launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, st);
+  launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, st);
 }
 
 // One attempt of the adaptive step rule (launch count: 4).
 static void enqueue_attempt(pdlp_ctx* h, DevState* st) {
   launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimalA{h->x, h->xb, h->sx, h->c, h->l, h->u, h->part_x, 0.0, 0.0, 0.0}, st);
   launch_rows<OpSpmv>(h, h->K, h->x,
-                      EpiDualA{h->y, h->yb, h->sy, h->kxp, h->kxb, h->q, h->part_y, (int)h->m1, 0.0, 0.0, 0.0, 0.0},
+                      EpiDualA{h->y, h->yb, h->sy, h->kxp, h->kxb, h->q, h->part_y, (int)h->m1_int, 0.0, 0.0, 0.0, 0.0},
                       st);
   k_step_decide<<<1, 1024, 0, h->s>>>(h->part_x, h->Kt.ntasks, h->part_y, h->K.ntasks, st);
   k_step_restore<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x, h->xb, h->npad, h->y, h->yb, h->kxp,
@@ -286,7 +293,7 @@ static void enqueue_attempt(pdlp_ctx* h, DevState* st) {
 
 static void enqueue_iteration32(pdlp_ctx* h, const DevState* st) {
   launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, st);
-  launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1, 0.f}, st);
+  launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1_int, 0.f}, st);
 }
 
 static KktInputs kkt_inputs(pdlp_ctx* h) {
@@ -295,7 +302,7 @@ static KktInputs kkt_inputs(pdlp_ctx* h) {
   in.invDr = h->invDr;
   in.c = h->c; in.l = h->l; in.u = h->u; in.g_c = h->g_c; in.g_a = h->g_a; in.x = h->x; in.sx = h->sx;
   in.xa = h->xa; in.invDc = h->invDc;
-  in.m = h->m; in.n = h->n; in.m1 = (int)h->m1; in.rows_blocks = h->nb_rows;
+  in.m = h->mpad; in.n = h->n; in.m1 = (int)h->m1_int; in.rows_blocks = h->nb_rows;
   return in;
 }
 
@@ -455,7 +462,7 @@ static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
           if (primal)
             launch_rows<OpSpmv>(h, D, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
           else
-            launch_rows<OpSpmv>(h, D, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, h->st_tmp);
+            launch_rows<OpSpmv>(h, D, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, h->st_tmp);
         }
         CK(cudaEventRecord(e1, h->s));
         CKL("autotune launch");
@@ -574,13 +581,18 @@ struct Layout {
 // Appends the layout of one LP (rows rp[rp0..rp0+m], entries from nnz0, columns
 // [col0, col0 + n) of the caller's concatenated vectors) to L at internal offsets
 // L.mpad / L.npad, and pads both to a multiple of 32 (at least 32).
+// Rows at least this long that are more than 4 times longer than the next row in
+// length order are stored as wide rows (layout.h).
+constexpr int64_t kWideMin = 1024;
+
 static void append_lp_layout(Layout& L, const HostLP& H, int64_t rp0, int64_t nnz0, int64_t out0, int64_t m,
                              int64_t n, int64_t m1, int64_t row0, int64_t col0, std::vector<int64_t>& k_est,
                              std::vector<int64_t>& k_eln, std::vector<int32_t>& k_ecol, std::vector<int32_t>& k_esrc,
                              std::vector<int64_t>& t_est, std::vector<int64_t>& t_eln, std::vector<int32_t>& t_ecol,
-                             std::vector<int32_t>& t_esrc) {
+                             std::vector<int32_t>& t_esrc, bool wide_ok = false,
+                             std::vector<uint8_t>* k_wide = nullptr, int64_t* m1_int = nullptr) {
   const int64_t nnz = H.rp[(size_t)(rp0 + m)];
-  const int64_t mp = std::max<int64_t>(32, (m + 31) / 32 * 32), np = std::max<int64_t>(32, (n + 31) / 32 * 32);
+  const int64_t np = std::max<int64_t>(32, (n + 31) / 32 * 32);
   const int64_t rbase = L.mpad, cbase = L.npad;
   std::vector<int64_t> rlen((size_t)m), clen((size_t)n, 0);
   for (int64_t i = 0; i < m; ++i) rlen[(size_t)i] = H.rp[(size_t)(rp0 + i + 1)] - H.rp[(size_t)(rp0 + i)];
@@ -589,17 +601,54 @@ static void append_lp_layout(Layout& L, const HostLP& H, int64_t rp0, int64_t nn
   sort_by_length_desc(rlen, 0, m1, pr);
   sort_by_length_desc(rlen, m1, m, pr);
   sort_by_length_desc(clen, 0, n, pc);
+  // internal row order: equality rows, then inequality rows, each by decreasing length;
+  // a wide row starts a chunk and is followed by 31 empty padding rows (-1)
+  std::vector<int32_t> ord;
+  std::vector<uint8_t> wflag;
+  ord.reserve((size_t)m + 64);
+  auto emit_block = [&](int64_t p0, int64_t p1) {
+    int64_t p = p0;
+    while (wide_ok && p < p1) {
+      const int64_t len = rlen[(size_t)pr[(size_t)p]];
+      const int64_t next = p + 1 < p1 ? rlen[(size_t)pr[(size_t)p + 1]] : 0;
+      if (len < kWideMin || len <= 4 * next) break;
+      while (ord.size() % 32) {
+        ord.push_back(-1);
+        wflag.push_back(0);
+      }
+      ord.push_back(pr[(size_t)p]);
+      wflag.push_back(1);
+      for (int k = 0; k < 31; ++k) {
+        ord.push_back(-1);
+        wflag.push_back(0);
+      }
+      ++p;
+    }
+    for (; p < p1; ++p) {
+      ord.push_back(pr[(size_t)p]);
+      wflag.push_back(0);
+    }
+  };
+  emit_block(0, m1);
+  if (m1_int) *m1_int = (int64_t)ord.size();
+  emit_block(m1, m);
+  const int64_t mint = (int64_t)ord.size();
+  const int64_t mp = std::max<int64_t>(32, (mint + 31) / 32 * 32);
+  ord.resize((size_t)mp, -1);
+  wflag.resize((size_t)mp, 0);
+  if (k_wide) *k_wide = wflag;
   std::vector<int32_t> lpos_r((size_t)std::max<int64_t>(m, 1)), lpos_c((size_t)n);
-  for (int64_t p = 0; p < m; ++p) lpos_r[(size_t)pr[(size_t)p]] = (int32_t)p;
+  for (int64_t p = 0; p < mp; ++p)
+    if (ord[(size_t)p] >= 0) lpos_r[(size_t)ord[(size_t)p]] = (int32_t)p;
   for (int64_t p = 0; p < n; ++p) lpos_c[(size_t)pc[(size_t)p]] = (int32_t)p;
-  for (int64_t p = 0; p < mp; ++p) L.perm_r.push_back(p < m ? (int32_t)(row0 + pr[(size_t)p]) : -1);
+  for (int64_t p = 0; p < mp; ++p) L.perm_r.push_back(ord[(size_t)p] >= 0 ? (int32_t)(row0 + ord[(size_t)p]) : -1);
   for (int64_t p = 0; p < np; ++p) L.perm_c.push_back(p < n ? (int32_t)(col0 + pc[(size_t)p]) : -1);
   for (int64_t i = 0; i < m; ++i) L.pos_r[(size_t)(row0 + i)] = (int32_t)(rbase + lpos_r[(size_t)i]);
   for (int64_t j = 0; j < n; ++j) L.pos_c[(size_t)(col0 + j)] = (int32_t)(cbase + lpos_c[(size_t)j]);
   // K rows: entries in CSR order, columns renumbered
   for (int64_t p = 0; p < mp; ++p) {
-    if (p < m) {
-      const int64_t i = pr[(size_t)p];
+    if (ord[(size_t)p] >= 0) {
+      const int64_t i = ord[(size_t)p];
       k_est.push_back(out0 + H.rp[(size_t)(rp0 + i)]);
       k_eln.push_back(rlen[(size_t)i]);
     } else {
@@ -673,8 +722,12 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
     std::vector<int64_t> k_est, k_eln, t_est, t_eln;
     std::vector<int32_t> k_ecol((size_t)h->nnz), k_esrc((size_t)h->nnz), t_ecol((size_t)h->nnz),
         t_esrc((size_t)h->nnz);
-    append_lp_layout(Lo, H, 0, 0, 0, m, n, m1, 0, 0, k_est, k_eln, k_ecol, k_esrc, t_est, t_eln, t_ecol, t_esrc);
-    Lo.SK = build_sell(Lo.mpad, k_est, k_eln, k_ecol, k_esrc);
+    std::vector<uint8_t> k_wide;
+    int64_t m1i = m1;
+    append_lp_layout(Lo, H, 0, 0, 0, m, n, m1, 0, 0, k_est, k_eln, k_ecol, k_esrc, t_est, t_eln, t_ecol, t_esrc,
+                     true, &k_wide, &m1i);
+    h->m1_int = m1i;
+    Lo.SK = build_sell(Lo.mpad, k_est, k_eln, k_ecol, k_esrc, 0, &k_wide);
     Lo.SKt = build_sell(Lo.npad, t_est, t_eln, t_ecol, t_esrc);
   }
   device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
@@ -787,9 +840,9 @@ static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const 
       k_scale_factor<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->Dr, h->tm, mp);
       k_scale_factor<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->Dc, h->tn, np);
       k_scale_sell2<<<grid_for(h->K.nchunks * 32), 256, 0, h->s>>>(h->K.val, h->K.col, h->K.chunk_ptr,
-                                                                  h->K.nchunks, h->tm, h->tn, 0);
+                                                                  h->K.nchunks, h->tm, h->tn, 0, h->K.wide);
       k_scale_sell2<<<grid_for(h->Kt.nchunks * 32), 256, 0, h->s>>>(h->Kt.val, h->Kt.col, h->Kt.chunk_ptr,
-                                                                   h->Kt.nchunks, h->tm, h->tn, 1);
+                                                                   h->Kt.nchunks, h->tm, h->tn, 1, h->Kt.wide);
       CKL("scaling pass");
     }
   }
@@ -962,7 +1015,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   }
   CK(cudaEventRecord(h->ev_t0, h->s));
   k_init_point<<<grid_for(std::max(np, mp)), 256, 0, h->s>>>(h->x, xs, h->l, h->u, n, np, h->y, ys, m, mp,
-                                                              (int)h->m1);
+                                                              (int)h->m1_int);
   const double w0 = omega0 > 0.0 ? omega0 : h->omega0;
   DevState& s0 = h->st_init;
   std::memset(&s0, 0, sizeof(s0));
@@ -1660,6 +1713,7 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->norm_K = h->normK;
     info->batch_team = h->last_team;
     info->batch_resident = h->last_resident ? 1 : 0;
+    info->wide_rows_K = h->K.nwide;
     return PDLP_OK;
   });
 }
@@ -1688,9 +1742,9 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
           launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
         CK(cudaEventRecord(ev[2 * i + 1], h->s));
         if (h->p.precision == PDLP_MIXED)
-          launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1, 0.f}, h->st_tmp);
+          launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1_int, 0.f}, h->st_tmp);
         else
-          launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1, 0.0}, h->st_tmp);
+          launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, h->st_tmp);
         CK(cudaEventRecord(ev[2 * i + 2], h->s));
       }
       CKL("timed iterations");

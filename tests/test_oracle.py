@@ -420,3 +420,26 @@ def test_adaptive_planted_small_reaches_planted_objective(scaling):
     Kx = dense(lp) @ x
     pr = np.concatenate([Kx[: lp["m1"]] - lp["q"][: lp["m1"]], np.maximum(lp["q"][lp["m1"]:] - Kx[lp["m1"]:], 0)])
     assert np.linalg.norm(pr) <= 1e-8 * (1 + np.linalg.norm(lp["q"])) * (1 + 1e-9)
+
+
+# ---------------------------------------------------------------- PageRank-shaped LP
+
+def test_pagerank_lp_optimum_is_the_pagerank_vector():
+    """The generator's x_star is the PageRank vector by its definition (the fixed point
+    of x = damping S x + (1 - damping)/n with sum 1, reached here by plain power
+    iteration on the link matrix), and the oracle's solution at 1e-8 is that vector."""
+    lp = lpgen.pagerank(300, seed=1)
+    n = lp["n"]
+    # the link matrix from the LP's inequality rows: row i = e_i - damping S_i
+    K = dense(lp).toarray()
+    S = (np.eye(n) - K[1:n + 1]) / 0.85
+    assert np.allclose(S.sum(axis=0), 1.0)            # column-stochastic
+    x = np.full(n, 1.0 / n)
+    for _ in range(500):
+        x = 0.85 * S @ x + 0.15 / n
+    assert abs(x.sum() - 1.0) < 1e-12
+    np.testing.assert_allclose(lp["x_star"], x, rtol=1e-12, atol=0)
+    for scaling in (0, 1):
+        r = oracle.solve(lp, tol=1e-8, scaling=scaling)
+        assert r["status"] == oracle.STATUS_OPTIMAL
+        assert np.abs(r["x"] - x).max() <= 1e-5 * x.max()
