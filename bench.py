@@ -316,6 +316,72 @@ def bench_mcf(args):
     print(json.dumps(out))
 
 
+def bench_pagerank(args):
+    """PageRank-shaped LP of the size of the paper's rand_1m instance (lpgen.pagerank:
+    n = 1e6 columns, m = 1e6 + 1 rows, nnz = 8e6, one dense row stored as a wide row),
+    Ruiz + Pock-Chambolle scaling: time to 1e-6 relative KKT (the accuracy of the
+    paper's large-instance table) with the constant step of Section 2, with the
+    adaptive step rule and in mixed precision; PDHG iterations/s; the CPU oracle's time
+    per iteration on the same LP (a few iterations, single thread)."""
+    import torch
+    import lpgen
+    import oracle
+    import paper_2312_14832_b300 as pk
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    lp = lpgen.pagerank(args.pr_nodes, seed=0)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    out = {"metric": METRIC, "unit": "s to 1e-6", "n_gpus": 1, "higher_is_better": False,
+           "data": "synthetic", "impl": "ours-pagerank", "dtype": "f64",
+           "config": {"workload": f"PageRank LP on a random graph (out-degree 6, damping 0.85), n={lp['n']}, "
+                                  f"m={lp['m']}, nnz={len(lp['val'])}; Ruiz(10)+Pock-Chambolle scaling",
+                      "tol": 1e-6, "check_every": CHECK_EVERY},
+           "paper_context": {"instance": "rand_1m_nodes (m=1,000,001, n=1e6, nnz=7,999,982)",
+                             "cuPDLP-C H100 s": 3.56, "note": "different random graph; context only"}}
+    runs = (("constant", dict(step_rule=0, precision=pk.FP64)), ("adaptive", dict(step_rule=1, precision=pk.FP64)),
+            ("mixed", dict(step_rule=0, precision=pk.MIXED)))
+    for name, kw in runs:
+        t0 = time.perf_counter()
+        s = pk.Solver.from_lp(lp, scaling=1, stream=stream.cuda_stream, **kw)
+        setup_s = time.perf_counter() - t0
+        s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False)   # graph capture
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = args.steps * CHECK_EVERY
+        e0.record(stream)
+        s.solve(tol=0.0, max_iter=iters, want_point=False, mixed_switch_tol=1e-30)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ips = iters / (e0.elapsed_time(e1) * 1e-3)
+        r = s.solve(tol=1e-6, time_limit_s=args.pr_budget)
+        err = float(np.abs(r["x"] - lp["x_star"]).max() / lp["x_star"].max())
+        out[name] = {"time_to_1e-6_s": r["device_ms"] * 1e-3, "wall_s": r["solve_s"], "iters": r["iters"],
+                     "accepted": r["accepted"], "fp32_iters": r["fp32_iters"], "restarts": r["restarts"],
+                     "status": ["optimal", "iter_limit", "time_limit", "numerical"][r["status"]],
+                     "rel_errors": [r["rel_primal"], r["rel_dual"], r["rel_gap"]],
+                     "max_rel_dev_from_pagerank_vector": err, "iter_per_s": ips, "setup_s": setup_s,
+                     "wide_rows_K": s.info()["wide_rows_K"]}
+        s.close()
+    # the CPU oracle: time per PDHG step on the same LP (scaled problem not needed for a step)
+    x = np.zeros(lp["n"])
+    y = np.zeros(lp["m"])
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < 10.0:
+        x, y = oracle.pdhg_step(lp, x, y, 0.5, 1.0)
+        k += 1
+    cpu_it_s = (time.perf_counter() - t0) / k
+    best = min(out[nm]["time_to_1e-6_s"] for nm, _ in runs if out[nm]["status"] == "optimal")
+    out["value"] = best
+    out["cpu_baseline"] = {"value": cpu_it_s * out["constant"]["iters"], "unit": "s to 1e-6 (estimated)",
+                           "cores": 1, "kind": "oracle",
+                           "sample": f"{k} oracle PDHG steps ({cpu_it_s * 1e3:.1f} ms each) x the GPU's "
+                                     f"constant-step iteration count"}
+    out["generate_s"] = gen_s
+    print(json.dumps(out))
+
+
 def bench_warmstart(args):
     """Learned warm start on a transportation family (lpgen.transport_family(S, D), seed 0):
     solutions of args.ws_train instances (seeds 1..) from the batched solver train the
@@ -362,7 +428,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batched", "mcf", "warmstart"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "medium", "small", "batched", "mcf", "warmstart", "pagerank"])
     ap.add_argument("--ttt-budget", type=float, default=0.0,
                     help="seconds for a cold time-to-1e-4 solve of the bench workload (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -372,6 +439,8 @@ def main():
     ap.add_argument("--batch-scaling", type=int, default=0)
     ap.add_argument("--seq-sample", type=int, default=32)
     ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-1e-4 solve (mcf)")
+    ap.add_argument("--pr-nodes", type=int, default=1_000_000)
+    ap.add_argument("--pr-budget", type=float, default=60.0, help="seconds per time-to-1e-6 solve (pagerank)")
     ap.add_argument("--ws-train", type=int, default=50000)
     ap.add_argument("--ws-heldout", type=int, default=1000)
     ap.add_argument("--ws-epochs", type=int, default=30)
@@ -386,6 +455,9 @@ def main():
         return
     if args.workload == "warmstart":
         bench_warmstart(args)
+        return
+    if args.workload == "pagerank":
+        bench_pagerank(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
