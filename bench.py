@@ -382,6 +382,56 @@ def bench_pagerank(args):
     print(json.dumps(out))
 
 
+def bench_teams(args):
+    """Small LPs on the batched persistent kernel with thread-block-cluster teams: the
+    small planted LP alone (time to 1e-4 and 1e-8 for teams of 1..16 CTAs, matrix
+    slices streamed or resident in shared memory; best of 3 launches), and 64 planted
+    LPs with n ~ U(2000, 5000).  --fixed-iters N instead runs one launch of N iterations
+    of the small LP (team --team-one, resident slices), for profiler captures."""
+    import torch
+    import lpgen
+    import paper_2312_14832_b300 as pk
+    torch.cuda.set_device(0)
+    lp = lpgen.planted_small(0)
+    if args.fixed_iters > 0:
+        with pk.BatchSolver.from_lps([lp]) as b:
+            r = b.solve(tol=0.0, max_iter=args.fixed_iters, want_points=False, cluster_ctas=args.team_one,
+                        resident=2)[0]
+        print(json.dumps({"impl": "ours-teams-fixed", "iters": r["iters"], "device_ms": r["device_ms"],
+                          "team": args.team_one}))
+        return
+    out = {"metric": METRIC, "unit": "ms to 1e-4 (small planted LP)", "n_gpus": 1, "higher_is_better": False,
+           "data": "synthetic", "impl": "ours-teams", "dtype": "f64",
+           "config": {"workload": "small planted LP (m1=200, m2=300, n=1000, nnz=5000), one LP per launch; "
+                                  "64 planted LPs n~U(2000,5000)"}}
+    small = {}
+    with pk.BatchSolver.from_lps([lp]) as b:
+        for team in (1, 2, 4, 8, 16, 0):
+            for res in (1, 2):
+                b.solve(tol=1e-4, want_points=False, cluster_ctas=team, resident=res)
+                row = {}
+                for tol in (1e-4, 1e-8):
+                    best = None
+                    for _ in range(3):
+                        r = b.solve(tol=tol, want_points=False, cluster_ctas=team, resident=res)[0]
+                        best = r["device_ms"] if best is None else min(best, r["device_ms"])
+                    row[f"{tol:.0e}"] = {"ms": best, "iters": r["iters"], "us_per_iter": 1e3 * best / r["iters"]}
+                inf = b.info()
+                row["team"], row["resident"] = inf["batch_team"], inf["batch_resident"]
+                small[f"team={team} resident={res}"] = row
+    out["small"] = small
+    lps = lpgen.batch_planted(64, seed=11, n_lo=2000, n_hi=5000)
+    med = {}
+    with pk.BatchSolver.from_lps(lps) as b:
+        for team in (1, 2, 4, 8, 0):
+            r = b.solve(tol=1e-4, want_points=False, cluster_ctas=team)
+            med[f"team={team}"] = {"ms": r[0]["device_ms"], "team": b.info()["batch_team"],
+                                   "iters_max": max(x["iters"] for x in r)}
+    out["medium64"] = med
+    out["value"] = min(v["1e-04"]["ms"] for v in small.values())
+    print(json.dumps(out))
+
+
 def bench_warmstart(args):
     """Learned warm start on a transportation family (lpgen.transport_family(S, D), seed 0):
     solutions of args.ws_train instances (seeds 1..) from the batched solver train the
@@ -429,7 +479,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large",
-                    choices=["large", "medium", "small", "batched", "mcf", "warmstart", "pagerank"])
+                    choices=["large", "medium", "small", "batched", "mcf", "warmstart", "pagerank", "teams"])
     ap.add_argument("--ttt-budget", type=float, default=0.0,
                     help="seconds for a cold time-to-1e-4 solve of the bench workload (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -439,6 +489,8 @@ def main():
     ap.add_argument("--batch-scaling", type=int, default=0)
     ap.add_argument("--seq-sample", type=int, default=32)
     ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-1e-4 solve (mcf)")
+    ap.add_argument("--fixed-iters", type=int, default=0, help="teams: one launch of this many iterations")
+    ap.add_argument("--team-one", type=int, default=1, help="teams: CTAs per LP for --fixed-iters")
     ap.add_argument("--pr-nodes", type=int, default=1_000_000)
     ap.add_argument("--pr-budget", type=float, default=60.0, help="seconds per time-to-1e-6 solve (pagerank)")
     ap.add_argument("--ws-train", type=int, default=50000)
@@ -458,6 +510,9 @@ def main():
         return
     if args.workload == "pagerank":
         bench_pagerank(args)
+        return
+    if args.workload == "teams":
+        bench_teams(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
