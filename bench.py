@@ -483,6 +483,9 @@ def main():
     ap.add_argument("--ttt-budget", type=float, default=0.0,
                     help="seconds for a cold time-to-1e-4 solve of the bench workload (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--step-rule", type=int, default=0, choices=[0, 1],
+                    help="timed solve: 0 constant step (Section 2), 1 adaptive rule (units: attempts)")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the small-LP time-to-tolerance section")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="LPs in the batched workload")
     ap.add_argument("--batch-max-iter", type=int, default=200000)
@@ -551,7 +554,7 @@ def main():
     s = pk.Solver.from_lp(lp, scaling=1, stream=stream.cuda_stream)
     info = s.info()
     iters = args.steps * CHECK_EVERY
-    s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False)
+    s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False, step_rule=args.step_rule)
 
     def barrier():
         if dist is not None:
@@ -562,7 +565,7 @@ def main():
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    r = s.solve(tol=0.0, max_iter=iters, want_point=False)
+    r = s.solve(tol=0.0, max_iter=iters, want_point=False, step_rule=args.step_rule)
     e1.record(stream)
     barrier()
     clocks = clk.stop()
@@ -595,14 +598,16 @@ def main():
 
     # time to tolerance: on the small planted LP (GPU and CPU oracle, 1e-4 and 1e-8), and
     # optionally on the bench workload itself (cold start, with a time budget)
-    ttt = {"small_planted": time_to_tol_small(pk)}
+    ttt = {} if args.no_ttt else {"small_planted": time_to_tol_small(pk)}
     if args.ttt_budget > 0:
-        rt = s.solve(tol=1e-4, time_limit_s=args.ttt_budget, want_point=False)
-        ttt["workload_1e-4"] = {
-            "status": ["optimal", "iter_limit", "time_limit", "numerical"][rt["status"]],
-            "iters": rt["iters"], "restarts": rt["restarts"], "device_s": rt["device_ms"] * 1e-3,
-            "wall_s": rt["solve_s"], "rel_primal": rt["rel_primal"], "rel_dual": rt["rel_dual"],
-            "rel_gap": rt["rel_gap"], "primal_obj": rt["primal_obj"], "obj_star": lp.get("obj_star")}
+        for name, rule in (("workload_1e-4", 0), ("workload_1e-4_adaptive", 1)):
+            rt = s.solve(tol=1e-4, time_limit_s=args.ttt_budget, want_point=False, step_rule=rule)
+            ttt[name] = {
+                "status": ["optimal", "iter_limit", "time_limit", "numerical"][rt["status"]],
+                "iters": rt["iters"], "accepted": rt["accepted"], "restarts": rt["restarts"],
+                "device_s": rt["device_ms"] * 1e-3, "wall_s": rt["solve_s"], "rel_primal": rt["rel_primal"],
+                "rel_dual": rt["rel_dual"], "rel_gap": rt["rel_gap"], "primal_obj": rt["primal_obj"],
+                "obj_star": lp.get("obj_star")}
     s.close()
 
     # end to end through the public API with host buffers: setup (H2D, layout), solve, D2H

@@ -34,6 +34,7 @@ struct DevState {
   double wsum, pw;
   long long accepted;
   int rejects, accept;
+  double p3, p6;   // (s+1)^-0.3 and (s+1)^-0.6 for the next acceptance decision
 };
 
 struct DevParams {
@@ -372,19 +373,30 @@ struct EpiDualA {
   }
 };
 
-// Acceptance test and next step size of the adaptive rule, after one attempt:
-//   eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy'K dx|)   (+inf when 0),
-//   accept when eta <= eta_max (or after 64 rejections in a row),
-//   next eta = min((1 - (s+1)^-0.3) eta_max, (1 + (s+1)^-0.6) eta), s = accepted + 1.
-// The partials are added in a fixed order (thread-strided, warps in order).
-__global__ void __launch_bounds__(1024) k_step_decide(const double* __restrict__ px, int ntx,
-                                                      const double* __restrict__ py, int nty, DevState* st) {
+// Partial sums of the attempt's per-task partials: block b < kStepParts adds a fixed
+// contiguous segment of px (||dx||^2) and of py (||dy||^2, dy'K dx pairs) into
+// out[3 b .. 3 b + 2]; the extra block kStepParts computes the two powers of the
+// step-size update meanwhile (they depend only on the count of kept steps).
+constexpr int kStepParts = 128;
+__global__ void __launch_bounds__(256) k_step_partial(const double* __restrict__ px, int ntx,
+                                                      const double* __restrict__ py, int nty, double* __restrict__ out,
+                                                      DevState* st) {
   if (st->done) return;
-  __shared__ double red[3][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (blockIdx.x == kStepParts) {
+    if (threadIdx.x == 0) {
+      const double sidx = (double)(st->accepted + 2);
+      st->p3 = pow(sidx, -0.3);
+      st->p6 = pow(sidx, -0.6);
+    }
+    return;
+  }
+  __shared__ double red[3][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int cx = (ntx + kStepParts - 1) / kStepParts, cy = (nty + kStepParts - 1) / kStepParts;
+  const int x0 = blockIdx.x * cx, x1 = min(ntx, x0 + cx), y0 = blockIdx.x * cy, y1 = min(nty, y0 + cy);
   double a = 0.0, b = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < ntx; i += blockDim.x) a += px[i];
-  for (int i = threadIdx.x; i < nty; i += blockDim.x) {
+  for (int i = x0 + (int)threadIdx.x; i < x1; i += blockDim.x) a += px[i];
+  for (int i = y0 + (int)threadIdx.x; i < y1; i += blockDim.x) {
     b += py[2 * i];
     c += py[2 * i + 1];
   }
@@ -397,19 +409,34 @@ __global__ void __launch_bounds__(1024) k_step_decide(const double* __restrict__
     red[2][wid] = c;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
-  for (int w = 0; w < nw; ++w) {
-    dx2 += red[0][w];
-    dy2 += red[1][w];
-    inter += red[2][w];
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    out[3 * blockIdx.x + threadIdx.x] = t;
   }
+}
+
+// Acceptance test and next step size of the adaptive rule, after one attempt (one warp,
+// the kStepParts block sums added in a fixed order):
+//   eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy'K dx|)   (+inf when 0),
+//   accept when eta <= eta_max (or after 64 rejections in a row),
+//   next eta = min((1 - (s+1)^-0.3) eta_max, (1 + (s+1)^-0.6) eta), s = accepted + 1.
+__global__ void __launch_bounds__(32) k_step_decide(const double* __restrict__ parts, DevState* st) {
+  if (st->done) return;
+  const int lane = threadIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int p = lane; p < kStepParts; p += 32) {
+    a += parts[3 * p];
+    b += parts[3 * p + 1];
+    c += parts[3 * p + 2];
+  }
+  const double dx2 = warp_sum(a), dy2 = warp_sum(b), inter = warp_sum(c);
+  if (lane != 0) return;
   st->wsum += st->pw;   // the pending weight went into the sums in this attempt
   const double eta = st->eta, w = st->omega;
   const double emax = inter == 0.0 ? __longlong_as_double(0x7FF0000000000000LL)
                                    : (w * dx2 + dy2 / w) / (2.0 * fabs(inter));
-  const double sidx = (double)(st->accepted + 2);
-  const double e1 = (1.0 - pow(sidx, -0.3)) * emax, e2 = (1.0 + pow(sidx, -0.6)) * eta;
+  const double e1 = (1.0 - st->p3) * emax, e2 = (1.0 + st->p6) * eta;
   const double enext = e1 < e2 ? e1 : e2;
   const bool acc = eta <= emax || st->rejects >= 64;
   st->accept = acc ? 1 : 0;

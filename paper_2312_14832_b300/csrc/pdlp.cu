@@ -135,7 +135,7 @@ struct pdlp_ctx {
   int gm_full_len = -1, gm_rem_len = -1;
   int64_t fp32_iters = 0;   // iterations of the last solve run in FP32
   // adaptive step rule (params.step_rule = 1): backups of the point, per-task partials
-  double *xb = nullptr, *yb = nullptr, *kxb = nullptr, *part_x = nullptr, *part_y = nullptr;
+  double *xb = nullptr, *yb = nullptr, *kxb = nullptr, *part_x = nullptr, *part_y = nullptr, *part_s = nullptr;
   double eta_adapt0 = 1.0;   // 1 / max |K_ij| of the scaled K
   bool power_done = false;   // the power-iteration step size has been computed
   cudaGraphExec_t ga_full = nullptr, ga_rem = nullptr;
@@ -280,15 +280,17 @@ static void enqueue_iteration(pdlp_ctx* h, const DevState* st) {
   launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, st);
 }
 
-// One attempt of the adaptive step rule (launch count: 4).
+// One attempt of the adaptive step rule (launch count: 5).
 static void enqueue_attempt(pdlp_ctx* h, DevState* st) {
   launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimalA{h->x, h->xb, h->sx, h->c, h->l, h->u, h->part_x, 0.0, 0.0, 0.0}, st);
   launch_rows<OpSpmv>(h, h->K, h->x,
                       EpiDualA{h->y, h->yb, h->sy, h->kxp, h->kxb, h->q, h->part_y, (int)h->m1_int, 0.0, 0.0, 0.0, 0.0},
                       st);
-  k_step_decide<<<1, 1024, 0, h->s>>>(h->part_x, h->Kt.ntasks, h->part_y, h->K.ntasks, st);
-  k_step_restore<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x, h->xb, h->npad, h->y, h->yb, h->kxp,
-                                                                         h->kxb, h->mpad, st);
+  k_step_partial<<<kStepParts + 1, 256, 0, h->s>>>(h->part_x, h->Kt.ntasks, h->part_y, h->K.ntasks, h->part_s, st);
+  k_step_decide<<<1, 32, 0, h->s>>>(h->part_s, st);
+  // a kept step (most attempts) makes this a no-op, so it gets one block per SM
+  k_step_restore<<<std::min(grid_for(std::max(h->npad, h->mpad)), 148), 256, 0, h->s>>>(
+      h->x, h->xb, h->npad, h->y, h->yb, h->kxp, h->kxb, h->mpad, st);
 }
 
 static void enqueue_iteration32(pdlp_ctx* h, const DevState* st) {
@@ -970,6 +972,7 @@ static void ensure_adaptive_buffers(pdlp_ctx* h) {
   h->kxb = dalloc<double>(h, h->mpad);
   h->part_x = dalloc<double>(h, std::max<int64_t>(1, h->Kt.ntasks));
   h->part_y = dalloc<double>(h, 2 * std::max<int64_t>(1, h->K.ntasks));
+  h->part_s = dalloc<double>(h, 3 * kStepParts);
 }
 
 static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0, double omega0,
@@ -1076,7 +1079,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
                                        : (fullint ? h->g_full : h->g_rem);
         const int len = fullint ? L : rem;
         CK(cudaGraphLaunch(g, h->s));
-        launches += adaptive ? 4 * len + 9 : 2 * len + (phase32 ? 12 : 8);
+        launches += adaptive ? 5 * len + 9 : 2 * len + (phase32 ? 12 : 8);
         if (phase32) fp32_intervals.emplace_back(issued_k, len);
         issued_k += len;
         const int slot = (int)(issued % kRing);
