@@ -116,6 +116,11 @@ typedef struct {
                               steps' eta; iteration counts (max_iter, check_every, iters)
                               count attempts.  Not with PDLP_MIXED; not for batches.       */
   int32_t reserved1;       /* must be 0                                                     */
+  int64_t batch_tail_iters; /* pdlp_batch_solve: > 0 runs the batch in two stages: every LP
+                              stops (resumably, at a check) after this many iterations; the
+                              LPs that did not finish then continue in a second launch with
+                              teams sized for their number (cluster_ctas 0).  The result is
+                              the uninterrupted solve's up to summation order.  0 = one launch */
 } pdlp_params;
 
 typedef struct {
@@ -164,7 +169,8 @@ typedef struct {
   int32_t batch_team;          /* batch handles: CTAs per LP of the last pdlp_batch_solve    */
   int32_t batch_resident;      /* batch handles: 1 if that launch ran from shared memory      */
   int32_t wide_rows_K;         /* rows of K stored spread over a chunk's lanes (dense rows)   */
-  int32_t reserved;
+  int32_t batch_resumed;       /* batch handles: LPs continued in the second stage of the last
+                                  pdlp_batch_solve (batch_tail_iters > 0)                     */
 } pdlp_info;
 
 /* Fills p with the defaults listed above. */

@@ -21,7 +21,7 @@ class Params(C.Structure):
                 ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("tile_chunks", C.c_int32),
                 ("spmv_batch", C.c_int32), ("precision", C.c_int32),
                 ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32),
-                ("step_rule", C.c_int32), ("reserved1", C.c_int32)]
+                ("step_rule", C.c_int32), ("reserved1", C.c_int32), ("batch_tail_iters", C.c_int64)]
 
 
 class Result(C.Structure):
@@ -50,7 +50,7 @@ class Info(C.Structure):
                 ("algorithmic_bytes_per_iter", C.c_double), ("stored_bytes_per_iter", C.c_double),
                 ("eta", C.c_double), ("omega0", C.c_double), ("norm_K", C.c_double),
                 ("batch_team", C.c_int32), ("batch_resident", C.c_int32),
-                ("wide_rows_K", C.c_int32), ("reserved", C.c_int32)]
+                ("wide_rows_K", C.c_int32), ("batch_resumed", C.c_int32)]
 
 
 # every function declared in include/pdlp.h: name -> (restype, argtypes)

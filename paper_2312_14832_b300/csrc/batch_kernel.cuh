@@ -56,6 +56,9 @@ struct BatchArgs {
   double step_scale, eta_fixed, omega_fixed;
   int xs_off, ys_off, red_off;   // offsets (doubles) of x, y and the reduction area in shared memory
   int part_off;                  // team partial sums (kPartBuf doubles)
+  long long slice_iters;         // > 0: an LP stops (resumably) at the first check after this many
+                                 // iterations in this launch
+  int resume;                    // 1: every LP of the queue continues from its suspended state
 };
 
 constexpr int kMaxTeam = 16;                         // CTAs per LP (non-portable cluster size)
@@ -416,6 +419,13 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       uS[j] = A.u[gj];
     }
     for (int i = tid; i < nro; i += nt) qS[i] = A.q[D.r0 + ir0 + i];
+    if (A.resume) {
+      for (int j = tid; j < nco; j += nt) sxS[j] = A.sx[D.c0 + jc0 + j];
+      for (int i = tid; i < nro; i += nt) {
+        syS[i] = A.sy[D.r0 + ir0 + i];
+        kxS[i] = A.kxp[D.r0 + ir0 + i];
+      }
+    }
     kpS = kp;
     kvS = kv;
     kgS = kg;
@@ -454,9 +464,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     }
   };
 
-  // ---- step size: power iteration on K'K from v0 = 1/sqrt(n)
+  // ---- step size: power iteration on K'K from v0 = 1/sqrt(n) (a resumed LP keeps its own)
   double eta = A.eta_fixed;
-  if (!(eta > 0.0)) {
+  if (!(eta > 0.0) && !A.resume) {
     const double v0 = 1.0 / sqrt((double)n);
     for (int j = tid; j < D.npad; j += nt) xs[j] = j < n ? v0 : 0.0;
     __syncthreads();
@@ -509,55 +519,68 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   P.cnorm = scal[1];
   P.qnorm = scal[2];
 
-  // ---- initial point (the warm start or 0, projected onto X and Y) and anchor; every
-  // CTA fills its own replicas, the owners the per-entry vectors
-  for (int j = tid; j < D.npad; j += nt) {
-    const int64_t gj = D.c0 + j;
-    const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
-    xs[j] = x0;
-    if (j >= jc0 && j < jc1) {
-      A.xa[gj] = x0;
-      A.sx[gj] = 0.0;
-      sxv[j - jofs] = 0.0;
+  if (A.resume) {
+    // ---- continue a suspended LP: its state, its current point (kept in xout / yout),
+    // and the running sums, anchor and K x that stayed in global memory
+    for (int j = tid; j < D.npad; j += nt) xs[j] = A.xout[D.c0 + j];
+    for (int i = tid; i < D.mpad; i += nt) ys[i] = A.yout[D.r0 + i];
+    if (tid == 0) {
+      S = A.st[b];
+      S.suspended = 0;
     }
-  }
-  for (int i = tid; i < D.mpad; i += nt) {
-    const int64_t gi = D.r0 + i;
-    double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
-    if (i >= D.m1) y0 = max0(y0);
-    ys[i] = y0;
-    if (i >= ir0 && i < ir1) {
-      A.ya[gi] = y0;
-      A.sy[gi] = 0.0;
-      syv[i - iofs] = 0.0;
+    __syncthreads();
+  } else {
+    // ---- initial point (the warm start or 0, projected onto X and Y) and anchor; every
+    // CTA fills its own replicas, the owners the per-entry vectors
+    for (int j = tid; j < D.npad; j += nt) {
+      const int64_t gj = D.c0 + j;
+      const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
+      xs[j] = x0;
+      if (j >= jc0 && j < jc1) {
+        A.xa[gj] = x0;
+        A.sx[gj] = 0.0;
+        sxv[j - jofs] = 0.0;
+      }
     }
+    for (int i = tid; i < D.mpad; i += nt) {
+      const int64_t gi = D.r0 + i;
+      double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
+      if (i >= D.m1) y0 = max0(y0);
+      ys[i] = y0;
+      if (i >= ir0 && i < ir1) {
+        A.ya[gi] = y0;
+        A.sy[gi] = 0.0;
+        syv[i - iofs] = 0.0;
+      }
+    }
+    __syncthreads();
+    Kmul(true, nullptr, [&](int i, double s) {
+      A.kxp[D.r0 + i] = s;
+      kxv[i - iofs] = s;
+    });
+    Tmul(true, nullptr,
+                                [&](int j, double s) { A.g[D.c0 + j] = s; });
+    __syncthreads();
+    if (tid == 0) {
+      memset(&S, 0, sizeof(S));
+      S.eta = eta;
+      S.omega = omega;
+      S.tau = eta / omega;
+      S.sigma = eta * omega;
+    }
+    __syncthreads();
+    batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T);
+    if (tid == 0) {
+      const double gap = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
+      S.kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap, S.omega);
+      S.kkt_prev = __longlong_as_double(0x7FF0000000000000LL);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  Kmul(true, nullptr, [&](int i, double s) {
-    A.kxp[D.r0 + i] = s;
-    kxv[i - iofs] = s;
-  });
-  Tmul(true, nullptr,
-                              [&](int j, double s) { A.g[D.c0 + j] = s; });
-  __syncthreads();
-  if (tid == 0) {
-    memset(&S, 0, sizeof(S));
-    S.eta = eta;
-    S.omega = omega;
-    S.tau = eta / omega;
-    S.sigma = eta * omega;
-  }
-  __syncthreads();
-  batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T);
-  if (tid == 0) {
-    const double gap = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
-    S.kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap, S.omega);
-    S.kkt_prev = __longlong_as_double(0x7FF0000000000000LL);
-  }
-  __syncthreads();
 
   // ---- iterations (Section 2: primal step, dual step with extrapolation) and checks
-  long long k = 0, t = 0;
+  long long k = S.k, t = S.t;
+  const long long k_start = k;
   int until_check = A.check_every;
   for (;;) {
     const bool at_limit = k >= A.max_iter;
@@ -618,6 +641,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     }
     __syncthreads();
     if (S.done) break;
+    const bool suspend = A.slice_iters > 0 && k - k_start >= A.slice_iters;
     if (S.restart_flag) {
       const bool avg = S.cand_avg;
       if (avg) {
@@ -638,6 +662,29 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       t = 0;
       __syncthreads();
     }
+    if (suspend) break;
+  }
+  if (!S.done) {
+    // ---- suspended by the iteration slice: the current point goes to xout / yout, the
+    // running sums (written at this check), anchor and K x stay in global memory
+    if constexpr (kRes) {
+      // a restart at this check cleared the shared-memory sums and may have replaced K x
+      for (int j = jc0 + tid; j < jc1; j += nt) A.sx[D.c0 + j] = sxv[j - jofs];
+      for (int i = ir0 + tid; i < ir1; i += nt) {
+        A.sy[D.r0 + i] = syv[i - iofs];
+        A.kxp[D.r0 + i] = kxv[i - iofs];
+      }
+    }
+    for (int j = jc0 + tid; j < jc1; j += nt) A.xout[D.c0 + j] = xs[j];
+    for (int i = ir0 + tid; i < ir1; i += nt) A.yout[D.r0 + i] = ys[i];
+    if (tid == 0 && T.rank == 0) {
+      S.k = k;
+      S.t = t;
+      S.suspended = 1;
+      A.st[b] = S;
+    }
+    T.sync();
+    return;
   }
   // ---- returned point and state (the global sums were written at the last check)
   const bool avg = S.which == 1 && t > 0;

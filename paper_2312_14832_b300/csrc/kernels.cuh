@@ -35,6 +35,8 @@ struct DevState {
   long long accepted;
   int rejects, accept;
   double p3, p6;   // (s+1)^-0.3 and (s+1)^-0.6 for the next acceptance decision
+  int suspended;   // batched solver: stopped at a check by its iteration slice, resumable
+  int pad_s;
 };
 
 struct DevParams {

@@ -123,6 +123,8 @@ struct pdlp_ctx {
   size_t batch_smem = 0;
   int last_team = 0;         // CTAs per LP and resident mode of the last batched launch
   bool last_resident = false;
+  int32_t* order2 = nullptr; // queue of the second stage (LPs stopped by the slice)
+  int64_t last_resumed = 0;  // LPs continued in the second stage of the last solve
   std::vector<int32_t> hk_cptr, ht_cptr;  // host copies of the chunk pointers of K and K'
   int dev_smem_optin = 0;
   int xs_off = 0, ys_off = 0, red_off = 0;
@@ -1372,13 +1374,76 @@ static long long resident_need(const pdlp_ctx* h, int team) {
   return need;
 }
 
-static int batch_team_size(const pdlp_ctx* h, const pdlp_params& sp) {
-  if (sp.cluster_ctas > 0) return sp.cluster_ctas;
+static int batch_team_size(const pdlp_ctx* h, int64_t count, int team_req) {
+  if (team_req > 0) return team_req;
   int team = 1;
-  while (team < kMaxTeam && h->count * (int64_t)(team * 2) <= (int64_t)h->batch_resident &&
+  while (team < kMaxTeam && count * (int64_t)(team * 2) <= (int64_t)h->batch_resident &&
          h->team_npad_max >= (int64_t)(team * 2) * 64)
     team *= 2;
   return team;
+}
+
+// One launch of the persistent batched kernel over A.count LPs (A.order): team size,
+// resident slices and grid chosen for that count.
+static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp, int64_t count, int team_req) {
+  const int team = batch_team_size(h, count, team_req);
+  // resident slices: the largest one of any LP and CTA decides the launch's shared memory
+  const long long res_bytes = resident_need(h, team);
+  const size_t res_smem = h->batch_smem + (size_t)((res_bytes + 7) / 8 * 8);
+  bool resident = false;
+  if (sp.resident != 1 && res_smem <= (size_t)h->dev_smem_optin) {
+    if (sp.resident == 2) {
+      resident = true;
+    } else {
+      // automatic: only while it keeps as many CTAs per SM as the streaming kernel
+      int a = 0, r = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<false, false>, kBatchThreads,
+                                                       h->batch_smem));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_batch_solve<false, true>, kBatchThreads, res_smem));
+      resident = r >= a;
+    }
+  }
+  const size_t smem = resident ? res_smem : h->batch_smem;
+  int grid = 0;
+  if (team == 1) {
+    int per_sm = 0, sms = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, resident ? (const void*)k_batch_solve<false, true> : (const void*)k_batch_solve<false, false>,
+        kBatchThreads, smem));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    if (per_sm < 1) invalid("batched kernel does not fit on an SM");
+    grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)team;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h->s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (team > 1) {
+    cfg.gridDim = dim3((unsigned)team);
+    int nc = 0;
+    CK(cudaOccupancyMaxActiveClusters(
+        &nc, resident ? (const void*)k_batch_solve<true, true> : (const void*)k_batch_solve<true, false>, &cfg));
+    if (nc < 1) invalid("a cluster of this many CTAs does not fit on the GPU");
+    grid = (int)std::min<int64_t>((int64_t)nc, count) * team;
+  }
+  cfg.gridDim = dim3((unsigned)grid);
+  h->last_team = team;
+  h->last_resident = resident;
+  if (team == 1) {
+    if (resident) k_batch_solve<false, true><<<grid, kBatchThreads, smem, h->s>>>(A);
+    else k_batch_solve<false, false><<<grid, kBatchThreads, smem, h->s>>>(A);
+  } else {
+    if (resident) CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, true>, A));
+    else CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, false>, A));
+  }
+  CKL("k_batch_solve");
 }
 
 static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0,
@@ -1387,6 +1452,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   if (sp.cluster_ctas < 0 || sp.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
   if (sp.resident < 0 || sp.resident > 2) invalid("resident must be 0, 1 or 2");
   if (sp.step_rule != 0) invalid("batches use the constant step (step_rule 0)");
+  if (sp.batch_tail_iters < 0) invalid("batch_tail_iters must be >= 0");
   auto t_start = std::chrono::steady_clock::now();
   BatchArgs A;
   A.x0 = nullptr;
@@ -1440,65 +1506,30 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.ys_off = h->ys_off;
   A.red_off = h->red_off;
   A.part_off = h->part_off;
-  const int team = batch_team_size(h, sp);
-  // resident slices: the largest one of any LP and CTA decides the launch's shared memory
-  const long long res_bytes = resident_need(h, team);
-  const size_t res_smem = h->batch_smem + (size_t)((res_bytes + 7) / 8 * 8);
-  bool resident = false;
-  if (sp.resident != 1 && res_smem <= (size_t)h->dev_smem_optin) {
-    if (sp.resident == 2) {
-      resident = true;
-    } else {
-      // automatic: only while it keeps as many CTAs per SM as the streaming kernel
-      int a = 0, r = 0;
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<false, false>, kBatchThreads,
-                                                       h->batch_smem));
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_batch_solve<false, true>, kBatchThreads, res_smem));
-      resident = r >= a;
+  A.slice_iters = sp.batch_tail_iters > 0 ? sp.batch_tail_iters : 0;
+  A.resume = 0;
+  h->last_resumed = 0;
+  CK(cudaEventRecord(h->ev_t0, h->s));
+  launch_batch(h, A, sp, h->count, sp.cluster_ctas);
+  if (A.slice_iters > 0) {
+    // second stage: the LPs stopped by the slice continue, with teams sized for their number
+    CK(cudaMemcpyAsync(h->hstate.data(), h->bstate, sizeof(DevState) * h->count, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    std::vector<int32_t> rest;
+    for (int64_t b = 0; b < h->count; ++b)
+      if (h->hstate[(size_t)b].suspended) rest.push_back((int32_t)b);
+    h->last_resumed = (int64_t)rest.size();
+    if (!rest.empty()) {
+      if (!h->order2) h->order2 = dalloc<int32_t>(h, (size_t)h->count);
+      CK(cudaMemcpyAsync(h->order2, rest.data(), sizeof(int32_t) * rest.size(), cudaMemcpyHostToDevice, h->s));
+      BatchArgs A2 = A;
+      A2.order = h->order2;
+      A2.count = (int32_t)rest.size();
+      A2.resume = 1;
+      A2.slice_iters = 0;
+      launch_batch(h, A2, sp, (int64_t)rest.size(), 0);
     }
   }
-  const size_t smem = resident ? res_smem : h->batch_smem;
-  int grid = 0;
-  if (team == 1) {
-    int per_sm = 0, sms = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, resident ? (const void*)k_batch_solve<false, true> : (const void*)k_batch_solve<false, false>,
-        kBatchThreads, smem));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
-    if (per_sm < 1) invalid("batched kernel does not fit on an SM");
-    grid = (int)std::min<int64_t>((int64_t)per_sm * sms, h->count);
-  }
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)team;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kBatchThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = h->s;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  if (team > 1) {
-    cfg.gridDim = dim3((unsigned)team);
-    int nc = 0;
-    CK(cudaOccupancyMaxActiveClusters(
-        &nc, resident ? (const void*)k_batch_solve<true, true> : (const void*)k_batch_solve<true, false>, &cfg));
-    if (nc < 1) invalid("a cluster of this many CTAs does not fit on the GPU");
-    grid = (int)std::min<int64_t>((int64_t)nc, h->count) * team;
-  }
-  cfg.gridDim = dim3((unsigned)grid);
-  h->last_team = team;
-  h->last_resident = resident;
-  CK(cudaEventRecord(h->ev_t0, h->s));
-  if (team == 1) {
-    if (resident) k_batch_solve<false, true><<<grid, kBatchThreads, smem, h->s>>>(A);
-    else k_batch_solve<false, false><<<grid, kBatchThreads, smem, h->s>>>(A);
-  } else {
-    if (resident) CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, true>, A));
-    else CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, false>, A));
-  }
-  CKL("k_batch_solve");
   CK(cudaEventRecord(h->ev_t1, h->s));
   CK(cudaStreamSynchronize(h->s));
   float dev_ms = 0.f;
@@ -1717,6 +1748,7 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->batch_team = h->last_team;
     info->batch_resident = h->last_resident ? 1 : 0;
     info->wide_rows_K = h->K.nwide;
+    info->batch_resumed = (int32_t)h->last_resumed;
     return PDLP_OK;
   });
 }

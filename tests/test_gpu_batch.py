@@ -197,3 +197,35 @@ def test_cluster_warm_start_and_rerun(pk):
                 ref = oracle.solve(lp, tol=0.0, max_iter=300, x0=x0[i], y0=y0[i], omega0=float(w0[i]))
                 close_rel(r["x"], ref["x"], 1e-10)
                 close_rel(r["y"], ref["y"], 1e-10)
+
+
+@pytest.mark.parametrize("scaling,resident", [(0, 1), (1, 0)])
+def test_two_stage_tail_matches_oracle(pk, scaling, resident):
+    """batch_tail_iters: every LP stops at the first check after 192 iterations and the
+    unfinished ones continue in a second launch on teams; the point after 1000
+    iterations is the oracle's (the continuation changes only summation order)."""
+    lps = fixed_iteration_batch()
+    with pk.BatchSolver.from_lps(lps, scaling=scaling) as b:
+        res = b.solve(tol=0.0, max_iter=1000, batch_tail_iters=192, resident=resident)
+        info = b.info()
+    assert info["batch_resumed"] == len(lps)
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=0.0, max_iter=1000, scaling=scaling)
+        assert r["iters"] == 1000 and r["status"] == pk.ITER_LIMIT
+        assert r["restarts"] == ref["restarts"] and r["which"] == ref["which"]
+        assert abs(r["omega"] - ref["omega"]) <= 1e-6 * ref["omega"]
+        close_rel(r["x"], ref["x"], 1e-10)
+        close_rel(r["y"], ref["y"], 1e-10)
+
+
+def test_two_stage_tail_at_tolerance(pk):
+    lps = mixed_batch()
+    with pk.BatchSolver.from_lps(lps) as b:
+        res = b.solve(tol=1e-8, max_iter=500_000, batch_tail_iters=256)
+        resumed = b.info()["batch_resumed"]
+    assert resumed > 0
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=1e-8, max_iter=500_000)
+        assert r["status"] == ref["status"] == pk.OPTIMAL
+        assert r["iters"] == ref["iters"]
+        assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
