@@ -231,11 +231,45 @@ def bench_batched(args):
     b.solve(tol=1e-4, max_iter=64, want_points=False)      # warm-up launch
     clk = Clocks(0)
     res = b.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False)
+    one_launch_s = res[0]["device_ms"] * 1e-3
+    two_stage = None
+    if args.batch_tail > 0:
+        # the same solve in two stages: LPs past batch_tail iterations continue on teams
+        res2 = b.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False, batch_tail_iters=args.batch_tail)
+        inf = b.info()
+        same = all(r1["iters"] == r2["iters"] for r1, r2 in zip(res, res2))
+        two_stage = {"device_s": res2[0]["device_ms"] * 1e-3, "tail_iters": args.batch_tail,
+                     "resumed": inf["batch_resumed"], "second_stage_team": inf["batch_team"],
+                     "same_iteration_counts": same,
+                     "max_rel_obj_diff": max(abs(r1["primal_obj"] - r2["primal_obj"]) / (1 + abs(r1["primal_obj"]))
+                                             for r1, r2 in zip(res, res2))}
+        if res2[0]["device_ms"] < res[0]["device_ms"]:
+            res = res2
+    mixed = None
+    if args.batch_mixed:
+        # FP32 iterations with FP64 checks; unfinished LPs continue in FP64
+        bm = pk.BatchSolver.from_lps(lps, scaling=args.batch_scaling, precision=pk.MIXED)
+        bm.solve(tol=1e-4, max_iter=64, want_points=False)
+        rm = bm.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False)
+        fp32 = np.array([r["fp32_iters"] for r in rm])
+        itm = np.array([r["iters"] for r in rm])
+        mixed = {"device_s": rm[0]["device_ms"] * 1e-3, "lps_per_s": args.count / (rm[0]["device_ms"] * 1e-3),
+                 "optimal": int(sum(r["status"] == 0 for r in rm)), "iters_mean": float(itm.mean()),
+                 "fp32_iter_share": float(fp32.sum() / max(itm.sum(), 1)),
+                 "continued_in_fp64": bm.info()["batch_resumed"],
+                 "max_rel_obj_diff_vs_fp64": max(abs(a["primal_obj"] - c["primal_obj"]) / (1 + abs(a["primal_obj"]))
+                                                 for a, c in zip(res, rm)),
+                 "max_rel_error": max(max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) for r in rm)}
+        bm.close()
     clocks = clk.stop()
     dev_s = res[0]["device_ms"] * 1e-3
     iters = np.array([r["iters"] for r in res])
     status = np.array([r["status"] for r in res])
     fma = float(np.sum(2.0 * np.array(nnz) * iters))
+    slow = int(np.argmax(iters))
+    tail = {"iters_p50": float(np.percentile(iters, 50)), "iters_p99": float(np.percentile(iters, 99)),
+            "slowest_lp": {"index": slow, "iters": int(iters[slow]), "n": int(lps[slow]["n"]),
+                           "m": int(lps[slow]["m"]), "nnz": nnz[slow]}}
     b.close()
     # sequential single-LP solves on a sample
     stride = max(1, args.count // args.seq_sample)
@@ -259,6 +293,7 @@ def bench_batched(args):
            "sequential": {"sample": len(sample), "sample_s": seq_s, "sample_iters": seq_it,
                           "estimated_total_s": seq_total, "lps_per_s": args.count / seq_total},
            "speedup_vs_sequential": seq_total / dev_s, "setup_s": setup_s, "generate_s": gen_s,
+           "one_launch_device_s": one_launch_s, "two_stage": two_stage, "tail": tail, "mixed": mixed,
            "clocks": clocks}
     print(json.dumps(out))
 
@@ -490,6 +525,9 @@ def main():
     ap.add_argument("--count", type=int, default=4096, help="LPs in the batched workload")
     ap.add_argument("--batch-max-iter", type=int, default=200000)
     ap.add_argument("--batch-scaling", type=int, default=0)
+    ap.add_argument("--batch-mixed", type=int, default=1, help="batched: also time the FP32 variant")
+    ap.add_argument("--batch-tail", type=int, default=8192,
+                    help="batched: also time the two-stage solve (LPs past this many iterations continue on teams)")
     ap.add_argument("--seq-sample", type=int, default=32)
     ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-1e-4 solve (mcf)")
     ap.add_argument("--fixed-iters", type=int, default=0, help="teams: one launch of this many iterations")

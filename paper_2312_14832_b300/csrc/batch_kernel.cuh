@@ -59,6 +59,10 @@ struct BatchArgs {
   long long slice_iters;         // > 0: an LP stops (resumably) at the first check after this many
                                  // iterations in this launch
   int resume;                    // 1: every LP of the queue continues from its suspended state
+  // FP32 iterations (k_batch_solve32): FP32 values, problem vectors, interval sums and K x
+  const float *k_val32, *t_val32, *c32, *l32, *u32, *q32;
+  float *sx32, *sy32, *kxp32;
+  double switch_tol;             // FP32 until the FP64-measured error is <= this (or stalls)
 };
 
 constexpr int kMaxTeam = 16;                         // CTAs per LP (non-portable cluster size)
@@ -87,7 +91,8 @@ struct Team {
     else return p;
   }
   // a[i] = v in the replica of every CTA of the team
-  __device__ __forceinline__ void put(double* a, int i, double v) const {
+  template <class V>
+  __device__ __forceinline__ void put(V* a, int i, V v) const {
     if constexpr (kCl) {
       for (int k = 0; k < size; ++k) {
         int r = rank + k;
@@ -124,7 +129,10 @@ enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
 // c0+w+nw, ...  Each lane sums its row, gathering src[col - base], then calls
 // epi(local_row, sum), local_row counted from chunk cbase (the LP's first chunk).
 // Loads of kBB slots are issued together.
-constexpr int kBB = 4;
+#ifndef PDLP_BATCH_LOADS
+#define PDLP_BATCH_LOADS 4
+#endif
+constexpr int kBB = PDLP_BATCH_LOADS;
 template <int SRC, bool kMatS, class F>
 __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
                                            const double* __restrict__ val, int c0, int c1, int cbase,
@@ -260,10 +268,12 @@ __device__ __forceinline__ double team_norm(const double* v, int j0, int j1, dou
 template <bool kCl>
 __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, bool avg_is_cur, double it,
                                           double* red, double* tot, int ir0, int ir1, int jc0, int jc1,
-                                          double* part, int& flip, const Team<kCl>& T) {
+                                          double* part, int& flip, const Team<kCl>& T,
+                                          bool cur_global = false) {
   extern __shared__ double bsm[];
-  const double* xs = bsm + A.xs_off;
-  const double* ys = bsm + A.ys_off;
+  // the current point: the FP64 replicas, or (FP32 iterations) its FP64 copy in xout / yout
+  const double* xs = cur_global ? A.xout + D.c0 : bsm + A.xs_off;
+  const double* ys = cur_global ? A.yout + D.r0 : bsm + A.ys_off;
   {
     double acc[8];
 #pragma unroll
@@ -693,6 +703,322 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   for (int i = ir0 + tid; i < ir1; i += nt) A.yout[D.r0 + i] = avg ? A.sy[D.r0 + i] * it : ys[i];
   if (tid == 0 && T.rank == 0) A.st[b] = S;
   T.sync();   // no CTA writes the next LP into a replica (or slice) that is still being read
+}
+
+// FP32 rows of chunks [c0, c1) (values A.k_val32 / t_val32 in global memory; gathers
+// from the float replicas src); same order per row as batch_rows.
+template <class F>
+__device__ __forceinline__ void batch_rows32(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
+                                             const float* __restrict__ val, int c0, int c1, int cbase, int64_t base,
+                                             const float* src, F epi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int ch = c0 + wid; ch < c1; ch += nw) {
+    const int s0 = cptr[ch], s1 = cptr[ch + 1];
+    float acc = 0.0f;
+    for (int s = s0; s < s1; s += kBB) {
+      const int nb = min(kBB, s1 - s);
+      float v[kBB], xv[kBB];
+      int ci[kBB];
+#pragma unroll
+      for (int j = 0; j < kBB; ++j)
+        if (j < nb) {
+          v[j] = __ldcs(val + (size_t)(s + j) * 32 + lane);
+          ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
+        }
+#pragma unroll
+      for (int j = 0; j < kBB; ++j) xv[j] = j < nb ? src[ci[j]] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < kBB; ++j)
+        if (j < nb) acc = fmaf(v[j], xv[j], acc);
+    }
+    epi((ch - cbase) * 32 + lane, acc);
+  }
+}
+
+// Mixed precision for a batch (the NEXT-1 split, one LP per team): FP32 iterations on
+// float replicas, values and problem vectors, FP32 running sums over one check interval
+// folded into the FP64 sums at every check; every check in FP64 (FP64 copy of the point
+// in xout / yout, K x recomputed in FP64) with the restart rule of Section 2.  An LP
+// whose FP64-measured error reaches A.switch_tol, or stops improving by 10 % for 16
+// checks, is suspended with its FP64 state and finishes in FP64 (a resumed launch of
+// k_batch_solve).  No resident slices.
+template <bool kCl>
+__device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T) {
+  extern __shared__ double bsm[];
+  double* xs = bsm + A.xs_off;   // FP64 replicas: power iteration only
+  double* ys = bsm + A.ys_off;
+  float* xf = reinterpret_cast<float*>(xs);
+  float* yf = reinterpret_cast<float*>(ys);
+  double* red = bsm + A.red_off;
+  double* part = bsm + A.part_off;
+  __shared__ DevState S;
+  __shared__ double tot[NQ];
+  __shared__ double scal[4];
+  const LpDesc D = A.desc[b];
+  const int n = D.n, m = D.m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int flip = 0;
+  const int kr0 = split_point(A.k_cptr, D.kc0, D.kc1, T.rank, T.size);
+  const int kr1 = split_point(A.k_cptr, D.kc0, D.kc1, T.rank + 1, T.size);
+  const int tr0 = split_point(A.t_cptr, D.tc0, D.tc1, T.rank, T.size);
+  const int tr1 = split_point(A.t_cptr, D.tc0, D.tc1, T.rank + 1, T.size);
+  const int ir0 = (kr0 - D.kc0) * 32, ir1 = (kr1 - D.kc0) * 32;
+  const int jc0 = (tr0 - D.tc0) * 32, jc1 = (tr1 - D.tc0) * 32;
+  const int mo1 = min(ir1, m), no1 = min(jc1, n);
+  double* x64 = A.xout + D.c0;   // FP64 copy of the current point (all columns of the LP)
+  double* y64 = A.yout + D.r0;
+
+  // ---- step size: power iteration on K'K in FP64 (as the FP64 solver)
+  double eta = A.eta_fixed;
+  if (!(eta > 0.0)) {
+    const double v0 = 1.0 / sqrt((double)n);
+    for (int j = tid; j < D.npad; j += nt) xs[j] = j < n ? v0 : 0.0;
+    __syncthreads();
+    for (int it = 0; it < A.power_iters; ++it) {
+      batch_rows<kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A,
+                                   [&](int i, double s) { T.put(ys, i, s); });
+      T.sync();
+      batch_rows<kSrcSmemY, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A,
+                                   [&](int j, double s) { A.g[D.c0 + j] = s; });
+      __syncthreads();
+      const double nw = team_norm(A.g + D.c0, jc0, jc1, red, part, flip, T);
+      if (nw != 0.0)
+        for (int j = jc0 + tid; j < jc1; j += nt) T.put(xs, j, A.g[D.c0 + j] / nw);
+      T.sync();
+    }
+    batch_rows<kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A,
+                                 [&](int i, double s) { T.put(ys, i, s); });
+    T.sync();
+    const double sn = m > 0 ? team_norm(ys, ir0, ir1, red, part, flip, T) : 0.0;
+    eta = sn > 0.0 ? A.step_scale / sn : 1.0;
+  }
+  double omega = A.omega_fixed;
+  {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = jc0 + tid; j < no1; j += nt) {
+      const double cj = A.c[D.c0 + j];
+      const double cu = cj * A.invDc[D.c0 + j];
+      a[0] = fma(cj, cj, a[0]);
+      a[2] = fma(cu, cu, a[2]);
+    }
+    for (int i = ir0 + tid; i < mo1; i += nt) {
+      const double qi = A.q[D.r0 + i];
+      const double qu = qi * A.invDr[D.r0 + i];
+      a[1] = fma(qi, qi, a[1]);
+      a[3] = fma(qu, qu, a[3]);
+    }
+    team_sum<4>(a, red, part, flip, T);
+    if (tid == 0) {
+      const double cn = sqrt(red[0]), qn = sqrt(red[1]);
+      scal[0] = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
+      scal[1] = sqrt(red[2]);
+      scal[2] = sqrt(red[3]);
+    }
+    __syncthreads();
+    if (!(omega > 0.0)) omega = scal[0];
+    if (A.omega0 != nullptr && A.omega0[b] > 0.0) omega = A.omega0[b];
+  }
+  DevParams P = A.P;
+  P.cnorm = scal[1];
+  P.qnorm = scal[2];
+
+  // ---- initial point: FP64 copy (owners) and float replicas (every CTA), anchor, sums
+  for (int j = tid; j < D.npad; j += nt) {
+    const int64_t gj = D.c0 + j;
+    const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
+    xf[j] = (float)x0;
+    if (j >= jc0 && j < jc1) {
+      x64[j] = x0;
+      A.xa[gj] = x0;
+      A.sx[gj] = 0.0;
+      A.sx32[gj] = 0.0f;
+    }
+  }
+  for (int i = tid; i < D.mpad; i += nt) {
+    const int64_t gi = D.r0 + i;
+    double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
+    if (i >= D.m1) y0 = max0(y0);
+    yf[i] = (float)y0;
+    if (i >= ir0 && i < ir1) {
+      y64[i] = y0;
+      A.ya[gi] = y0;
+      A.sy[gi] = 0.0;
+      A.sy32[gi] = 0.0f;
+    }
+  }
+  __threadfence();
+  T.sync();
+  batch_rows<kSrcGlobal, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, x64, A, [&](int i, double s) {
+    A.kxp[D.r0 + i] = s;
+    A.kxp32[D.r0 + i] = (float)s;
+  });
+  batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, y64, A,
+                                [&](int j, double s) { A.g[D.c0 + j] = s; });
+  __syncthreads();
+  if (tid == 0) {
+    memset(&S, 0, sizeof(S));
+    S.eta = eta;
+    S.omega = omega;
+    S.tau = eta / omega;
+    S.sigma = eta * omega;
+  }
+  __syncthreads();
+  batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T, true);
+  if (tid == 0) {
+    const double gap = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
+    S.kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap, S.omega);
+    S.kkt_prev = __longlong_as_double(0x7FF0000000000000LL);
+  }
+  __syncthreads();
+
+  // ---- FP32 iterations, FP64 checks
+  long long k = 0, t = 0;
+  int until_check = A.check_every;
+  double best_err = __longlong_as_double(0x7FF0000000000000LL);
+  int since_best = 0;
+  bool to_fp64 = false;
+  for (;;) {
+    const bool at_limit = k >= A.max_iter;
+    if (!at_limit) {
+      const float tau = (float)S.tau, sigma = (float)S.sigma;
+      batch_rows32(A.t_cptr, A.t_col, A.t_val32, tr0, tr1, D.tc0, D.r0, yf, [&](int j, float gsum) {
+        const int64_t gj = D.c0 + j;
+        float xn = fmaf(-tau, A.c32[gj] - gsum, xf[j]);
+        xn = fminf(fmaxf(xn, A.l32[gj]), A.u32[gj]);
+        T.put(xf, j, xn);
+        A.sx32[gj] = A.sx32[gj] + xn;
+      });
+      T.sync();
+      batch_rows32(A.k_cptr, A.k_col, A.k_val32, kr0, kr1, D.kc0, D.c0, xf, [&](int i, float v) {
+        const int64_t gi = D.r0 + i;
+        float yn = fmaf(sigma, fmaf(-2.0f, v, A.q32[gi] + A.kxp32[gi]), yf[i]);
+        if (i >= D.m1) yn = fmaxf(yn, 0.0f);
+        T.put(yf, i, yn);
+        A.sy32[gi] = A.sy32[gi] + yn;
+        A.kxp32[gi] = v;
+      });
+      T.sync();
+      ++k;
+      ++t;
+      if (--until_check > 0 && k < A.max_iter) continue;
+      until_check = A.check_every;
+    }
+    // ---- FP64 check: fold the interval sums, FP64 copy of the point, FP64 products
+    for (int j = jc0 + tid; j < jc1; j += nt) {
+      const int64_t gj = D.c0 + j;
+      A.sx[gj] += (double)A.sx32[gj];
+      A.sx32[gj] = 0.0f;
+      x64[j] = (double)xf[j];
+    }
+    for (int i = ir0 + tid; i < ir1; i += nt) {
+      const int64_t gi = D.r0 + i;
+      A.sy[gi] += (double)A.sy32[gi];
+      A.sy32[gi] = 0.0f;
+      y64[i] = (double)yf[i];
+    }
+    __threadfence();
+    T.sync();
+    const double it = t > 0 ? 1.0 / (double)t : 0.0;
+    batch_rows<kSrcGlobal, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, x64, A,
+                                  [&](int i, double s) { A.kxp[D.r0 + i] = s; });
+    batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, y64, A,
+                                  [&](int j, double s) { A.g[D.c0 + j] = s; });
+    batch_rows<kSrcGlobal, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, A.sx + D.c0, A,
+                                  [&](int i, double s) { A.kx_a[D.r0 + i] = s * it; });
+    batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, A.sy + D.r0, A,
+                                  [&](int j, double s) { A.g_a[D.c0 + j] = s * it; });
+    __syncthreads();
+    batch_kkt(A, D, t == 0, it, red, tot, ir0, ir1, jc0, jc1, part, flip, T, true);
+    if (tid == 0) {
+      S.k = k;
+      S.t = t;
+      S.inv_t = it;
+      decide_core(tot, &S, P, k >= A.max_iter, nullptr);
+    }
+    __syncthreads();
+    if (S.done) break;
+    // switch to FP64 iterations (the same test on every CTA: S is identical)
+    const double e = S.last_err;
+    if (e < 0.9 * best_err) {
+      best_err = e;
+      since_best = 0;
+    } else {
+      ++since_best;
+    }
+    to_fp64 = e <= A.switch_tol || since_best >= 16;
+    if (S.restart_flag) {
+      const bool avg = S.cand_avg;
+      // every CTA refreshes its float replicas from the new FP64 point before the
+      // owners overwrite the FP64 copy and clear the sums
+      for (int j = tid; j < D.npad; j += nt) xf[j] = (float)(avg ? A.sx[D.c0 + j] * it : x64[j]);
+      for (int i = tid; i < D.mpad; i += nt) yf[i] = (float)(avg ? A.sy[D.r0 + i] * it : y64[i]);
+      T.sync();
+      for (int j = jc0 + tid; j < jc1; j += nt) {
+        const int64_t gj = D.c0 + j;
+        const double v = avg ? A.sx[gj] * it : x64[j];
+        x64[j] = v;
+        A.xa[gj] = v;
+        A.sx[gj] = 0.0;
+      }
+      for (int i = ir0 + tid; i < ir1; i += nt) {
+        const int64_t gi = D.r0 + i;
+        const double v = avg ? A.sy[gi] * it : y64[i];
+        y64[i] = v;
+        A.ya[gi] = v;
+        A.sy[gi] = 0.0;
+        if (avg) A.kxp[gi] = A.kx_a[gi];
+        A.kxp32[gi] = (float)A.kxp[gi];
+      }
+      t = 0;
+      __syncthreads();
+    } else {
+      // K x of the FP32 iterations continues from its FP64 value
+      for (int i = ir0 + tid; i < ir1; i += nt) A.kxp32[D.r0 + i] = (float)A.kxp[D.r0 + i];
+      __syncthreads();
+    }
+    if (to_fp64) break;
+  }
+  if (!S.done) {
+    // ---- to FP64: the point in xout / yout, FP64 sums, anchor and K x are all in place
+    if (tid == 0 && T.rank == 0) {
+      S.k = k;
+      S.t = t;
+      S.k32 = k;
+      S.suspended = 1;
+      A.st[b] = S;
+    }
+    T.sync();
+    return;
+  }
+  const bool avg = S.which == 1 && t > 0;
+  const double it = t > 0 ? 1.0 / (double)t : 0.0;
+  for (int j = jc0 + tid; j < jc1; j += nt) A.xout[D.c0 + j] = avg ? A.sx[D.c0 + j] * it : x64[j];
+  for (int i = ir0 + tid; i < ir1; i += nt) A.yout[D.r0 + i] = avg ? A.sy[D.r0 + i] * it : y64[i];
+  if (tid == 0 && T.rank == 0) {
+    S.k32 = k;
+    A.st[b] = S;
+  }
+  T.sync();
+}
+
+template <bool kCl>
+__global__ void __launch_bounds__(256, 2) k_batch_solve32(BatchArgs A) {
+  __shared__ int lp;
+  Team<kCl> T;
+  T.init();
+  const int teams = (int)gridDim.x / T.size;
+  for (;;) {
+    if (T.rank == 0 && threadIdx.x == 0) {
+      const int v = atomicAdd(A.next, 1);
+      if (v == A.count + teams - 1) *A.next = 0;
+      for (int r = 0; r < T.size; ++r) *T.at(&lp, r) = v;
+    }
+    T.sync();
+    const int v = lp;
+    T.sync();
+    if (v >= A.count) break;
+    batch_solve_one32<kCl>(A, A.order[v], T);
+  }
 }
 
 // Persistent solver: teams draw LPs from the queue until it is empty.  The counter

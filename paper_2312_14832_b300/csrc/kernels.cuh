@@ -37,6 +37,7 @@ struct DevState {
   double p3, p6;   // (s+1)^-0.3 and (s+1)^-0.6 for the next acceptance decision
   int suspended;   // batched solver: stopped at a check by its iteration slice, resumable
   int pad_s;
+  long long k32;   // batched mixed precision: iterations run in FP32
 };
 
 struct DevParams {

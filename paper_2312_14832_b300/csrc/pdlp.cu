@@ -1293,7 +1293,8 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
     invalid("an LP of the batch is too large for one CTA's shared memory (needs (n + m) padded doubles)");
   int static_max = 0;
   for (const void* f : {(const void*)k_batch_solve<false, false>, (const void*)k_batch_solve<false, true>,
-                        (const void*)k_batch_solve<true, false>, (const void*)k_batch_solve<true, true>}) {
+                        (const void*)k_batch_solve<true, false>, (const void*)k_batch_solve<true, true>,
+                        (const void*)k_batch_solve32<false>, (const void*)k_batch_solve32<true>}) {
     cudaFuncAttributes fa;
     CK(cudaFuncGetAttributes(&fa, f));
     static_max = std::max(static_max, (int)fa.sharedSizeBytes);
@@ -1308,8 +1309,13 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   CK(cudaFuncSetAttribute(k_batch_solve<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
   CK(cudaFuncSetAttribute(k_batch_solve<true, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   CK(cudaFuncSetAttribute(k_batch_solve<true, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  CK(cudaFuncSetAttribute(k_batch_solve32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  CK(cudaFuncSetAttribute(k_batch_solve32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  CK(cudaFuncSetAttribute(k_batch_solve32<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   h->hk_cptr = Lo.SK.chunk_ptr;
   h->ht_cptr = Lo.SKt.chunk_ptr;
+  if (P.precision == PDLP_MIXED) setup_mixed(h);
+  else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
   int per_sm = 0, sms = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<false, false>, kBatchThreads,
                                                    h->batch_smem));
@@ -1385,13 +1391,14 @@ static int batch_team_size(const pdlp_ctx* h, int64_t count, int team_req) {
 
 // One launch of the persistent batched kernel over A.count LPs (A.order): team size,
 // resident slices and grid chosen for that count.
-static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp, int64_t count, int team_req) {
+static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp, int64_t count, int team_req,
+                         bool fp32 = false) {
   const int team = batch_team_size(h, count, team_req);
   // resident slices: the largest one of any LP and CTA decides the launch's shared memory
   const long long res_bytes = resident_need(h, team);
   const size_t res_smem = h->batch_smem + (size_t)((res_bytes + 7) / 8 * 8);
   bool resident = false;
-  if (sp.resident != 1 && res_smem <= (size_t)h->dev_smem_optin) {
+  if (!fp32 && sp.resident != 1 && res_smem <= (size_t)h->dev_smem_optin) {
     if (sp.resident == 2) {
       resident = true;
     } else {
@@ -1408,7 +1415,10 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp,
   if (team == 1) {
     int per_sm = 0, sms = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, resident ? (const void*)k_batch_solve<false, true> : (const void*)k_batch_solve<false, false>,
+        &per_sm,
+        fp32       ? (const void*)k_batch_solve32<false>
+        : resident ? (const void*)k_batch_solve<false, true>
+                   : (const void*)k_batch_solve<false, false>,
         kBatchThreads, smem));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
     if (per_sm < 1) invalid("batched kernel does not fit on an SM");
@@ -1428,8 +1438,11 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp,
   if (team > 1) {
     cfg.gridDim = dim3((unsigned)team);
     int nc = 0;
-    CK(cudaOccupancyMaxActiveClusters(
-        &nc, resident ? (const void*)k_batch_solve<true, true> : (const void*)k_batch_solve<true, false>, &cfg));
+    CK(cudaOccupancyMaxActiveClusters(&nc,
+                                      fp32       ? (const void*)k_batch_solve32<true>
+                                      : resident ? (const void*)k_batch_solve<true, true>
+                                                 : (const void*)k_batch_solve<true, false>,
+                                      &cfg));
     if (nc < 1) invalid("a cluster of this many CTAs does not fit on the GPU");
     grid = (int)std::min<int64_t>((int64_t)nc, count) * team;
   }
@@ -1437,10 +1450,12 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp,
   h->last_team = team;
   h->last_resident = resident;
   if (team == 1) {
-    if (resident) k_batch_solve<false, true><<<grid, kBatchThreads, smem, h->s>>>(A);
+    if (fp32) k_batch_solve32<false><<<grid, kBatchThreads, smem, h->s>>>(A);
+    else if (resident) k_batch_solve<false, true><<<grid, kBatchThreads, smem, h->s>>>(A);
     else k_batch_solve<false, false><<<grid, kBatchThreads, smem, h->s>>>(A);
   } else {
-    if (resident) CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, true>, A));
+    if (fp32) CK(cudaLaunchKernelEx(&cfg, k_batch_solve32<true>, A));
+    else if (resident) CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, true>, A));
     else CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, false>, A));
   }
   CKL("k_batch_solve");
@@ -1506,12 +1521,20 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.ys_off = h->ys_off;
   A.red_off = h->red_off;
   A.part_off = h->part_off;
-  A.slice_iters = sp.batch_tail_iters > 0 ? sp.batch_tail_iters : 0;
+  const bool mixed = h->p.precision == PDLP_MIXED;
+  A.k_val32 = h->K.val32;
+  A.t_val32 = h->Kt.val32;
+  A.c32 = h->c32; A.l32 = h->l32; A.u32 = h->u32; A.q32 = h->q32;
+  A.sx32 = h->sx32; A.sy32 = h->sy32; A.kxp32 = h->kxp32;
+  A.switch_tol = sp.mixed_switch_tol > 0.0 ? sp.mixed_switch_tol : std::max(sp.tol, 1e-5);
+  A.slice_iters = (!mixed && sp.batch_tail_iters > 0) ? sp.batch_tail_iters : 0;
   A.resume = 0;
   h->last_resumed = 0;
   CK(cudaEventRecord(h->ev_t0, h->s));
-  launch_batch(h, A, sp, h->count, sp.cluster_ctas);
-  if (A.slice_iters > 0) {
+  // mixed precision: FP32 iterations first; the LPs that leave them unfinished are
+  // suspended with their FP64 state and continue in FP64 (second stage)
+  launch_batch(h, A, sp, h->count, sp.cluster_ctas, mixed);
+  if (A.slice_iters > 0 || mixed) {
     // second stage: the LPs stopped by the slice continue, with teams sized for their number
     CK(cudaMemcpyAsync(h->hstate.data(), h->bstate, sizeof(DevState) * h->count, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
@@ -1563,7 +1586,8 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
       r.eta = S.eta;
       r.solve_s = wall;
       r.device_ms = dev_ms;
-      r.launches = 1;
+      r.launches = 1 + (h->last_resumed > 0 ? 1 : 0);
+      r.fp32_iters = S.k32;
     }
   }
   h->solved = true;

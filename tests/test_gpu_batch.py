@@ -229,3 +229,49 @@ def test_two_stage_tail_at_tolerance(pk):
         assert r["status"] == ref["status"] == pk.OPTIMAL
         assert r["iters"] == ref["iters"]
         assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
+
+
+def _check_point(lp, x, y, tol):
+    rp, rd, rg = oracle.relative_errors(lp, x, y)
+    assert max(rp, rd, rg) <= tol * (1 + 1e-6), (rp, rd, rg)
+
+
+@pytest.mark.parametrize("team", [1, 4])
+def test_batch_mixed_precision_at_1e4(pk, team):
+    """FP32 iterations with FP64 checks (precision = MIXED): every returned point passes
+    the tests of Section 2 (re-evaluated by the oracle's KKT routine) and its objective
+    agrees with the FP64 oracle within the requested accuracy (1e-3 relative at 1e-4,
+    as for the single-LP mixed precision)."""
+    lps = mixed_batch()
+    with pk.BatchSolver.from_lps(lps, precision=pk.MIXED) as b:
+        res = b.solve(tol=1e-4, max_iter=500_000, cluster_ctas=team)
+    assert sum(r["fp32_iters"] for r in res) > 0
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=1e-4, max_iter=500_000)
+        assert r["status"] == pk.OPTIMAL
+        assert r["fp32_iters"] <= r["iters"]
+        _check_point(lp, r["x"], r["y"], 1e-4)
+        assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-3 * (1 + abs(ref["primal_obj"]))
+
+
+def test_batch_mixed_precision_refines_to_1e8(pk):
+    lps = mixed_batch()
+    with pk.BatchSolver.from_lps(lps, precision=pk.MIXED) as b:
+        res = b.solve(tol=1e-8, max_iter=500_000)
+        resumed = b.info()["batch_resumed"]
+    assert resumed > 0                                   # FP64 refinement ran
+    assert any(0 < r["fp32_iters"] < r["iters"] for r in res)
+    for lp, r in zip(lps, res):
+        ref = oracle.solve(lp, tol=1e-8, max_iter=500_000)
+        assert r["status"] == pk.OPTIMAL
+        _check_point(lp, r["x"], r["y"], 1e-8)
+        assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
+
+
+def test_batch_mixed_precision_iteration_limit(pk):
+    lps = fixed_iteration_batch()[:4]
+    with pk.BatchSolver.from_lps(lps, precision=pk.MIXED) as b:
+        res = b.solve(tol=0.0, max_iter=300, mixed_switch_tol=1e-30)
+    for r in res:
+        assert r["iters"] == 300 and r["status"] == pk.ITER_LIMIT and r["fp32_iters"] == 300
+        assert np.all(np.isfinite(r["x"])) and np.all(np.isfinite(r["y"]))
