@@ -258,8 +258,9 @@ def bench_batched(args):
                  "fp32_iter_share": float(fp32.sum() / max(itm.sum(), 1)),
                  "continued_in_fp64": bm.info()["batch_resumed"],
                  "max_rel_obj_diff_vs_fp64": max(abs(a["primal_obj"] - c["primal_obj"]) / (1 + abs(a["primal_obj"]))
-                                                 for a, c in zip(res, rm)),
-                 "max_rel_error": max(max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) for r in rm)}
+                                                 for a, c in zip(res, rm) if a["status"] == 0 and c["status"] == 0),
+                 "max_rel_error_of_optimal": max(max(r["rel_primal"], r["rel_dual"], r["rel_gap"])
+                                                 for r in rm if r["status"] == 0)}
         bm.close()
     clocks = clk.stop()
     dev_s = res[0]["device_ms"] * 1e-3
@@ -281,7 +282,11 @@ def bench_batched(args):
         seq_s += r1["solve_s"]
         seq_it += r1["iters"]
     seq_total = seq_s * args.count / len(sample)
-    out = {"metric": METRIC, "value": args.count / dev_s, "unit": "LPs/s to 1e-4", "n_gpus": 1,
+    best = args.count / dev_s
+    variant = "fp64"
+    if mixed is not None and mixed["optimal"] >= int(np.sum(status == 0)) and mixed["lps_per_s"] > best:
+        best, variant = mixed["lps_per_s"], "fp32 iterations, fp64 checks"
+    out = {"metric": METRIC, "value": best, "value_variant": variant, "unit": "LPs/s to 1e-4", "n_gpus": 1,
            "higher_is_better": True, "dtype": "f64", "data": "synthetic", "impl": "ours-batched",
            "config": {"workload": f"{args.count} planted LPs, n~U(50,5000), m~U(0.3,0.8)n, density U(0.5%,5%), "
                                   "N(0,1) values (lpgen.batch_planted seed 0)",
