@@ -82,20 +82,29 @@ def kernel_bytes(lp):
 
 
 def stored_traffic(kernel, workload_name):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+    committed ncu summary profiles/ncu_traffic.txt, if it was taken on the current
+    kernel source and this workload; else None.  Format: `key = value` lines
+    (source_sha, workload) and `kernel <name> = <bytes per launch>` lines."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
-        with open(path) as f:
-            rec = json.load(f)
+        lines = open(path).read().splitlines()
     except OSError:
         return None
+    rec, kern = {}, {}
+    for ln in lines:
+        if "=" not in ln or ln.lstrip().startswith("#"):
+            continue
+        key, val = (t.strip() for t in ln.split("=", 1))
+        if key.startswith("kernel "):
+            kern[key[len("kernel "):].strip()] = float(val)
+        else:
+            rec[key] = val
     src = os.path.join(ROOT, "paper_2312_14832_b300", "csrc", "kernels.cuh")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    k = rec.get("kernels", {}).get(kernel)
-    if not k or rec.get("source_sha") != h or rec.get("workload") != workload_name:
+    if rec.get("source_sha") != h or rec.get("workload") != workload_name:
         return None
-    return k.get("dram_bytes_per_launch")
+    return kern.get(kernel)
 
 
 class Clocks:
