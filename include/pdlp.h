@@ -100,10 +100,13 @@ typedef struct {
                               slice of the rows and columns): 1..16, or 0 = automatic
                               (one CTA per LP when the batch fills the GPU, else up to
                               16 per LP)                                                    */
-  int32_t resident;        /* pdlp_batch_solve: copy each CTA's slice of K and K' and the
-                              vectors of its rows and columns into shared memory for the
-                              iterations: 0 = automatic (when every LP's slices fit without
-                              lowering the CTAs per SM), 1 = never, 2 = whenever they fit  */
+  int32_t resident;        /* pdlp_batch_solve: where the iterations find their data.
+                              0 = automatic; 1 = x, y in shared memory (one replica per
+                              CTA), K and K' streamed; 2 = also each CTA's slice of K, K'
+                              and of the row and column vectors copied into shared memory
+                              when it fits (automatic: when that keeps the CTAs per SM);
+                              3 = x, y in global memory, one copy per LP (automatic when
+                              x and y of the largest LP do not fit in shared memory)      */
   int32_t step_rule;       /* pdlp_solve: 0 = the constant step eta of Section 2;
                               1 = the adaptive step rule of the cited PDLP paper
                               (Applegate et al. 2021): an attempt with step eta is kept when
@@ -167,7 +170,8 @@ typedef struct {
   double stored_bytes_per_iter;      /* the same with padding slots counted               */
   double eta, omega0, norm_K;
   int32_t batch_team;          /* batch handles: CTAs per LP of the last pdlp_batch_solve    */
-  int32_t batch_resident;      /* batch handles: 1 if that launch ran from shared memory      */
+  int32_t batch_resident;      /* batch handles, last launch: 0 replicas, 1 resident slices,
+                                  3 iterates in global memory                                 */
   int32_t wide_rows_K;         /* rows of K stored spread over a chunk's lanes (dense rows)   */
   int32_t batch_resumed;       /* batch handles: LPs continued in the second stage of the last
                                   pdlp_batch_solve (batch_tail_iters > 0)                     */

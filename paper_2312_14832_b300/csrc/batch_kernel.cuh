@@ -63,6 +63,10 @@ struct BatchArgs {
   const float *k_val32, *t_val32, *c32, *l32, *u32, *q32;
   float *sx32, *sy32, *kxp32;
   double switch_tol;             // FP32 until the FP64-measured error is <= this (or stalls)
+  // iterates in global memory (LPs too large for shared-memory replicas): one copy per LP,
+  // shared by the team, gathered through L2
+  double *xg, *yg;
+  float *xg32, *yg32;
 };
 
 constexpr int kMaxTeam = 16;                         // CTAs per LP (non-portable cluster size)
@@ -268,12 +272,10 @@ __device__ __forceinline__ double team_norm(const double* v, int j0, int j1, dou
 template <bool kCl>
 __device__ __forceinline__ void batch_kkt(const BatchArgs& A, const LpDesc& D, bool avg_is_cur, double it,
                                           double* red, double* tot, int ir0, int ir1, int jc0, int jc1,
-                                          double* part, int& flip, const Team<kCl>& T,
-                                          bool cur_global = false) {
-  extern __shared__ double bsm[];
-  // the current point: the FP64 replicas, or (FP32 iterations) its FP64 copy in xout / yout
-  const double* xs = cur_global ? A.xout + D.c0 : bsm + A.xs_off;
-  const double* ys = cur_global ? A.yout + D.r0 : bsm + A.ys_off;
+                                          double* part, int& flip, const Team<kCl>& T, const double* xs,
+                                          const double* ys) {
+  // xs, ys: the current point of the LP (indices local to the LP; this CTA reads its own
+  // rows and columns only)
   {
     double acc[8];
 #pragma unroll
@@ -354,11 +356,15 @@ __host__ __device__ inline long long resident_bytes(long long kch, long long ksl
 // into shared memory first, so an iteration touches only shared memory (and, in a
 // cluster, the replicas of the other CTAs); the running sums and K x are written back
 // to global memory at every check.
-template <bool kCl, bool kRes>
+// kGlob: the iterates live in global memory (A.xg, A.yg), one copy per LP shared by the
+// team (each CTA writes only its own rows and columns, gathers go through L2).
+template <bool kCl, bool kRes, bool kGlob>
 __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
+  static_assert(!(kRes && kGlob), "resident slices gather from shared-memory replicas");
   extern __shared__ double bsm[];
-  double* xs = bsm + A.xs_off;
-  double* ys = bsm + A.ys_off;
+  const LpDesc& D0 = A.desc[b];
+  double* xs = kGlob ? A.xg + D0.c0 : bsm + A.xs_off;
+  double* ys = kGlob ? A.yg + D0.r0 : bsm + A.ys_off;
   double* red = bsm + A.red_off;
   double* part = bsm + A.part_off;
   __shared__ DevState S;
@@ -376,6 +382,18 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   const int ir0 = (kr0 - D.kc0) * 32, ir1 = (kr1 - D.kc0) * 32;
   const int jc0 = (tr0 - D.tc0) * 32, jc1 = (tr1 - D.tc0) * 32;
   const int mo1 = min(ir1, m), no1 = min(jc1, n);
+  // the entries of the iterates this CTA writes when it sets them all: its whole replica,
+  // or (global iterates) its own rows and columns; then a barrier over the team
+  const int xw0 = kGlob ? jc0 : 0, xw1 = kGlob ? jc1 : D.npad;
+  const int yw0 = kGlob ? ir0 : 0, yw1 = kGlob ? ir1 : D.mpad;
+  auto fill_sync = [&]() {
+    if constexpr (kGlob) T.sync();
+    else __syncthreads();
+  };
+  auto put = [&](double* a, int i, double v) {
+    if constexpr (kGlob) a[i] = v;
+    else T.put(a, i, v);
+  };
 
   // per-entry vectors as the iterations see them: v[i - ofs]
   const double* cv = A.c + D.c0;
@@ -459,6 +477,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     if constexpr (kRes) {
       if (from_replica) rows_s(kpS, kvS, kgS, kr1 - kr0, ir0, xs, epi);
       else rows_s(kpS, kvS, kgS, kr1 - kr0, ir0, gsrc, epi);
+    } else if constexpr (kGlob) {
+      batch_rows<kSrcGlobal, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, from_replica ? xs : gsrc, A,
+                                    epi);
     } else {
       if (from_replica) batch_rows<kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A, epi);
       else batch_rows<kSrcGlobal, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, gsrc, A, epi);
@@ -468,6 +489,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     if constexpr (kRes) {
       if (from_replica) rows_s(tpS, tvS, tgS, tr1 - tr0, jc0, ys, epi);
       else rows_s(tpS, tvS, tgS, tr1 - tr0, jc0, gsrc, epi);
+    } else if constexpr (kGlob) {
+      batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, from_replica ? ys : gsrc, A,
+                                    epi);
     } else {
       if (from_replica) batch_rows<kSrcSmemY, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A, epi);
       else batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, gsrc, A, epi);
@@ -478,22 +502,22 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   double eta = A.eta_fixed;
   if (!(eta > 0.0) && !A.resume) {
     const double v0 = 1.0 / sqrt((double)n);
-    for (int j = tid; j < D.npad; j += nt) xs[j] = j < n ? v0 : 0.0;
-    __syncthreads();
+    for (int j = xw0 + tid; j < xw1; j += nt) xs[j] = j < n ? v0 : 0.0;
+    fill_sync();
     for (int it = 0; it < A.power_iters; ++it) {
       Kmul(true, nullptr,
-                                  [&](int i, double s) { T.put(ys, i, s); });
+                                  [&](int i, double s) { put(ys, i, s); });
       T.sync();
       Tmul(true, nullptr,
                                   [&](int j, double s) { A.g[D.c0 + j] = s; });
       __syncthreads();
       const double nw = team_norm(A.g + D.c0, jc0, jc1, red, part, flip, T);
       if (nw != 0.0)
-        for (int j = jc0 + tid; j < jc1; j += nt) T.put(xs, j, A.g[D.c0 + j] / nw);
+        for (int j = jc0 + tid; j < jc1; j += nt) put(xs, j, A.g[D.c0 + j] / nw);
       T.sync();
     }
     Kmul(true, nullptr,
-                                [&](int i, double s) { T.put(ys, i, s); });
+                                [&](int i, double s) { put(ys, i, s); });
     T.sync();
     const double sn = m > 0 ? team_norm(ys, ir0, ir1, red, part, flip, T) : 0.0;
     eta = sn > 0.0 ? A.step_scale / sn : 1.0;
@@ -532,17 +556,17 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   if (A.resume) {
     // ---- continue a suspended LP: its state, its current point (kept in xout / yout),
     // and the running sums, anchor and K x that stayed in global memory
-    for (int j = tid; j < D.npad; j += nt) xs[j] = A.xout[D.c0 + j];
-    for (int i = tid; i < D.mpad; i += nt) ys[i] = A.yout[D.r0 + i];
+    for (int j = xw0 + tid; j < xw1; j += nt) xs[j] = A.xout[D.c0 + j];
+    for (int i = yw0 + tid; i < yw1; i += nt) ys[i] = A.yout[D.r0 + i];
     if (tid == 0) {
       S = A.st[b];
       S.suspended = 0;
     }
-    __syncthreads();
+    fill_sync();
   } else {
     // ---- initial point (the warm start or 0, projected onto X and Y) and anchor; every
     // CTA fills its own replicas, the owners the per-entry vectors
-    for (int j = tid; j < D.npad; j += nt) {
+    for (int j = xw0 + tid; j < xw1; j += nt) {
       const int64_t gj = D.c0 + j;
       const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
       xs[j] = x0;
@@ -552,7 +576,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
         sxv[j - jofs] = 0.0;
       }
     }
-    for (int i = tid; i < D.mpad; i += nt) {
+    for (int i = yw0 + tid; i < yw1; i += nt) {
       const int64_t gi = D.r0 + i;
       double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
       if (i >= D.m1) y0 = max0(y0);
@@ -563,7 +587,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
         syv[i - iofs] = 0.0;
       }
     }
-    __syncthreads();
+    fill_sync();
     Kmul(true, nullptr, [&](int i, double s) {
       A.kxp[D.r0 + i] = s;
       kxv[i - iofs] = s;
@@ -579,7 +603,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       S.sigma = eta * omega;
     }
     __syncthreads();
-    batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T);
+    batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T, xs, ys);
     if (tid == 0) {
       const double gap = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
       S.kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap, S.omega);
@@ -599,7 +623,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       Tmul(true, nullptr, [&](int j, double gsum) {
         const int jl = j - jofs;
         const double xn = clamp_box(fma(-tau, cv[jl] - gsum, xs[j]), lv[jl], uv[jl]);
-        T.put(xs, j, xn);
+        put(xs, j, xn);
         sxv[jl] = sxv[jl] + xn;
       });
       T.sync();
@@ -608,7 +632,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
         const double e = qv[il] + kxv[il];
         double yn = fma(sigma, fma(-2.0, v, e), ys[i]);
         if (i >= D.m1) yn = max0(yn);
-        T.put(ys, i, yn);
+        put(ys, i, yn);
         syv[il] = syv[il] + yn;
         kxv[il] = v;
       });
@@ -642,7 +666,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     Tmul(false, A.sy + D.r0,
                                  [&](int j, double s) { A.g_a[D.c0 + j] = s * it; });
     __syncthreads();
-    batch_kkt(A, D, t == 0, it, red, tot, ir0, ir1, jc0, jc1, part, flip, T);
+    batch_kkt(A, D, t == 0, it, red, tot, ir0, ir1, jc0, jc1, part, flip, T, xs, ys);
     if (tid == 0) {
       S.k = k;
       S.t = t;
@@ -655,8 +679,8 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     if (S.restart_flag) {
       const bool avg = S.cand_avg;
       if (avg) {
-        for (int j = tid; j < D.npad; j += nt) xs[j] = A.sx[D.c0 + j] * it;
-        for (int i = tid; i < D.mpad; i += nt) ys[i] = A.sy[D.r0 + i] * it;
+        for (int j = xw0 + tid; j < xw1; j += nt) xs[j] = A.sx[D.c0 + j] * it;
+        for (int i = yw0 + tid; i < yw1; i += nt) ys[i] = A.sy[D.r0 + i] * it;
       }
       T.sync();   // every replica is read before the owners clear the sums
       for (int j = jc0 + tid; j < jc1; j += nt) {
@@ -707,7 +731,7 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
 
 // FP32 rows of chunks [c0, c1) (values A.k_val32 / t_val32 in global memory; gathers
 // from the float replicas src); same order per row as batch_rows.
-template <class F>
+template <bool kGlobSrc, class F>
 __device__ __forceinline__ void batch_rows32(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
                                              const float* __restrict__ val, int c0, int c1, int cbase, int64_t base,
                                              const float* src, F epi) {
@@ -726,7 +750,7 @@ __device__ __forceinline__ void batch_rows32(const int32_t* __restrict__ cptr, c
           ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
         }
 #pragma unroll
-      for (int j = 0; j < kBB; ++j) xv[j] = j < nb ? src[ci[j]] : 0.0f;
+      for (int j = 0; j < kBB; ++j) xv[j] = j < nb ? (kGlobSrc ? __ldcg(src + ci[j]) : src[ci[j]]) : 0.0f;
 #pragma unroll
       for (int j = 0; j < kBB; ++j)
         if (j < nb) acc = fmaf(v[j], xv[j], acc);
@@ -742,13 +766,16 @@ __device__ __forceinline__ void batch_rows32(const int32_t* __restrict__ cptr, c
 // whose FP64-measured error reaches A.switch_tol, or stops improving by 10 % for 16
 // checks, is suspended with its FP64 state and finishes in FP64 (a resumed launch of
 // k_batch_solve).  No resident slices.
-template <bool kCl>
+template <bool kCl, bool kGlob>
 __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T) {
   extern __shared__ double bsm[];
-  double* xs = bsm + A.xs_off;   // FP64 replicas: power iteration only
-  double* ys = bsm + A.ys_off;
-  float* xf = reinterpret_cast<float*>(xs);
-  float* yf = reinterpret_cast<float*>(ys);
+  const LpDesc& D0 = A.desc[b];
+  // FP64 iterates (power iteration only) and FP32 iterates: shared-memory replicas over the
+  // same space, or one copy each in global memory (kGlob)
+  double* xs = kGlob ? A.xg + D0.c0 : bsm + A.xs_off;
+  double* ys = kGlob ? A.yg + D0.r0 : bsm + A.ys_off;
+  float* xf = kGlob ? A.xg32 + D0.c0 : reinterpret_cast<float*>(bsm + A.xs_off);
+  float* yf = kGlob ? A.yg32 + D0.r0 : reinterpret_cast<float*>(bsm + A.ys_off);
   double* red = bsm + A.red_off;
   double* part = bsm + A.part_off;
   __shared__ DevState S;
@@ -767,27 +794,34 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
   const int mo1 = min(ir1, m), no1 = min(jc1, n);
   double* x64 = A.xout + D.c0;   // FP64 copy of the current point (all columns of the LP)
   double* y64 = A.yout + D.r0;
+  const int xw0 = kGlob ? jc0 : 0, xw1 = kGlob ? jc1 : D.npad;
+  const int yw0 = kGlob ? ir0 : 0, yw1 = kGlob ? ir1 : D.mpad;
+  auto put = [&](auto* a, int i, auto v) {
+    if constexpr (kGlob) a[i] = v;
+    else T.put(a, i, v);
+  };
 
   // ---- step size: power iteration on K'K in FP64 (as the FP64 solver)
   double eta = A.eta_fixed;
   if (!(eta > 0.0)) {
     const double v0 = 1.0 / sqrt((double)n);
-    for (int j = tid; j < D.npad; j += nt) xs[j] = j < n ? v0 : 0.0;
-    __syncthreads();
+    for (int j = xw0 + tid; j < xw1; j += nt) xs[j] = j < n ? v0 : 0.0;
+    if constexpr (kGlob) T.sync();
+    else __syncthreads();
     for (int it = 0; it < A.power_iters; ++it) {
-      batch_rows<kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A,
-                                   [&](int i, double s) { T.put(ys, i, s); });
+      batch_rows<kGlob ? kSrcGlobal : kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A,
+                                                         [&](int i, double s) { put(ys, i, s); });
       T.sync();
-      batch_rows<kSrcSmemY, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A,
-                                   [&](int j, double s) { A.g[D.c0 + j] = s; });
+      batch_rows<kGlob ? kSrcGlobal : kSrcSmemY, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A,
+                                                         [&](int j, double s) { A.g[D.c0 + j] = s; });
       __syncthreads();
       const double nw = team_norm(A.g + D.c0, jc0, jc1, red, part, flip, T);
       if (nw != 0.0)
-        for (int j = jc0 + tid; j < jc1; j += nt) T.put(xs, j, A.g[D.c0 + j] / nw);
+        for (int j = jc0 + tid; j < jc1; j += nt) put(xs, j, A.g[D.c0 + j] / nw);
       T.sync();
     }
-    batch_rows<kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A,
-                                 [&](int i, double s) { T.put(ys, i, s); });
+    batch_rows<kGlob ? kSrcGlobal : kSrcSmemX, false>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A,
+                                                       [&](int i, double s) { put(ys, i, s); });
     T.sync();
     const double sn = m > 0 ? team_norm(ys, ir0, ir1, red, part, flip, T) : 0.0;
     eta = sn > 0.0 ? A.step_scale / sn : 1.0;
@@ -823,7 +857,7 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
   P.qnorm = scal[2];
 
   // ---- initial point: FP64 copy (owners) and float replicas (every CTA), anchor, sums
-  for (int j = tid; j < D.npad; j += nt) {
+  for (int j = xw0 + tid; j < xw1; j += nt) {
     const int64_t gj = D.c0 + j;
     const double x0 = j < n ? clamp_box(A.x0 ? A.x0[gj] : 0.0, A.l[gj], A.u[gj]) : 0.0;
     xf[j] = (float)x0;
@@ -834,7 +868,7 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
       A.sx32[gj] = 0.0f;
     }
   }
-  for (int i = tid; i < D.mpad; i += nt) {
+  for (int i = yw0 + tid; i < yw1; i += nt) {
     const int64_t gi = D.r0 + i;
     double y0 = (A.y0 && i < m) ? A.y0[gi] : 0.0;
     if (i >= D.m1) y0 = max0(y0);
@@ -863,7 +897,7 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
     S.sigma = eta * omega;
   }
   __syncthreads();
-  batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T, true);
+  batch_kkt(A, D, true, 0.0, red, tot, ir0, ir1, jc0, jc1, part, flip, T, x64, y64);
   if (tid == 0) {
     const double gap = tot[Q_QY_C] + tot[Q_LT_C] - tot[Q_CX_C];
     S.kkt_anchor = kkt_w(tot[Q_PRS_C], tot[Q_DRS_C], gap, S.omega);
@@ -881,19 +915,19 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
     const bool at_limit = k >= A.max_iter;
     if (!at_limit) {
       const float tau = (float)S.tau, sigma = (float)S.sigma;
-      batch_rows32(A.t_cptr, A.t_col, A.t_val32, tr0, tr1, D.tc0, D.r0, yf, [&](int j, float gsum) {
+      batch_rows32<kGlob>(A.t_cptr, A.t_col, A.t_val32, tr0, tr1, D.tc0, D.r0, yf, [&](int j, float gsum) {
         const int64_t gj = D.c0 + j;
         float xn = fmaf(-tau, A.c32[gj] - gsum, xf[j]);
         xn = fminf(fmaxf(xn, A.l32[gj]), A.u32[gj]);
-        T.put(xf, j, xn);
+        put(xf, j, xn);
         A.sx32[gj] = A.sx32[gj] + xn;
       });
       T.sync();
-      batch_rows32(A.k_cptr, A.k_col, A.k_val32, kr0, kr1, D.kc0, D.c0, xf, [&](int i, float v) {
+      batch_rows32<kGlob>(A.k_cptr, A.k_col, A.k_val32, kr0, kr1, D.kc0, D.c0, xf, [&](int i, float v) {
         const int64_t gi = D.r0 + i;
         float yn = fmaf(sigma, fmaf(-2.0f, v, A.q32[gi] + A.kxp32[gi]), yf[i]);
         if (i >= D.m1) yn = fmaxf(yn, 0.0f);
-        T.put(yf, i, yn);
+        put(yf, i, yn);
         A.sy32[gi] = A.sy32[gi] + yn;
         A.kxp32[gi] = v;
       });
@@ -928,7 +962,7 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
     batch_rows<kSrcGlobal, false>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, A.sy + D.r0, A,
                                   [&](int j, double s) { A.g_a[D.c0 + j] = s * it; });
     __syncthreads();
-    batch_kkt(A, D, t == 0, it, red, tot, ir0, ir1, jc0, jc1, part, flip, T, true);
+    batch_kkt(A, D, t == 0, it, red, tot, ir0, ir1, jc0, jc1, part, flip, T, x64, y64);
     if (tid == 0) {
       S.k = k;
       S.t = t;
@@ -950,8 +984,8 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
       const bool avg = S.cand_avg;
       // every CTA refreshes its float replicas from the new FP64 point before the
       // owners overwrite the FP64 copy and clear the sums
-      for (int j = tid; j < D.npad; j += nt) xf[j] = (float)(avg ? A.sx[D.c0 + j] * it : x64[j]);
-      for (int i = tid; i < D.mpad; i += nt) yf[i] = (float)(avg ? A.sy[D.r0 + i] * it : y64[i]);
+      for (int j = xw0 + tid; j < xw1; j += nt) xf[j] = (float)(avg ? A.sx[D.c0 + j] * it : x64[j]);
+      for (int i = yw0 + tid; i < yw1; i += nt) yf[i] = (float)(avg ? A.sy[D.r0 + i] * it : y64[i]);
       T.sync();
       for (int j = jc0 + tid; j < jc1; j += nt) {
         const int64_t gj = D.c0 + j;
@@ -1001,7 +1035,7 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
   T.sync();
 }
 
-template <bool kCl>
+template <bool kCl, bool kGlob>
 __global__ void __launch_bounds__(256, 2) k_batch_solve32(BatchArgs A) {
   __shared__ int lp;
   Team<kCl> T;
@@ -1017,13 +1051,13 @@ __global__ void __launch_bounds__(256, 2) k_batch_solve32(BatchArgs A) {
     const int v = lp;
     T.sync();
     if (v >= A.count) break;
-    batch_solve_one32<kCl>(A, A.order[v], T);
+    batch_solve_one32<kCl, kGlob>(A, A.order[v], T);
   }
 }
 
 // Persistent solver: teams draw LPs from the queue until it is empty.  The counter
 // resets itself: the last of the failing draws (one per team) stores 0.
-template <bool kCl, bool kRes>
+template <bool kCl, bool kRes, bool kGlob>
 __global__ void __launch_bounds__(256, 2) k_batch_solve(BatchArgs A) {
   __shared__ int lp;
   Team<kCl> T;
@@ -1039,7 +1073,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_solve(BatchArgs A) {
     const int v = lp;
     T.sync();
     if (v >= A.count) break;
-    batch_solve_one<kCl, kRes>(A, A.order[v], T);
+    batch_solve_one<kCl, kRes, kGlob>(A, A.order[v], T);
   }
 }
 

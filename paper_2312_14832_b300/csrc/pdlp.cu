@@ -123,7 +123,12 @@ struct pdlp_ctx {
   size_t batch_smem = 0;
   int last_team = 0;         // CTAs per LP and resident mode of the last batched launch
   bool last_resident = false;
+  bool last_glob = false;
   int32_t* order2 = nullptr; // queue of the second stage (LPs stopped by the slice)
+  bool batch_glob = false;   // x and y of the largest LP do not fit in shared memory
+  size_t glob_smem = 0;      // shared memory of a launch with global iterates
+  double *xg = nullptr, *yg = nullptr;      // global iterates (allocated on first use)
+  float *xg32 = nullptr, *yg32 = nullptr;
   int64_t last_resumed = 0;  // LPs continued in the second stage of the last solve
   std::vector<int32_t> hk_cptr, ht_cptr;  // host copies of the chunk pointers of K and K'
   int dev_smem_optin = 0;
@@ -509,7 +514,7 @@ static void check_params(const pdlp_params& P) {
   if (P.check_every < 1) invalid("check_every must be >= 1");
   if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
   if (P.cluster_ctas < 0 || P.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
-  if (P.resident < 0 || P.resident > 2) invalid("resident must be 0, 1 or 2");
+  if (P.resident < 0 || P.resident > 3) invalid("resident must be 0, 1, 2 or 3");
   if (P.step_rule < 0 || P.step_rule > 1) invalid("step_rule must be 0 or 1");
   if (P.reserved1 != 0) invalid("reserved1 must be 0");
 }
@@ -1280,45 +1285,42 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   }
   device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
 
-  // shared memory per CTA: x and y of the largest LP plus the reduction scratch
+  // shared memory per CTA: x and y of the largest LP plus the reduction scratch; when
+  // they do not fit, the iterates go to global memory (one copy per LP)
   h->xs_off = 0;
   h->ys_off = (int)npad_max;
   h->red_off = (int)(npad_max + mpad_max);
   h->part_off = h->red_off + kBatchRed;
   h->batch_smem = (size_t)(npad_max + mpad_max + kBatchRed + kPartBuf) * sizeof(double);
+  h->glob_smem = (size_t)(kBatchRed + kPartBuf) * sizeof(double);
   int dev_smem = 0;
   CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-  const size_t static_smem = sizeof(DevState) + (NQ + 8) * sizeof(double) + 64;
-  if (h->batch_smem + static_smem > (size_t)dev_smem)
-    invalid("an LP of the batch is too large for one CTA's shared memory (needs (n + m) padded doubles)");
   int static_max = 0;
-  for (const void* f : {(const void*)k_batch_solve<false, false>, (const void*)k_batch_solve<false, true>,
-                        (const void*)k_batch_solve<true, false>, (const void*)k_batch_solve<true, true>,
-                        (const void*)k_batch_solve32<false>, (const void*)k_batch_solve32<true>}) {
+  const void* kernels[] = {(const void*)k_batch_solve<false, false, false>, (const void*)k_batch_solve<false, true, false>,
+                           (const void*)k_batch_solve<true, false, false>,  (const void*)k_batch_solve<true, true, false>,
+                           (const void*)k_batch_solve<false, false, true>,  (const void*)k_batch_solve<true, false, true>,
+                           (const void*)k_batch_solve32<false, false>,      (const void*)k_batch_solve32<true, false>,
+                           (const void*)k_batch_solve32<false, true>,       (const void*)k_batch_solve32<true, true>};
+  for (const void* f : kernels) {
     cudaFuncAttributes fa;
     CK(cudaFuncGetAttributes(&fa, f));
     static_max = std::max(static_max, (int)fa.sharedSizeBytes);
   }
   const int smem_cap = dev_smem - static_max;
-  if (smem_cap < (int)h->batch_smem)
-    invalid("an LP of the batch is too large for one CTA's shared memory (needs (n + m) padded doubles)");
+  h->batch_glob = smem_cap < (int)h->batch_smem;
   h->dev_smem_optin = smem_cap;
-  CK(cudaFuncSetAttribute(k_batch_solve<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  CK(cudaFuncSetAttribute(k_batch_solve<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  CK(cudaFuncSetAttribute(k_batch_solve<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  CK(cudaFuncSetAttribute(k_batch_solve<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  CK(cudaFuncSetAttribute(k_batch_solve<true, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  CK(cudaFuncSetAttribute(k_batch_solve<true, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  CK(cudaFuncSetAttribute(k_batch_solve32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  CK(cudaFuncSetAttribute(k_batch_solve32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  CK(cudaFuncSetAttribute(k_batch_solve32<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  for (const void* f : kernels) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  for (int i = 2; i < 10; ++i)
+    if (i != 4 && i != 6 && i != 8)   // the cluster (team) kernels
+      CK(cudaFuncSetAttribute(kernels[i], cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   h->hk_cptr = Lo.SK.chunk_ptr;
   h->ht_cptr = Lo.SKt.chunk_ptr;
   if (P.precision == PDLP_MIXED) setup_mixed(h);
   else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
   int per_sm = 0, sms = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<false, false>, kBatchThreads,
-                                                   h->batch_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, h->batch_glob ? (const void*)k_batch_solve<false, false, true> : (const void*)k_batch_solve<false, false, false>,
+      kBatchThreads, h->batch_glob ? h->glob_smem : h->batch_smem));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
   if (per_sm < 1) invalid("batched kernel does not fit on an SM");
   h->batch_resident = per_sm * sms;
@@ -1391,39 +1393,65 @@ static int batch_team_size(const pdlp_ctx* h, int64_t count, int team_req) {
 
 // One launch of the persistent batched kernel over A.count LPs (A.order): team size,
 // resident slices and grid chosen for that count.
-static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp, int64_t count, int team_req,
+// One launch of the persistent batched kernel over A.count LPs (A.order): team size,
+// placement of the iterates (shared-memory replicas, with or without resident matrix
+// slices, or global memory) and grid chosen for that count.
+static void launch_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp, int64_t count, int team_req,
                          bool fp32 = false) {
   const int team = batch_team_size(h, count, team_req);
+  BatchArgs A = A0;
+  const bool glob = h->batch_glob || sp.resident == 3;
+  if (glob) {
+    if (!h->xg) {
+      h->xg = dalloc<double>(h, (size_t)h->npad);
+      h->yg = dalloc<double>(h, (size_t)std::max<int64_t>(h->mpad, 1));
+    }
+    if (fp32 && !h->xg32) {
+      h->xg32 = dalloc<float>(h, (size_t)h->npad);
+      h->yg32 = dalloc<float>(h, (size_t)std::max<int64_t>(h->mpad, 1));
+    }
+    A.xs_off = A.ys_off = 0;
+    A.red_off = 0;
+    A.part_off = kBatchRed;
+  }
+  A.xg = h->xg;
+  A.yg = h->yg;
+  A.xg32 = h->xg32;
+  A.yg32 = h->yg32;
   // resident slices: the largest one of any LP and CTA decides the launch's shared memory
-  const long long res_bytes = resident_need(h, team);
-  const size_t res_smem = h->batch_smem + (size_t)((res_bytes + 7) / 8 * 8);
   bool resident = false;
-  if (!fp32 && sp.resident != 1 && res_smem <= (size_t)h->dev_smem_optin) {
-    if (sp.resident == 2) {
-      resident = true;
-    } else {
-      // automatic: only while it keeps as many CTAs per SM as the streaming kernel
-      int a = 0, r = 0;
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<false, false>, kBatchThreads,
-                                                       h->batch_smem));
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_batch_solve<false, true>, kBatchThreads, res_smem));
-      resident = r >= a;
+  size_t res_smem = 0;
+  if (!glob && !fp32 && sp.resident != 1) {
+    const long long res_bytes = resident_need(h, team);
+    res_smem = h->batch_smem + (size_t)((res_bytes + 7) / 8 * 8);
+    if (res_smem <= (size_t)h->dev_smem_optin) {
+      if (sp.resident == 2) {
+        resident = true;
+      } else {
+        // automatic: only while it keeps as many CTAs per SM as the streaming kernel
+        int a = 0, r = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_solve<false, false, false>, kBatchThreads,
+                                                         h->batch_smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_batch_solve<false, true, false>, kBatchThreads,
+                                                         res_smem));
+        resident = r >= a;
+      }
     }
   }
-  const size_t smem = resident ? res_smem : h->batch_smem;
+  const size_t smem = glob ? h->glob_smem : resident ? res_smem : h->batch_smem;
+  // the kernel: [team > 1][fp32][resident][glob]
+  const void* kfn;
+  if (team == 1)
+    kfn = fp32       ? (glob ? (const void*)k_batch_solve32<false, true> : (const void*)k_batch_solve32<false, false>)
+          : glob     ? (const void*)k_batch_solve<false, false, true>
+          : resident ? (const void*)k_batch_solve<false, true, false>
+                     : (const void*)k_batch_solve<false, false, false>;
+  else
+    kfn = fp32       ? (glob ? (const void*)k_batch_solve32<true, true> : (const void*)k_batch_solve32<true, false>)
+          : glob     ? (const void*)k_batch_solve<true, false, true>
+          : resident ? (const void*)k_batch_solve<true, true, false>
+                     : (const void*)k_batch_solve<true, false, false>;
   int grid = 0;
-  if (team == 1) {
-    int per_sm = 0, sms = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm,
-        fp32       ? (const void*)k_batch_solve32<false>
-        : resident ? (const void*)k_batch_solve<false, true>
-                   : (const void*)k_batch_solve<false, false>,
-        kBatchThreads, smem));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
-    if (per_sm < 1) invalid("batched kernel does not fit on an SM");
-    grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
-  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1433,31 +1461,27 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A, const pdlp_params& sp,
   cfg.blockDim = dim3(kBatchThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = h->s;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  if (team > 1) {
+  if (team == 1) {
+    int per_sm = 0, sms = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBatchThreads, smem));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+    if (per_sm < 1) invalid("batched kernel does not fit on an SM");
+    grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
+  } else {
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     cfg.gridDim = dim3((unsigned)team);
     int nc = 0;
-    CK(cudaOccupancyMaxActiveClusters(&nc,
-                                      fp32       ? (const void*)k_batch_solve32<true>
-                                      : resident ? (const void*)k_batch_solve<true, true>
-                                                 : (const void*)k_batch_solve<true, false>,
-                                      &cfg));
+    CK(cudaOccupancyMaxActiveClusters(&nc, kfn, &cfg));
     if (nc < 1) invalid("a cluster of this many CTAs does not fit on the GPU");
     grid = (int)std::min<int64_t>((int64_t)nc, count) * team;
   }
   cfg.gridDim = dim3((unsigned)grid);
   h->last_team = team;
   h->last_resident = resident;
-  if (team == 1) {
-    if (fp32) k_batch_solve32<false><<<grid, kBatchThreads, smem, h->s>>>(A);
-    else if (resident) k_batch_solve<false, true><<<grid, kBatchThreads, smem, h->s>>>(A);
-    else k_batch_solve<false, false><<<grid, kBatchThreads, smem, h->s>>>(A);
-  } else {
-    if (fp32) CK(cudaLaunchKernelEx(&cfg, k_batch_solve32<true>, A));
-    else if (resident) CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, true>, A));
-    else CK(cudaLaunchKernelEx(&cfg, k_batch_solve<true, false>, A));
-  }
+  h->last_glob = glob;
+  void* args[] = {(void*)&A};
+  CK(cudaLaunchKernelExC(&cfg, kfn, args));
   CKL("k_batch_solve");
 }
 
@@ -1465,7 +1489,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
                             const double* omega0, pdlp_result* res, double* x_out, double* y_out) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   if (sp.cluster_ctas < 0 || sp.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
-  if (sp.resident < 0 || sp.resident > 2) invalid("resident must be 0, 1 or 2");
+  if (sp.resident < 0 || sp.resident > 3) invalid("resident must be 0, 1, 2 or 3");
   if (sp.step_rule != 0) invalid("batches use the constant step (step_rule 0)");
   if (sp.batch_tail_iters < 0) invalid("batch_tail_iters must be >= 0");
   auto t_start = std::chrono::steady_clock::now();
@@ -1770,7 +1794,7 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->omega0 = h->omega0;
     info->norm_K = h->normK;
     info->batch_team = h->last_team;
-    info->batch_resident = h->last_resident ? 1 : 0;
+    info->batch_resident = h->last_glob ? 3 : (h->last_resident ? 1 : 0);
     info->wide_rows_K = h->K.nwide;
     info->batch_resumed = (int32_t)h->last_resumed;
     return PDLP_OK;

@@ -132,10 +132,11 @@ def test_batch_warm_start_matches_oracle(pk):
         close_rel(r["y"], ref["y"], 1e-10)
 
 
-@pytest.mark.parametrize("team,resident", [(2, 1), (2, 2), (8, 1), (8, 2), (16, 2)])
+@pytest.mark.parametrize("team,resident", [(2, 1), (2, 2), (8, 1), (8, 2), (16, 2), (1, 3), (4, 3)])
 def test_cluster_team_iterates_after_1000(pk, team, resident):
     """Several CTAs (a thread-block cluster) share each LP, with the matrix streamed from
-    global memory (resident=1) or staged in shared memory (2): same iterates as the oracle."""
+    global memory (resident=1), staged in shared memory (2), or the iterates themselves
+    in global memory (3, one copy per LP): same iterates as the oracle."""
     lps = fixed_iteration_batch()
     with pk.BatchSolver.from_lps(lps, scaling=1) as b:
         res = b.solve(tol=0.0, max_iter=1000, cluster_ctas=team, resident=resident)
@@ -145,6 +146,8 @@ def test_cluster_team_iterates_after_1000(pk, team, resident):
             assert info["batch_resident"] == 0
         if team >= 8 and resident == 2:   # every slice fits once the LPs are cut 8 ways
             assert info["batch_resident"] == 1
+        if resident == 3:
+            assert info["batch_resident"] == 3
     for lp, r in zip(lps, res):
         ref = oracle.solve(lp, tol=0.0, max_iter=1000, scaling=1)
         assert r["iters"] == 1000 and r["status"] == pk.ITER_LIMIT
@@ -199,7 +202,7 @@ def test_cluster_warm_start_and_rerun(pk):
                 close_rel(r["y"], ref["y"], 1e-10)
 
 
-@pytest.mark.parametrize("scaling,resident", [(0, 1), (1, 0)])
+@pytest.mark.parametrize("scaling,resident", [(0, 1), (1, 0), (1, 3)])
 def test_two_stage_tail_matches_oracle(pk, scaling, resident):
     """batch_tail_iters: every LP stops at the first check after 192 iterations and the
     unfinished ones continue in a second launch on teams; the point after 1000
@@ -236,15 +239,15 @@ def _check_point(lp, x, y, tol):
     assert max(rp, rd, rg) <= tol * (1 + 1e-6), (rp, rd, rg)
 
 
-@pytest.mark.parametrize("team", [1, 4])
-def test_batch_mixed_precision_at_1e4(pk, team):
+@pytest.mark.parametrize("team,resident", [(1, 0), (4, 0), (1, 3), (4, 3)])
+def test_batch_mixed_precision_at_1e4(pk, team, resident):
     """FP32 iterations with FP64 checks (precision = MIXED): every returned point passes
     the tests of Section 2 (re-evaluated by the oracle's KKT routine) and its objective
     agrees with the FP64 oracle within the requested accuracy (1e-3 relative at 1e-4,
     as for the single-LP mixed precision)."""
     lps = mixed_batch()
     with pk.BatchSolver.from_lps(lps, precision=pk.MIXED) as b:
-        res = b.solve(tol=1e-4, max_iter=500_000, cluster_ctas=team)
+        res = b.solve(tol=1e-4, max_iter=500_000, cluster_ctas=team, resident=resident)
     assert sum(r["fp32_iters"] for r in res) > 0
     for lp, r in zip(lps, res):
         ref = oracle.solve(lp, tol=1e-4, max_iter=500_000)
@@ -275,3 +278,21 @@ def test_batch_mixed_precision_iteration_limit(pk):
     for r in res:
         assert r["iters"] == 300 and r["status"] == pk.ITER_LIMIT and r["fp32_iters"] == 300
         assert np.all(np.isfinite(r["x"])) and np.all(np.isfinite(r["y"]))
+
+
+def test_global_iterates_for_an_lp_too_large_for_shared_memory(pk):
+    """x and y of this LP (n + m > 30000) do not fit in one CTA's shared memory: the
+    batch keeps them in global memory (automatic) and still matches the oracle."""
+    lps = [lpgen.planted_random(np.random.default_rng(31), 6000, 9000, 24000, 60000)]
+    lps.append(lpgen.planted_small(5))
+    with pk.BatchSolver.from_lps(lps, scaling=1) as b:
+        res = b.solve(tol=0.0, max_iter=400)
+        assert b.info()["batch_resident"] == 3
+        res_t = b.solve(tol=1e-6, max_iter=200_000, cluster_ctas=8)
+    for lp, r, rt in zip(lps, res, res_t):
+        ref = oracle.solve(lp, tol=0.0, max_iter=400, scaling=1)
+        assert r["restarts"] == ref["restarts"]
+        close_rel(r["x"], ref["x"], 1e-10)
+        close_rel(r["y"], ref["y"], 1e-10)
+        reft = oracle.solve(lp, tol=1e-6, max_iter=200_000, scaling=1)
+        assert rt["status"] == reft["status"] == pk.OPTIMAL and rt["iters"] == reft["iters"]
