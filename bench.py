@@ -497,12 +497,16 @@ def bench_warmstart(args):
     gen_s = time.perf_counter() - t0
     P = np.array([lp["features"] for lp in train])
     t0 = time.perf_counter()
-    X, Y, W, its, st, dev = ws.solve_family(train, tol=1e-6)
+    fam_params = {"precision": 1} if args.ws_train_mixed else {}
+    X, Y, W, its, st, dev = ws.solve_family(train, tol=args.ws_train_tol, chunk=args.ws_chunk, **fam_params)
     data_s = time.perf_counter() - t0
+    print(f"training data: {len(train)} LPs in {data_s:.1f} s (device {dev:.1f} s)", file=sys.stderr, flush=True)
     model = ws.WarmStart(P.shape[1], train[0]["n"], train[0]["m"], hidden=1024, max_batch=256, seed=0)
     fit = model.fit(P, X, Y, W, epochs=args.ws_epochs, batch=256, lr=1e-3)
+    del X, Y
+    print(f"training: {fit['train_device_s']:.1f} s device", file=sys.stderr, flush=True)
     Ph = np.array([lp["features"] for lp in held])
-    ev = ws.evaluate(model, held, Ph, tols=(1e-4, 1e-8))
+    ev = ws.evaluate(model, held, Ph, tols=tuple(float(t) for t in args.ws_tols.split(",")))
     model.close()
     n_in, hid, n_out = P.shape[1], 1024, train[0]["n"] + train[0]["m"] + 1
     flop_step = 2 * 256 * (n_in * hid + hid * hid + hid * n_out) * 3
@@ -512,7 +516,8 @@ def bench_warmstart(args):
            "config": {"workload": f"transportation family {args.ws_supplies} x {args.ws_demands} (n="
                                   f"{train[0]['n']}, m={train[0]['m']}), s,d ~ Gamma(2,50), costs = distance + "
                                   "N(0,0.05); MLP in -> 1024 -> 1024 -> n+m+1 (BF16, tcgen05)",
-                      "train": len(train), "heldout": len(held), "epochs": args.ws_epochs},
+                      "train": len(train), "heldout": len(held), "epochs": args.ws_epochs,
+                      "train_tol": args.ws_train_tol, "train_fp32": bool(args.ws_train_mixed)},
            "evaluation": ev, "train_loss_first_last": [float(fit["losses"][0]), float(fit["losses"][-1])],
            "train_device_s": fit["train_device_s"],
            "train_tflops": flop_step * steps / max(fit["train_device_s"], 1e-9) / 1e12,
@@ -551,6 +556,10 @@ def main():
     ap.add_argument("--ws-train", type=int, default=50000)
     ap.add_argument("--ws-heldout", type=int, default=1000)
     ap.add_argument("--ws-epochs", type=int, default=30)
+    ap.add_argument("--ws-train-tol", type=float, default=1e-6)
+    ap.add_argument("--ws-train-mixed", type=int, default=0, help="training solves with FP32 iterations")
+    ap.add_argument("--ws-chunk", type=int, default=4096, help="LPs per batched launch of the training solves")
+    ap.add_argument("--ws-tols", default="1e-4,1e-8")
     ap.add_argument("--ws-supplies", type=int, default=40)
     ap.add_argument("--ws-demands", type=int, default=60)
     args = ap.parse_args()

@@ -82,10 +82,14 @@ class WarmStart:
         self.net.close()
 
 
-def evaluate(model, lps, P, tols=(1e-4, 1e-8), **params):
+def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
     """Cold start against the learned warm start (with the KKT fallback) on held-out LPs,
     all in one batched launch per solve.  Returns per tolerance the mean iterations and
-    the batch device time of both, and how many LPs used the prediction."""
+    the batch device time of both, and how many LPs used the prediction.
+
+    budget: iteration budget of a warm-started solve; an LP that has not converged
+    within it falls back to a cold start, and its count is the budget plus the cold
+    solve's iterations (the cold solves of the comparison are those re-solves)."""
     x0, y0, w0 = model.predict(P)
     out = {}
     with BatchSolver.from_lps(lps, **params) as b:
@@ -99,9 +103,14 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), **params):
         ws = np.where(use, w0, 0.0)
         for tol in tols:
             cold = b.solve(tol=tol, want_points=False)
-            warm = b.solve(tol=tol, want_points=False, x0=xs, y0=ys, omega0=ws)
+            wkw = {} if budget is None else {"max_iter": int(budget)}
+            warm = b.solve(tol=tol, want_points=False, x0=xs, y0=ys, omega0=ws, **wkw)
             ci = np.array([r["iters"] for r in cold])
             wi = np.array([r["iters"] for r in warm])
+            over = np.array([r["status"] != 0 for r in warm]) if budget is not None else np.zeros(len(lps), bool)
+            wi = np.where(over, wi + ci, wi)
+            if budget is not None:
+                warm = [c if o else w for w, c, o in zip(warm, cold, over)]
             out[f"{tol:.0e}"] = dict(
                 cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()),
                 iters_ratio=float(ci.mean() / max(wi.mean(), 1e-9)),
@@ -109,7 +118,8 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), **params):
                 time_ratio=cold[0]["device_ms"] / max(warm[0]["device_ms"], 1e-9),
                 cold_optimal=int(sum(r["status"] == 0 for r in cold)),
                 warm_optimal=int(sum(r["status"] == 0 for r in warm)),
-                warm_fewer_iters=int(np.sum(wi < ci)), warm_more_iters=int(np.sum(wi > ci)))
+                warm_fewer_iters=int(np.sum(wi < ci)), warm_more_iters=int(np.sum(wi > ci)),
+                fell_back_after_budget=int(over.sum()))
     out["used_prediction"] = int(use.sum())
     out["initial_err_cold_median"] = float(np.median(e_cold))
     out["initial_err_pred_median"] = float(np.median(e_pred))
