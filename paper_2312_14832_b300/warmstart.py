@@ -107,6 +107,7 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
             warm = b.solve(tol=tol, want_points=False, x0=xs, y0=ys, omega0=ws, **wkw)
             ci = np.array([r["iters"] for r in cold])
             wi = np.array([r["iters"] for r in warm])
+            warm_ms = warm[0]["device_ms"]
             over = np.array([r["status"] != 0 for r in warm]) if budget is not None else np.zeros(len(lps), bool)
             wi = np.where(over, wi + ci, wi)
             if budget is not None:
@@ -114,8 +115,8 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
             out[f"{tol:.0e}"] = dict(
                 cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()),
                 iters_ratio=float(ci.mean() / max(wi.mean(), 1e-9)),
-                cold_device_s=cold[0]["device_ms"] * 1e-3, warm_device_s=warm[0]["device_ms"] * 1e-3,
-                time_ratio=cold[0]["device_ms"] / max(warm[0]["device_ms"], 1e-9),
+                cold_device_s=cold[0]["device_ms"] * 1e-3, warm_device_s=warm_ms * 1e-3,
+                time_ratio=cold[0]["device_ms"] / max(warm_ms, 1e-9),
                 cold_optimal=int(sum(r["status"] == 0 for r in cold)),
                 warm_optimal=int(sum(r["status"] == 0 for r in warm)),
                 warm_fewer_iters=int(np.sum(wi < ci)), warm_more_iters=int(np.sum(wi > ci)),
