@@ -48,6 +48,8 @@ extern "C" {
                                NaN value, l > u, m1 > m, bad parameter */
 #define PDLP_ENOMEM (-2)    /* device or host allocation failed */
 #define PDLP_ECUDA (-3)     /* a CUDA runtime call failed (message in pdlp_last_error) */
+#define PDLP_ETIMEOUT (-4)  /* a bounded device-side wait gave up (spin limit); the kernel
+                               set its error flag and returned, the context stays usable */
 #define PDLP_EINTERNAL (-5) /* internal consistency check failed */
 
 /* solve outcome (pdlp_result.status) */
@@ -233,6 +235,13 @@ int64_t pdlp_get_log(pdlp_handle h, pdlp_check_record* rec, int64_t cap);
  * back on the way out; with scaling off the kernels see the input values as given). */
 int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out);
 
+/* Bound duals lambda = proj_Lambda(c - K'y) of a dual point y (Section 2: Lambda_j is
+ * {0}, R^-, R^+ or R as l_j, u_j are infinite or finite), on the original (unscaled)
+ * problem; the solver does not return lambda with the point.  y: m host doubles (device
+ * when params.inputs_on_device), lambda_out: n host doubles.  Single-LP handles only.
+ * Errors: PDLP_EINVAL (NULL pointers, batch handle), PDLP_ECUDA. */
+int pdlp_bound_duals(pdlp_handle h, const double* y, double* lambda_out);
+
 /* Layout, step size and byte model of the handle. */
 int pdlp_get_info(pdlp_handle h, pdlp_info* info);
 
@@ -283,7 +292,7 @@ int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, const double* x0, cons
  * device array, bias FP32 device array or NULL.  M and N multiples of 128, K a multiple
  * of 64.  Used by the learned warm start (a spec extension: the paper has no
  * learned component); exposed for testing.  Runs on `stream` (NULL = default) and
- * waits for it.  Errors: PDLP_EINVAL (shapes), PDLP_ECUDA, PDLP_EINTERNAL (an internal
+ * waits for it.  Errors: PDLP_EINVAL (shapes), PDLP_ECUDA, PDLP_ETIMEOUT (an mbarrier
  * wait gave up). */
 int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
                  int32_t relu, void* stream);

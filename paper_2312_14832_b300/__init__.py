@@ -151,6 +151,13 @@ class Solver:
         self._check(self._lib.pdlp_spmv(self._h, 1 if transpose else 0, a.ptr, self._ptr(out)))
         return out
 
+    def bound_duals(self, y):
+        """lambda = proj_Lambda(c - K'y) on the original problem (the solver returns x, y)."""
+        a = _Arg(y, np.float64, self.device) if self.m else None
+        out = self._out(self.n)
+        self._check(self._lib.pdlp_bound_duals(self._h, a.ptr if a else None, self._ptr(out)))
+        return out
+
     def info(self) -> dict:
         i = _lib.Info()
         self._check(self._lib.pdlp_get_info(self._h, C.byref(i)))

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pdlp_get_restarts": (C.c_int64, [_vp, _vp, _i64]),
     "pdlp_get_log": (C.c_int64, [_vp, C.POINTER(CheckRecord), _i64]),
     "pdlp_spmv": (C.c_int, [_vp, _i32, _vp, _vp]),
+    "pdlp_bound_duals": (C.c_int, [_vp, _vp, _vp]),
     "pdlp_get_info": (C.c_int, [_vp, C.POINTER(Info)]),
     "pdlp_time_iterations": (C.c_int, [_vp, _i64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pdlp_spmv_csr_noalloc": (C.c_int, [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),

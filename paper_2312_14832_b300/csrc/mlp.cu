@@ -62,7 +62,7 @@ extern "C" int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, cons
   }
   if (herr) {
     set_thread_error("pdlp_tc_gemm: an mbarrier wait gave up (spin limit)");
-    return PDLP_EINTERNAL;
+    return PDLP_ETIMEOUT;
   }
   return PDLP_OK;
 }

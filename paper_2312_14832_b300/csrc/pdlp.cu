@@ -269,6 +269,23 @@ __global__ void k_scale_sell2(double* v, const int32_t* col, const int32_t* chun
   }
 }
 
+// Bound duals in scaled, internal order: lam = proj_Lambda(c - g) (Section 2: Lambda_j is
+// {0}, R^-, R^+ or R as l_j, u_j are infinite or finite); positive scalings keep the cone.
+__global__ void k_bound_duals(double* lam, const double* c, const double* g, const double* l, const double* u,
+                              int64_t n) {
+  PDLP_GRID_STRIDE(j, n) {
+    const double d = c[j] - g[j];
+    const bool lf = !is_neg_inf(l[j]), uf = !is_pos_inf(u[j]);
+    const bool neg = __double2hiint(d) < 0;
+    double v;
+    if (lf && uf) v = d;
+    else if (lf) v = neg ? 0.0 : d;
+    else if (uf) v = neg ? d : 0.0;
+    else v = 0.0;
+    lam[j] = v;
+  }
+}
+
 // dst = average of the inner loop (sum * 1/t), or the current iterate when t = 0
 __global__ void k_average(double* dst, const double* sum, const double* cur, const DevState* st, int64_t n) {
   const bool empty = st->t == 0;
@@ -1763,6 +1780,21 @@ int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out) {
       copy_out(h, out, h->stage_n, h->n);
     }
     CKL("pdlp_spmv");
+    CK(cudaStreamSynchronize(h->s));
+    return PDLP_OK;
+  });
+}
+
+int pdlp_bound_duals(pdlp_handle h, const double* y, double* lambda_out) {
+  return guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle");
+    if (!lambda_out || (h->m > 0 && !y)) invalid("null array");
+    if (h->m > 0) copy_in(h, h->stage_m, y, h->m);
+    k_permute_in<<<grid_for(h->mpad), 256, 0, h->s>>>(h->tm, h->stage_m, h->perm_r, h->Dr, h->mpad, 0.0);
+    launch_rows<OpSpmv>(h, h->Kt, h->tm, EpiStore{h->g_a, 0, 1.0}, nullptr);
+    k_bound_duals<<<grid_for(h->npad), 256, 0, h->s>>>(h->tn, h->c, h->g_a, h->l, h->u, h->npad);
+    k_unpermute_scale<<<grid_for(h->n), 256, 0, h->s>>>(h->stage_n, h->tn, h->invDc, h->pos_c, h->n);
+    copy_out(h, lambda_out, h->stage_n, h->n);
     CK(cudaStreamSynchronize(h->s));
     return PDLP_OK;
   });

@@ -197,3 +197,26 @@ def test_invalid_inputs_are_rejected(pk):
     bad["val"][0] = np.nan
     with pytest.raises(pk.SolverError):
         pk.Solver.from_lp(bad)
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_bound_duals(pk, scaling):
+    """pdlp_bound_duals: lambda = proj_Lambda(c - K'y) on the original problem, for any y
+    (the oracle's projection applied to a scipy product), and at the solution the
+    reduced costs that the dual residual test of Section 2 measures."""
+    import scipy.sparse as sp
+    lp = lpgen.planted_small(4)
+    K = sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(lp["m"], lp["n"]))
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal(lp["m"])
+    with pk.Solver.from_lp(lp, scaling=scaling) as s:
+        lam = s.bound_duals(y)
+        r = s.solve(tol=1e-8)
+        lam_sol = s.bound_duals(r["y"])
+    d = lp["c"] - K.T @ y
+    want = np.array([oracle.proj_lambda(dj, lj, uj) for dj, lj, uj in zip(d, lp["l"], lp["u"])])
+    bound = 1e-13 * (np.abs(lp["c"]) + abs(K).T @ np.abs(y)) + 1e-300
+    near = np.abs(d) <= bound          # sign decided by rounding: either side is right
+    assert np.all((np.abs(lam - want) <= bound) | near)
+    rd = np.linalg.norm(lp["c"] - K.T @ r["y"] - lam_sol) / (1 + np.linalg.norm(lp["c"]))
+    assert rd <= 1e-8 * (1 + 1e-6)
