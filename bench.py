@@ -507,6 +507,12 @@ def bench_warmstart(args):
     print(f"training: {fit['train_device_s']:.1f} s device", file=sys.stderr, flush=True)
     Ph = np.array([lp["features"] for lp in held])
     ev = ws.evaluate(model, held, Ph, tols=tuple(float(t) for t in args.ws_tols.split(",")))
+    if args.ws_tols_hi:
+        k = min(args.ws_heldout_hi, len(held))
+        ev_hi = ws.evaluate(model, held[:k], Ph[:k], tols=tuple(float(t) for t in args.ws_tols_hi.split(",")))
+        for key, val in ev_hi.items():
+            if key.startswith("1e") or key[0].isdigit():
+                ev[key] = dict(val, heldout=k)
     model.close()
     n_in, hid, n_out = P.shape[1], 1024, train[0]["n"] + train[0]["m"] + 1
     flop_step = 2 * 256 * (n_in * hid + hid * hid + hid * n_out) * 3
@@ -560,6 +566,8 @@ def main():
     ap.add_argument("--ws-train-mixed", type=int, default=0, help="training solves with FP32 iterations")
     ap.add_argument("--ws-chunk", type=int, default=4096, help="LPs per batched launch of the training solves")
     ap.add_argument("--ws-tols", default="1e-4,1e-8")
+    ap.add_argument("--ws-tols-hi", default="", help="tolerances evaluated on the first --ws-heldout-hi LPs only")
+    ap.add_argument("--ws-heldout-hi", type=int, default=300)
     ap.add_argument("--ws-supplies", type=int, default=40)
     ap.add_argument("--ws-demands", type=int, default=60)
     args = ap.parse_args()
