@@ -136,6 +136,16 @@ enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
 #ifndef PDLP_BATCH_LOADS
 #define PDLP_BATCH_LOADS 4
 #endif
+// CTAs per SM the register allocation is sized for.  The one-CTA-per-LP FP64 kernel is
+// latency-bound and gains from a third CTA even with the register spills that brings
+// (2048 planted LPs: 5.73 s -> 4.90 s); the FP32 kernel loses (4.49 s -> 6.47 s) and the
+// cluster kernels lose a few per cent, so they keep two.
+#ifndef PDLP_BATCH_MIN_BLOCKS
+#define PDLP_BATCH_MIN_BLOCKS 3
+#endif
+#ifndef PDLP_BATCH32_MIN_BLOCKS
+#define PDLP_BATCH32_MIN_BLOCKS 2
+#endif
 constexpr int kBB = PDLP_BATCH_LOADS;
 template <int SRC, bool kMatS, class F>
 __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
@@ -1036,7 +1046,7 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
 }
 
 template <bool kCl, bool kGlob>
-__global__ void __launch_bounds__(256, 2) k_batch_solve32(BatchArgs A) {
+__global__ void __launch_bounds__(256, PDLP_BATCH32_MIN_BLOCKS) k_batch_solve32(BatchArgs A) {
   __shared__ int lp;
   Team<kCl> T;
   T.init();
@@ -1058,7 +1068,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_solve32(BatchArgs A) {
 // Persistent solver: teams draw LPs from the queue until it is empty.  The counter
 // resets itself: the last of the failing draws (one per team) stores 0.
 template <bool kCl, bool kRes, bool kGlob>
-__global__ void __launch_bounds__(256, 2) k_batch_solve(BatchArgs A) {
+__global__ void __launch_bounds__(256, kCl ? 2 : PDLP_BATCH_MIN_BLOCKS) k_batch_solve(BatchArgs A) {
   __shared__ int lp;
   Team<kCl> T;
   T.init();
