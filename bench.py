@@ -159,8 +159,10 @@ class Clocks:
 
 def time_to_tol_small(pk, seed=0):
     """Cold-start time to 1e-4 and 1e-8 relative KKT on the small planted LP (m1=200,
-    m2=300, n=1000, nnz=5000): GPU (device time of pdlp_solve, CUDA events) and the CPU
-    oracle (wall time of the whole oracle solve, single thread)."""
+    m2=300, n=1000, nnz=5000): GPU (device time of pdlp_solve, CUDA events; the automatic
+    engine is the persistent one for this LP, engine 1 the kernels launched per
+    iteration), the batched solver with one LP, and the CPU oracle (wall time of the
+    whole oracle solve, single thread)."""
     import lpgen
     import oracle
     lp = lpgen.planted_small(seed)
@@ -176,8 +178,11 @@ def time_to_tol_small(pk, seed=0):
                                             "rel_obj_err_vs_planted": abs(r["primal_obj"] - lp["obj_star"]) /
                                             abs(lp["obj_star"])}
     with pk.Solver.from_lp(lp) as s:
-        s.solve(tol=1e-4, want_point=False)   # warm-up (graph capture)
+        s.solve(tol=1e-4, want_point=False, engine=1)   # warm-up (graph capture)
         for tol in (1e-4, 1e-8):
+            rk = s.solve(tol=tol, want_point=False, engine=1)
+            out[f"kernels_{tol:.0e}"] = {"gpu_s": rk["device_ms"] * 1e-3, "gpu_wall_s": rk["solve_s"],
+                                         "iters": rk["iters"], "note": "engine 1: kernels launched per iteration"}
             r = s.solve(tol=tol, want_point=False)
             t0 = time.perf_counter()
             ref = oracle.solve(lp, tol=tol)

@@ -120,7 +120,14 @@ typedef struct {
                               scaled K (or params.eta); averages are weighted by the kept
                               steps' eta; iteration counts (max_iter, check_every, iters)
                               count attempts.  Not with PDLP_MIXED; not for batches.       */
-  int32_t reserved1;       /* must be 0                                                     */
+  int32_t engine;          /* pdlp_solve: 0 = automatic (the persistent engine for an LP of at
+                              most 2^18 nonzeros whose x and y fit in one CTA's shared
+                              memory, FP64 with the constant step and no time limit; the
+                              kernels launched per iteration otherwise), 1 = kernels per
+                              iteration, 2 = persistent engine (PDLP_EINVAL when the LP does
+                              not qualify).  The persistent engine is the batched solver on
+                              the handle's own data: one thread-block cluster runs the
+                              whole solve in one launch.                                   */
   int64_t batch_tail_iters; /* pdlp_batch_solve: > 0 runs the batch in two stages: every LP
                               stops (resumably, at a check) after this many iterations; the
                               LPs that did not finish then continue in a second launch with

@@ -67,6 +67,11 @@ struct BatchArgs {
   // shared by the team, gathered through L2
   double *xg, *yg;
   float *xg32, *yg32;
+  // one LP run for a single-LP handle: its current point at the end, its restart
+  // iterations and check records (null for batches)
+  double *xcur, *ycur;
+  long long* restarts;
+  CheckRecord* log;
 };
 
 constexpr int kMaxTeam = 16;                         // CTAs per LP (non-portable cluster size)
@@ -681,7 +686,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       S.k = k;
       S.t = t;
       S.inv_t = it;
-      decide_core(tot, &S, P, k >= A.max_iter, nullptr);
+      const long long nc = S.ncheck;
+      const CheckRecord rec = decide_core(tot, &S, P, k >= A.max_iter, T.rank == 0 ? A.restarts : nullptr);
+      if (A.log != nullptr && T.rank == 0 && nc < P.log_cap) A.log[nc] = rec;
     }
     __syncthreads();
     if (S.done) break;
@@ -735,6 +742,10 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   const double it = t > 0 ? 1.0 / (double)t : 0.0;
   for (int j = jc0 + tid; j < jc1; j += nt) A.xout[D.c0 + j] = avg ? A.sx[D.c0 + j] * it : xs[j];
   for (int i = ir0 + tid; i < ir1; i += nt) A.yout[D.r0 + i] = avg ? A.sy[D.r0 + i] * it : ys[i];
+  if (A.xcur != nullptr) {
+    for (int j = jc0 + tid; j < jc1; j += nt) A.xcur[D.c0 + j] = xs[j];
+    for (int i = ir0 + tid; i < ir1; i += nt) A.ycur[D.r0 + i] = ys[i];
+  }
   if (tid == 0 && T.rank == 0) A.st[b] = S;
   T.sync();   // no CTA writes the next LP into a replica (or slice) that is still being read
 }

@@ -125,6 +125,7 @@ struct pdlp_ctx {
   bool last_resident = false;
   bool last_glob = false;
   int32_t* order2 = nullptr; // queue of the second stage (LPs stopped by the slice)
+  bool small_engine = false; // single-LP handle that can run the persistent engine
   bool batch_glob = false;   // x and y of the largest LP do not fit in shared memory
   size_t glob_smem = 0;      // shared memory of a launch with global iterates
   double *xg = nullptr, *yg = nullptr;      // global iterates (allocated on first use)
@@ -533,7 +534,7 @@ static void check_params(const pdlp_params& P) {
   if (P.cluster_ctas < 0 || P.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
   if (P.resident < 0 || P.resident > 3) invalid("resident must be 0, 1, 2 or 3");
   if (P.step_rule < 0 || P.step_rule > 1) invalid("step_rule must be 0 or 1");
-  if (P.reserved1 != 0) invalid("reserved1 must be 0");
+  if (P.engine < 0 || P.engine > 2) invalid("engine must be 0, 1 or 2");
 }
 
 // Copies (from host or device) and validates one LP in CSR form; rows_total and the
@@ -607,6 +608,10 @@ struct Layout {
 // Appends the layout of one LP (rows rp[rp0..rp0+m], entries from nnz0, columns
 // [col0, col0 + n) of the caller's concatenated vectors) to L at internal offsets
 // L.mpad / L.npad, and pads both to a multiple of 32 (at least 32).
+// Single-LP handles up to this many nonzeros get the persistent engine (when x and y fit
+// in one CTA's shared memory and no row is wide).
+constexpr int64_t kSmallEngineNnz = (int64_t)1 << 18;
+
 // Rows at least this long that are more than 4 times longer than the next row in
 // length order are stored as wide rows (layout.h).
 constexpr int64_t kWideMin = 1024;
@@ -716,6 +721,10 @@ static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const 
                                 const double* l_in, const double* u_in);
 static void estimate_step_and_weight(pdlp_ctx* h);
 static void setup_mixed(pdlp_ctx* h);
+static void init_batch_launch(pdlp_ctx* h, const Layout& Lo, int64_t npad_max, int64_t mpad_max);
+static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0,
+                            const double* omega0, pdlp_result* res, double* x_out, double* y_out, bool single,
+                            double omega0_single);
 
 static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr_in,
                        const int32_t* col_in, const double* val_in, const double* c_in,
@@ -767,6 +776,32 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   estimate_step_and_weight(h);
   if (P.precision == PDLP_MIXED) setup_mixed(h);
   else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
+  // persistent engine for a small LP: the batched kernel on this handle's own layout and
+  // vectors (same internal order when no row is wide), x and y in shared memory
+  h->small_engine = false;
+  if (P.engine != 1 && P.precision == PDLP_FP64 && h->K.nwide == 0 && h->nnz <= kSmallEngineNnz) {
+    LpDesc D{};
+    D.m = (int32_t)m;
+    D.n = (int32_t)n;
+    D.m1 = (int32_t)h->m1_int;
+    D.kc0 = 0;
+    D.kc1 = (int32_t)Lo.SK.nchunks;
+    D.tc0 = 0;
+    D.tc1 = (int32_t)Lo.SKt.nchunks;
+    D.r0 = 0;
+    D.c0 = 0;
+    D.mpad = (int32_t)Lo.mpad;
+    D.npad = (int32_t)Lo.npad;
+    h->hdesc.assign(1, D);
+    h->count = 1;
+    try {
+      init_batch_launch(h, Lo, Lo.npad, Lo.mpad);
+      h->small_engine = !h->batch_glob;
+    } catch (const std::string&) {
+      h->small_engine = false;   // the kernels launched per iteration remain
+    }
+  }
+  if (P.engine == 2 && !h->small_engine) invalid("engine 2: this LP does not fit the persistent engine");
 }
 
 // FP32 copies of the scaled matrix values and problem vectors, FP32 iterates.
@@ -1007,6 +1042,19 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   if (adaptive && h->p.precision == PDLP_MIXED) invalid("the adaptive step rule runs in FP64 only");
   if (adaptive) ensure_adaptive_buffers(h);
   if (!adaptive && !h->power_done) power_step(h);
+  if (sp.engine < 0 || sp.engine > 2) invalid("engine must be 0, 1 or 2");
+  {
+    // the persistent engine: automatic for a small LP with the constant step in FP64 and
+    // no time limit, or when asked for
+    const bool can = h->small_engine && !adaptive && h->p.precision == PDLP_FP64;
+    if (sp.engine == 2 && !can) invalid("engine 2 needs a small FP64 LP with the constant step");
+    if (can && (sp.engine == 2 || (sp.engine == 0 && !std::isfinite(sp.time_limit_s)))) {
+      pdlp_params bp = sp;
+      bp.resident = 0;
+      bp.batch_tail_iters = 0;
+      return batch_solve_impl(h, bp, x0, y0, nullptr, res, x_out, y_out, true, omega0);
+    }
+  }
   auto t_start = std::chrono::steady_clock::now();
   const int64_t n = h->n, m = h->m, np = h->npad, mp = h->mpad;
   int64_t launches = 0;
@@ -1211,12 +1259,76 @@ static int guarded(pdlp_ctx* h, F&& f) {
   }
 }
 
-}  // namespace pdlp
 
 // ------------------------------------------------------------------ batches
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchRed = NQ * (1 + kBatchThreads / 32);   // block_sum scratch (doubles)
+
+// Launch resources of the persistent batched kernel for the h->count LPs described by
+// h->hdesc over the layout Lo: shared-memory plan, kernel attributes, occupancy, the
+// queue (largest LP first) and the per-LP state and output arrays.
+static void init_batch_launch(pdlp_ctx* h, const Layout& Lo, int64_t npad_max, int64_t mpad_max) {
+  const int64_t count = h->count;
+  // shared memory per CTA: x and y of the largest LP plus the reduction scratch; when
+  // they do not fit, the iterates go to global memory (one copy per LP)
+  h->xs_off = 0;
+  h->ys_off = (int)npad_max;
+  h->red_off = (int)(npad_max + mpad_max);
+  h->part_off = h->red_off + kBatchRed;
+  h->batch_smem = (size_t)(npad_max + mpad_max + kBatchRed + kPartBuf) * sizeof(double);
+  h->glob_smem = (size_t)(kBatchRed + kPartBuf) * sizeof(double);
+  int dev_smem = 0;
+  CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+  int static_max = 0;
+  const void* kernels[] = {(const void*)k_batch_solve<false, false, false>, (const void*)k_batch_solve<false, true, false>,
+                           (const void*)k_batch_solve<true, false, false>,  (const void*)k_batch_solve<true, true, false>,
+                           (const void*)k_batch_solve<false, false, true>,  (const void*)k_batch_solve<true, false, true>,
+                           (const void*)k_batch_solve32<false, false>,      (const void*)k_batch_solve32<true, false>,
+                           (const void*)k_batch_solve32<false, true>,       (const void*)k_batch_solve32<true, true>};
+  for (const void* f : kernels) {
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, f));
+    static_max = std::max(static_max, (int)fa.sharedSizeBytes);
+  }
+  const int smem_cap = dev_smem - static_max;
+  h->batch_glob = smem_cap < (int)h->batch_smem;
+  h->dev_smem_optin = smem_cap;
+  for (const void* f : kernels) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
+  for (int i = 2; i < 10; ++i)
+    if (i != 4 && i != 6 && i != 8)   // the cluster (team) kernels
+      CK(cudaFuncSetAttribute(kernels[i], cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  h->hk_cptr = Lo.SK.chunk_ptr;
+  h->ht_cptr = Lo.SKt.chunk_ptr;
+  int per_sm = 0, sms = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, h->batch_glob ? (const void*)k_batch_solve<false, false, true> : (const void*)k_batch_solve<false, false, false>,
+      kBatchThreads, h->batch_glob ? h->glob_smem : h->batch_smem));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+  if (per_sm < 1) invalid("batched kernel does not fit on an SM");
+  h->batch_resident = per_sm * sms;
+  h->batch_grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
+  h->team_npad_max = npad_max;
+
+  // queue order: largest LP (most nonzeros) first
+  std::vector<int32_t> ord((size_t)count);
+  for (int64_t b = 0; b < count; ++b) ord[(size_t)b] = (int32_t)b;
+  std::vector<int64_t> work((size_t)count);
+  for (int64_t b = 0; b < count; ++b) {
+    const LpDesc& D = h->hdesc[(size_t)b];
+    std::vector<int32_t> dummy;
+    work[(size_t)b] = (int64_t)(Lo.SK.chunk_ptr[(size_t)D.kc1] - Lo.SK.chunk_ptr[(size_t)D.kc0]) + D.mpad + D.npad;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b2) { return work[(size_t)a] > work[(size_t)b2]; });
+  h->desc = upload(h, h->hdesc);
+  h->order = upload(h, ord);
+  h->next = dalloc<int32_t>(h, 1);
+  h->bstate = dalloc<DevState>(h, (size_t)count);
+  h->bx = dalloc<double>(h, h->npad);
+  h->by = dalloc<double>(h, h->mpad);
+  h->hstate.resize((size_t)count);
+  CK(cudaStreamSynchronize(h->s));
+}
 
 static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, const int64_t* n_in,
                              const int64_t* m1_in, const int64_t* row_ptr_in, const int32_t* col_in,
@@ -1302,65 +1414,9 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   }
   device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
 
-  // shared memory per CTA: x and y of the largest LP plus the reduction scratch; when
-  // they do not fit, the iterates go to global memory (one copy per LP)
-  h->xs_off = 0;
-  h->ys_off = (int)npad_max;
-  h->red_off = (int)(npad_max + mpad_max);
-  h->part_off = h->red_off + kBatchRed;
-  h->batch_smem = (size_t)(npad_max + mpad_max + kBatchRed + kPartBuf) * sizeof(double);
-  h->glob_smem = (size_t)(kBatchRed + kPartBuf) * sizeof(double);
-  int dev_smem = 0;
-  CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-  int static_max = 0;
-  const void* kernels[] = {(const void*)k_batch_solve<false, false, false>, (const void*)k_batch_solve<false, true, false>,
-                           (const void*)k_batch_solve<true, false, false>,  (const void*)k_batch_solve<true, true, false>,
-                           (const void*)k_batch_solve<false, false, true>,  (const void*)k_batch_solve<true, false, true>,
-                           (const void*)k_batch_solve32<false, false>,      (const void*)k_batch_solve32<true, false>,
-                           (const void*)k_batch_solve32<false, true>,       (const void*)k_batch_solve32<true, true>};
-  for (const void* f : kernels) {
-    cudaFuncAttributes fa;
-    CK(cudaFuncGetAttributes(&fa, f));
-    static_max = std::max(static_max, (int)fa.sharedSizeBytes);
-  }
-  const int smem_cap = dev_smem - static_max;
-  h->batch_glob = smem_cap < (int)h->batch_smem;
-  h->dev_smem_optin = smem_cap;
-  for (const void* f : kernels) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap));
-  for (int i = 2; i < 10; ++i)
-    if (i != 4 && i != 6 && i != 8)   // the cluster (team) kernels
-      CK(cudaFuncSetAttribute(kernels[i], cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  h->hk_cptr = Lo.SK.chunk_ptr;
-  h->ht_cptr = Lo.SKt.chunk_ptr;
+  init_batch_launch(h, Lo, npad_max, mpad_max);
   if (P.precision == PDLP_MIXED) setup_mixed(h);
   else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
-  int per_sm = 0, sms = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, h->batch_glob ? (const void*)k_batch_solve<false, false, true> : (const void*)k_batch_solve<false, false, false>,
-      kBatchThreads, h->batch_glob ? h->glob_smem : h->batch_smem));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
-  if (per_sm < 1) invalid("batched kernel does not fit on an SM");
-  h->batch_resident = per_sm * sms;
-  h->batch_grid = (int)std::min<int64_t>((int64_t)per_sm * sms, count);
-  h->team_npad_max = npad_max;
-
-  // queue order: largest LP (most nonzeros) first
-  std::vector<int32_t> ord((size_t)count);
-  for (int64_t b = 0; b < count; ++b) ord[(size_t)b] = (int32_t)b;
-  std::vector<int64_t> work((size_t)count);
-  for (int64_t b = 0; b < count; ++b) {
-    const LpDesc& D = h->hdesc[(size_t)b];
-    std::vector<int32_t> dummy;
-    work[(size_t)b] = (int64_t)(Lo.SK.chunk_ptr[(size_t)D.kc1] - Lo.SK.chunk_ptr[(size_t)D.kc0]) + D.mpad + D.npad;
-  }
-  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b2) { return work[(size_t)a] > work[(size_t)b2]; });
-  h->desc = upload(h, h->hdesc);
-  h->order = upload(h, ord);
-  h->next = dalloc<int32_t>(h, 1);
-  h->bstate = dalloc<DevState>(h, (size_t)count);
-  h->bx = dalloc<double>(h, h->npad);
-  h->by = dalloc<double>(h, h->mpad);
-  h->hstate.resize((size_t)count);
   CK(cudaStreamSynchronize(h->s));
 }
 
@@ -1502,8 +1558,12 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp
   CKL("k_batch_solve");
 }
 
+// single: one LP of a single-LP handle through the persistent engine (omega0_single is
+// its initial primal weight, <= 0 for the handle's ω₀; the current point, restarts and
+// check records go to the handle's own arrays).
 static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0,
-                            const double* omega0, pdlp_result* res, double* x_out, double* y_out) {
+                            const double* omega0, pdlp_result* res, double* x_out, double* y_out, bool single,
+                            double omega0_single) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   if (sp.cluster_ctas < 0 || sp.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
   if (sp.resident < 0 || sp.resident > 3) invalid("resident must be 0, 1, 2 or 3");
@@ -1529,6 +1589,9 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
     copy_in(h, h->bomega, omega0, h->count);
     A.omega0 = h->bomega;
   }
+  A.xcur = A.ycur = nullptr;
+  A.restarts = nullptr;
+  A.log = nullptr;
   A.desc = h->desc;
   A.order = h->order;
   A.count = (int32_t)h->count;
@@ -1558,6 +1621,17 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.step_scale = h->p.step_scale;
   A.eta_fixed = h->p.eta;
   A.omega_fixed = 0.0;
+  if (single) {
+    // the same step size and primal weight as the launch-per-kernel path
+    A.eta_fixed = h->eta;
+    A.omega_fixed = omega0_single > 0.0 ? omega0_single : h->omega0;
+    A.xcur = h->x;
+    A.ycur = h->y;
+    A.restarts = h->restarts;
+    A.log = h->log;
+    A.P.log_cap = h->log_cap;
+    A.P.restart_cap = h->restart_cap;
+  }
   A.xs_off = h->xs_off;
   A.ys_off = h->ys_off;
   A.red_off = h->red_off;
@@ -1629,11 +1703,21 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
       r.device_ms = dev_ms;
       r.launches = 1 + (h->last_resumed > 0 ? 1 : 0);
       r.fp32_iters = S.k32;
+      r.accepted = S.k;
     }
+  }
+  if (single) {
+    // the handle's state as the launch-per-kernel path leaves it (averages, restart and
+    // check counts for pdlp_get_iterate / get_restarts / get_log)
+    CK(cudaMemcpy(h->st, h->hstate.data(), sizeof(DevState), cudaMemcpyHostToDevice));
+    h->last_ncheck = h->hstate[0].ncheck;
+    h->last_nrestart = h->hstate[0].nrestart;
   }
   h->solved = true;
   return PDLP_OK;
 }
+
+}  // namespace pdlp
 
 // ------------------------------------------------------------------ C ABI
 
@@ -1919,7 +2003,7 @@ int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, const double* x0, cons
   return guarded(h, [&]() {
     if (!h->is_batch) invalid("not a batch handle (use pdlp_solve)");
     pdlp_params sp = p ? *p : h->p;
-    return batch_solve_impl(h, sp, x0, y0, omega0, res, x_out, y_out);
+    return batch_solve_impl(h, sp, x0, y0, omega0, res, x_out, y_out, false, 0.0);
   });
 }
 

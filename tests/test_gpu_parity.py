@@ -87,10 +87,14 @@ def test_spmv_scaled_roundtrip(pk):
 
 # ---------------------------------------------------------------- iterates
 
-def _compare_iterates(pk, lp, iters, **params):
+def _compare_iterates(pk, lp, iters, engine=0, **params):
+    """engine 1: kernels launched per iteration (CUDA graphs); 2: the persistent engine
+    (one launch of the batched kernel on a thread-block cluster)."""
     ref = oracle.solve(lp, tol=0.0, max_iter=iters, **params)
-    with pk.Solver.from_lp(lp, scaling=params.get("scaling", 0)) as s:
+    with pk.Solver.from_lp(lp, scaling=params.get("scaling", 0), engine=engine) as s:
         r = s.solve(tol=0.0, max_iter=iters)
+        if engine == 2:
+            assert r["launches"] == 1
         assert r["iters"] == ref["iters"] == iters
         assert r["status"] == pk.ITER_LIMIT
         np.testing.assert_array_equal(s.restarts(), ref["restart_iters"])
@@ -107,10 +111,14 @@ def _compare_iterates(pk, lp, iters, **params):
     return r, ref
 
 
+ENGINES = [1, 2]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("seed", [0, 1, 2])
 @pytest.mark.parametrize("scaling", [0, 1])
-def test_iterates_after_1000_small_planted(pk, seed, scaling):
-    _compare_iterates(pk, lpgen.planted_small(seed), 1000, scaling=scaling)
+def test_iterates_after_1000_small_planted(pk, seed, scaling, engine):
+    _compare_iterates(pk, lpgen.planted_small(seed), 1000, engine=engine, scaling=scaling)
 
 
 def test_iterates_after_1000_zipf(pk):
@@ -118,28 +126,31 @@ def test_iterates_after_1000_zipf(pk):
     _compare_iterates(pk, lp, 1000, scaling=1)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("iters", [0, 1, 63, 64, 100])
-def test_iteration_counts_and_ragged_intervals(pk, iters):
-    _compare_iterates(pk, lpgen.planted_small(4), iters)
+def test_iteration_counts_and_ragged_intervals(pk, iters, engine):
+    _compare_iterates(pk, lpgen.planted_small(4), iters, engine=engine)
 
 
-def test_box_only_lp(pk):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_box_only_lp(pk, engine):
     lp = lpgen.box_only(3, n=100, free_frac=0.2)
     ref = oracle.solve(lp, tol=1e-10, max_iter=100000)
-    with pk.Solver.from_lp(lp) as s:
+    with pk.Solver.from_lp(lp, engine=engine) as s:
         r = s.solve(tol=1e-10, max_iter=100000)
     assert r["status"] == pk.OPTIMAL and r["iters"] == ref["iters"]
     close_rel(r["x"], ref["x"], 1e-12)
     assert r["eta"] == 1.0
 
 
-def test_warm_start_matches_oracle(pk):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_warm_start_matches_oracle(pk, engine):
     lp = lpgen.planted_small(6)
     rng = np.random.default_rng(0)
     x0 = lp["x_star"] + 0.1 * rng.standard_normal(lp["n"])
     y0 = lp["y_star"] + 0.1 * rng.standard_normal(lp["m"])
     ref = oracle.solve(lp, tol=0.0, max_iter=500, x0=x0, y0=y0)
-    with pk.Solver.from_lp(lp) as s:
+    with pk.Solver.from_lp(lp, engine=engine) as s:
         r = s.solve(x0=x0, y0=y0, tol=0.0, max_iter=500)
         xc, yc = s.iterate(0)
     close_rel(xc, ref["x_cur"], 1e-10)
@@ -150,10 +161,11 @@ def test_warm_start_matches_oracle(pk):
 
 @pytest.mark.parametrize("tol", [1e-4, 1e-8])
 @pytest.mark.parametrize("scaling", [0, 1])
-def test_objective_at_tolerance(pk, tol, scaling):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_objective_at_tolerance(pk, tol, scaling, engine):
     lp = lpgen.planted_small(0)
     ref = oracle.solve(lp, tol=tol, scaling=scaling)
-    with pk.Solver.from_lp(lp, scaling=scaling) as s:
+    with pk.Solver.from_lp(lp, scaling=scaling, engine=engine) as s:
         r = s.solve(tol=tol)
     assert r["status"] == pk.OPTIMAL
     assert r["iters"] == ref["iters"]
@@ -174,9 +186,10 @@ def test_tiny_lp_objective(pk, seed):
     assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
 
 
-def test_solves_are_deterministic(pk):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_solves_are_deterministic(pk, engine):
     lp = lpgen.planted_zipf(seed=7, n=8000, m=4000, nnz=80000)
-    with pk.Solver.from_lp(lp, scaling=1) as s:
+    with pk.Solver.from_lp(lp, scaling=1, engine=engine) as s:
         a = s.solve(tol=0.0, max_iter=700)
         b = s.solve(tol=0.0, max_iter=700)
         np.testing.assert_array_equal(a["x"], b["x"])
@@ -220,3 +233,22 @@ def test_bound_duals(pk, scaling):
     assert np.all((np.abs(lam - want) <= bound) | near)
     rd = np.linalg.norm(lp["c"] - K.T @ r["y"] - lam_sol) / (1 + np.linalg.norm(lp["c"]))
     assert rd <= 1e-8 * (1 + 1e-6)
+
+
+def test_engine_selection(pk):
+    """The persistent engine is chosen automatically for a small FP64 LP, not with the
+    adaptive rule, a time limit or mixed precision, and engine 2 is refused where it
+    cannot run."""
+    lp = lpgen.planted_small(1)
+    with pk.Solver.from_lp(lp) as s:
+        assert s.solve(tol=1e-4)["launches"] == 1
+        assert s.solve(tol=1e-4, engine=1)["launches"] > 1
+        assert s.solve(tol=1e-4, time_limit_s=100.0)["launches"] > 1
+        assert s.solve(tol=1e-4, step_rule=1)["launches"] > 1
+        with pytest.raises(pk.SolverError):
+            s.solve(tol=1e-4, engine=2, step_rule=1)
+    with pk.Solver.from_lp(lp, precision=pk.MIXED) as s:
+        assert s.solve(tol=1e-4)["launches"] > 1
+    big = lpgen.planted_zipf(seed=1, n=200000, m=100000, nnz=2000000)
+    with pytest.raises(pk.SolverError):
+        pk.Solver.from_lp(big, engine=2)
