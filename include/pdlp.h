@@ -260,12 +260,16 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info);
 int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual);
 
 /* ---------------------------------------------------------------- batches
- * Many independent LPs solved by one persistent kernel launch: each CTA of the launch
- * takes LPs from a queue (largest first) and runs the whole restarted PDHG of one LP
- * (power iteration for eta, iterations, checks, restarts, termination) with that
- * LP's x and y in shared memory.  Each LP must satisfy (n + m, each rounded up to a
- * multiple of 32) * 8 bytes + 5 KB <= the per-block shared-memory limit (about
- * 28,000 rows plus columns on this GPU). */
+ * Many independent LPs solved by one persistent kernel launch: each team of the launch
+ * (one CTA, or a thread-block cluster of up to 16 CTAs that split the LP's rows and
+ * columns; params.cluster_ctas) takes LPs from a queue (largest first) and runs the
+ * whole restarted PDHG of one LP (power iteration for eta, iterations, checks,
+ * restarts, termination).  x and y live in shared memory (a replica per CTA) when
+ * (n + m, each rounded up to a multiple of 32) * 8 bytes + 9 KB fits the per-block
+ * limit (about 27,000 rows plus columns), else in global memory (one copy per LP);
+ * params.resident selects this by hand.  params.precision = PDLP_MIXED runs FP32
+ * iterations with FP64 checks, the LPs it leaves unfinished continue in FP64;
+ * params.batch_tail_iters moves long-running LPs to a second launch on teams. */
 
 /* Sets up a batch of `count` LPs given back to back:
  *   m[count], n[count], m1[count] : host arrays of each LP's sizes (m1 <= m, n >= 1).
@@ -277,8 +281,7 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
  * omega0 are computed per LP inside the solve.  The same handle type as pdlp_setup;
  * free it with pdlp_free.  Single-LP calls on it (pdlp_solve, pdlp_get_iterate,
  * pdlp_time_iterations) return PDLP_EINVAL; pdlp_spmv applies the block-diagonal K.
- * Errors: PDLP_EINVAL (sizes, CSR, bounds; an LP too large for one CTA), PDLP_ENOMEM,
- * PDLP_ECUDA. */
+ * Errors: PDLP_EINVAL (sizes, CSR, bounds), PDLP_ENOMEM, PDLP_ECUDA. */
 int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const int64_t* n, const int64_t* m1,
                      const int64_t* row_ptr, const int32_t* col_idx, const double* val, const double* c,
                      const double* q, const double* l, const double* u, const pdlp_params* p);
@@ -286,7 +289,8 @@ int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const in
 /* Solves every LP of the batch from (x0, y0) projected onto X and Y (NULL = 0 for
  * every LP, the cold start) with initial primal weights omega0[count] (NULL or <= 0 =
  * ||c||/||q|| of the LP), using the tolerance, iteration limit, check interval and
- * restart factors of p (NULL = setup params; time_limit_s is not used).  x0 (sum n_b)
+ * restart factors of p (NULL = setup params; time_limit_s is not used; precision is the
+ * setup's).  x0 (sum n_b)
  * and y0 (sum m_b) are back to back in the caller's order, unscaled.  res[count]
  * receives one result per LP (solve_s and device_ms are those of the whole batch);
  * x_out and y_out (either may be NULL) receive the returned points, back to back. */
