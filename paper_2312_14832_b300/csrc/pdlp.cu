@@ -3,11 +3,14 @@
 //
 // pdlp_setup builds the length-sorted SELL-32 layout of K and K' on the host,
 // moves it to the device, scales (Ruiz + Pock-Chambolle) and estimates ||K||_2
-// with device kernels.  pdlp_solve runs the iteration as CUDA graphs, one graph
-// per check interval: check_every x (primal kernel, dual kernel) followed by the
-// check (three SpMVs, the KKT reductions, the restart decision and the restart
-// itself), all state on the device.  The host only launches graphs and reads a
-// small status record a few intervals behind the device.
+// with device kernels.  pdlp_solve has two engines.  The kernels launched per
+// iteration run as CUDA graphs, one graph per check interval: check_every x (primal
+// kernel, dual kernel) followed by the check (three SpMVs, the KKT reductions, the
+// restart decision and the restart itself), all state on the device; the host only
+// launches graphs and reads a small status record a few intervals behind the device.
+// The persistent engine (small LPs) runs the batched kernel of batch_kernel.cuh on the
+// handle's own arrays: one thread-block cluster, the whole solve in one launch.
+// pdlp_batch_setup / pdlp_batch_solve run many LPs through that kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -108,7 +111,7 @@ struct pdlp_ctx {
   cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
   int g_full_len = -1, g_rem_len = -1;
   std::vector<cudaEvent_t> timing_events;
-  // batch handles (pdlp_batch_setup): one block-diagonal layout, one LP per CTA
+  // batch handles (pdlp_batch_setup): one block-diagonal layout, one LP per team of CTAs
   bool is_batch = false;
   int64_t count = 0;
   LpDesc* desc = nullptr;
