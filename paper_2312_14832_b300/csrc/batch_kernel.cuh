@@ -151,6 +151,9 @@ enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
 #ifndef PDLP_BATCH32_MIN_BLOCKS
 #define PDLP_BATCH32_MIN_BLOCKS 2
 #endif
+#ifndef PDLP_BATCH32_GLOB_MIN_BLOCKS
+#define PDLP_BATCH32_GLOB_MIN_BLOCKS 3   // FP32 kernel with the iterates in global memory (300 transport LPs: 0.90 -> 0.81 ms per iteration)
+#endif
 constexpr int kBB = PDLP_BATCH_LOADS;
 template <int SRC, bool kMatS, class F>
 __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
@@ -192,6 +195,61 @@ __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, con
         if (j < nb) acc = fma(v[j], xv[j], acc);
     }
     epi((ch - cbase) * 32 + lane, acc);
+  }
+}
+
+// batch_rows with the epilogue split in two: pre(row) issues the loads of the row's
+// epilogue operands before the row's products (their latency overlaps the slot loop),
+// epi(row, sum, pre) finishes it; the next chunk's bounds are loaded ahead as well.
+template <int SRC, class Pre, class F>
+__device__ __forceinline__ void batch_rows_p(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
+                                             const double* __restrict__ val, int c0, int c1, int cbase,
+                                             int64_t base, const double* gsrc, const BatchArgs& A, Pre pre, F epi) {
+  extern __shared__ double bsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* xs = bsm + A.xs_off;
+  const double* ys = bsm + A.ys_off;
+  int ch = c0 + wid;
+  int s0 = 0, s1 = 0;
+  if (ch < c1) {
+    s0 = cptr[ch];
+    s1 = cptr[ch + 1];
+  }
+  for (; ch < c1; ch += nw) {
+    const int row = (ch - cbase) * 32 + lane;
+    const auto pv = pre(row);
+    int n0 = 0, n1 = 0;
+    if (ch + nw < c1) {
+      n0 = cptr[ch + nw];
+      n1 = cptr[ch + nw + 1];
+    }
+    double acc = 0.0;
+    for (int s = s0; s < s1; s += kBB) {
+      const int nb = min(kBB, s1 - s);
+      double v[kBB], xv[kBB];
+      int ci[kBB];
+#pragma unroll
+      for (int j = 0; j < kBB; ++j)
+        if (j < nb) {
+          v[j] = __ldcs(val + (size_t)(s + j) * 32 + lane);
+          ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
+        }
+#pragma unroll
+      for (int j = 0; j < kBB; ++j) {
+        xv[j] = 0.0;
+        if (j < nb) {
+          if (SRC == kSrcSmemX) xv[j] = xs[ci[j]];
+          else if (SRC == kSrcSmemY) xv[j] = ys[ci[j]];
+          else xv[j] = __ldcg(gsrc + ci[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kBB; ++j)
+        if (j < nb) acc = fma(v[j], xv[j], acc);
+    }
+    epi(row, acc, pv);
+    s0 = n0;
+    s1 = n1;
   }
 }
 
@@ -635,22 +693,44 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
     const bool at_limit = k >= A.max_iter;
     if (!at_limit) {
       const double tau = S.tau, sigma = S.sigma;
-      Tmul(true, nullptr, [&](int j, double gsum) {
+      // primal step (Section 2) on g = K'y of this CTA's columns
+      struct PreP { double c, l, u, sx, x; };
+      auto pre_p = [&](int j) {
         const int jl = j - jofs;
-        const double xn = clamp_box(fma(-tau, cv[jl] - gsum, xs[j]), lv[jl], uv[jl]);
+        return PreP{cv[jl], lv[jl], uv[jl], sxv[jl], xs[j]};
+      };
+      auto epi_p = [&](int j, double gsum, const PreP& p) {
+        const double xn = clamp_box(fma(-tau, p.c - gsum, p.x), p.l, p.u);
         put(xs, j, xn);
-        sxv[jl] = sxv[jl] + xn;
-      });
+        sxv[j - jofs] = p.sx + xn;
+      };
+      if constexpr (kRes)
+        Tmul(true, nullptr, [&](int j, double gsum) { epi_p(j, gsum, pre_p(j)); });
+      else if constexpr (kGlob)
+        batch_rows_p<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
+      else
+        batch_rows_p<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A, pre_p, epi_p);
       T.sync();
-      Kmul(true, nullptr, [&](int i, double v) {
+      // dual step with extrapolation (Section 2) on v = K x of this CTA's rows
+      struct PreD { double q, kx, y, sy; };
+      auto pre_d = [&](int i) {
         const int il = i - iofs;
-        const double e = qv[il] + kxv[il];
-        double yn = fma(sigma, fma(-2.0, v, e), ys[i]);
+        return PreD{qv[il], kxv[il], ys[i], syv[il]};
+      };
+      auto epi_d = [&](int i, double v, const PreD& p) {
+        const double e = p.q + p.kx;
+        double yn = fma(sigma, fma(-2.0, v, e), p.y);
         if (i >= D.m1) yn = max0(yn);
         put(ys, i, yn);
-        syv[il] = syv[il] + yn;
-        kxv[il] = v;
-      });
+        syv[i - iofs] = p.sy + yn;
+        kxv[i - iofs] = v;
+      };
+      if constexpr (kRes)
+        Kmul(true, nullptr, [&](int i, double v) { epi_d(i, v, pre_d(i)); });
+      else if constexpr (kGlob)
+        batch_rows_p<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
+      else
+        batch_rows_p<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A, pre_d, epi_d);
       T.sync();
       ++k;
       ++t;
@@ -777,6 +857,49 @@ __device__ __forceinline__ void batch_rows32(const int32_t* __restrict__ cptr, c
         if (j < nb) acc = fmaf(v[j], xv[j], acc);
     }
     epi((ch - cbase) * 32 + lane, acc);
+  }
+}
+
+// batch_rows32 with the epilogue operands and the next chunk's bounds loaded ahead.
+template <bool kGlobSrc, class Pre, class F>
+__device__ __forceinline__ void batch_rows32_p(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
+                                               const float* __restrict__ val, int c0, int c1, int cbase,
+                                               int64_t base, const float* src, Pre pre, F epi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int ch = c0 + wid;
+  int s0 = 0, s1 = 0;
+  if (ch < c1) {
+    s0 = cptr[ch];
+    s1 = cptr[ch + 1];
+  }
+  for (; ch < c1; ch += nw) {
+    const int row = (ch - cbase) * 32 + lane;
+    const auto pv = pre(row);
+    int n0 = 0, n1 = 0;
+    if (ch + nw < c1) {
+      n0 = cptr[ch + nw];
+      n1 = cptr[ch + nw + 1];
+    }
+    float acc = 0.0f;
+    for (int s = s0; s < s1; s += kBB) {
+      const int nb = min(kBB, s1 - s);
+      float v[kBB], xv[kBB];
+      int ci[kBB];
+#pragma unroll
+      for (int j = 0; j < kBB; ++j)
+        if (j < nb) {
+          v[j] = __ldcs(val + (size_t)(s + j) * 32 + lane);
+          ci[j] = __ldcs(col + (size_t)(s + j) * 32 + lane) - (int)base;
+        }
+#pragma unroll
+      for (int j = 0; j < kBB; ++j) xv[j] = j < nb ? (kGlobSrc ? __ldcg(src + ci[j]) : src[ci[j]]) : 0.0f;
+#pragma unroll
+      for (int j = 0; j < kBB; ++j)
+        if (j < nb) acc = fmaf(v[j], xv[j], acc);
+    }
+    epi(row, acc, pv);
+    s0 = n0;
+    s1 = n1;
   }
 }
 
@@ -936,22 +1059,35 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
     const bool at_limit = k >= A.max_iter;
     if (!at_limit) {
       const float tau = (float)S.tau, sigma = (float)S.sigma;
-      batch_rows32<kGlob>(A.t_cptr, A.t_col, A.t_val32, tr0, tr1, D.tc0, D.r0, yf, [&](int j, float gsum) {
-        const int64_t gj = D.c0 + j;
-        float xn = fmaf(-tau, A.c32[gj] - gsum, xf[j]);
-        xn = fminf(fmaxf(xn, A.l32[gj]), A.u32[gj]);
-        put(xf, j, xn);
-        A.sx32[gj] = A.sx32[gj] + xn;
-      });
+      struct PreP { float c, l, u, sx, x; };
+      batch_rows32_p<kGlob>(
+          A.t_cptr, A.t_col, A.t_val32, tr0, tr1, D.tc0, D.r0, yf,
+          [&](int j) {
+            const int64_t gj = D.c0 + j;
+            return PreP{A.c32[gj], A.l32[gj], A.u32[gj], A.sx32[gj], xf[j]};
+          },
+          [&](int j, float gsum, const PreP& p) {
+            float xn = fmaf(-tau, p.c - gsum, p.x);
+            xn = fminf(fmaxf(xn, p.l), p.u);
+            put(xf, j, xn);
+            A.sx32[D.c0 + j] = p.sx + xn;
+          });
       T.sync();
-      batch_rows32<kGlob>(A.k_cptr, A.k_col, A.k_val32, kr0, kr1, D.kc0, D.c0, xf, [&](int i, float v) {
-        const int64_t gi = D.r0 + i;
-        float yn = fmaf(sigma, fmaf(-2.0f, v, A.q32[gi] + A.kxp32[gi]), yf[i]);
-        if (i >= D.m1) yn = fmaxf(yn, 0.0f);
-        put(yf, i, yn);
-        A.sy32[gi] = A.sy32[gi] + yn;
-        A.kxp32[gi] = v;
-      });
+      struct PreD { float q, kx, y, sy; };
+      batch_rows32_p<kGlob>(
+          A.k_cptr, A.k_col, A.k_val32, kr0, kr1, D.kc0, D.c0, xf,
+          [&](int i) {
+            const int64_t gi = D.r0 + i;
+            return PreD{A.q32[gi], A.kxp32[gi], yf[i], A.sy32[gi]};
+          },
+          [&](int i, float v, const PreD& p) {
+            float yn = fmaf(sigma, fmaf(-2.0f, v, p.q + p.kx), p.y);
+            if (i >= D.m1) yn = fmaxf(yn, 0.0f);
+            put(yf, i, yn);
+            const int64_t gi = D.r0 + i;
+            A.sy32[gi] = p.sy + yn;
+            A.kxp32[gi] = v;
+          });
       T.sync();
       ++k;
       ++t;
@@ -1057,7 +1193,8 @@ __device__ void batch_solve_one32(const BatchArgs& A, int b, const Team<kCl>& T)
 }
 
 template <bool kCl, bool kGlob>
-__global__ void __launch_bounds__(256, PDLP_BATCH32_MIN_BLOCKS) k_batch_solve32(BatchArgs A) {
+__global__ void __launch_bounds__(256, (kGlob && !kCl) ? PDLP_BATCH32_GLOB_MIN_BLOCKS : PDLP_BATCH32_MIN_BLOCKS)
+    k_batch_solve32(BatchArgs A) {
   __shared__ int lp;
   Team<kCl> T;
   T.init();
