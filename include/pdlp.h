@@ -184,6 +184,10 @@ typedef struct {
   int32_t wide_rows_K;         /* rows of K stored spread over a chunk's lanes (dense rows)   */
   int32_t batch_resumed;       /* batch handles: LPs continued in the second stage of the last
                                   pdlp_batch_solve (batch_tail_iters > 0)                     */
+  /* single-LP handles: wall time of the setup phases (ms): copy and validation of the
+     input, the host-side layout, device upload + scaling, the SpMV autotuner, the step
+     size and primal weight (power iteration) with the rest of the setup */
+  double setup_validate_ms, setup_layout_ms, setup_device_ms, setup_tune_ms, setup_step_ms;
 } pdlp_info;
 
 /* Fills p with the defaults listed above. */

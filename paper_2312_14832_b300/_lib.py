@@ -50,7 +50,9 @@ class Info(C.Structure):
                 ("algorithmic_bytes_per_iter", C.c_double), ("stored_bytes_per_iter", C.c_double),
                 ("eta", C.c_double), ("omega0", C.c_double), ("norm_K", C.c_double),
                 ("batch_team", C.c_int32), ("batch_resident", C.c_int32),
-                ("wide_rows_K", C.c_int32), ("batch_resumed", C.c_int32)]
+                ("wide_rows_K", C.c_int32), ("batch_resumed", C.c_int32),
+                ("setup_validate_ms", C.c_double), ("setup_layout_ms", C.c_double),
+                ("setup_device_ms", C.c_double), ("setup_tune_ms", C.c_double), ("setup_step_ms", C.c_double)]
 
 
 # every function declared in include/pdlp.h: name -> (restype, argtypes)

@@ -5,11 +5,11 @@
 
 namespace pdlp {
 
-void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi,
+void sort_by_length_desc(const std::vector<int32_t>& len, int64_t lo, int64_t hi,
                          std::vector<int32_t>& perm) {
   if (hi <= lo) return;
   int64_t maxlen = 0;
-  for (int64_t i = lo; i < hi; ++i) maxlen = std::max(maxlen, len[(size_t)i]);
+  for (int64_t i = lo; i < hi; ++i) maxlen = std::max<int64_t>(maxlen, len[(size_t)i]);
   // counting sort on length, descending, stable in the original index
   std::vector<int64_t> cnt((size_t)maxlen + 2, 0);
   for (int64_t i = lo; i < hi; ++i) cnt[(size_t)(maxlen - len[(size_t)i])]++;
@@ -22,9 +22,7 @@ void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi
   for (int64_t i = lo; i < hi; ++i) perm[(size_t)cnt[(size_t)(maxlen - len[(size_t)i])]++] = (int32_t)i;
 }
 
-SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
-                    const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
-                    const std::vector<int32_t>& esrc, int32_t pad_col, const std::vector<uint8_t>* wide_row) {
+SellHost sell_shape(int64_t rows, const std::vector<int32_t>& elen, const std::vector<uint8_t>* wide_row) {
   SellHost S;
   S.rows = rows;
   S.rows_pad = std::max<int64_t>(32, (rows + 31) / 32 * 32);
@@ -35,46 +33,60 @@ SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
     int64_t L = 1;
     if (wide_row && ch * 32 < rows && (*wide_row)[(size_t)(ch * 32)]) {
       S.wide[(size_t)ch] = 1;
-      L = std::max<int64_t>(1, (elen[(size_t)(ch * 32)] + 31) / 32);
+      L = std::max<int64_t>(1, ((int64_t)elen[(size_t)(ch * 32)] + 31) / 32);
     } else {
-      for (int64_t r = ch * 32; r < std::min(rows, ch * 32 + 32); ++r) L = std::max(L, elen[(size_t)r]);
+      for (int64_t r = ch * 32; r < std::min(rows, ch * 32 + 32); ++r) L = std::max<int64_t>(L, elen[(size_t)r]);
     }
     S.chunk_ptr[(size_t)ch + 1] = S.chunk_ptr[(size_t)ch] + (int32_t)L;
   }
+  return S;
+}
+
+SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
+                    const std::vector<int32_t>& elen, const std::vector<int32_t>& ecol,
+                    const std::vector<int32_t>& esrc, int32_t pad_col, const std::vector<uint8_t>* wide_row) {
+  SellHost S = sell_shape(rows, elen, wide_row);
   size_t total = (size_t)S.chunk_ptr.back() * 32;
-  S.col.assign(total, pad_col);
-  S.src.assign(total, -1);
-  for (int64_t ch = 0; ch < S.nchunks; ++ch) {
-    int64_t base = S.chunk_ptr[(size_t)ch];
-    int64_t clen = S.chunk_ptr[(size_t)ch + 1] - base;
-    if (S.wide[(size_t)ch]) {
-      // entry k of the row in slot k / 32, lane k % 32; padding gathers its first column
-      const int64_t r = ch * 32, st = estart[(size_t)r], L = elen[(size_t)r];
-      for (int64_t k = 0; k < clen * 32; ++k) {
-        const size_t e = (size_t)base * 32 + (size_t)k;
-        if (k < L) {
+  S.col.resize(total);
+  S.src.resize(total);
+  // chunks are independent: each writes its own slots (entries, then padding)
+  parallel_ranges(S.nchunks, [&](int64_t ch0, int64_t ch1) {
+    for (int64_t ch = ch0; ch < ch1; ++ch) {
+      const int64_t base = S.chunk_ptr[(size_t)ch];
+      const int64_t clen = S.chunk_ptr[(size_t)ch + 1] - base;
+      if (S.wide[(size_t)ch]) {
+        // entry k of the row in slot k / 32, lane k % 32; padding gathers its first column
+        const int64_t r = ch * 32, st = estart[(size_t)r], L = elen[(size_t)r];
+        for (int64_t k = 0; k < clen * 32; ++k) {
+          const size_t e = (size_t)base * 32 + (size_t)k;
+          if (k < L) {
+            S.col[e] = ecol[(size_t)(st + k)];
+            S.src[e] = esrc[(size_t)(st + k)];
+          } else {
+            S.col[e] = L > 0 ? ecol[(size_t)st] : pad_col;
+            S.src[e] = -1;
+          }
+        }
+        continue;
+      }
+      for (int64_t lane = 0; lane < 32; ++lane) {
+        const int64_t r = ch * 32 + lane;
+        const int64_t st = r < rows ? estart[(size_t)r] : 0, L = r < rows ? elen[(size_t)r] : 0;
+        for (int64_t k = 0; k < L; ++k) {
+          const size_t e = (size_t)(base + k) * 32 + (size_t)lane;
           S.col[e] = ecol[(size_t)(st + k)];
           S.src[e] = esrc[(size_t)(st + k)];
-        } else if (L > 0) {
-          S.col[e] = ecol[(size_t)st];
+        }
+        // padding slots gather the row's own first column (already in cache), value 0
+        const int32_t pc = L > 0 ? ecol[(size_t)st] : pad_col;
+        for (int64_t k = L; k < clen; ++k) {
+          const size_t e = (size_t)(base + k) * 32 + (size_t)lane;
+          S.col[e] = pc;
+          S.src[e] = -1;
         }
       }
-      continue;
     }
-    for (int64_t lane = 0; lane < 32; ++lane) {
-      int64_t r = ch * 32 + lane;
-      if (r >= rows) break;
-      int64_t st = estart[(size_t)r], L = elen[(size_t)r];
-      for (int64_t k = 0; k < L; ++k) {
-        size_t e = (size_t)(base + k) * 32 + (size_t)lane;
-        S.col[e] = ecol[(size_t)(st + k)];
-        S.src[e] = esrc[(size_t)(st + k)];
-      }
-      // padding slots gather the row's own first column (already in cache), value 0
-      if (L > 0)
-        for (int64_t k = L; k < clen; ++k) S.col[(size_t)(base + k) * 32 + (size_t)lane] = ecol[(size_t)st];
-    }
-  }
+  }, 256);
   return S;
 }
 

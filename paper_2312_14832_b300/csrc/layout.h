@@ -19,10 +19,32 @@
 // lanes' partial sums are combined by a fixed warp reduction.  So the row costs its own
 // length / 32 slots instead of its length times 32.
 #pragma once
+#include <algorithm>
 #include <cstdint>
+#include <thread>
 #include <vector>
 
 namespace pdlp {
+
+// Runs f(begin, end) over [0, n) cut into contiguous ranges, one per host thread (up to
+// the hardware's count, and only as many as leave min_per_thread items each).  Every
+// index is handled by exactly one call; f must not throw (report failures through
+// per-range results instead).
+template <class F>
+void parallel_ranges(int64_t n, F f, int64_t min_per_thread = (int64_t)1 << 16) {
+  if (n <= 0) return;
+  int64_t t = (int64_t)std::max(1u, std::thread::hardware_concurrency());
+  t = std::min<int64_t>(t, 32);
+  t = std::max<int64_t>(1, std::min<int64_t>(t, n / std::max<int64_t>(1, min_per_thread)));
+  if (t == 1) {
+    f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve((size_t)t);
+  for (int64_t i = 0; i < t; ++i) th.emplace_back([&, i]() { f(n * i / t, n * (i + 1) / t); });
+  for (auto& x : th) x.join();
+}
 
 struct SellTask {
   int32_t s0, s1;   // slot range [s0, s1) of this warp task
@@ -51,16 +73,20 @@ struct TaskPlan {
 };
 
 // Permutation by decreasing length (stable) of the indices [lo, hi), written to perm[lo..hi).
-void sort_by_length_desc(const std::vector<int64_t>& len, int64_t lo, int64_t hi,
+void sort_by_length_desc(const std::vector<int32_t>& len, int64_t lo, int64_t hi,
                          std::vector<int32_t>& perm);
 
-// Builds the SELL-32 arrays of a matrix whose internal row p (0 <= p < rows) has the
-// entries estart[p] .. estart[p] + elen[p] - 1 of the entry arrays ecol / esrc.
-// Padding slots of empty rows point at column pad_col.  wide_row (optional, per row):
-// rows stored spread over their chunk's lanes; such a row is the first of its chunk and
-// the other 31 rows of the chunk are empty.
+// The shape of the SELL-32 layout of a matrix whose internal row p (0 <= p < rows) has
+// elen[p] entries: chunk_ptr and the wide flags, no entry arrays.  wide_row (optional,
+// per row): rows stored spread over their chunk's lanes; such a row is the first of its
+// chunk and the other 31 rows of the chunk are empty.
+SellHost sell_shape(int64_t rows, const std::vector<int32_t>& elen, const std::vector<uint8_t>* wide_row = nullptr);
+
+// sell_shape plus the entry arrays: row p has the entries estart[p] .. estart[p] +
+// elen[p] - 1 of ecol / esrc.  Padding slots take the column of the row's first entry,
+// or pad_col for an empty row.
 SellHost build_sell(int64_t rows, const std::vector<int64_t>& estart,
-                    const std::vector<int64_t>& elen, const std::vector<int32_t>& ecol,
+                    const std::vector<int32_t>& elen, const std::vector<int32_t>& ecol,
                     const std::vector<int32_t>& esrc, int32_t pad_col = 0,
                     const std::vector<uint8_t>* wide_row = nullptr);
 

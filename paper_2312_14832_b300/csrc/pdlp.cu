@@ -1,9 +1,11 @@
 // Host driver and C ABI of the restarted-PDHG solver (declarations and contract in
 // include/pdlp.h; method: arXiv 2312.14832, Section 2).
 //
-// pdlp_setup builds the length-sorted SELL-32 layout of K and K' on the host,
-// moves it to the device, scales (Ruiz + Pock-Chambolle) and estimates ||K||_2
-// with device kernels.  pdlp_solve has two engines.  The kernels launched per
+// pdlp_setup orders rows and columns by length on the host (O(m + n) work), builds the
+// SELL-32 layouts of K and K' on the device from the caller's CSR arrays
+// (layout_kernels.cuh: checks, CSC order by radix sort, per-slot fill), scales
+// (Ruiz + Pock-Chambolle) and estimates ||K||_2 with device kernels.  Batches keep
+// the host builder of layout.cpp (their LPs are small), which yields the same layouts.  pdlp_solve has two engines.  The kernels launched per
 // iteration run as CUDA graphs, one graph per check interval: check_every x (primal
 // kernel, dual kernel) followed by the check (three SpMVs, the KKT reductions, the
 // restart decision and the restart itself), all state on the device; the host only
@@ -14,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -25,6 +28,7 @@
 #include "batch_kernel.cuh"
 #include "kernels.cuh"
 #include "layout.h"
+#include "layout_kernels.cuh"
 #include "pdlp.h"
 
 namespace pdlp {
@@ -134,6 +138,7 @@ struct pdlp_ctx {
   double *xg = nullptr, *yg = nullptr;      // global iterates (allocated on first use)
   float *xg32 = nullptr, *yg32 = nullptr;
   int64_t last_resumed = 0;  // LPs continued in the second stage of the last solve
+  double setup_ms[5] = {};   // setup phases (pdlp_info)
   std::vector<int32_t> hk_cptr, ht_cptr;  // host copies of the chunk pointers of K and K'
   int dev_smem_optin = 0;
   int xs_off = 0, ys_off = 0, red_off = 0;
@@ -195,8 +200,20 @@ static void launch_rows(pdlp_ctx* h, const DevSell& S, const typename Epi::T* xg
   else sell_rows_kernel<Op, Epi, 8><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
 }
 
-static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const TaskPlan& P,
-                              const double* d_csr_val) {
+// The caller's matrix on the device, with what the device layout builder derives from
+// it: tp = column starts of the CSC order (n + 1), csc = entry indices in CSC order,
+// rowof = the row of each entry.
+struct DevCsr {
+  const int64_t* rp;
+  const int32_t* col;
+  const double* val;
+  const int32_t* tp;
+  const int32_t* csc;
+  const int32_t* rowof;
+};
+
+// Uploads the shape and task plan of a layout and allocates its arrays.
+static void alloc_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const TaskPlan& P) {
   D.rows = S.rows;
   D.rows_pad = S.rows_pad;
   D.nchunks = S.nchunks;
@@ -204,7 +221,6 @@ static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const 
   D.split = P.split_chunks;
   D.ntasks = (int32_t)P.tasks.size();
   D.chunk_ptr = upload(h, S.chunk_ptr);
-  D.col = upload(h, S.col);
   D.tasks = upload(h, P.tasks);
   D.gpart = dalloc<double>(h, (size_t)D.ntasks * 32);
   D.cnt = dalloc<int32_t>(h, (size_t)D.ntasks);
@@ -212,11 +228,34 @@ static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const 
   D.nwide = 0;
   for (uint8_t f : S.wide) D.nwide += f != 0;
   D.wide = D.nwide > 0 ? upload(h, S.wide) : nullptr;
+}
+
+// Layout built on the host (S.col, S.src): upload, then gather the values.
+static void build_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const TaskPlan& P,
+                              const double* d_csr_val) {
+  alloc_device_sell(h, D, S, P);
+  D.col = upload(h, S.col);
   int32_t* d_src = upload(h, S.src);
   k_gather_values<<<grid_for(D.slots * 32), 256, 0, h->s>>>(D.val, d_src, d_csr_val, D.slots * 32);
   CKL("k_gather_values");
   CK(cudaStreamSynchronize(h->s));
   dfree(h, d_src);
+}
+
+// Layout filled on the device from the caller's matrix (S holds the shape only): K rows
+// from the CSR rows, K' rows from the CSC order.  Needs perm_* and pos_* on the device.
+static void fill_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const TaskPlan& P, const DevCsr& C,
+                             bool transpose) {
+  alloc_device_sell(h, D, S, P);
+  const int64_t total = D.slots * 32;
+  D.col = dalloc<int32_t>(h, (size_t)total);
+  if (!transpose)
+    k_fill_sell<int64_t><<<grid_for(total), 256, 0, h->s>>>(D.chunk_ptr, D.nchunks, D.wide, total, h->perm_r, C.rp,
+                                                           nullptr, C.col, h->pos_c, C.val, 0, D.col, D.val);
+  else
+    k_fill_sell<int32_t><<<grid_for(total), 256, 0, h->s>>>(D.chunk_ptr, D.nchunks, D.wide, total, h->perm_c, C.tp,
+                                                           C.csc, C.rowof, h->pos_r, C.val, 0, D.col, D.val);
+  CKL("k_fill_sell");
 }
 
 // Replaces the warp-task plan of a device layout (the arrays of values and indices stay).
@@ -543,6 +582,20 @@ static void check_params(const pdlp_params& P) {
 // Copies (from host or device) and validates one LP in CSR form; rows_total and the
 // sizes of the arrays are given by the caller (a batch validates each LP's rows and
 // columns against its own n through col_limit).
+// True when pred(i) holds for every i in [0, n) (checked in parallel ranges).
+template <class P>
+static bool all_of_range(int64_t n, P pred) {
+  std::atomic<int> bad{0};
+  parallel_ranges(n, [&](int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i)
+      if (!pred(i)) {
+        bad.store(1, std::memory_order_relaxed);
+        return;
+      }
+  });
+  return bad.load() == 0;
+}
+
 static void fetch_and_validate(pdlp_ctx* h, int64_t rows, int64_t cols, const int64_t* row_ptr_in,
                                const int32_t* col_in, const double* val_in, const double* c_in,
                                const double* q_in, const double* l_in, const double* u_in, HostLP& H,
@@ -550,8 +603,13 @@ static void fetch_and_validate(pdlp_ctx* h, int64_t rows, int64_t cols, const in
   const bool dev_in = h->p.inputs_on_device != 0;
   auto fetch = [&](void* dst, const void* src, size_t bytes) {
     if (bytes == 0) return;
-    if (dev_in) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
-    else std::memcpy(dst, src, bytes);
+    if (dev_in) {
+      CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    } else {
+      parallel_ranges((int64_t)bytes, [&](int64_t a, int64_t b) {
+        std::memcpy(static_cast<char*>(dst) + a, static_cast<const char*>(src) + a, (size_t)(b - a));
+      }, (int64_t)1 << 22);
+    }
   };
   H.rp.resize((size_t)rp_count);
   fetch(H.rp.data(), row_ptr_in, sizeof(int64_t) * rp_count);
@@ -574,8 +632,8 @@ static void fetch_and_validate(pdlp_ctx* h, int64_t rows, int64_t cols, const in
   fetch(H.l.data(), l_in, sizeof(double) * cols);
   fetch(H.u.data(), u_in, sizeof(double) * cols);
   fetch(H.q.data(), q_in, sizeof(double) * h->m);
-  for (int64_t k = 0; k < nnz; ++k)
-    if (!std::isfinite(H.val[(size_t)k])) invalid("non-finite matrix value");
+  if (!all_of_range(nnz, [&](int64_t k) { return std::isfinite(H.val[(size_t)k]); }))
+    invalid("non-finite matrix value");
   for (int64_t j = 0; j < cols; ++j) {
     const double a = H.l[(size_t)j], b = H.u[(size_t)j];
     if (!std::isfinite(H.c[(size_t)j])) invalid("non-finite c");
@@ -592,10 +650,11 @@ static int64_t check_csr(const HostLP& H, int64_t rp0, int64_t m, int64_t n, int
   for (int64_t i = 0; i < m; ++i)
     if (H.rp[(size_t)(rp0 + i + 1)] < H.rp[(size_t)(rp0 + i)]) invalid("row_ptr must be nondecreasing");
   const int64_t nnz = H.rp[(size_t)(rp0 + m)];
-  for (int64_t k = 0; k < nnz; ++k) {
-    const int32_t cc = H.col[(size_t)(nnz0 + k)];
-    if (cc < 0 || cc >= n) invalid("column index out of range");
-  }
+  if (!all_of_range(nnz, [&](int64_t k) {
+        const int32_t cc = H.col[(size_t)(nnz0 + k)];
+        return cc >= 0 && cc < n;
+      }))
+    invalid("column index out of range");
   return nnz;
 }
 
@@ -608,9 +667,6 @@ struct Layout {
   int64_t mpad = 0, npad = 0;
 };
 
-// Appends the layout of one LP (rows rp[rp0..rp0+m], entries from nnz0, columns
-// [col0, col0 + n) of the caller's concatenated vectors) to L at internal offsets
-// L.mpad / L.npad, and pads both to a multiple of 32 (at least 32).
 // Single-LP handles up to this many nonzeros get the persistent engine (when x and y fit
 // in one CTA's shared memory and no row is wide).
 constexpr int64_t kSmallEngineNnz = (int64_t)1 << 18;
@@ -619,25 +675,41 @@ constexpr int64_t kSmallEngineNnz = (int64_t)1 << 18;
 // length order are stored as wide rows (layout.h).
 constexpr int64_t kWideMin = 1024;
 
-static void append_lp_layout(Layout& L, const HostLP& H, int64_t rp0, int64_t nnz0, int64_t out0, int64_t m,
-                             int64_t n, int64_t m1, int64_t row0, int64_t col0, std::vector<int64_t>& k_est,
-                             std::vector<int64_t>& k_eln, std::vector<int32_t>& k_ecol, std::vector<int32_t>& k_esrc,
-                             std::vector<int64_t>& t_est, std::vector<int64_t>& t_eln, std::vector<int32_t>& t_ecol,
-                             std::vector<int32_t>& t_esrc, bool wide_ok = false,
-                             std::vector<uint8_t>* k_wide = nullptr, int64_t* m1_int = nullptr) {
-  const int64_t nnz = H.rp[(size_t)(rp0 + m)];
-  const int64_t np = std::max<int64_t>(32, (n + 31) / 32 * 32);
-  const int64_t rbase = L.mpad, cbase = L.npad;
-  std::vector<int64_t> rlen((size_t)m), clen((size_t)n, 0);
-  for (int64_t i = 0; i < m; ++i) rlen[(size_t)i] = H.rp[(size_t)(rp0 + i + 1)] - H.rp[(size_t)(rp0 + i)];
-  for (int64_t k = 0; k < nnz; ++k) clen[(size_t)H.col[(size_t)(nnz0 + k)]]++;
-  std::vector<int32_t> pr((size_t)std::max<int64_t>(m, 1)), pc((size_t)n);
+// Row and column order of one LP inside a layout (local indices count from the LP's
+// first row / column; internal ones from its first internal row / column).
+struct LpOrder {
+  std::vector<int32_t> ord;      // internal row -> local row, -1 for padding (mp entries)
+  std::vector<int32_t> pc;       // internal column -> local column (n entries)
+  std::vector<int32_t> lpos_r;   // local row -> internal row
+  std::vector<int32_t> lpos_c;   // local column -> internal column
+  std::vector<int32_t> rlen, clen;
+  int64_t m = 0, n = 0, rbase = 0, cbase = 0, mp = 0, np = 0;
+};
+
+// Orders the rows and columns of one LP (row pointers rp[0..m], starting at 0; column
+// counts clen) and appends them to L at internal offsets L.mpad / L.npad: rows are
+// equality rows, then inequality rows, each by decreasing length; columns by decreasing
+// length; both padded to a multiple of 32 (at least 32).  A wide row (wide_ok) starts a
+// chunk and is followed by 31 empty padding rows.  Appends the entry counts of the
+// internal rows of K (k_eln) and of K' (t_eln).  O(m + n) work.
+static void order_lp(Layout& L, LpOrder& O, const int64_t* rp, std::vector<int32_t>&& clen, int64_t m, int64_t n,
+                     int64_t m1, int64_t row0, int64_t col0, std::vector<int32_t>& k_eln, std::vector<int32_t>& t_eln,
+                     bool wide_ok = false, std::vector<uint8_t>* k_wide = nullptr, int64_t* m1_int = nullptr) {
+  O.m = m;
+  O.n = n;
+  O.rbase = L.mpad;
+  O.cbase = L.npad;
+  O.np = std::max<int64_t>(32, (n + 31) / 32 * 32);
+  O.clen = std::move(clen);
+  O.rlen.resize((size_t)m);
+  for (int64_t i = 0; i < m; ++i) O.rlen[(size_t)i] = (int32_t)(rp[i + 1] - rp[i]);
+  const std::vector<int32_t>& rlen = O.rlen;
+  std::vector<int32_t> pr((size_t)std::max<int64_t>(m, 1));
+  O.pc.resize((size_t)n);
   sort_by_length_desc(rlen, 0, m1, pr);
   sort_by_length_desc(rlen, m1, m, pr);
-  sort_by_length_desc(clen, 0, n, pc);
-  // internal row order: equality rows, then inequality rows, each by decreasing length;
-  // a wide row starts a chunk and is followed by 31 empty padding rows (-1)
-  std::vector<int32_t> ord;
+  sort_by_length_desc(O.clen, 0, n, O.pc);
+  std::vector<int32_t>& ord = O.ord;
   std::vector<uint8_t> wflag;
   ord.reserve((size_t)m + 64);
   auto emit_block = [&](int64_t p0, int64_t p1) {
@@ -667,61 +739,134 @@ static void append_lp_layout(Layout& L, const HostLP& H, int64_t rp0, int64_t nn
   if (m1_int) *m1_int = (int64_t)ord.size();
   emit_block(m1, m);
   const int64_t mint = (int64_t)ord.size();
-  const int64_t mp = std::max<int64_t>(32, (mint + 31) / 32 * 32);
+  O.mp = std::max<int64_t>(32, (mint + 31) / 32 * 32);
+  const int64_t mp = O.mp, np = O.np;
   ord.resize((size_t)mp, -1);
   wflag.resize((size_t)mp, 0);
-  if (k_wide) *k_wide = wflag;
-  std::vector<int32_t> lpos_r((size_t)std::max<int64_t>(m, 1)), lpos_c((size_t)n);
+  if (k_wide) *k_wide = std::move(wflag);
+  O.lpos_r.resize((size_t)std::max<int64_t>(m, 1));
+  O.lpos_c.resize((size_t)n);
   for (int64_t p = 0; p < mp; ++p)
-    if (ord[(size_t)p] >= 0) lpos_r[(size_t)ord[(size_t)p]] = (int32_t)p;
-  for (int64_t p = 0; p < n; ++p) lpos_c[(size_t)pc[(size_t)p]] = (int32_t)p;
+    if (ord[(size_t)p] >= 0) O.lpos_r[(size_t)ord[(size_t)p]] = (int32_t)p;
+  for (int64_t p = 0; p < n; ++p) O.lpos_c[(size_t)O.pc[(size_t)p]] = (int32_t)p;
   for (int64_t p = 0; p < mp; ++p) L.perm_r.push_back(ord[(size_t)p] >= 0 ? (int32_t)(row0 + ord[(size_t)p]) : -1);
-  for (int64_t p = 0; p < np; ++p) L.perm_c.push_back(p < n ? (int32_t)(col0 + pc[(size_t)p]) : -1);
-  for (int64_t i = 0; i < m; ++i) L.pos_r[(size_t)(row0 + i)] = (int32_t)(rbase + lpos_r[(size_t)i]);
-  for (int64_t j = 0; j < n; ++j) L.pos_c[(size_t)(col0 + j)] = (int32_t)(cbase + lpos_c[(size_t)j]);
-  // K rows: entries in CSR order, columns renumbered
-  for (int64_t p = 0; p < mp; ++p) {
-    if (ord[(size_t)p] >= 0) {
-      const int64_t i = ord[(size_t)p];
-      k_est.push_back(out0 + H.rp[(size_t)(rp0 + i)]);
-      k_eln.push_back(rlen[(size_t)i]);
-    } else {
-      k_est.push_back(0);
-      k_eln.push_back(0);
-    }
-  }
-  for (int64_t k = 0; k < nnz; ++k) {
-    k_ecol[(size_t)(out0 + k)] = (int32_t)(cbase + lpos_c[(size_t)H.col[(size_t)(nnz0 + k)]]);
-    k_esrc[(size_t)(out0 + k)] = (int32_t)(nnz0 + k);
-  }
-  // K' rows (columns of K): entries in increasing row order
-  std::vector<int64_t> tp((size_t)n + 1, 0);
-  for (int64_t j = 0; j < n; ++j) tp[(size_t)j + 1] = tp[(size_t)j] + clen[(size_t)j];
-  std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
-  for (int64_t i = 0; i < m; ++i)
-    for (int64_t k = H.rp[(size_t)(rp0 + i)]; k < H.rp[(size_t)(rp0 + i + 1)]; ++k) {
-      const int64_t at = out0 + fill[(size_t)H.col[(size_t)(nnz0 + k)]]++;
-      t_ecol[(size_t)at] = (int32_t)(rbase + lpos_r[(size_t)i]);
-      t_esrc[(size_t)at] = (int32_t)(nnz0 + k);
-    }
-  for (int64_t p = 0; p < np; ++p) {
-    if (p < n) {
-      const int64_t j = pc[(size_t)p];
-      t_est.push_back(out0 + tp[(size_t)j]);
-      t_eln.push_back(clen[(size_t)j]);
-    } else {
-      t_est.push_back(0);
-      t_eln.push_back(0);
-    }
-  }
+  for (int64_t p = 0; p < np; ++p) L.perm_c.push_back(p < n ? (int32_t)(col0 + O.pc[(size_t)p]) : -1);
+  for (int64_t i = 0; i < m; ++i) L.pos_r[(size_t)(row0 + i)] = (int32_t)(O.rbase + O.lpos_r[(size_t)i]);
+  for (int64_t j = 0; j < n; ++j) L.pos_c[(size_t)(col0 + j)] = (int32_t)(O.cbase + O.lpos_c[(size_t)j]);
+  for (int64_t p = 0; p < mp; ++p) k_eln.push_back(ord[(size_t)p] >= 0 ? rlen[(size_t)ord[(size_t)p]] : 0);
+  for (int64_t p = 0; p < np; ++p) t_eln.push_back(p < n ? O.clen[(size_t)O.pc[(size_t)p]] : 0);
   L.mpad += mp;
   L.npad += np;
 }
 
+// Host entry lists of one LP for build_sell: internal K row p has the entries
+// k_est[p] .. of (k_ecol, k_esrc) in the caller's order, with columns renumbered;
+// internal K' row p (a column of K) has the column's entries by increasing row.  col
+// holds the LP's nnz column indices, which are entries nnz0 .. of the caller's arrays.
+static void host_entries(const LpOrder& O, const int64_t* rp, const int32_t* col, int64_t nnz0, int64_t nnz,
+                         std::vector<int64_t>& k_est, std::vector<int32_t>& k_ecol, std::vector<int32_t>& k_esrc,
+                         std::vector<int64_t>& t_est, std::vector<int32_t>& t_ecol, std::vector<int32_t>& t_esrc) {
+  const int64_t m = O.m, n = O.n;
+  k_ecol.resize((size_t)nnz);
+  k_esrc.resize((size_t)nnz);
+  t_ecol.resize((size_t)nnz);
+  t_esrc.resize((size_t)nnz);
+  for (int64_t p = 0; p < O.mp; ++p) k_est.push_back(O.ord[(size_t)p] >= 0 ? rp[O.ord[(size_t)p]] : 0);
+  for (int64_t k = 0; k < nnz; ++k) {
+    k_ecol[(size_t)k] = (int32_t)(O.cbase + O.lpos_c[(size_t)col[k]]);
+    k_esrc[(size_t)k] = (int32_t)(nnz0 + k);
+  }
+  std::vector<int64_t> tp((size_t)n + 1, 0);
+  for (int64_t j = 0; j < n; ++j) tp[(size_t)j + 1] = tp[(size_t)j] + O.clen[(size_t)j];
+  std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int64_t at = fill[(size_t)col[k]]++;
+      t_ecol[(size_t)at] = (int32_t)(O.rbase + O.lpos_r[(size_t)i]);
+      t_esrc[(size_t)at] = (int32_t)(nnz0 + k);
+    }
+  for (int64_t p = 0; p < O.np; ++p) t_est.push_back(p < n ? tp[(size_t)O.pc[(size_t)p]] : 0);
+}
+
+// Checks c, l, u (n entries) and q (m entries): read in place from host inputs, from a
+// host copy of device inputs.
+static void check_vectors(pdlp_ctx* h, int64_t n, int64_t m, const double* c_in, const double* q_in,
+                          const double* l_in, const double* u_in) {
+  std::vector<double> hc, hl, hu, hq;
+  const double *c = c_in, *l = l_in, *u = u_in, *q = q_in;
+  if (h->p.inputs_on_device) {
+    auto fetch = [](std::vector<double>& v, const double* src, int64_t count) {
+      v.resize((size_t)count);
+      if (count > 0) CK(cudaMemcpy(v.data(), src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+      return v.data();
+    };
+    c = fetch(hc, c_in, n);
+    l = fetch(hl, l_in, n);
+    u = fetch(hu, u_in, n);
+    q = fetch(hq, q_in, m);
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    const double a = l[j], b = u[j];
+    if (!std::isfinite(c[j])) invalid("non-finite c");
+    if (std::isnan(a) || std::isnan(b) || a == INFINITY || b == -INFINITY || a > b)
+      invalid("bounds must satisfy l <= u, l < +inf, u > -inf");
+  }
+  for (int64_t i = 0; i < m; ++i)
+    if (!std::isfinite(q[i])) invalid("non-finite q");
+}
+
+// In-place exclusive prefix sums of a[0, n) on the handle's stream (total below 2^31).
+static void dev_exclusive_scan(pdlp_ctx* h, int32_t* a, int64_t n) {
+  if (n <= 0) return;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  int32_t* sums = dalloc<int32_t>(h, (size_t)tiles);
+  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, h->s>>>(a, n, sums);
+  CKL("k_scan_tiles");
+  if (tiles > 1) {
+    dev_exclusive_scan(h, sums, tiles);
+    k_scan_add<<<grid_for(n), 256, 0, h->s>>>(a, n, sums);
+    CKL("k_scan_add");
+  }
+  CK(cudaStreamSynchronize(h->s));
+  dfree(h, sums);
+}
+
+// The entry indices 0 .. nnz-1 sorted by their column col[k] in [0, n), equal columns in
+// increasing index: the CSC order of a CSR matrix.  ceil(log2 n / 8) stable radix passes
+// of 8 bits (at least one).  The result is an allocation of the handle.
+static int32_t* dev_csc_order(pdlp_ctx* h, const int32_t* d_col, int64_t nnz, int64_t n) {
+  if (nnz == 0) return dalloc<int32_t>(h, 1);
+  int bits = 0;
+  while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
+  const int passes = std::max(1, (bits + 7) / 8);
+  const int64_t tiles = (nnz + kRadixTile - 1) / kRadixTile;
+  int32_t* hist = dalloc<int32_t>(h, (size_t)(256 * tiles));
+  int32_t* kb[2] = {dalloc<int32_t>(h, (size_t)nnz), dalloc<int32_t>(h, (size_t)nnz)};
+  int32_t* vb[2] = {dalloc<int32_t>(h, (size_t)nnz), dalloc<int32_t>(h, (size_t)nnz)};
+  const int32_t* kin = d_col;
+  const int32_t* vin = nullptr;
+  int cur = 0;
+  for (int ps = 0; ps < passes; ++ps) {
+    k_radix_hist<<<(unsigned)tiles, kRadixThreads, 0, h->s>>>(kin, nnz, 8 * ps, hist, tiles);
+    CKL("k_radix_hist");
+    dev_exclusive_scan(h, hist, 256 * tiles);
+    k_radix_scatter<<<(unsigned)tiles, kRadixThreads, 0, h->s>>>(kin, vin, nnz, 8 * ps, hist, tiles, kb[cur],
+                                                                    vb[cur]);
+    CKL("k_radix_scatter");
+    kin = kb[cur];
+    vin = vb[cur];
+    cur ^= 1;
+  }
+  CK(cudaStreamSynchronize(h->s));
+  int32_t* out = vb[cur ^ 1];
+  for (void* v : {(void*)hist, (void*)kb[0], (void*)kb[1], (void*)vb[cur]}) dfree(h, v);
+  return out;
+}
+
 // Upload of the layouts and values, problem vectors in internal order, unscaled norms,
 // scaling and the scaled problem vectors: everything both handle kinds share.
-static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const double* c_in, const double* q_in,
-                                const double* l_in, const double* u_in);
+static void device_setup_common(pdlp_ctx* h, Layout& Lo, const DevCsr* dc, const std::vector<double>* hval,
+                                const double* c_in, const double* q_in, const double* l_in, const double* u_in);
 static void estimate_step_and_weight(pdlp_ctx* h);
 static void setup_mixed(pdlp_ctx* h);
 static void init_batch_launch(pdlp_ctx* h, const Layout& Lo, int64_t npad_max, int64_t mpad_max);
@@ -738,37 +883,87 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   check_params(P);
   if (!row_ptr_in || !c_in || !l_in || !u_in || (m > 0 && !q_in)) invalid("null input array");
   init_handle_resources(h);
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
+  auto tp = clk::now();
   h->m = m;
   h->n = n;
   h->m1 = m1;
-  // nnz from the last row pointer
-  {
-    int64_t last = 0;
-    if (P.inputs_on_device) CK(cudaMemcpy(&last, row_ptr_in + m, sizeof(int64_t), cudaMemcpyDeviceToHost));
-    else last = row_ptr_in[m];
-    if (last < 0 || last >= ((int64_t)1 << 31)) invalid("nnz must be in [0, 2^31)");
-    h->nnz = last;
+  const bool dev_in = P.inputs_on_device != 0;
+  // device inputs are read on this handle's stream and by copies to the host: the
+  // caller's stream must have finished writing them
+  if (dev_in && P.stream) CK(cudaStreamSynchronize((cudaStream_t)P.stream));
+  // row pointers on the host: the caller's array, or a copy of the device array
+  std::vector<int64_t> rp_copy;
+  const int64_t* rp = row_ptr_in;
+  if (dev_in) {
+    rp_copy.resize((size_t)m + 1);
+    CK(cudaMemcpy(rp_copy.data(), row_ptr_in, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost));
+    rp = rp_copy.data();
   }
-  HostLP H;
-  fetch_and_validate(h, m, n, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, m + 1);
-  check_csr(H, 0, m, n, 0);
+  if (rp[m] < 0 || rp[m] >= ((int64_t)1 << 31)) invalid("nnz must be in [0, 2^31)");
+  if (rp[0] != 0) invalid("row_ptr[0] must be 0");
+  for (int64_t i = 0; i < m; ++i)
+    if (rp[i + 1] < rp[i]) invalid("row_ptr must be nondecreasing");
+  const int64_t nnz = rp[m];
+  h->nnz = nnz;
+  if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
+  check_vectors(h, n, m, c_in, q_in, l_in, u_in);
 
+  // the matrix goes to the device as it is; the entries are checked and the columns
+  // counted there
+  const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int64_t* d_rp = dalloc<int64_t>(h, (size_t)m + 1);
+  int32_t* d_col = dalloc<int32_t>(h, (size_t)nnz);
+  double* d_val = dalloc<double>(h, (size_t)nnz);
+  int32_t* d_tp = dalloc<int32_t>(h, (size_t)n + 1);   // column counts, then column starts
+  int* d_flags = dalloc<int>(h, 1);
+  CK(cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, h->s));
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(d_col, col_in, sizeof(int32_t) * nnz, kind, h->s));
+    CK(cudaMemcpyAsync(d_val, val_in, sizeof(double) * nnz, kind, h->s));
+  }
+  k_check_count<<<grid_for(nnz), 256, 0, h->s>>>(d_col, d_val, nnz, (int32_t)n, d_tp, d_flags);
+  CKL("k_check_count");
+  int flags = 0;
+  std::vector<int32_t> clen((size_t)n);
+  CK(cudaMemcpyAsync(&flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(clen.data(), d_tp, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (flags & kBadVal) invalid("non-finite matrix value");
+  if (flags & kBadCol) invalid("column index out of range");
+  h->setup_ms[0] = ms_since(tp);
+  tp = clk::now();
+
+  // row and column order and the chunk shapes on the host
   Layout Lo;
   Lo.pos_r.assign((size_t)m, 0);
   Lo.pos_c.assign((size_t)n, 0);
   {
-    std::vector<int64_t> k_est, k_eln, t_est, t_eln;
-    std::vector<int32_t> k_ecol((size_t)h->nnz), k_esrc((size_t)h->nnz), t_ecol((size_t)h->nnz),
-        t_esrc((size_t)h->nnz);
+    std::vector<int32_t> k_eln, t_eln;
     std::vector<uint8_t> k_wide;
     int64_t m1i = m1;
-    append_lp_layout(Lo, H, 0, 0, 0, m, n, m1, 0, 0, k_est, k_eln, k_ecol, k_esrc, t_est, t_eln, t_ecol, t_esrc,
-                     true, &k_wide, &m1i);
+    LpOrder O;
+    order_lp(Lo, O, rp, std::move(clen), m, n, m1, 0, 0, k_eln, t_eln, true, &k_wide, &m1i);
     h->m1_int = m1i;
-    Lo.SK = build_sell(Lo.mpad, k_est, k_eln, k_ecol, k_esrc, 0, &k_wide);
-    Lo.SKt = build_sell(Lo.npad, t_est, t_eln, t_ecol, t_esrc);
+    Lo.SK = sell_shape(Lo.mpad, k_eln, &k_wide);
+    Lo.SKt = sell_shape(Lo.npad, t_eln);
   }
-  device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
+  h->setup_ms[1] = ms_since(tp);
+  tp = clk::now();
+  // K' from the CSC order: column starts, entries sorted by column, row of each entry
+  dev_exclusive_scan(h, d_tp, n + 1);
+  int32_t* d_csc = dev_csc_order(h, d_col, nnz, n);
+  int32_t* d_rowof = dalloc<int32_t>(h, (size_t)nnz);
+  k_row_of<<<grid_for(m * 32), 256, 0, h->s>>>(d_rp, m, d_rowof);
+  CKL("k_row_of");
+  const DevCsr dc{d_rp, d_col, d_val, d_tp, d_csc, d_rowof};
+  device_setup_common(h, Lo, &dc, nullptr, c_in, q_in, l_in, u_in);
+  for (void* v : {(void*)d_rp, (void*)d_col, (void*)d_val, (void*)d_tp, (void*)d_flags, (void*)d_csc, (void*)d_rowof})
+    dfree(h, v);
+  CK(cudaStreamSynchronize(h->s));
+  h->setup_ms[2] = ms_since(tp);
+  tp = clk::now();
 
   // ---- SpMV schedule per layout: explicit parameters, or timed candidates for large K
   const bool auto_tile = P.tile_slots == 0 && P.tile_chunks == 0 && P.spmv_batch == 0;
@@ -776,6 +971,8 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
     autotune(h, h->Kt, Lo.SKt, true);
     autotune(h, h->K, Lo.SK, false);
   }
+  h->setup_ms[3] = ms_since(tp);
+  tp = clk::now();
   estimate_step_and_weight(h);
   if (P.precision == PDLP_MIXED) setup_mixed(h);
   else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
@@ -805,6 +1002,8 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
     }
   }
   if (P.engine == 2 && !h->small_engine) invalid("engine 2: this LP does not fit the persistent engine");
+  CK(cudaStreamSynchronize(h->s));
+  h->setup_ms[4] = ms_since(tp);
 }
 
 // FP32 copies of the scaled matrix values and problem vectors, FP32 iterates.
@@ -824,8 +1023,8 @@ static void setup_mixed(pdlp_ctx* h) {
   CK(cudaStreamSynchronize(h->s));
 }
 
-static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const double* c_in, const double* q_in,
-                                const double* l_in, const double* u_in) {
+static void device_setup_common(pdlp_ctx* h, Layout& Lo, const DevCsr* dc, const std::vector<double>* hval,
+                                const double* c_in, const double* q_in, const double* l_in, const double* u_in) {
   const pdlp_params& P = h->p;
   const int64_t m = h->m, n = h->n;
   h->mpad = Lo.mpad;
@@ -837,15 +1036,19 @@ static void device_setup_common(pdlp_ctx* h, Layout& Lo, const HostLP& H, const 
   h->K.tchunks = h->Kt.tchunks = tchunks;
   h->K.batch = h->Kt.batch = (P.spmv_batch == 4) ? 4 : 8;
 
-  double* d_val = upload(h, H.val);
-  build_device_sell(h, h->K, Lo.SK, PK, d_val);
-  build_device_sell(h, h->Kt, Lo.SKt, PKt, d_val);
-  dfree(h, d_val);
-
   h->perm_r = upload(h, Lo.perm_r);
   h->pos_r = upload(h, Lo.pos_r);
   h->perm_c = upload(h, Lo.perm_c);
   h->pos_c = upload(h, Lo.pos_c);
+  if (dc) {
+    fill_device_sell(h, h->K, Lo.SK, PK, *dc, false);
+    fill_device_sell(h, h->Kt, Lo.SKt, PKt, *dc, true);
+  } else {
+    double* d_val = upload(h, *hval);
+    build_device_sell(h, h->K, Lo.SK, PK, d_val);
+    build_device_sell(h, h->Kt, Lo.SKt, PKt, d_val);
+    dfree(h, d_val);
+  }
 
   const int64_t mp = h->mpad, np = h->npad;
   h->c = dalloc<double>(h, np);
@@ -1385,11 +1588,16 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   for (int64_t b = 0; b < count; ++b) {
     const int64_t m = lm[(size_t)b], n = ln[(size_t)b];
     const int64_t lnnz = check_csr(H, rp0, m, n, nnz0);
-    std::vector<int64_t> k_est, k_eln, t_est, t_eln;
-    std::vector<int32_t> k_ecol((size_t)lnnz), k_esrc((size_t)lnnz), t_ecol((size_t)lnnz), t_esrc((size_t)lnnz);
+    const int64_t* lrp = H.rp.data() + rp0;
+    const int32_t* lcol = H.col.data() + nnz0;
+    std::vector<int32_t> clen((size_t)n, 0);
+    for (int64_t k = 0; k < lnnz; ++k) clen[(size_t)lcol[k]]++;
+    std::vector<int64_t> k_est, t_est;
+    std::vector<int32_t> k_eln, t_eln, k_ecol, k_esrc, t_ecol, t_esrc;
     const int64_t rbase = Lo.mpad, cbase = Lo.npad;
-    append_lp_layout(Lo, H, rp0, nnz0, 0, m, n, lm1[(size_t)b], row0, col0, k_est, k_eln, k_ecol, k_esrc, t_est,
-                     t_eln, t_ecol, t_esrc);
+    LpOrder O;
+    order_lp(Lo, O, lrp, std::move(clen), m, n, lm1[(size_t)b], row0, col0, k_eln, t_eln);
+    host_entries(O, lrp, lcol, nnz0, lnnz, k_est, k_ecol, k_esrc, t_est, t_ecol, t_esrc);
     const int64_t mp = Lo.mpad - rbase, np = Lo.npad - cbase;
     SellHost sk = build_sell(mp, k_est, k_eln, k_ecol, k_esrc, (int32_t)cbase);
     SellHost stt = build_sell(np, t_est, t_eln, t_ecol, t_esrc, (int32_t)rbase);
@@ -1415,7 +1623,7 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
     row0 += m;
     col0 += n;
   }
-  device_setup_common(h, Lo, H, c_in, q_in, l_in, u_in);
+  device_setup_common(h, Lo, nullptr, &H.val, c_in, q_in, l_in, u_in);
 
   init_batch_launch(h, Lo, npad_max, mpad_max);
   if (P.precision == PDLP_MIXED) setup_mixed(h);
@@ -1916,6 +2124,11 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->batch_resident = h->last_glob ? 3 : (h->last_resident ? 1 : 0);
     info->wide_rows_K = h->K.nwide;
     info->batch_resumed = (int32_t)h->last_resumed;
+    info->setup_validate_ms = h->setup_ms[0];
+    info->setup_layout_ms = h->setup_ms[1];
+    info->setup_device_ms = h->setup_ms[2];
+    info->setup_tune_ms = h->setup_ms[3];
+    info->setup_step_ms = h->setup_ms[4];
     return PDLP_OK;
   });
 }

@@ -1,0 +1,120 @@
+"""The device layout builder of pdlp_setup against the host builder of pdlp_batch_setup.
+
+For an LP without wide rows both builders must produce the same SELL-32 layouts of K
+and K' (rows by decreasing length, equality rows first; K rows in the caller's entry
+order, K' rows by increasing row), so with the same schedule parameters the products
+K v and K' v of a single-LP handle and of a batch holding only that LP agree bit for
+bit.  The cases span one to three radix passes of the CSC sort (n up to 2^17), several
+scan tiles, ragged tails, empty rows and columns, repeated columns within a row and
+equality rows; scipy checks the products besides (1e-13 of sum |K_ij v_j| per row).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULE = dict(tile_slots=64, tile_chunks=4, spmv_batch=8)
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_2312_14832_b300 import build
+    build.build()
+    import paper_2312_14832_b300 as pk
+    return pk
+
+
+def _lp(seed, m, n, max_len, m1_frac=0.3, zipf=True, repeats=True):
+    """Row lengths up to max_len (< 1024, so no wide rows); columns Zipf-skewed (long
+    and empty columns), drawn with replacement when repeats (repeated columns in a row)."""
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(0, max_len + 1, size=m)
+    lengths[rng.random(m) < 0.05] = 0
+    rows = np.repeat(np.arange(m), lengths)
+    if zipf:
+        w = 1.0 / np.arange(1, n + 1) ** 1.1
+        cols = rng.choice(n, size=rows.size, p=w / w.sum())
+    else:
+        cols = rng.integers(0, n, size=rows.size)
+    if not repeats:
+        keep = np.unique(rows.astype(np.int64) * n + cols, return_index=True)[1]
+        keep.sort()
+        rows, cols = rows[keep], cols[keep]
+    vals = rng.standard_normal(rows.size) * 10.0 ** rng.uniform(-2, 2, rows.size)
+    rp = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rp, rows + 1, 1)
+    rp = np.cumsum(rp)
+    order = np.argsort(rows, kind="stable")   # already row-major; keeps in-row order
+    return dict(m=m, n=n, m1=int(m * m1_frac), row_ptr=rp, col_idx=cols[order].astype(np.int32),
+                val=vals[order], c=rng.standard_normal(n), q=rng.standard_normal(m),
+                l=-np.ones(n), u=np.ones(n))
+
+
+CASES = {
+    "tiny": (0, 40, 30, 6),
+    "two_passes": (1, 700, 300, 40),
+    "three_passes": (2, 6000, 70000, 120),
+    "tall": (3, 50000, 900, 25),
+    "ragged": (4, 33, 100001, 700),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_device_layout_equals_host_layout(pk, case, scaling):
+    seed, m, n, max_len = CASES[case]
+    lp = _lp(seed, m, n, max_len)
+    rng = np.random.default_rng(seed + 100)
+    x = rng.standard_normal(n)
+    y = rng.standard_normal(m)
+    with pk.Solver.from_lp(lp, scaling=scaling, **SCHEDULE) as s, \
+            pk.BatchSolver.from_lps([lp], scaling=scaling, **SCHEDULE) as b:
+        assert s.info()["wide_rows_K"] == 0
+        kx, kty = s.spmv(x), s.spmv(y, transpose=True)
+        np.testing.assert_array_equal(kx, b.spmv(x))
+        np.testing.assert_array_equal(kty, b.spmv(y, transpose=True))
+    K = sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(m, n))
+    A = abs(K)
+    assert np.all(np.abs(kx - K @ x) <= 1e-13 * (A @ np.abs(x)) + 1e-300)
+    assert np.all(np.abs(kty - K.T @ y) <= 1e-13 * (A.T @ np.abs(y)) + 1e-300)
+
+
+def test_device_inputs_give_the_same_layout(pk):
+    """Device-resident inputs (copied device to device) build the same layout as host
+    inputs: identical products."""
+    import torch
+    lp = _lp(5, 3000, 20000, 60)
+    dev = {k: (torch.as_tensor(v).cuda() if isinstance(v, np.ndarray) else v) for k, v in lp.items()}
+    x = np.random.default_rng(6).standard_normal(lp["n"])
+    with pk.Solver.from_lp(lp, scaling=1, **SCHEDULE) as a, pk.Solver.from_lp(dev, scaling=1, **SCHEDULE) as b:
+        np.testing.assert_array_equal(a.spmv(x), b.spmv(torch.as_tensor(x).cuda()).cpu().numpy())
+
+
+def test_empty_matrix_and_no_rows(pk):
+    """nnz = 0 (one row without entries) and m = 0: the layouts are padding only."""
+    n = 50
+    base = dict(n=n, c=np.ones(n), l=np.zeros(n), u=np.ones(n))
+    for m in (0, 1):
+        lp = dict(base, m=m, m1=0, row_ptr=np.zeros(m + 1, dtype=np.int64), col_idx=np.zeros(0, np.int32),
+                  val=np.zeros(0), q=np.zeros(m))
+        with pk.Solver.from_lp(lp, scaling=1) as s:
+            assert np.all(s.spmv(np.ones(n)) == 0.0)
+            if m:
+                assert np.all(s.spmv(np.ones(m), transpose=True) == 0.0)
+            r = s.solve(tol=1e-8)
+            np.testing.assert_allclose(r["x"], np.zeros(n), atol=1e-8)
+
+
+def test_invalid_entries_are_rejected_on_the_device(pk):
+    """Column indices out of range (either side) and non-finite values are found by the
+    device check; a non-finite value is reported first, as before."""
+    lp = _lp(7, 200, 300, 20)
+    for k, v in (("col_idx", -1), ("col_idx", 300), ("val", np.inf), ("val", np.nan)):
+        bad = dict(lp, **{k: lp[k].copy()})
+        bad[k][len(bad[k]) // 2] = v
+        with pytest.raises(pk.SolverError) as e:
+            pk.Solver.from_lp(bad)
+        assert ("column index" in str(e.value)) == (k == "col_idx")
