@@ -133,6 +133,10 @@ typedef struct {
                               LPs that did not finish then continue in a second launch with
                               teams sized for their number (cluster_ctas 0).  The result is
                               the uninterrupted solve's up to summation order.  0 = one launch */
+  int32_t host_layout;     /* setup: 0 = the SELL layouts are built on the device from the
+                              caller's arrays (the host only orders rows and columns);
+                              1 = built entirely on the host (the reference builder: the
+                              same layouts, slower for large inputs)                       */
 } pdlp_params;
 
 typedef struct {

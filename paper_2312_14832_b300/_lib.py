@@ -21,7 +21,8 @@ class Params(C.Structure):
                 ("stream", C.c_void_p), ("log_capacity", C.c_int32), ("tile_chunks", C.c_int32),
                 ("spmv_batch", C.c_int32), ("precision", C.c_int32),
                 ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32),
-                ("step_rule", C.c_int32), ("engine", C.c_int32), ("batch_tail_iters", C.c_int64)]
+                ("step_rule", C.c_int32), ("engine", C.c_int32), ("batch_tail_iters", C.c_int64),
+                ("host_layout", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -20,15 +20,29 @@ namespace pdlp {
 // Input-check flags.
 enum : int { kBadCol = 1, kBadVal = 2 };
 
-// Checks every entry (column in [0, n), finite value) and counts the entries of each
-// column; entries with a bad column are not counted.
-__global__ void k_check_count(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t nnz,
-                              int32_t n, int32_t* __restrict__ clen, int* __restrict__ flags) {
+// Checks every entry of `count` LPs stored back to back (LP b: entries ent0[b] ..
+// ent0[b+1] - 1, columns col0[b] .. col0[b+1] - 1 of the global numbering): a local
+// column in [0, n_b) and a finite value.  Rewrites each column index as global and
+// counts the entries of each global column; entries with a bad column are left alone.
+__global__ void k_check_count(int32_t* __restrict__ col, const double* __restrict__ val, int64_t nnz,
+                              const int64_t* __restrict__ ent0, const int64_t* __restrict__ col0, int64_t count,
+                              int32_t* __restrict__ clen, int* __restrict__ flags) {
   int bad = 0;
   PDLP_GRID_STRIDE(k, nnz) {
+    int64_t lo = 0, hi = count - 1;   // the LP of entry k: the last b with ent0[b] <= k
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (ent0[mid] <= k) lo = mid;
+      else hi = mid - 1;
+    }
+    const int64_t c0 = col0[lo], nb = col0[lo + 1] - c0;
     const int32_t j = col[k];
-    if (j < 0 || j >= n) bad |= kBadCol;
-    else atomicAdd(&clen[j], 1);
+    if (j < 0 || j >= nb) {
+      bad |= kBadCol;
+    } else {
+      col[k] = (int32_t)(c0 + j);
+      atomicAdd(&clen[c0 + j], 1);
+    }
     if (!isfinite(val[k])) bad |= kBadVal;
   }
   if (bad) atomicOr(flags, bad);
@@ -169,14 +183,15 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
 // chunk's first row with entry (s - cptr[ch]) * 32 + lane.  Row p is the source row
 // r = perm[p] (-1: padding) whose entries are q = order[t] (order == nullptr: q = t) for
 // t in [ptr[r], ptr[r + 1]); an entry's output column is kmap[key[q]] and its value
-// val[q].  Padding slots take value 0 and the column of the row's first entry (pad_col
-// for an empty row), as in build_sell.
+// val[q].  Padding slots take value 0 and the column of the row's first entry, or for
+// an empty row pad[ch] (the first internal column of the chunk's LP), as in build_sell.
 template <class PT>
 __global__ void k_fill_sell(const int32_t* __restrict__ cptr, int64_t nchunks, const uint8_t* __restrict__ wide,
                             int64_t total, const int32_t* __restrict__ perm, const PT* __restrict__ ptr,
                             const int32_t* __restrict__ order, const int32_t* __restrict__ key,
-                            const int32_t* __restrict__ kmap, const double* __restrict__ val, int32_t pad_col,
-                            int32_t* __restrict__ out_col, double* __restrict__ out_val) {
+                            const int32_t* __restrict__ kmap, const double* __restrict__ val,
+                            const int32_t* __restrict__ pad, int32_t* __restrict__ out_col,
+                            double* __restrict__ out_val) {
   PDLP_GRID_STRIDE(e, total) {
     const int64_t s = e >> 5;
     const int lane = (int)(e & 31);
@@ -200,7 +215,7 @@ __global__ void k_fill_sell(const int32_t* __restrict__ cptr, int64_t nchunks, c
       out_col[e] = kmap[key[q]];
       out_val[e] = val[q];
     } else {
-      int32_t c = pad_col;
+      int32_t c = pad[lo];
       if (len > 0) c = kmap[key[order ? (int64_t)order[st] : st]];
       out_col[e] = c;
       out_val[e] = 0.0;

@@ -210,6 +210,8 @@ struct DevCsr {
   const int32_t* tp;
   const int32_t* csc;
   const int32_t* rowof;
+  const int32_t* kpad;   // padding column of each K chunk (first internal column of its LP)
+  const int32_t* tpad;   // padding column of each K' chunk (first internal row of its LP)
 };
 
 // Uploads the shape and task plan of a layout and allocates its arrays.
@@ -251,10 +253,10 @@ static void fill_device_sell(pdlp_ctx* h, DevSell& D, const SellHost& S, const T
   D.col = dalloc<int32_t>(h, (size_t)total);
   if (!transpose)
     k_fill_sell<int64_t><<<grid_for(total), 256, 0, h->s>>>(D.chunk_ptr, D.nchunks, D.wide, total, h->perm_r, C.rp,
-                                                           nullptr, C.col, h->pos_c, C.val, 0, D.col, D.val);
+                                                           nullptr, C.col, h->pos_c, C.val, C.kpad, D.col, D.val);
   else
     k_fill_sell<int32_t><<<grid_for(total), 256, 0, h->s>>>(D.chunk_ptr, D.nchunks, D.wide, total, h->perm_c, C.tp,
-                                                           C.csc, C.rowof, h->pos_r, C.val, 0, D.col, D.val);
+                                                           C.csc, C.rowof, h->pos_r, C.val, C.tpad, D.col, D.val);
   CKL("k_fill_sell");
 }
 
@@ -577,6 +579,7 @@ static void check_params(const pdlp_params& P) {
   if (P.resident < 0 || P.resident > 3) invalid("resident must be 0, 1, 2 or 3");
   if (P.step_rule < 0 || P.step_rule > 1) invalid("step_rule must be 0 or 1");
   if (P.engine < 0 || P.engine > 2) invalid("engine must be 0, 1 or 2");
+  if (P.host_layout < 0 || P.host_layout > 1) invalid("host_layout must be 0 or 1");
 }
 
 // Copies (from host or device) and validates one LP in CSR form; rows_total and the
@@ -863,6 +866,76 @@ static int32_t* dev_csc_order(pdlp_ctx* h, const int32_t* d_col, int64_t nnz, in
   return out;
 }
 
+// The caller's matrix on the device: count LPs back to back in one global numbering of
+// rows and columns, and what the device builder derives from it (DevCsr).
+struct DevMatrix {
+  int64_t* rp = nullptr;     // global row pointers (M + 1)
+  int32_t* col = nullptr;    // global column of each entry
+  double* val = nullptr;
+  int32_t* tp = nullptr;     // entries per global column, then column starts (N + 1)
+  int32_t* csc = nullptr;
+  int32_t* rowof = nullptr;
+  int32_t* kpad = nullptr;
+  int32_t* tpad = nullptr;
+  DevCsr csr() const { return DevCsr{rp, col, val, tp, csc, rowof, kpad, tpad}; }
+};
+
+// Copies the matrix of count = ent0.size() - 1 LPs to the device (LP b: entries
+// ent0[b] .. ent0[b+1] - 1 with local columns, its columns col0[b] .. col0[b+1] - 1 of
+// the global numbering; grp: global row pointers, host), checks the entries there and
+// counts the entries of each global column (clen, host).  Throws on a bad entry.
+static DevMatrix upload_matrix(pdlp_ctx* h, int64_t M, int64_t N, int64_t nnz, const int64_t* grp,
+                               const std::vector<int64_t>& ent0, const std::vector<int64_t>& col0,
+                               const int32_t* col_in, const double* val_in, std::vector<int32_t>& clen) {
+  DevMatrix A;
+  const cudaMemcpyKind kind = h->p.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  A.rp = dalloc<int64_t>(h, (size_t)M + 1);
+  A.col = dalloc<int32_t>(h, (size_t)nnz);
+  A.val = dalloc<double>(h, (size_t)nnz);
+  A.tp = dalloc<int32_t>(h, (size_t)N + 1);
+  int64_t* d_ent0 = upload(h, ent0);
+  int64_t* d_col0 = upload(h, col0);
+  int* d_flags = dalloc<int>(h, 1);
+  CK(cudaMemcpyAsync(A.rp, grp, sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, h->s));
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(A.col, col_in, sizeof(int32_t) * nnz, kind, h->s));
+    CK(cudaMemcpyAsync(A.val, val_in, sizeof(double) * nnz, kind, h->s));
+  }
+  k_check_count<<<grid_for(nnz), 256, 0, h->s>>>(A.col, A.val, nnz, d_ent0, d_col0, (int64_t)ent0.size() - 1, A.tp,
+                                                 d_flags);
+  CKL("k_check_count");
+  int flags = 0;
+  clen.resize((size_t)N);
+  CK(cudaMemcpyAsync(&flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(clen.data(), A.tp, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  for (void* v : {(void*)d_ent0, (void*)d_col0, (void*)d_flags}) dfree(h, v);
+  if (flags & kBadVal) invalid("non-finite matrix value");
+  if (flags & kBadCol) invalid("column index out of range");
+  return A;
+}
+
+// What K' needs: column starts (in place of the counts), the CSC order and the row of
+// each entry; and the padding column of each chunk of both layouts.
+static void finish_matrix(pdlp_ctx* h, DevMatrix& A, int64_t M, int64_t N, int64_t nnz,
+                          const std::vector<int32_t>& kpad, const std::vector<int32_t>& tpad) {
+  dev_exclusive_scan(h, A.tp, N + 1);
+  A.csc = dev_csc_order(h, A.col, nnz, N);
+  A.rowof = dalloc<int32_t>(h, (size_t)nnz);
+  k_row_of<<<grid_for(M * 32), 256, 0, h->s>>>(A.rp, M, A.rowof);
+  CKL("k_row_of");
+  A.kpad = upload(h, kpad);
+  A.tpad = upload(h, tpad);
+}
+
+static void free_matrix(pdlp_ctx* h, DevMatrix& A) {
+  CK(cudaStreamSynchronize(h->s));
+  for (void* v : {(void*)A.rp, (void*)A.col, (void*)A.val, (void*)A.tp, (void*)A.csc, (void*)A.rowof, (void*)A.kpad,
+                  (void*)A.tpad})
+    if (v) dfree(h, v);
+  A = DevMatrix{};
+}
+
 // Upload of the layouts and values, problem vectors in internal order, unscaled norms,
 // scaling and the scaled problem vectors: everything both handle kinds share.
 static void device_setup_common(pdlp_ctx* h, Layout& Lo, const DevCsr* dc, const std::vector<double>* hval,
@@ -910,57 +983,51 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
   check_vectors(h, n, m, c_in, q_in, l_in, u_in);
 
-  // the matrix goes to the device as it is; the entries are checked and the columns
-  // counted there
-  const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  int64_t* d_rp = dalloc<int64_t>(h, (size_t)m + 1);
-  int32_t* d_col = dalloc<int32_t>(h, (size_t)nnz);
-  double* d_val = dalloc<double>(h, (size_t)nnz);
-  int32_t* d_tp = dalloc<int32_t>(h, (size_t)n + 1);   // column counts, then column starts
-  int* d_flags = dalloc<int>(h, 1);
-  CK(cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, h->s));
-  if (nnz > 0) {
-    CK(cudaMemcpyAsync(d_col, col_in, sizeof(int32_t) * nnz, kind, h->s));
-    CK(cudaMemcpyAsync(d_val, val_in, sizeof(double) * nnz, kind, h->s));
-  }
-  k_check_count<<<grid_for(nnz), 256, 0, h->s>>>(d_col, d_val, nnz, (int32_t)n, d_tp, d_flags);
-  CKL("k_check_count");
-  int flags = 0;
-  std::vector<int32_t> clen((size_t)n);
-  CK(cudaMemcpyAsync(&flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-  CK(cudaMemcpyAsync(clen.data(), d_tp, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
-  if (flags & kBadVal) invalid("non-finite matrix value");
-  if (flags & kBadCol) invalid("column index out of range");
-  h->setup_ms[0] = ms_since(tp);
-  tp = clk::now();
-
-  // row and column order and the chunk shapes on the host
   Layout Lo;
   Lo.pos_r.assign((size_t)m, 0);
   Lo.pos_c.assign((size_t)n, 0);
-  {
-    std::vector<int32_t> k_eln, t_eln;
-    std::vector<uint8_t> k_wide;
-    int64_t m1i = m1;
-    LpOrder O;
+  std::vector<int32_t> k_eln, t_eln;
+  std::vector<uint8_t> k_wide;
+  int64_t m1i = m1;
+  LpOrder O;
+  if (P.host_layout) {
+    // the reference builder: entries copied, checked and laid out on the host
+    HostLP H;
+    fetch_and_validate(h, m, n, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, m + 1);
+    check_csr(H, 0, m, n, 0);
+    std::vector<int32_t> clen((size_t)n, 0);
+    for (int64_t k = 0; k < nnz; ++k) clen[(size_t)H.col[(size_t)k]]++;
+    h->setup_ms[0] = ms_since(tp);
+    tp = clk::now();
+    order_lp(Lo, O, rp, std::move(clen), m, n, m1, 0, 0, k_eln, t_eln, true, &k_wide, &m1i);
+    std::vector<int64_t> k_est, t_est;
+    std::vector<int32_t> k_ecol, k_esrc, t_ecol, t_esrc;
+    host_entries(O, rp, H.col.data(), 0, nnz, k_est, k_ecol, k_esrc, t_est, t_ecol, t_esrc);
+    Lo.SK = build_sell(Lo.mpad, k_est, k_eln, k_ecol, k_esrc, 0, &k_wide);
+    Lo.SKt = build_sell(Lo.npad, t_est, t_eln, t_ecol, t_esrc);
+    h->m1_int = m1i;
+    h->setup_ms[1] = ms_since(tp);
+    tp = clk::now();
+    device_setup_common(h, Lo, nullptr, &H.val, c_in, q_in, l_in, u_in);
+  } else {
+    // the matrix goes to the device as it is: entries checked and columns counted there;
+    // the host orders rows and columns (O(m + n)); the device fills the layouts
+    std::vector<int32_t> clen;
+    DevMatrix A = upload_matrix(h, m, n, nnz, rp, {0, nnz}, {0, n}, col_in, val_in, clen);
+    h->setup_ms[0] = ms_since(tp);
+    tp = clk::now();
     order_lp(Lo, O, rp, std::move(clen), m, n, m1, 0, 0, k_eln, t_eln, true, &k_wide, &m1i);
     h->m1_int = m1i;
     Lo.SK = sell_shape(Lo.mpad, k_eln, &k_wide);
     Lo.SKt = sell_shape(Lo.npad, t_eln);
+    h->setup_ms[1] = ms_since(tp);
+    tp = clk::now();
+    finish_matrix(h, A, m, n, nnz, std::vector<int32_t>((size_t)Lo.SK.nchunks, 0),
+                  std::vector<int32_t>((size_t)Lo.SKt.nchunks, 0));
+    const DevCsr dc = A.csr();
+    device_setup_common(h, Lo, &dc, nullptr, c_in, q_in, l_in, u_in);
+    free_matrix(h, A);
   }
-  h->setup_ms[1] = ms_since(tp);
-  tp = clk::now();
-  // K' from the CSC order: column starts, entries sorted by column, row of each entry
-  dev_exclusive_scan(h, d_tp, n + 1);
-  int32_t* d_csc = dev_csc_order(h, d_col, nnz, n);
-  int32_t* d_rowof = dalloc<int32_t>(h, (size_t)nnz);
-  k_row_of<<<grid_for(m * 32), 256, 0, h->s>>>(d_rp, m, d_rowof);
-  CKL("k_row_of");
-  const DevCsr dc{d_rp, d_col, d_val, d_tp, d_csc, d_rowof};
-  device_setup_common(h, Lo, &dc, nullptr, c_in, q_in, l_in, u_in);
-  for (void* v : {(void*)d_rp, (void*)d_col, (void*)d_val, (void*)d_tp, (void*)d_flags, (void*)d_csc, (void*)d_rowof})
-    dfree(h, v);
   CK(cudaStreamSynchronize(h->s));
   h->setup_ms[2] = ms_since(tp);
   tp = clk::now();
@@ -1564,46 +1631,49 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   h->m = M;
   h->n = N;
   h->m1 = 0;
-  // total nonzeros from each LP's last row pointer
-  std::vector<int64_t> rp((size_t)R);
-  if (P.inputs_on_device) CK(cudaMemcpy(rp.data(), row_ptr_in, sizeof(int64_t) * R, cudaMemcpyDeviceToHost));
-  else std::memcpy(rp.data(), row_ptr_in, sizeof(int64_t) * R);
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
+  auto t0 = clk::now();
+  const bool dev_in = P.inputs_on_device != 0;
+  if (dev_in && P.stream) CK(cudaStreamSynchronize((cudaStream_t)P.stream));
+  // row pointers on the host (the caller's array or a copy); each LP's start at 0 and
+  // nondecreasing; nonzeros from each LP's last row pointer
+  std::vector<int64_t> rp_copy;
+  const int64_t* rp = row_ptr_in;
+  if (dev_in) {
+    rp_copy.resize((size_t)R);
+    CK(cudaMemcpy(rp_copy.data(), row_ptr_in, sizeof(int64_t) * R, cudaMemcpyDeviceToHost));
+    rp = rp_copy.data();
+  }
+  std::vector<int64_t> ent0((size_t)count + 1, 0), col0v((size_t)count + 1, 0);
   int64_t nnz = 0;
   for (int64_t b = 0, r = 0; b < count; ++b) {
-    r += lm[(size_t)b];
-    if (rp[(size_t)r] < 0) invalid("negative row pointer");
-    nnz += rp[(size_t)r];
-    r += 1;
+    const int64_t m = lm[(size_t)b];
+    if (rp[r + m] < 0) invalid("negative row pointer");
+    if (rp[r] != 0) invalid("row_ptr[0] must be 0");
+    for (int64_t i = 0; i < m; ++i)
+      if (rp[r + i + 1] < rp[r + i]) invalid("row_ptr must be nondecreasing");
+    nnz += rp[r + m];
+    if (nnz >= ((int64_t)1 << 31)) invalid("total nnz must be below 2^31");
+    ent0[(size_t)b + 1] = nnz;
+    col0v[(size_t)b + 1] = col0v[(size_t)b] + ln[(size_t)b];
+    r += m + 1;
   }
-  if (nnz >= ((int64_t)1 << 31)) invalid("total nnz must be below 2^31");
   h->nnz = nnz;
-  HostLP H;
-  fetch_and_validate(h, M, N, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, R);
+  if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
+  check_vectors(h, N, M, c_in, q_in, l_in, u_in);
 
   Layout Lo;
   Lo.pos_r.assign((size_t)M, 0);
   Lo.pos_c.assign((size_t)N, 0);
   h->hdesc.resize((size_t)count);
-  int64_t rp0 = 0, nnz0 = 0, row0 = 0, col0 = 0, npad_max = 0, mpad_max = 0;
-  for (int64_t b = 0; b < count; ++b) {
-    const int64_t m = lm[(size_t)b], n = ln[(size_t)b];
-    const int64_t lnnz = check_csr(H, rp0, m, n, nnz0);
-    const int64_t* lrp = H.rp.data() + rp0;
-    const int32_t* lcol = H.col.data() + nnz0;
-    std::vector<int32_t> clen((size_t)n, 0);
-    for (int64_t k = 0; k < lnnz; ++k) clen[(size_t)lcol[k]]++;
-    std::vector<int64_t> k_est, t_est;
-    std::vector<int32_t> k_eln, t_eln, k_ecol, k_esrc, t_ecol, t_esrc;
-    const int64_t rbase = Lo.mpad, cbase = Lo.npad;
-    LpOrder O;
-    order_lp(Lo, O, lrp, std::move(clen), m, n, lm1[(size_t)b], row0, col0, k_eln, t_eln);
-    host_entries(O, lrp, lcol, nnz0, lnnz, k_est, k_ecol, k_esrc, t_est, t_ecol, t_esrc);
+  int64_t npad_max = 0, mpad_max = 0;
+  // appends LP b's layouts (shape only, or with host entry arrays) and its descriptor
+  auto add_lp = [&](int64_t b, SellHost&& sk, SellHost&& stt, int64_t rbase, int64_t cbase) {
     const int64_t mp = Lo.mpad - rbase, np = Lo.npad - cbase;
-    SellHost sk = build_sell(mp, k_est, k_eln, k_ecol, k_esrc, (int32_t)cbase);
-    SellHost stt = build_sell(np, t_est, t_eln, t_ecol, t_esrc, (int32_t)rbase);
     LpDesc& D = h->hdesc[(size_t)b];
-    D.m = (int32_t)m;
-    D.n = (int32_t)n;
+    D.m = (int32_t)lm[(size_t)b];
+    D.n = (int32_t)ln[(size_t)b];
     D.m1 = (int32_t)lm1[(size_t)b];
     D.pad0 = 0;
     D.kc0 = (int32_t)Lo.SK.nchunks;
@@ -1618,17 +1688,82 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
     D.npad = (int32_t)np;
     npad_max = std::max(npad_max, np);
     mpad_max = std::max(mpad_max, mp);
-    rp0 += m + 1;
-    nnz0 += lnnz;
-    row0 += m;
-    col0 += n;
+  };
+  if (P.host_layout) {
+    // the reference builder: entries copied, checked and laid out on the host
+    HostLP H;
+    fetch_and_validate(h, M, N, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, R);
+    h->setup_ms[0] = ms_since(t0);
+    t0 = clk::now();
+    int64_t rp0 = 0, row0 = 0;
+    for (int64_t b = 0; b < count; ++b) {
+      const int64_t m = lm[(size_t)b], n = ln[(size_t)b], nnz0 = ent0[(size_t)b];
+      const int64_t lnnz = check_csr(H, rp0, m, n, nnz0);
+      const int64_t* lrp = H.rp.data() + rp0;
+      const int32_t* lcol = H.col.data() + nnz0;
+      std::vector<int32_t> clen((size_t)n, 0);
+      for (int64_t k = 0; k < lnnz; ++k) clen[(size_t)lcol[k]]++;
+      std::vector<int64_t> k_est, t_est;
+      std::vector<int32_t> k_eln, t_eln, k_ecol, k_esrc, t_ecol, t_esrc;
+      const int64_t rbase = Lo.mpad, cbase = Lo.npad;
+      LpOrder O;
+      order_lp(Lo, O, lrp, std::move(clen), m, n, lm1[(size_t)b], row0, col0v[(size_t)b], k_eln, t_eln);
+      host_entries(O, lrp, lcol, nnz0, lnnz, k_est, k_ecol, k_esrc, t_est, t_ecol, t_esrc);
+      SellHost sk = build_sell(O.mp, k_est, k_eln, k_ecol, k_esrc, (int32_t)cbase);
+      SellHost stt = build_sell(O.np, t_est, t_eln, t_ecol, t_esrc, (int32_t)rbase);
+      add_lp(b, std::move(sk), std::move(stt), rbase, cbase);
+      rp0 += m + 1;
+      row0 += m;
+    }
+    h->setup_ms[1] = ms_since(t0);
+    t0 = clk::now();
+    device_setup_common(h, Lo, nullptr, &H.val, c_in, q_in, l_in, u_in);
+  } else {
+    // one global numbering: global row pointers, entries checked and counted on the
+    // device; each LP ordered on the host; the layouts filled on the device
+    std::vector<int64_t> grp((size_t)M + 1);
+    for (int64_t b = 0, r = 0, g = 0; b < count; ++b) {
+      const int64_t m = lm[(size_t)b];
+      for (int64_t i = 0; i <= m; ++i) grp[(size_t)(g + i)] = ent0[(size_t)b] + rp[r + i];
+      r += m + 1;
+      g += m;
+    }
+    std::vector<int32_t> clen;
+    DevMatrix A = upload_matrix(h, M, N, nnz, grp.data(), ent0, col0v, col_in, val_in, clen);
+    h->setup_ms[0] = ms_since(t0);
+    t0 = clk::now();
+    std::vector<int32_t> kpad, tpad;
+    int64_t r = 0, row0 = 0;
+    for (int64_t b = 0; b < count; ++b) {
+      const int64_t m = lm[(size_t)b], n = ln[(size_t)b], c0 = col0v[(size_t)b];
+      std::vector<int32_t> k_eln, t_eln;
+      const int64_t rbase = Lo.mpad, cbase = Lo.npad;
+      LpOrder O;
+      order_lp(Lo, O, rp + r, std::vector<int32_t>(clen.begin() + c0, clen.begin() + c0 + n), m, n,
+               lm1[(size_t)b], row0, c0, k_eln, t_eln);
+      SellHost sk = sell_shape(O.mp, k_eln), stt = sell_shape(O.np, t_eln);
+      kpad.insert(kpad.end(), (size_t)sk.nchunks, (int32_t)cbase);
+      tpad.insert(tpad.end(), (size_t)stt.nchunks, (int32_t)rbase);
+      add_lp(b, std::move(sk), std::move(stt), rbase, cbase);
+      r += m + 1;
+      row0 += m;
+    }
+    h->setup_ms[1] = ms_since(t0);
+    t0 = clk::now();
+    finish_matrix(h, A, M, N, nnz, kpad, tpad);
+    const DevCsr dc = A.csr();
+    device_setup_common(h, Lo, &dc, nullptr, c_in, q_in, l_in, u_in);
+    free_matrix(h, A);
   }
-  device_setup_common(h, Lo, nullptr, &H.val, c_in, q_in, l_in, u_in);
+  CK(cudaStreamSynchronize(h->s));
+  h->setup_ms[2] = ms_since(t0);
+  t0 = clk::now();
 
   init_batch_launch(h, Lo, npad_max, mpad_max);
   if (P.precision == PDLP_MIXED) setup_mixed(h);
   else if (P.precision != PDLP_FP64) invalid("precision must be PDLP_FP64 or PDLP_MIXED");
   CK(cudaStreamSynchronize(h->s));
+  h->setup_ms[4] = ms_since(t0);
 }
 
 // CTAs per LP: the requested count, else one CTA per LP when the batch has enough LPs

@@ -1,12 +1,14 @@
-"""The device layout builder of pdlp_setup against the host builder of pdlp_batch_setup.
+"""The device layout builder (default) against the host builder (host_layout=1).
 
-For an LP without wide rows both builders must produce the same SELL-32 layouts of K
-and K' (rows by decreasing length, equality rows first; K rows in the caller's entry
-order, K' rows by increasing row), so with the same schedule parameters the products
-K v and K' v of a single-LP handle and of a batch holding only that LP agree bit for
-bit.  The cases span one to three radix passes of the CSC sort (n up to 2^17), several
-scan tiles, ragged tails, empty rows and columns, repeated columns within a row and
-equality rows; scipy checks the products besides (1e-13 of sum |K_ij v_j| per row).
+Both must produce the same SELL-32 layouts of K and K' (rows by decreasing length,
+equality rows first, wide rows spread over a chunk; K rows in the caller's entry order,
+K' rows by increasing row; padding columns inside each LP's range), so with the same
+schedule parameters the products K v and K' v agree bit for bit: single-LP handles
+built both ways, batches built both ways, and a single-LP handle against a batch
+holding only that LP.  The cases span one to three radix passes of the CSC sort (n up
+to 2^17), several scan tiles, ragged tails, empty rows, columns and LPs, repeated
+columns within a row, equality rows and wide rows; scipy checks the products besides
+(1e-13 of sum |K_ij v_j| per row).
 """
 import numpy as np
 import pytest
@@ -80,6 +82,67 @@ def test_device_layout_equals_host_layout(pk, case, scaling):
     A = abs(K)
     assert np.all(np.abs(kx - K @ x) <= 1e-13 * (A @ np.abs(x)) + 1e-300)
     assert np.all(np.abs(kty - K.T @ y) <= 1e-13 * (A.T @ np.abs(y)) + 1e-300)
+
+
+WIDE = {"wide_rows": (8, 3000, 5000, 30)}
+
+
+@pytest.mark.parametrize("case", list(CASES) + list(WIDE))
+def test_device_builder_equals_host_builder(pk, case):
+    seed, m, n, max_len = {**CASES, **WIDE}[case]
+    lp = _lp(seed, m, n, max_len)
+    if case in WIDE:   # two dense rows (one equality, one inequality): wide rows
+        rp, ci, v = lp["row_ptr"], lp["col_idx"], lp["val"]
+        rows = [np.arange(n, dtype=np.int32)[::s] for s in (1, 2)]
+        lens = np.diff(rp)
+        lens[0], lens[-1] = rows[0].size, rows[1].size
+        newc = [rows[0]] + [ci[rp[i]:rp[i + 1]] for i in range(1, m - 1)] + [rows[1]]
+        lp = dict(lp, row_ptr=np.concatenate([[0], np.cumsum(lens)]).astype(np.int64),
+                  col_idx=np.concatenate(newc).astype(np.int32),
+                  val=np.random.default_rng(9).standard_normal(int(lens.sum())))
+    rng = np.random.default_rng(seed + 200)
+    x, y = rng.standard_normal(n), rng.standard_normal(m)
+    with pk.Solver.from_lp(lp, scaling=1, **SCHEDULE) as a, \
+            pk.Solver.from_lp(lp, scaling=1, host_layout=1, **SCHEDULE) as b:
+        assert a.info()["wide_rows_K"] == b.info()["wide_rows_K"] == (2 if case in WIDE else 0)
+        np.testing.assert_array_equal(a.spmv(x), b.spmv(x))
+        np.testing.assert_array_equal(a.spmv(y, transpose=True), b.spmv(y, transpose=True))
+        r1, r2 = a.solve(max_iter=300, tol=0.0), b.solve(max_iter=300, tol=0.0)
+        np.testing.assert_array_equal(r1["x"], r2["x"])
+        np.testing.assert_array_equal(r1["y"], r2["y"])
+
+
+def test_batch_device_builder_equals_host_builder(pk):
+    """A batch of varied LPs (an LP without rows, a one-column LP, ragged sizes): both
+    builders give identical products and identical batched solves."""
+    lps = [_lp(20 + i, m, n, L) for i, (m, n, L) in
+           enumerate([(300, 500, 30), (0, 40, 1), (50, 1, 1), (1200, 900, 60), (33, 70001, 200), (7, 7, 7)])]
+    M, N = sum(lp["m"] for lp in lps), sum(lp["n"] for lp in lps)
+    rng = np.random.default_rng(30)
+    x, y = rng.standard_normal(N), rng.standard_normal(M)
+    with pk.BatchSolver.from_lps(lps, scaling=1, **SCHEDULE) as a, \
+            pk.BatchSolver.from_lps(lps, scaling=1, host_layout=1, **SCHEDULE) as b:
+        np.testing.assert_array_equal(a.spmv(x), b.spmv(x))
+        np.testing.assert_array_equal(a.spmv(y, transpose=True), b.spmv(y, transpose=True))
+        ra, rb = a.solve(max_iter=256, tol=0.0), b.solve(max_iter=256, tol=0.0)
+        for u, v in zip(ra, rb):
+            np.testing.assert_array_equal(u["x"], v["x"])
+            np.testing.assert_array_equal(u["y"], v["y"])
+    blocks = [sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(lp["m"], lp["n"])) for lp in lps]
+    K = sp.block_diag(blocks, format="csr")
+    kx = K @ x
+    with pk.BatchSolver.from_lps(lps, scaling=1) as a:
+        assert np.all(np.abs(a.spmv(x) - kx) <= 1e-13 * (abs(K) @ np.abs(x)) + 1e-300)
+
+
+def test_batch_column_outside_its_lp_is_rejected(pk):
+    """A column index valid for the whole batch but not for its own LP is an error."""
+    lps = [_lp(40, 100, 50, 10), _lp(41, 100, 80, 10)]
+    bad = dict(lps[0], col_idx=lps[0]["col_idx"].copy())
+    bad["col_idx"][5] = 60   # < 130 columns in total, >= 50 of LP 0
+    with pytest.raises(pk.SolverError) as e:
+        pk.BatchSolver.from_lps([bad, lps[1]])
+    assert "column index" in str(e.value)
 
 
 def test_device_inputs_give_the_same_layout(pk):
