@@ -188,9 +188,11 @@ typedef struct {
   int32_t wide_rows_K;         /* rows of K stored spread over a chunk's lanes (dense rows)   */
   int32_t batch_resumed;       /* batch handles: LPs continued in the second stage of the last
                                   pdlp_batch_solve (batch_tail_iters > 0)                     */
-  /* single-LP handles: wall time of the setup phases (ms): copy and validation of the
-     input, the host-side layout, device upload + scaling, the SpMV autotuner, the step
-     size and primal weight (power iteration) with the rest of the setup */
+  /* wall time of the setup phases (ms): copy and checks of the input; the host's part of
+     the layout (row and column order, chunk shapes; with host_layout = 1 the whole
+     layout); the device's part (layout fill, upload, scaling); the SpMV autotuner
+     (single-LP handles); the step size and primal weight (power iteration) with the rest
+     of the setup */
   double setup_validate_ms, setup_layout_ms, setup_device_ms, setup_tune_ms, setup_step_ms;
 } pdlp_info;
 
@@ -205,7 +207,9 @@ void pdlp_default_params(pdlp_params* p);
  *   c, l, u  : double[n]; l_j <= u_j, l_j in R or -INFINITY, u_j in R or +INFINITY.
  *   q        : double[m], finite.
  *   p        : parameters (NULL = defaults).
- * Copies every input; builds the length-sorted device layout of K and K', scales
+ * Copies every input (the matrix arrays straight to the device, where the entries are
+ * checked and the layouts filled; p->host_layout = 1 builds them on the host instead);
+ * builds the length-sorted device layout of K and K', scales
  * (if p->scaling), estimates ||K||_2 and sets eta and the initial primal weight
  * (Section 2 leaves both open: eta = step_scale/||K||_2, omega0 = ||c||/||q||).
  * On success *out owns all device memory of the solver.

@@ -1,4 +1,6 @@
-// Host-side construction of the device layout of K and K'.
+// The SELL-32 layout of K and K' and its host-side parts: the chunk shapes (sell_shape),
+// the warp-task plan (plan_tasks) and the complete host builder (build_sell), which the
+// device builder of layout_kernels.cuh reproduces and the tests compare against.
 //
 // Rows are renumbered in order of decreasing length (equality rows keep the
 // first m1 positions, so the dual sign projection stays "row >= m1"), columns
