@@ -296,6 +296,18 @@ def bench_batched(args):
         seq_s += r1["solve_s"]
         seq_it += r1["iters"]
     seq_total = seq_s * args.count / len(sample)
+    # the CPU oracle (single thread) solving LPs of the same sample to the same tolerance,
+    # for about args.cpu_seconds, scaled to the whole batch
+    import oracle
+    cpu_s, cpu_n, t_cpu = 0.0, 0, time.perf_counter()
+    for i in sample:
+        if time.perf_counter() - t_cpu > args.cpu_seconds:
+            break
+        t1 = time.perf_counter()
+        oracle.solve(lps[i], tol=1e-4, scaling=args.batch_scaling, max_iter=args.batch_max_iter)
+        cpu_s += time.perf_counter() - t1
+        cpu_n += 1
+    cpu_total = cpu_s * args.count / max(cpu_n, 1)
     best = args.count / dev_s
     variant = "fp64"
     if mixed is not None and mixed["optimal"] >= int(np.sum(status == 0)) and mixed["lps_per_s"] > best:
@@ -312,6 +324,9 @@ def bench_batched(args):
            "sequential": {"sample": len(sample), "sample_s": seq_s, "sample_iters": seq_it,
                           "estimated_total_s": seq_total, "lps_per_s": args.count / seq_total},
            "speedup_vs_sequential": seq_total / dev_s, "setup_s": setup_s, "generate_s": gen_s,
+           "cpu_baseline": {"value": args.count / cpu_total, "unit": "LPs/s to 1e-4", "cores": 1, "kind": "oracle",
+                            "sample": f"oracle.solve to 1e-4 on {cpu_n} LPs of the sample ({cpu_s:.1f} s), "
+                                      f"scaled to {args.count} LPs"},
            "one_launch_device_s": one_launch_s, "two_stage": two_stage, "tail": tail, "mixed": mixed,
            "clocks": clocks}
     print(json.dumps(out))
@@ -365,6 +380,14 @@ def bench_mcf(args):
                             "rel_x_diff": float(np.linalg.norm(out["fp64_x"] - out["mixed_x"]) /
                                                 np.linalg.norm(out["fp64_x"]))}
     del out["fp64_x"], out["mixed_x"]
+    import oracle
+    x, y, k, t0 = np.zeros(lp["n"]), np.zeros(lp["m"]), 0, time.perf_counter()
+    while time.perf_counter() - t0 < args.cpu_seconds:
+        x, y = oracle.pdhg_step(lp, x, y, 1e-3, 1.0)
+        k += 1
+    el = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": k / el, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle",
+                           "sample": f"{k} oracle PDHG steps (FP64) on the same LP, {el:.1f} s"}
     out["value"] = out["mixed"]["iter_per_s"]
     out["dtype"] = "f32 iterations / f64 checks"
     print(json.dumps(out))
@@ -483,6 +506,15 @@ def bench_teams(args):
                                    "iters_max": max(x["iters"] for x in r)}
     out["medium64"] = med
     out["value"] = min(v["1e-04"]["ms"] for v in small.values())
+    import oracle
+    t0, k = time.perf_counter(), 0
+    while k < 3 or time.perf_counter() - t0 < min(args.cpu_seconds, 5.0):
+        ro = oracle.solve(lp, tol=1e-4)
+        k += 1
+    out["cpu_baseline"] = {"value": (time.perf_counter() - t0) / k * 1e3, "unit": "ms to 1e-4 (small planted LP)",
+                           "cores": 1, "kind": "oracle",
+                           "sample": f"oracle.solve of the small planted LP to 1e-4, {k} runs, {int(ro['iters'])} "
+                                     "iterations each"}
     print(json.dumps(out))
 
 
@@ -519,6 +551,13 @@ def bench_warmstart(args):
             if key.startswith("1e") or key[0].isdigit():
                 ev[key] = dict(val, heldout=k)
     model.close()
+    # the CPU oracle, cold, on held-out LPs to 1e-4
+    import oracle
+    t0, k, it = time.perf_counter(), 0, 0
+    while k < len(held) and (k < 2 or time.perf_counter() - t0 < args.cpu_seconds):
+        it += int(oracle.solve(held[k], tol=1e-4)["iters"])
+        k += 1
+    cpu_s = time.perf_counter() - t0
     n_in, hid, n_out = P.shape[1], 1024, train[0]["n"] + train[0]["m"] + 1
     flop_step = 2 * 256 * (n_in * hid + hid * hid + hid * n_out) * 3
     steps = args.ws_epochs * (len(train) // 256)
@@ -531,6 +570,9 @@ def bench_warmstart(args):
                       "train_tol": args.ws_train_tol, "train_fp32": bool(args.ws_train_mixed)},
            "evaluation": ev, "train_loss_first_last": [float(fit["losses"][0]), float(fit["losses"][-1])],
            "train_device_s": fit["train_device_s"],
+           "cpu_baseline": {"value": cpu_s / k, "unit": "s per held-out LP to 1e-4, cold", "cores": 1,
+                            "kind": "oracle", "sample": f"oracle.solve on {k} held-out LPs ({it / k:.0f} "
+                                                        "iterations on average)"},
            "train_tflops": flop_step * steps / max(fit["train_device_s"], 1e-9) / 1e12,
            "data_generation": {"solve_device_s": dev, "wall_s": data_s, "mean_iters": float(its.mean()),
                                "optimal": int(np.sum(st == 0)), "generate_s": gen_s}}
@@ -552,6 +594,8 @@ def main():
                     help="timed solve: 0 constant step (Section 2), 1 adaptive rule (units: attempts)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the small-LP time-to-tolerance section")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU work of the oracle baseline in the batched and mcf workloads")
     ap.add_argument("--count", type=int, default=4096, help="LPs in the batched workload")
     ap.add_argument("--batch-max-iter", type=int, default=200000)
     ap.add_argument("--batch-scaling", type=int, default=0)
