@@ -1,0 +1,104 @@
+"""Parity at the full size of the large workload: lpgen.planted_zipf(seed 0), n = 2e6,
+m = 1e6, about 2e7 nonzeros, the LP bench.py times, set up as bench.py does (Ruiz +
+Pock-Chambolle scaling, SpMV schedule chosen by the setup autotuner, the kernels
+launched per iteration as CUDA graphs).
+
+  * K x and K'y on sampled rows and columns (random ones, the longest, the ragged ends)
+    against the oracle's SpMV of the sampled sub-matrices: 1e-12 of sum |K_ij v_j|
+    (the products of the scaled layout carry a few extra roundings).
+  * Two check intervals, 128 PDHG iterations, with their restart decisions: every
+    element of the current and average iterates against the oracle at 1e-10 relative,
+    the same restarts and primal weight.  eta is given (0.9, the step of this scaled LP
+    to within 0.2 %), so the oracle skips its 100 power iterations on this LP.  The
+    adaptive step rule likewise over 64 attempts.
+  * The device layout builder against the host builder: bit-identical products (with
+    one fixed schedule on both), so the radix sort and the fill hold at 2e7 entries.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+ETA = 0.9
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_2312_14832_b300 import build
+    build.build()
+    import paper_2312_14832_b300 as pk
+    return pk
+
+
+@pytest.fixture(scope="module")
+def big():
+    lp = lpgen.planted_zipf(seed=0)
+    K = sp.csr_matrix((lp["val"], lp["col_idx"], lp["row_ptr"]), shape=(lp["m"], lp["n"]))
+    return lp, K
+
+
+def _sample(rng, lengths, count):
+    order = np.argsort(-lengths, kind="stable")
+    n = lengths.shape[0]
+    pick = np.concatenate([rng.choice(n, count, replace=False), order[:50], order[-50:],
+                           np.arange(max(0, n - 40), n)])
+    return np.unique(pick)
+
+
+def _rows_lp(M, rows):
+    S = M[rows].tocsr()
+    return dict(m=S.shape[0], n=S.shape[1], row_ptr=S.indptr.astype(np.int64), col_idx=S.indices.astype(np.int32),
+                val=S.data)
+
+
+def test_fullsize_spmv_on_sampled_rows_and_columns(pk, big):
+    lp, K = big
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(lp["n"])
+    y = rng.standard_normal(lp["m"])
+    rows = _sample(rng, np.diff(K.indptr), 2000)
+    Kt = K.T.tocsr()
+    cols = _sample(rng, np.diff(Kt.indptr), 2000)
+    with pk.Solver.from_lp(lp, scaling=1) as s:
+        assert s.info()["tasks_K"] > 10000   # the autotuned schedule of the full LP
+        kx = s.spmv(x)
+        kty = s.spmv(y, transpose=True)
+    A = abs(K)
+    want = oracle.spmv(_rows_lp(K, rows), x)
+    assert np.all(np.abs(kx[rows] - want) <= 1e-12 * (A[rows] @ np.abs(x)) + 1e-300)
+    want_t = oracle.spmv(_rows_lp(Kt, cols), y)
+    assert np.all(np.abs(kty[cols] - want_t) <= 1e-12 * (A.T.tocsr()[cols] @ np.abs(y)) + 1e-300)
+
+
+@pytest.mark.parametrize("step_rule,iters", [(0, 128), (1, 64)])
+def test_fullsize_check_intervals(pk, big, step_rule, iters):
+    lp, _ = big
+    ref = oracle.solve(lp, tol=0.0, max_iter=iters, scaling=1, eta=ETA, step_rule=step_rule)
+    with pk.Solver.from_lp(lp, scaling=1, eta=ETA, step_rule=step_rule) as s:
+        r = s.solve(tol=0.0, max_iter=iters)
+        assert r["launches"] > 1   # the kernels launched per iteration, as in the bench
+        assert r["iters"] == ref["iters"] == iters
+        np.testing.assert_array_equal(s.restarts(), ref["restart_iters"])
+        xc, yc = s.iterate(0)
+        xa, ya = s.iterate(1)
+    for got, want in ((xc, ref["x_cur"]), (yc, ref["y_cur"]), (xa, ref["x_avg"]), (ya, ref["y_avg"])):
+        scale = np.abs(want).max()
+        assert np.abs(got - want).max() <= 1e-10 * scale
+        assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+    assert abs(r["omega"] - ref["omega"]) <= 1e-10 * ref["omega"]
+
+
+def test_fullsize_device_builder_equals_host_builder(pk, big):
+    lp, _ = big
+    fixed = dict(tile_slots=32, tile_chunks=4, spmv_batch=8)
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(lp["n"]), rng.standard_normal(lp["m"])
+    with pk.Solver.from_lp(lp, scaling=1, **fixed) as a:
+        ax, ay = a.spmv(x), a.spmv(y, transpose=True)
+    with pk.Solver.from_lp(lp, scaling=1, host_layout=1, **fixed) as b:
+        np.testing.assert_array_equal(ax, b.spmv(x))
+        np.testing.assert_array_equal(ay, b.spmv(y, transpose=True))
