@@ -13,6 +13,19 @@ launched per iteration as CUDA graphs).
     adaptive step rule likewise over 64 attempts.
   * The device layout builder against the host builder: bit-identical products (with
     one fixed schedule on both), so the radix sort and the fill hold at 2e7 entries.
+
+The other full-size workloads, each in the configuration bench.py times:
+  * the multicommodity-flow LP (n = 8e6, 2.4e7 nonzeros): one check interval in FP64
+    element by element against the oracle; MIXED (FP32 iterations, FP64 checks) to 1e-4,
+    the returned point re-checked by the oracle's KKT routine, the objective within 1e-6
+    of the FP64 solve;
+  * the 4096-LP batch (5.5e8 nonzeros): the FP64 two-stage solve and the MIXED solve to
+    1e-4; sampled LPs (evenly spaced, the largest, the one that reaches the iteration
+    cap) solved by the oracle: the same status and iteration count and the objective
+    within 1e-6 (FP64), the point within the tolerance and the objective within 1e-3
+    (MIXED);
+  * the 200 x 300 transportation family (n = 60000): eight members batched, cold and
+    warm-started from a perturbed optimum, against the oracle from the same points.
 """
 import numpy as np
 import pytest
@@ -102,3 +115,78 @@ def test_fullsize_device_builder_equals_host_builder(pk, big):
     with pk.Solver.from_lp(lp, scaling=1, host_layout=1, **fixed) as b:
         np.testing.assert_array_equal(ax, b.spmv(x))
         np.testing.assert_array_equal(ay, b.spmv(y, transpose=True))
+
+
+def _check_point(lp, x, y, tol):
+    rp, rd, rg = oracle.relative_errors(lp, x, y)
+    assert max(rp, rd, rg) <= tol * (1 + 1e-6), (rp, rd, rg)
+
+
+def test_fullsize_mcf(pk):
+    lp = lpgen.mcf(0)
+    iters = 64
+    ref = oracle.solve(lp, tol=0.0, max_iter=iters, scaling=1, eta=ETA)
+    with pk.Solver.from_lp(lp, scaling=1, eta=ETA) as s:
+        r = s.solve(tol=0.0, max_iter=iters)
+        assert r["iters"] == ref["iters"] == iters
+        np.testing.assert_array_equal(s.restarts(), ref["restart_iters"])
+        xc, yc = s.iterate(0)
+    for got, want in ((xc, ref["x_cur"]), (yc, ref["y_cur"])):
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    with pk.Solver.from_lp(lp, scaling=1) as s:
+        r64 = s.solve(tol=1e-4)
+    with pk.Solver.from_lp(lp, scaling=1, precision=pk.MIXED) as s:
+        rm = s.solve(tol=1e-4)
+    assert r64["status"] == rm["status"] == pk.OPTIMAL
+    assert rm["fp32_iters"] > 0
+    _check_point(lp, r64["x"], r64["y"], 1e-4)
+    _check_point(lp, rm["x"], rm["y"], 1e-4)
+    assert abs(rm["primal_obj"] - r64["primal_obj"]) <= 1e-6 * abs(r64["primal_obj"])
+
+
+def test_fullsize_batch_4096(pk):
+    lps = lpgen.batch_planted(4096, seed=0)
+    nnz = np.array([lp["val"].shape[0] for lp in lps])
+    with pk.BatchSolver.from_lps(lps) as b:
+        res = b.solve(tol=1e-4, max_iter=200000, want_points=False, batch_tail_iters=8192)
+    its = np.array([r["iters"] for r in res])
+    sample = sorted(set(range(0, 4096, 512)) | {int(np.argmax(nnz)), int(np.argmax(its))})
+    with pk.BatchSolver.from_lps([lps[i] for i in sample]) as b:   # the sampled LPs' points
+        pts = b.solve(tol=1e-4, max_iter=200000)
+    with pk.BatchSolver.from_lps(lps, precision=pk.MIXED) as b:
+        rm = b.solve(tol=1e-4, max_iter=200000, want_points=False)
+    del b
+    for k, i in enumerate(sample):
+        lp, r = lps[i], res[i]
+        ref = oracle.solve(lp, tol=1e-4, max_iter=200000)
+        assert r["status"] == ref["status"], i
+        assert r["iters"] == ref["iters"] == pts[k]["iters"], i
+        if ref["status"] == pk.OPTIMAL:
+            assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"])), i
+            _check_point(lp, pts[k]["x"], pts[k]["y"], 1e-4)
+            assert rm[i]["status"] == pk.OPTIMAL, i
+            assert abs(rm[i]["primal_obj"] - ref["primal_obj"]) <= 1e-3 * (1 + abs(ref["primal_obj"])), i
+        else:
+            close = np.abs(pts[k]["x"] - ref["x"]).max() <= 1e-8 * max(np.abs(ref["x"]).max(), 1.0)
+            assert close, i
+
+
+def test_fullsize_transport_family_cold_and_warm(pk):
+    fam = lpgen.transport_family(200, 300, seed=0)
+    lps = [lpgen.transport_instance(fam, s) for s in range(100001, 100009)]
+    refs = [oracle.solve(lp, tol=1e-4) for lp in lps]
+    rng = np.random.default_rng(5)
+    x0 = [np.maximum(r["x"] * (1 + 0.05 * rng.standard_normal(lp["n"])), 0.0) for lp, r in zip(lps, refs)]
+    y0 = [r["y"] * (1 + 0.05 * rng.standard_normal(lp["m"])) for lp, r in zip(lps, refs)]
+    w0 = [1.0] * len(lps)
+    with pk.BatchSolver.from_lps(lps) as b:
+        cold = b.solve(tol=1e-4)
+        warm = b.solve(tol=1e-4, x0=x0, y0=y0, omega0=w0)
+        assert b.info()["batch_resident"] == 3   # iterates in global memory, as in the bench
+    for i, lp in enumerate(lps):
+        wref = oracle.solve(lp, tol=1e-4, x0=x0[i], y0=y0[i], omega0=w0[i])
+        for r, ref in ((cold[i], refs[i]), (warm[i], wref)):
+            assert r["status"] == ref["status"] == pk.OPTIMAL
+            assert r["iters"] == ref["iters"]
+            assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * (1 + abs(ref["primal_obj"]))
+            _check_point(lp, r["x"], r["y"], 1e-4)
