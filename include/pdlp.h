@@ -100,8 +100,11 @@ typedef struct {
   int32_t cluster_ctas;    /* pdlp_batch_solve: CTAs that share one LP (a thread-block
                               cluster; each keeps x and y in shared memory and owns a
                               slice of the rows and columns): 1..16, or 0 = automatic
-                              (one CTA per LP when the batch fills the GPU, else up to
-                              16 per LP)                                                    */
+                              (the largest power of two <= 16 whose CTAs for the batch
+                              come to at most 4 waves of the GPU's resident CTAs, with
+                              >= 64 columns of the largest LP per CTA, and at most 4
+                              with the iterates in global memory; one CTA per LP when
+                              the batch fills the GPU several times over)                  */
   int32_t resident;        /* pdlp_batch_solve: where the iterations find their data.
                               0 = automatic; 1 = x, y in shared memory (one replica per
                               CTA), K and K' streamed; 2 = also each CTA's slice of K, K'
