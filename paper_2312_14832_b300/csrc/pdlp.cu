@@ -298,19 +298,23 @@ __global__ void k_div_into(double* a, const double* w, const double* s, int64_t 
 
 // v <- (v * fr[i]) * fc[j] for K (transposed = 0: chunk rows are i, columns j) and for
 // K' (transposed = 1: chunk rows are j, columns i), so both copies round identically.
-// A wide chunk (wide[ch] != 0) holds one row, the chunk's first.
-__global__ void k_scale_sell2(double* v, const int32_t* col, const int32_t* chunk_ptr, int64_t nchunks,
+// One thread per (slot, lane) of the total = slots * 32 entries; a warp's slot is found
+// in chunk_ptr by binary search, so long chunks take no longer than short ones.  A wide
+// chunk (wide[ch] != 0) holds one row, the chunk's first.
+__global__ void k_scale_sell2(double* v, const int32_t* col, const int32_t* chunk_ptr, int64_t nchunks, int64_t total,
                               const double* fr, const double* fc, int transposed, const uint8_t* wide) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
-       ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t row = ch * 32 + ((wide != nullptr && wide[ch]) ? 0 : lane);
-    for (int64_t s = chunk_ptr[ch]; s < chunk_ptr[ch + 1]; ++s) {
-      const size_t e = (size_t)s * 32 + lane;
-      const double a = transposed ? fr[col[e]] : fr[row];
-      const double b = transposed ? fc[row] : fc[col[e]];
-      v[e] = (v[e] * a) * b;
+  PDLP_GRID_STRIDE(e, total) {
+    const int64_t s = e >> 5;
+    int64_t lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (chunk_ptr[mid] <= s) lo = mid;
+      else hi = mid - 1;
     }
+    const int64_t row = lo * 32 + ((wide != nullptr && wide[lo]) ? 0 : (e & 31));
+    const double a = transposed ? fr[col[e]] : fr[row];
+    const double b = transposed ? fc[row] : fc[col[e]];
+    v[e] = (v[e] * a) * b;
   }
 }
 
@@ -1173,10 +1177,11 @@ static void device_setup_common(pdlp_ctx* h, Layout& Lo, const DevCsr* dc, const
       }
       k_scale_factor<<<grid_for(mp), 256, 0, h->s>>>(h->tm, h->Dr, h->tm, mp);
       k_scale_factor<<<grid_for(np), 256, 0, h->s>>>(h->tn, h->Dc, h->tn, np);
-      k_scale_sell2<<<grid_for(h->K.nchunks * 32), 256, 0, h->s>>>(h->K.val, h->K.col, h->K.chunk_ptr,
-                                                                  h->K.nchunks, h->tm, h->tn, 0, h->K.wide);
-      k_scale_sell2<<<grid_for(h->Kt.nchunks * 32), 256, 0, h->s>>>(h->Kt.val, h->Kt.col, h->Kt.chunk_ptr,
-                                                                   h->Kt.nchunks, h->tm, h->tn, 1, h->Kt.wide);
+      k_scale_sell2<<<grid_for(h->K.slots * 32), 256, 0, h->s>>>(h->K.val, h->K.col, h->K.chunk_ptr, h->K.nchunks,
+                                                                h->K.slots * 32, h->tm, h->tn, 0, h->K.wide);
+      k_scale_sell2<<<grid_for(h->Kt.slots * 32), 256, 0, h->s>>>(h->Kt.val, h->Kt.col, h->Kt.chunk_ptr,
+                                                                 h->Kt.nchunks, h->Kt.slots * 32, h->tm, h->tn, 1,
+                                                                 h->Kt.wide);
       CKL("scaling pass");
     }
   }
