@@ -558,11 +558,12 @@ static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
 
 // ------------------------------------------------------------------ setup
 
-// Validated host copy of an LP (one LP, or the concatenation of a batch).
+// Host copy of the matrix of an LP (one LP, or the concatenation of a batch) for the
+// host builder.
 struct HostLP {
   std::vector<int64_t> rp;   // row pointers (per LP restarting at 0 for a batch)
   std::vector<int32_t> col;
-  std::vector<double> val, c, l, u, q;
+  std::vector<double> val;
 };
 
 static void init_handle_resources(pdlp_ctx* h) {
@@ -586,9 +587,6 @@ static void check_params(const pdlp_params& P) {
   if (P.host_layout < 0 || P.host_layout > 1) invalid("host_layout must be 0 or 1");
 }
 
-// Copies (from host or device) and validates one LP in CSR form; rows_total and the
-// sizes of the arrays are given by the caller (a batch validates each LP's rows and
-// columns against its own n through col_limit).
 // True when pred(i) holds for every i in [0, n) (checked in parallel ranges).
 template <class P>
 static bool all_of_range(int64_t n, P pred) {
@@ -603,10 +601,11 @@ static bool all_of_range(int64_t n, P pred) {
   return bad.load() == 0;
 }
 
-static void fetch_and_validate(pdlp_ctx* h, int64_t rows, int64_t cols, const int64_t* row_ptr_in,
-                               const int32_t* col_in, const double* val_in, const double* c_in,
-                               const double* q_in, const double* l_in, const double* u_in, HostLP& H,
-                               int64_t rp_count) {
+// The host builder's inputs (host_layout = 1): copies the row pointers (rp_count of
+// them), column indices and values of the matrix (h->nnz entries) to the host and checks
+// that the values are finite; the vectors are checked by check_vectors.
+static void fetch_matrix(pdlp_ctx* h, const int64_t* row_ptr_in, const int32_t* col_in, const double* val_in,
+                         HostLP& H, int64_t rp_count) {
   const bool dev_in = h->p.inputs_on_device != 0;
   auto fetch = [&](void* dst, const void* src, size_t bytes) {
     if (bytes == 0) return;
@@ -618,37 +617,15 @@ static void fetch_and_validate(pdlp_ctx* h, int64_t rows, int64_t cols, const in
       }, (int64_t)1 << 22);
     }
   };
+  const int64_t nnz = h->nnz;
   H.rp.resize((size_t)rp_count);
-  fetch(H.rp.data(), row_ptr_in, sizeof(int64_t) * rp_count);
-  (void)rows;
-  int64_t nnz = 0;
-  // the caller checks the row pointers of each LP and sets nnz through H.rp; here only sizes
-  for (int64_t i = 0; i < rp_count; ++i)
-    if (H.rp[(size_t)i] < 0) invalid("negative row pointer");
-  nnz = h->nnz;
-  if (nnz > 0 && (!col_in || !val_in)) invalid("null col_idx/val with nnz > 0");
   H.col.resize((size_t)nnz);
   H.val.resize((size_t)nnz);
-  H.c.resize((size_t)cols);
-  H.l.resize((size_t)cols);
-  H.u.resize((size_t)cols);
-  H.q.resize((size_t)h->m);
+  fetch(H.rp.data(), row_ptr_in, sizeof(int64_t) * rp_count);
   fetch(H.col.data(), col_in, sizeof(int32_t) * nnz);
   fetch(H.val.data(), val_in, sizeof(double) * nnz);
-  fetch(H.c.data(), c_in, sizeof(double) * cols);
-  fetch(H.l.data(), l_in, sizeof(double) * cols);
-  fetch(H.u.data(), u_in, sizeof(double) * cols);
-  fetch(H.q.data(), q_in, sizeof(double) * h->m);
   if (!all_of_range(nnz, [&](int64_t k) { return std::isfinite(H.val[(size_t)k]); }))
     invalid("non-finite matrix value");
-  for (int64_t j = 0; j < cols; ++j) {
-    const double a = H.l[(size_t)j], b = H.u[(size_t)j];
-    if (!std::isfinite(H.c[(size_t)j])) invalid("non-finite c");
-    if (std::isnan(a) || std::isnan(b) || a == INFINITY || b == -INFINITY || a > b)
-      invalid("bounds must satisfy l <= u, l < +inf, u > -inf");
-  }
-  for (int64_t i = 0; i < h->m; ++i)
-    if (!std::isfinite(H.q[(size_t)i])) invalid("non-finite q");
 }
 
 // Checks row pointers [rp0, rp0 + m] of one LP (starting at 0) and its column indices.
@@ -997,7 +974,7 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   if (P.host_layout) {
     // the reference builder: entries copied, checked and laid out on the host
     HostLP H;
-    fetch_and_validate(h, m, n, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, m + 1);
+    fetch_matrix(h, row_ptr_in, col_in, val_in, H, m + 1);
     check_csr(H, 0, m, n, 0);
     std::vector<int32_t> clen((size_t)n, 0);
     for (int64_t k = 0; k < nnz; ++k) clen[(size_t)H.col[(size_t)k]]++;
@@ -1697,7 +1674,7 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
   if (P.host_layout) {
     // the reference builder: entries copied, checked and laid out on the host
     HostLP H;
-    fetch_and_validate(h, M, N, row_ptr_in, col_in, val_in, c_in, q_in, l_in, u_in, H, R);
+    fetch_matrix(h, row_ptr_in, col_in, val_in, H, R);
     h->setup_ms[0] = ms_since(t0);
     t0 = clk::now();
     int64_t rp0 = 0, row0 = 0;
