@@ -316,7 +316,7 @@ int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, const double* x0, cons
  * C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then max(., 0) if relu) on the tcgen05
  * tensor cores: A and B BF16 row-major (K contiguous) device arrays, C FP32 row-major
  * device array, bias FP32 device array or NULL.  M and N multiples of 128, K a multiple
- * of 64.  Used by the learned warm start (a spec extension: the paper has no
+ * of 64.  Used by the learned warm start (an extension: the paper has no
  * learned component); exposed for testing.  Runs on `stream` (NULL = default) and
  * waits for it.  Errors: PDLP_EINVAL (shapes), PDLP_ECUDA, PDLP_ETIMEOUT (an mbarrier
  * wait gave up). */
@@ -324,7 +324,7 @@ int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, 
                  int32_t relu, void* stream);
 
 /* ---------------------------------------------------------------- warm-start network
- * A 3-layer MLP for learned warm starts (a spec extension; the paper has no
+ * A 3-layer MLP for learned warm starts (an extension; the paper has no
  * learned component):  Y = relu(relu(X W1' + b1) W2' + b2) W3' + b3,
  * W1 [hidden x n_in], W2 [hidden x hidden], W3 [n_out x hidden], row-major FP32 masters.
  * Every product runs on the tcgen05 tensor cores with BF16 operands and FP32

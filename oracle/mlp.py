@@ -1,4 +1,4 @@
-"""CPU reference of the warm-start network (the spec extension; the paper has no
+"""CPU reference of the warm-start network (an extension of the method; the paper has no
 learned component).  TEST INFRASTRUCTURE ONLY, like the rest of oracle/.
 
 Y = relu(relu(X W1' + b1) W2' + b2) W3' + b3, loss L = sum (Y - T)^2 / (2 rows n_out),

@@ -493,7 +493,7 @@ __global__ void k_absmax(const double* __restrict__ v, int64_t len, unsigned lon
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
-// Mixed precision (spec extension, not in the paper): the same primal and dual
+// Mixed precision (an extension, not in the paper): the same primal and dual
 // steps with FP32 iterates and FP32 arithmetic; the running sums of the inner loop
 // are FP32 over one check interval and folded into FP64 at every check.
 struct EpiPrimal32 {

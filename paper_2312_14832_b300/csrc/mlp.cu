@@ -1,4 +1,4 @@
-// The learned warm start's network (a spec extension; the paper has no learned
+// The learned warm start's network (an extension; the paper has no learned
 // component): a 3-layer MLP  X -> relu(X W1' + b1) -> relu(. W2' + b2) -> . W3' + b3,
 // BF16 operands on the tcgen05 tensor cores (tc_gemm.cuh) with FP32 accumulation,
 // FP32 master weights, MSE loss and AdamW, forward and backward all on the device.

@@ -1,4 +1,4 @@
-// Host driver and C ABI of the restarted-PDHG solver (declarations and contract in
+// Host side and C ABI of the restarted-PDHG solver (declarations and contract in
 // include/pdlp.h; method: arXiv 2312.14832, Section 2).
 //
 // pdlp_setup orders rows and columns by length on the host (O(m + n) work), builds the

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (derived from FP64 rounding of the sums and of the iteration):
   * SpMV: |gpu - oracle| <= 1e-13 * sum_j |K_ij x_j| per row (different summation
     order only; FP64 rounding is ~1e-16 per term).
   * iterates after a fixed number of PDHG iterations: relative 1e-10 in the 2-norm
