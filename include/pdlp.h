@@ -102,9 +102,9 @@ typedef struct {
                               slice of the rows and columns): 1..16, or 0 = automatic
                               (the largest power of two <= 16 whose CTAs for the batch
                               come to at most 4 waves of the GPU's resident CTAs, with
-                              >= 64 columns of the largest LP per CTA, and at most 4
-                              with the iterates in global memory; one CTA per LP when
-                              the batch fills the GPU several times over)                  */
+                              >= 64 columns of the largest LP per CTA; with the iterates
+                              in global memory at most 4 CTAs and one wave; one CTA per
+                              LP when the batch fills the GPU)                             */
   int32_t resident;        /* pdlp_batch_solve: where the iterations find their data.
                               0 = automatic; 1 = x, y in shared memory (one replica per
                               CTA), K and K' streamed; 2 = also each CTA's slice of K, K'

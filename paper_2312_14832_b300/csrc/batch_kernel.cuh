@@ -148,11 +148,21 @@ enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
 #ifndef PDLP_BATCH_MIN_BLOCKS
 #define PDLP_BATCH_MIN_BLOCKS 3
 #endif
+// With the iterates in global memory shared memory holds only the reduction scratch, and
+// the latency-bound kernels gain from a fourth CTA per SM despite the spills: 200 x 300
+// transportation LPs to 1e-4 (3000-iteration cap), 512 / 1000 LPs FP64 4.18 / 6.69 s ->
+// 2.89 / 5.72 s, FP32 4.18 / 6.50 s -> 2.61 / 4.95 s (64 LPs on teams of 4: 0.67 -> 0.79 s).
+#ifndef PDLP_BATCH_CL_GLOB_MIN_BLOCKS
+#define PDLP_BATCH_CL_GLOB_MIN_BLOCKS 4
+#endif
+#ifndef PDLP_BATCH_GLOB_MIN_BLOCKS
+#define PDLP_BATCH_GLOB_MIN_BLOCKS 4
+#endif
 #ifndef PDLP_BATCH32_MIN_BLOCKS
 #define PDLP_BATCH32_MIN_BLOCKS 2
 #endif
 #ifndef PDLP_BATCH32_GLOB_MIN_BLOCKS
-#define PDLP_BATCH32_GLOB_MIN_BLOCKS 3   // FP32 kernel with the iterates in global memory (300 transport LPs: 0.90 -> 0.81 ms per iteration)
+#define PDLP_BATCH32_GLOB_MIN_BLOCKS 4   // FP32 kernel with the iterates in global memory (see above)
 #endif
 constexpr int kBB = PDLP_BATCH_LOADS;
 // The row loops ask the L2 for the slots of the warp's next chunk while they work on the
@@ -1241,7 +1251,7 @@ __global__ void __launch_bounds__(256, (kGlob && !kCl) ? PDLP_BATCH32_GLOB_MIN_B
 // Persistent solver: teams draw LPs from the queue until it is empty.  The counter
 // resets itself: the last of the failing draws (one per team) stores 0.
 template <bool kCl, bool kRes, bool kGlob>
-__global__ void __launch_bounds__(256, kCl ? 2 : PDLP_BATCH_MIN_BLOCKS) k_batch_solve(BatchArgs A) {
+__global__ void __launch_bounds__(256, kCl ? (kGlob ? PDLP_BATCH_CL_GLOB_MIN_BLOCKS : 2) : (kGlob ? PDLP_BATCH_GLOB_MIN_BLOCKS : PDLP_BATCH_MIN_BLOCKS)) k_batch_solve(BatchArgs A) {
   __shared__ int lp;
   Team<kCl> T;
   T.init();

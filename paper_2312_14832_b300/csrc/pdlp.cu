@@ -1755,11 +1755,12 @@ static void batch_setup_impl(pdlp_ctx* h, int64_t count, const int64_t* m_in, co
 // that finished LPs free, so a few waves beat one wave of smaller teams: 16..256 planted
 // LPs with n ~ U(2000, 5000) chose 16, 16, 16, 8, 4 CTAs (within 4 % of the best of
 // 1..16 each; the former one-wave rule, 16, 8, 4, 2, 1, was up to 3.2x slower).  With
-// the iterates in global memory teams beyond 4 lose (64 transportation LPs, n = 60000:
-// 3.7 s with 4 CTAs, 4.5 s with 8, 6.9 s with 16), so the automatic choice stops at 4
-// there (64 / 256 / 512 of those LPs: 4 / 4 / 2 CTAs, within 8 % of the best).
+// the iterates in global memory (four CTAs per SM) teams beyond 4 lose and one wave is
+// best: 200 x 300 transportation LPs (n = 60000), 64 / 128 / 256 / 512 / 1000 of them,
+// get 4 / 4 / 2 / 1 / 1 CTAs, the best of 1, 2, 4 at each count.
 constexpr int64_t kTeamWaves = 4;
 constexpr int kTeamGlobMax = 4;
+constexpr int64_t kTeamWavesGlob = 1;
 // The same cut of chunks [c0, c1) into `size` pieces as split_point on the device.
 static int host_split_point(const std::vector<int32_t>& cptr, int c0, int c1, int r, int size) {
   if (r <= 0) return c0;
@@ -1795,8 +1796,9 @@ static long long resident_need(const pdlp_ctx* h, int team) {
 static int batch_team_size(const pdlp_ctx* h, int64_t count, int team_req, bool glob) {
   if (team_req > 0) return team_req;
   const int cap = glob ? kTeamGlobMax : kMaxTeam;
+  const int64_t waves = glob ? kTeamWavesGlob : kTeamWaves;
   int team = 1;
-  while (team < cap && count * (int64_t)(team * 2) <= kTeamWaves * (int64_t)h->batch_resident &&
+  while (team < cap && count * (int64_t)(team * 2) <= waves * (int64_t)h->batch_resident &&
          h->team_npad_max >= (int64_t)(team * 2) * 64)
     team *= 2;
   return team;
