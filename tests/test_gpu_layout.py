@@ -181,3 +181,52 @@ def test_invalid_entries_are_rejected_on_the_device(pk):
         with pytest.raises(pk.SolverError) as e:
             pk.Solver.from_lp(bad)
         assert ("column index" in str(e.value)) == (k == "col_idx")
+
+
+@pytest.mark.parametrize("host_layout", [0, 1])
+def test_batch_setup_from_device_arrays(pk, host_layout):
+    """pdlp_batch_setup with every array on the device (params.inputs_on_device = 1,
+    called through the C ABI): the same products and the same batched solve as the
+    same LPs from host arrays."""
+    import ctypes as C
+    import torch
+    from paper_2312_14832_b300 import _lib
+    lps = [_lp(50 + i, m, n, L) for i, (m, n, L) in enumerate([(300, 500, 30), (0, 40, 1), (1200, 900, 60)])]
+    M, N = sum(lp["m"] for lp in lps), sum(lp["n"] for lp in lps)
+    lib = _lib.load()
+    sizes = [np.array([lp[k] for lp in lps], dtype=np.int64) for k in ("m", "n", "m1")]
+    cat = lambda key, dt: torch.as_tensor(np.concatenate([np.asarray(lp[key], dtype=dt) for lp in lps])).cuda()
+    dev = [cat("row_ptr", np.int64), cat("col_idx", np.int32), cat("val", np.float64), cat("c", np.float64),
+           cat("q", np.float64), cat("l", np.float64), cat("u", np.float64)]
+    torch.cuda.synchronize()
+    p = pk.default_params(scaling=1, host_layout=host_layout, **SCHEDULE)
+    p.inputs_on_device = 1
+    h = C.c_void_p()
+    rc = lib.pdlp_batch_setup(C.byref(h), len(lps), *[a.ctypes.data for a in sizes],
+                              *[t.data_ptr() for t in dev], C.byref(p))
+    assert rc == 0, lib.pdlp_last_error(None).decode()
+    try:
+        rng = np.random.default_rng(60)
+        x, y = rng.standard_normal(N), rng.standard_normal(M)
+        outs = []
+        for v, tr, size in ((x, 0, M), (y, 1, N)):
+            vin = torch.as_tensor(v).cuda()
+            out = torch.empty(size, dtype=torch.float64, device="cuda")
+            assert lib.pdlp_spmv(h, tr, vin.data_ptr(), out.data_ptr()) == 0
+            outs.append(out.cpu().numpy())
+        res = (_lib.Result * len(lps))()
+        xo = torch.empty(N, dtype=torch.float64, device="cuda")
+        yo = torch.empty(M, dtype=torch.float64, device="cuda")
+        q = _lib.Params()
+        C.memmove(C.byref(q), C.byref(p), C.sizeof(q))
+        q.tol, q.max_iter = 0.0, 256
+        assert lib.pdlp_batch_solve(h, C.byref(q), None, None, None, res, xo.data_ptr(), yo.data_ptr()) == 0
+        xd, yd = xo.cpu().numpy(), yo.cpu().numpy()
+    finally:
+        lib.pdlp_free(h)
+    with pk.BatchSolver.from_lps(lps, scaling=1, **SCHEDULE) as b:
+        np.testing.assert_array_equal(outs[0], b.spmv(x))
+        np.testing.assert_array_equal(outs[1], b.spmv(y, transpose=True))
+        ref = b.solve(max_iter=256, tol=0.0)
+    np.testing.assert_array_equal(xd, np.concatenate([r["x"] for r in ref]))
+    np.testing.assert_array_equal(yd, np.concatenate([r["y"] for r in ref]))
