@@ -23,10 +23,11 @@
  *    pdlp_last_error(NULL) for a failed pdlp_setup).  No C++ exception
  *    crosses this boundary.
  *  - A handle is not thread-safe; use one handle per host thread.
- *  - Array arguments are plain pointers.  For pdlp_setup / pdlp_solve /
- *    pdlp_get_iterate / pdlp_spmv they are host pointers unless
- *    params.inputs_on_device = 1, in which case they are device pointers on
- *    the current CUDA device.  The library copies what it needs; callers keep
+ *  - Array arguments are plain pointers.  For pdlp_setup / pdlp_batch_setup
+ *    (whose per-LP size arrays are always host arrays) / pdlp_solve /
+ *    pdlp_batch_solve / pdlp_get_iterate / pdlp_spmv / pdlp_bound_duals they
+ *    are host pointers unless the setup's params.inputs_on_device = 1, in which
+ *    case they are device pointers on the current CUDA device.  The library copies what it needs; callers keep
  *    ownership of their arrays and may free them after the call returns.
  *  - All vectors the caller sees are in the caller's (original, unscaled)
  *    row and column order.
