@@ -260,8 +260,9 @@ int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out);
 
 /* Bound duals lambda = proj_Lambda(c - K'y) of a dual point y (Section 2: Lambda_j is
  * {0}, R^-, R^+ or R as l_j, u_j are infinite or finite), on the original (unscaled)
- * problem; the solver does not return lambda with the point.  y: m host doubles (device
- * when params.inputs_on_device), lambda_out: n host doubles.  Single-LP handles only.
+ * problem; the solver does not return lambda with the point.  y: m doubles, lambda_out:
+ * n doubles (both host arrays, or device arrays when the setup's params.inputs_on_device
+ * = 1).  Single-LP handles only.
  * Errors: PDLP_EINVAL (NULL pointers, batch handle), PDLP_ECUDA. */
 int pdlp_bound_duals(pdlp_handle h, const double* y, double* lambda_out);
 
