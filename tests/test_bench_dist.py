@@ -45,3 +45,21 @@ def test_replica_aggregation_two_gloo_ranks():
         ms, value = res[r]
         assert ms == pytest.approx(150.0)
         assert value == pytest.approx(2 * 640 / 0.150)
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference (the CPU oracle's PDHG step, timed on the host) prints one
+    JSON line with the contract's keys, on the small workload."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "small", "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "higher_is_better", "dtype", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
