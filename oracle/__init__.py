@@ -48,7 +48,14 @@ class Result(C.Structure):
                 ("restarts", C.c_int64), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("rel_primal", C.c_double), ("rel_dual", C.c_double), ("rel_gap", C.c_double),
                 ("kkt_omega", C.c_double), ("omega", C.c_double), ("eta", C.c_double),
-                ("accepted", C.c_int64)]
+                ("accepted", C.c_int64), ("checks", C.c_int64)]
+
+
+class CheckRecord(C.Structure):
+    _fields_ = [("k", C.c_int64), ("t", C.c_int64), ("restart", C.c_int32), ("candidate", C.c_int32),
+                ("omega", C.c_double), ("kkt_cur", C.c_double), ("kkt_avg", C.c_double),
+                ("kkt_anchor", C.c_double), ("rel_primal", C.c_double), ("rel_dual", C.c_double),
+                ("rel_gap", C.c_double)]
 
 
 class KKT(C.Structure):
@@ -79,6 +86,8 @@ def lib():
         L.orc_restart_decision.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int64, C.c_int64,
                                            C.c_double, C.c_double, C.c_double]
         L.orc_restart_decision.restype = C.c_int
+        L.orc_restart_candidate.argtypes = [C.c_double, C.c_double]
+        L.orc_restart_candidate.restype = C.c_int
         L.orc_scale.argtypes = [C.c_int64, C.c_int64, _i64p, _i32p, _dp, C.c_int32, C.c_int32, _dp, _dp]
         L.orc_power_norm.argtypes = [C.c_int64, C.c_int64, _i64p, _i32p, _dp, C.c_int32]
         L.orc_power_norm.restype = C.c_double
@@ -86,7 +95,7 @@ def lib():
                                     _dp, _dp, C.c_double, C.c_double, _dp, _dp]
         L.orc_solve.argtypes = [C.c_int64, C.c_int64, C.c_int64, _i64p, _i32p, _dp, _dp, _dp, _dp,
                                 _dp, C.POINTER(Params), _vp, _vp, C.POINTER(Result), _vp, _vp, _vp,
-                                _vp, _vp, _vp, _vp, C.c_int64]
+                                _vp, _vp, _vp, _vp, C.c_int64, _vp, C.c_int64]
         L.orc_solve.restype = C.c_int
         _lib = L
     return _lib
@@ -159,6 +168,11 @@ def restart_decision(kkt_c, kkt_anchor, kkt_prev_c, t, k, beta_suff=0.2, beta_ne
     return lib().orc_restart_decision(kkt_c, kkt_anchor, kkt_prev_c, t, k, beta_suff, beta_nec, beta_art)
 
 
+def restart_candidate(kkt_cur, kkt_avg):
+    """1 when the restart candidate is the average, 0 for the current iterate."""
+    return lib().orc_restart_candidate(float(kkt_cur), float(kkt_avg))
+
+
 def scale(lp, ruiz_iters=10, pock_chambolle=True):
     """Returns (scaled values, Dr, Dc)."""
     rp, ci, v = _csr(lp)
@@ -188,9 +202,10 @@ def pdhg_step(lp, x, y, eta, omega):
     return xx[: lp["n"]], yy[: lp["m"]]
 
 
-def solve(lp, params: Params | None = None, x0=None, y0=None, restart_cap=1 << 16, **kw):
+def solve(lp, params: Params | None = None, x0=None, y0=None, restart_cap=1 << 16, log_cap=0, **kw):
     """Restarted PDHG.  Returns a dict with the result fields, x/y (returned point),
-    x_cur/y_cur, x_avg/y_avg (unscaled) and the list of restart iterations."""
+    x_cur/y_cur, x_avg/y_avg (unscaled), the list of restart iterations and, when
+    log_cap > 0, the first log_cap per-check records as dicts ("log")."""
     p = params or default_params(**kw)
     if params is not None:
         for k, v in kw.items():
@@ -200,6 +215,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None, restart_cap=1 << 1
     bufs = {k: np.zeros(max(sz, 1)) for k, sz in
             (("x", n), ("y", m), ("x_cur", n), ("y_cur", m), ("x_avg", n), ("y_avg", m))}
     rs = np.zeros(restart_cap, dtype=np.int64)
+    logbuf = (CheckRecord * max(log_cap, 1))()
     R = Result()
     x0p = _f64(x0).ctypes.data if x0 is not None else None
     y0p = _f64(y0).ctypes.data if y0 is not None else None
@@ -213,7 +229,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None, restart_cap=1 << 1
                          C.byref(R), bufs["x"].ctypes.data, bufs["y"].ctypes.data,
                          bufs["x_cur"].ctypes.data, bufs["y_cur"].ctypes.data,
                          bufs["x_avg"].ctypes.data, bufs["y_avg"].ctypes.data, rs.ctypes.data,
-                         restart_cap)
+                         restart_cap, C.addressof(logbuf) if log_cap > 0 else None, log_cap)
     if rc != 0:
         raise ValueError("oracle rejected the input")
     out = {f: getattr(R, f) for f, _ in Result._fields_}
@@ -222,4 +238,7 @@ def solve(lp, params: Params | None = None, x0=None, y0=None, restart_cap=1 << 1
     for k in ("y", "y_cur", "y_avg"):
         out[k] = bufs[k][:m]
     out["restart_iters"] = rs[: min(R.restarts, restart_cap)].copy()
+    if log_cap > 0:
+        out["log"] = [{f: getattr(r, f) for f, _ in CheckRecord._fields_}
+                      for r in logbuf[: min(R.checks, log_cap)]]
     return out

@@ -83,11 +83,22 @@ typedef struct {
   int64_t iters, restarts;
   double primal_obj, dual_obj, rel_primal, rel_dual, rel_gap, kkt_omega, omega, eta;
   int64_t accepted;    /* steps accepted (= iters with the constant rule) */
+  int64_t checks;      /* checks made (restart / termination tests) */
 } orc_result;
 
 typedef struct {
   double pres2, dres2, pobj, dobj, gap;
 } orc_kkt;
+
+/* One record per check of orc_solve (optional output). */
+typedef struct {
+  int64_t k, t;        /* iteration count and inner-loop length at the check */
+  int32_t restart;     /* 0 none (or the solve ended here), 1/2/3 the restart condition that held */
+  int32_t candidate;   /* restart candidate: 0 current iterate, 1 average */
+  double omega;        /* primal weight in force at the check (before any update) */
+  double kkt_cur, kkt_avg, kkt_anchor;   /* KKT_omega (scaled problem) of z, z-bar, z^{n,0} */
+  double rel_primal, rel_dual, rel_gap;  /* relative tests of the point with the smaller largest ratio */
+} orc_check;
 
 /* ---------- linear algebra on CSR ---------- */
 
@@ -194,6 +205,13 @@ static double rel_errors(orc_kkt p, double qnorm, double cnorm, double* rp_, dou
 }
 
 /* ---------- restart conditions (Section 2, restart criteria) ---------- */
+
+/* The restart candidate: the current iterate when its KKT_omega is strictly smaller
+ * than the average's, otherwise the average.  Returns 1 for the average. */
+int orc_restart_candidate(double kkt_cur, double kkt_avg) {
+  if (kkt_cur < kkt_avg) return 0;
+  return 1;
+}
 
 /* 0: no restart; 1: sufficient decay; 2: necessary decay without local progress;
  * 3: long inner loop.  kkt_prev_c is +inf at the first check of an inner loop. */
@@ -320,12 +338,14 @@ static void unscale(int64_t len, const double* d, const double* a, double* out) 
 /* Returns 0 on success, -1 on bad input.  Outputs (all optional, unscaled, length n or m):
  * x_out/y_out = returned point; x_cur/y_cur = current iterate; x_avg/y_avg = average of
  * the current inner loop (equals the current iterate when t = 0); restart_iters receives
- * up to restart_cap iteration counts at which restarts happened. */
+ * up to restart_cap iteration counts at which restarts happened; check_log receives up to
+ * log_cap per-check records (the last one is the check that ended the solve). */
 int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t* ci,
               const double* val, const double* c, const double* q, const double* l,
               const double* u, const orc_params* P, const double* x0, const double* y0,
               orc_result* R, double* x_out, double* y_out, double* x_cur, double* y_cur,
-              double* x_avg, double* y_avg, int64_t* restart_iters, int64_t restart_cap) {
+              double* x_avg, double* y_avg, int64_t* restart_iters, int64_t restart_cap,
+              orc_check* check_log, int64_t log_cap) {
   if (m < 0 || n < 0 || m1 < 0 || m1 > m || P->check_every <= 0) return -1;
   int64_t nnz = rp[m];
   size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1), mb = sizeof(double) * (size_t)(m > 0 ? m : 1);
@@ -380,7 +400,7 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
   orc_kkt pa = orc_kkt_parts(m, n, m1, rp, ci, vt, ct, qt, lt, ut, x, y);
   double kkt_anchor = orc_kkt_omega(pa, omega);
   double kkt_prev_c = INFINITY;
-  int64_t k = 0, t = 0, nrestart = 0, accepted = 0;
+  int64_t k = 0, t = 0, nrestart = 0, accepted = 0, ncheck = 0;
   int rejects = 0;
   double wsum = 0.0;   /* sum of the weights of the iterates in sx, sy */
   double *xn = (double*)malloc(nb), *yn = (double*)malloc(mb);
@@ -437,6 +457,27 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
     double ec = rel_errors(uc, qnorm, cnorm, &rpc, &rdc, &rgc);
     double ea = rel_errors(ua, qnorm, cnorm, &rpa, &rda, &rga);
     int pass_c = ec <= P->tol, pass_a = ea <= P->tol;
+    /* KKT_omega of both points on the scaled problem (restart test and log) */
+    orc_kkt sc = orc_kkt_parts(m, n, m1, rp, ci, vt, ct, qt, lt, ut, x, y);
+    orc_kkt sa = orc_kkt_parts(m, n, m1, rp, ci, vt, ct, qt, lt, ut, xa, ya);
+    double kc = orc_kkt_omega(sc, omega), ka = orc_kkt_omega(sa, omega);
+    int cand_avg = orc_restart_candidate(kc, ka);
+    orc_check* rec = (check_log && ncheck < log_cap) ? &check_log[ncheck] : NULL;
+    ++ncheck;
+    if (rec) {
+      int cur_better = ec < ea;
+      rec->k = k;
+      rec->t = t;
+      rec->restart = 0;
+      rec->candidate = cand_avg;
+      rec->omega = omega;
+      rec->kkt_cur = kc;
+      rec->kkt_avg = ka;
+      rec->kkt_anchor = kkt_anchor;
+      rec->rel_primal = cur_better ? rpc : rpa;
+      rec->rel_dual = cur_better ? rdc : rda;
+      rec->rel_gap = cur_better ? rgc : rga;
+    }
     if (pass_c || pass_a || final_check) {
       if (pass_c || pass_a) status = 0;
       if (pass_c && !pass_a) which = 0;
@@ -446,15 +487,12 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
       frp = which ? rpa : rpc; frd = which ? rda : rdc; frg = which ? rga : rgc;
       break;
     }
-    /* restart candidate and conditions, KKT_omega on the scaled problem */
-    orc_kkt sc = orc_kkt_parts(m, n, m1, rp, ci, vt, ct, qt, lt, ut, x, y);
-    orc_kkt sa = orc_kkt_parts(m, n, m1, rp, ci, vt, ct, qt, lt, ut, xa, ya);
-    double kc = orc_kkt_omega(sc, omega), ka = orc_kkt_omega(sa, omega);
-    int cand_avg = !(kc < ka);
+    /* restart conditions for the candidate */
     double kkt_c = cand_avg ? ka : kc;
     orc_kkt pc = cand_avg ? sa : sc;
     int why = orc_restart_decision(kkt_c, kkt_anchor, kkt_prev_c, t, k, P->beta_suff, P->beta_nec,
                                    P->beta_art);
+    if (rec) rec->restart = why;
     if (why) {
       const double* xc = cand_avg ? xa : x;
       const double* yc = cand_avg ? ya : y;
@@ -505,6 +543,7 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
     R->omega = omega;
     R->eta = eta;
     R->accepted = accepted;
+    R->checks = ncheck;
   }
   free(vt); free(Dr); free(Dc); free(ct); free(lt); free(ut); free(qt);
   free(x); free(y); free(sx); free(sy); free(xa); free(ya); free(x0a); free(y0a);

@@ -87,12 +87,24 @@ def test_spmv_scaled_roundtrip(pk):
 
 # ---------------------------------------------------------------- iterates
 
+def compare_logs(got, ref, rel=1e-8):
+    """Per-check records: iteration counts, restart conditions and candidate choices
+    identical; omega, the KKT_omega values and the relative tests within rel (the points
+    agree to ~1e-15, and a residual near zero loses a few digits to cancellation)."""
+    assert len(got) == len(ref)
+    for g, o in zip(got, ref):
+        assert (g["k"], g["t"], g["restart"], g["candidate"]) == (o["k"], o["t"], o["restart"], o["candidate"])
+        for f in ("omega", "kkt_cur", "kkt_avg", "kkt_anchor", "rel_primal", "rel_dual", "rel_gap"):
+            assert abs(g[f] - o[f]) <= rel * abs(o[f]) + 1e-300, (f, g, o)
+
+
 def _compare_iterates(pk, lp, iters, engine=0, **params):
     """engine 1: kernels launched per iteration (CUDA graphs); 2: the persistent engine
     (one launch of the batched kernel on a thread-block cluster)."""
-    ref = oracle.solve(lp, tol=0.0, max_iter=iters, **params)
+    ref = oracle.solve(lp, tol=0.0, max_iter=iters, log_cap=4096, **params)
     with pk.Solver.from_lp(lp, scaling=params.get("scaling", 0), engine=engine) as s:
         r = s.solve(tol=0.0, max_iter=iters)
+        compare_logs(s.log(), ref["log"])
         if engine == 2:
             assert r["launches"] == 1
         assert r["iters"] == ref["iters"] == iters
@@ -112,6 +124,31 @@ def _compare_iterates(pk, lp, iters, engine=0, **params):
 
 
 ENGINES = [1, 2]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_first_restart_and_primal_weight_by_hand(pk, engine):
+    """min x s.t. x = 3 (x free), eta = 0.5, omega0 = 2, a check after every step.  By hand:
+    z^1 = (-0.25, 3.5); at the first check the current iterate and the average coincide,
+    so the candidate is the average (a tie, strict rule of Section 2); condition 3
+    restarts; omega becomes sqrt(2 * 3.5 / 0.25) = sqrt(28); KKT_2(z^1)^2 = 159.375 and
+    KKT_2(z^0)^2 = 36.25.  The oracle's test of the same case derives every number."""
+    lp = dict(m=1, n=1, m1=1, row_ptr=np.array([0, 1]), col_idx=np.array([0], dtype=np.int32),
+              val=np.array([1.0]), c=np.array([1.0]), q=np.array([3.0]), l=np.array([-np.inf]),
+              u=np.array([np.inf]))
+    with pk.Solver.from_lp(lp, engine=engine, check_every=1, eta=0.5) as s:
+        r = s.solve(tol=1e-12, max_iter=2, omega0=2.0)
+        log = s.log()
+        assert list(s.restarts()) == [1]
+    assert r["iters"] == 2 and len(log) == 2
+    assert (log[0]["k"], log[0]["t"], log[0]["restart"], log[0]["candidate"]) == (1, 1, 3, 1)
+    assert log[0]["kkt_cur"] == log[0]["kkt_avg"]
+    assert log[0]["kkt_cur"] == pytest.approx(np.sqrt(159.375), rel=1e-14)
+    assert log[0]["kkt_anchor"] == pytest.approx(np.sqrt(36.25), rel=1e-14)
+    assert r["omega"] == pytest.approx(np.sqrt(28.0), rel=1e-14)
+    assert log[1]["omega"] == pytest.approx(np.sqrt(28.0), rel=1e-14)
+    ref = oracle.solve(lp, tol=1e-12, max_iter=2, check_every=1, eta=0.5, omega0=2.0, log_cap=4)
+    compare_logs(log, ref["log"], rel=1e-14)
 
 
 @pytest.mark.parametrize("engine", ENGINES)

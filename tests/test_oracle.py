@@ -167,6 +167,110 @@ def test_restart_decision_conditions():
     assert d(2.0, 1.0, inf, 64, 64) == 3        # first loop: t = k
 
 
+def _lp2x2(l0):
+    """K = [A; G] = [[1, 2], [3, -1]] (one equality row, one >= row), q = (4, 3), c = (1, 1),
+    x_0 in [l0, inf), x_1 free."""
+    return dict(m=2, n=2, m1=1, row_ptr=np.array([0, 2, 4]), col_idx=np.array([0, 1, 0, 1], dtype=np.int32),
+                val=np.array([1.0, 2.0, 3.0, -1.0]), c=np.array([1.0, 1.0]), q=np.array([4.0, 3.0]),
+                l=np.array([l0, -np.inf]), u=np.array([np.inf, np.inf]))
+
+
+def test_kkt_omega_weights_by_hand():
+    """KKT_omega (Section 2, restart criteria) at points worked out by hand: omega^2 weighs
+    the primal residual, 1/omega^2 the dual residual, the gap enters unweighted.
+
+    Point 1: x = (1, 1), y = (0.5, 2), x_0 in [0, inf).
+      Kx = (3, 2): Ax - b = 3 - 4 = -1, [h - Gx]^+ = [3 - 2]^+ = 1          -> primal part 2
+      K'y = (6.5, -1), c - K'y = (-5.5, 2); Lambda_0 = R^+ gives lambda_0 = 0,
+      Lambda_1 = {0} gives lambda_1 = 0                                     -> dual part 34.25
+      q'y = 8, l'lambda^+ = u'lambda^- = 0, c'x = 2                          -> gap 6
+      KKT_2^2 = 4*2 + 34.25/4 + 36 = 52.5625 (KKT_2 = 7.25);  KKT_0.5^2 = 0.5 + 137 + 36 = 173.5
+    Point 2: x = (1, 1), y = (0, 0.1), x_0 in [0.5, inf).
+      primal part 2 as above; K'y = (0.3, -0.1), c - K'y = (0.7, 1.1), lambda = (0.7, 0)
+      -> dual part 1.21; dual objective q'y + l_0 lambda_0 = 0.3 + 0.35 = 0.65, c'x = 2 -> gap -1.35
+      KKT_2^2 = 8 + 0.3025 + 1.8225 = 10.125;  KKT_0.5^2 = 0.5 + 4.84 + 1.8225 = 7.1625
+    A swapped weighting gives 173.5 at omega = 2 for point 1 (and 52.5625 at 0.5).
+    """
+    p = oracle.kkt_parts(_lp2x2(0.0), np.array([1.0, 1.0]), np.array([0.5, 2.0]))
+    assert (p["pres2"], p["dres2"], p["pobj"], p["dobj"], p["gap"]) == (2.0, 34.25, 2.0, 8.0, 6.0)
+    assert oracle.kkt_omega(p, 2.0) == pytest.approx(7.25, rel=1e-15)
+    assert oracle.kkt_omega(p, 0.5) == pytest.approx(np.sqrt(173.5), rel=1e-15)
+    p = oracle.kkt_parts(_lp2x2(0.5), np.array([1.0, 1.0]), np.array([0.0, 0.1]))
+    assert p["pres2"] == 2.0 and p["pobj"] == 2.0
+    assert p["dres2"] == pytest.approx(1.21, rel=1e-15)
+    assert p["dobj"] == pytest.approx(0.65, rel=1e-15) and p["gap"] == pytest.approx(-1.35, rel=1e-15)
+    assert oracle.kkt_omega(p, 2.0) == pytest.approx(np.sqrt(10.125), rel=1e-15)
+    assert oracle.kkt_omega(p, 0.5) == pytest.approx(np.sqrt(7.1625), rel=1e-15)
+
+
+def _lp1x1():
+    """min x  s.t.  x = 3, x free: K = [1], m1 = 1, c = 1, q = 3."""
+    return dict(m=1, n=1, m1=1, row_ptr=np.array([0, 1]), col_idx=np.array([0], dtype=np.int32),
+                val=np.array([1.0]), c=np.array([1.0]), q=np.array([3.0]), l=np.array([-np.inf]),
+                u=np.array([np.inf]))
+
+
+def test_first_restart_and_primal_weight_by_hand():
+    """Two PDHG steps with a check after each, worked out by hand (Section 2 updates,
+    restart criteria; the primal-weight update is this build's reading S5).
+
+    eta = 0.5, omega = 2, z^0 = (0, 0):
+      x^1 = x^0 - (eta/omega)(c - K'y^0) = -0.25;  y^1 = y^0 + eta omega (q - K(2x^1 - x^0)) = 3.5
+    First check (k = t = 1): the average of one iterate is that iterate, so the two KKT values
+    tie and the candidate is the average (strict <).  KKT_2(z^0)^2 = 4*9 + 1/4 = 36.25;
+    KKT_2(z^1)^2 = 4*3.25^2 + 2.5^2/4 + (10.5 + 0.25)^2 = 159.375 > 0.8^2 * 36.25, so neither
+    decay condition holds and t >= 0.36 k (condition 3) restarts.  dx = 0.25, dy = 3.5:
+      omega <- exp(theta log(dy/dx) + (1 - theta) log omega) = sqrt(14 * 2) = sqrt(28) (theta = 0.5),
+      14 with theta = 1, 2 with theta = 0.
+    The new anchor is KKT at z^1 with the new omega: 28*10.5625 + 6.25/28 + 115.5625.
+    Relative tests at z^1: 3.25/(1+3), 2.5/(1+1), 10.75/(1 + 10.5 + 0.25).
+    """
+    lp = _lp1x1()
+    kw = dict(tol=1e-12, max_iter=2, check_every=1, eta=0.5, omega0=2.0, scaling=0, log_cap=4)
+    r = oracle.solve(lp, **kw)
+    assert list(r["restart_iters"]) == [1] and r["checks"] == 2
+    c0, c1 = r["log"]
+    assert (c0["k"], c0["t"], c0["restart"], c0["candidate"]) == (1, 1, 3, 1)
+    assert c0["omega"] == 2.0
+    assert c0["kkt_cur"] == c0["kkt_avg"] == pytest.approx(np.sqrt(159.375), rel=1e-15)
+    assert c0["kkt_anchor"] == pytest.approx(np.sqrt(36.25), rel=1e-15)
+    assert (c0["rel_primal"], c0["rel_dual"]) == (0.8125, 1.25)
+    assert c0["rel_gap"] == pytest.approx(10.75 / 11.75, rel=1e-15)
+    assert (c1["k"], c1["t"]) == (2, 1)
+    assert c1["omega"] == pytest.approx(np.sqrt(28.0), rel=1e-14)
+    assert c1["kkt_anchor"] == pytest.approx(np.sqrt(28 * 10.5625 + 6.25 / 28 + 115.5625), rel=1e-14)
+    assert r["omega"] == pytest.approx(np.sqrt(28.0), rel=1e-14)
+    assert oracle.solve(lp, **dict(kw, omega_theta=1.0))["omega"] == pytest.approx(14.0, rel=1e-14)
+    assert oracle.solve(lp, **dict(kw, omega_theta=0.0))["omega"] == pytest.approx(2.0, rel=1e-15)
+
+
+def test_initial_primal_weight_by_hand():
+    """Without a given omega0 the first primal weight is ||c|| / ||q|| = 1/3 (reading S4);
+    eta = 0.5 then gives x^1 = -1.5, y^1 = 0.5/3 * (3 + 3) = 1, so the first check sees
+    KKT_{1/3}(z^1)^2 = (1/9)(4.5)^2 + 9 * 0^2 + (3 + 1.5)^2 = 22.5 and KKT(z^0)^2 = 1 + 9 = 10."""
+    r = oracle.solve(_lp1x1(), tol=1e-12, max_iter=1, check_every=1, eta=0.5, scaling=0, log_cap=2)
+    c0 = r["log"][0]
+    assert c0["omega"] == pytest.approx(1.0 / 3.0, rel=1e-15)
+    assert c0["kkt_cur"] == pytest.approx(np.sqrt(22.5), rel=1e-15)
+    assert c0["kkt_anchor"] == pytest.approx(np.sqrt(10.0), rel=1e-15)
+    np.testing.assert_allclose(r["x_cur"], [-1.5], rtol=1e-15)
+    np.testing.assert_allclose(r["y_cur"], [1.0], rtol=1e-15)
+
+
+def test_restart_candidate_strict_rule():
+    """Section 2: the candidate is the current iterate only when its KKT_omega is strictly
+    smaller than the average's; a tie goes to the average (1)."""
+    cand = oracle.restart_candidate
+    assert cand(1.0, 1.0) == 1
+    assert cand(0.5, 1.0) == 0
+    assert cand(1.0, 0.5) == 1
+    assert cand(np.nextafter(1.0, 0.0), 1.0) == 0
+    assert cand(1.0, np.nextafter(1.0, 0.0)) == 1
+    assert cand(0.0, 0.0) == 1
+    assert cand(np.inf, np.inf) == 1
+    assert cand(3.0, np.inf) == 0
+
+
 # ---------------------------------------------------------------- scaling
 
 def test_ruiz_equilibrates():
