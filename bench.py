@@ -594,6 +594,8 @@ def main():
                     help="timed solve: 0 constant step (Section 2), 1 adaptive rule (units: attempts)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the small-LP time-to-tolerance section")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--spmv-stage", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="large: how the SpMVs read values and indices (0 = the setup autotuner's choice)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline in the batched and mcf workloads")
     ap.add_argument("--count", type=int, default=4096, help="LPs in the batched workload")
@@ -669,7 +671,7 @@ def main():
 
     lp, desc = workload(args.workload, rank)
     stream = torch.cuda.current_stream()
-    s = pk.Solver.from_lp(lp, scaling=1, stream=stream.cuda_stream)
+    s = pk.Solver.from_lp(lp, scaling=1, stream=stream.cuda_stream, spmv_stage=args.spmv_stage)
     info = s.info()
     iters = args.steps * CHECK_EVERY
     s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False, step_rule=args.step_rule)
@@ -733,7 +735,7 @@ def main():
     if not args.no_e2e:
         barrier()
         t0 = time.perf_counter()
-        s2 = pk.Solver.from_lp(lp, scaling=1)
+        s2 = pk.Solver.from_lp(lp, scaling=1, spmv_stage=args.spmv_stage)
         r2 = s2.solve(tol=0.0, max_iter=iters)
         _ = (r2["x"], r2["y"])
         torch.cuda.synchronize()
@@ -769,7 +771,8 @@ def main():
            "time_to_tol": ttt, "cpu_baseline": base, "e2e": e2e, "gpu_launches": int(r["launches"]),
            "device_ms_library": r["device_ms"], "clocks": clocks,
            "layout": {k: info[k] for k in ("slots_K", "slots_Kt", "tasks_K", "tasks_Kt", "split_chunks_K",
-                                           "split_chunks_Kt", "tile_slots_K")},
+                                           "split_chunks_Kt", "tile_slots_K", "spmv_batch_K", "spmv_stage_K",
+                                           "spmv_stage_Kt")},
            "eta": info["eta"], "norm_K": info["norm_K"]}
     print(json.dumps(out))
     if dist is not None:

@@ -141,6 +141,27 @@ typedef struct {
                               caller's arrays (the host only orders rows and columns);
                               1 = built entirely on the host (the reference builder: the
                               same layouts, slower for large inputs)                       */
+  int32_t spmv_stage;      /* setup, FP64 products of K and K': how a warp reads its slots'
+                              values and column indices.  1 = coalesced global loads;
+                              2 / 3 = staged in shared memory by one-dimensional bulk copies
+                              (cp.async.bulk, 8 slots per buffer, 2 / 3 buffers per warp),
+                              so that the load path serves only the gathers; 0 = chosen by
+                              the setup autotuner when it runs (nnz >= 2^20 and no explicit
+                              schedule), else 1.  All give bit-identical products for one
+                              task plan.  A staged kernel whose bounded wait gives up makes
+                              the call return PDLP_ETIMEOUT and the handle unusable.      */
+  int32_t batch_tune;      /* pdlp_batch_solve, when cluster_ctas and resident are both 0
+                              (automatic) and the batch is FP64: 0 = the first solve of the
+                              handle runs the online autotuner and later solves keep its
+                              choice; 1 = no tuning (the team-size rule above); 2 = tune
+                              again on this solve.  The autotuner times candidate team sizes
+                              (the rule's, half and twice it) and placements (streamed or
+                              resident slices, or global iterates) on the solve's own
+                              iterations: after a first slice of check_every iterations of
+                              every LP, each candidate runs the next slice of every LP still
+                              running as one resumed launch and is scored by bytes of work
+                              per second; the fastest runs the rest.  Results equal the
+                              untuned solve's up to summation order.                      */
 } pdlp_params;
 
 typedef struct {
@@ -198,6 +219,15 @@ typedef struct {
      (single-LP handles); the step size and primal weight (power iteration) with the rest
      of the setup */
   double setup_validate_ms, setup_layout_ms, setup_device_ms, setup_tune_ms, setup_step_ms;
+  int32_t spmv_stage_K, spmv_stage_Kt;   /* how the FP64 products read the value / index
+                                            stream: 1 coalesced loads, 2 / 3 staged in shared
+                                            memory by bulk copies (see pdlp_params)        */
+  int32_t batch_tuned;         /* batch handles: candidates the last pdlp_batch_solve timed
+                                  (0 when it did not tune); the first 8 of them:           */
+  int32_t tune_team[8];        /*   CTAs per LP                                            */
+  int32_t tune_resident[8];    /*   placement (1 streamed, 2 resident slices, 3 global)    */
+  double tune_gbs[8];          /*   score: stored bytes of the iterations run per second,
+                                    in GB/s                                                */
 } pdlp_info;
 
 /* Fills p with the defaults listed above. */
@@ -313,6 +343,13 @@ int pdlp_batch_setup(pdlp_handle* out, int64_t count, const int64_t* m, const in
  * x_out and y_out (either may be NULL) receive the returned points, back to back. */
 int pdlp_batch_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const double* y0, const double* omega0,
                      pdlp_result* res, double* x_out, double* y_out);
+
+/* Iteration counts at which LP `lp` (0 <= lp < count) of the last pdlp_batch_solve
+ * restarted (Section 2, restart criteria); the first 256 restarts of each LP are kept.
+ * Copies at most cap of them into the host array iters (may be NULL) and returns how
+ * many restarts the LP made, or a negative error code (PDLP_EINVAL: not a batch handle,
+ * lp out of range, or no solve yet). */
+int64_t pdlp_batch_get_restarts(pdlp_handle h, int64_t lp, int64_t* iters, int64_t cap);
 
 /* ---------------------------------------------------------------- dense kernels
  * C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then max(., 0) if relu) on the tcgen05

@@ -38,6 +38,14 @@ def default_params(**kw) -> _lib.Params:
     return p
 
 
+def _info_dict(i) -> dict:
+    out = {}
+    for f, _ in _lib.Info._fields_:
+        v = getattr(i, f)
+        out[f] = list(v) if isinstance(v, C.Array) else v
+    return out
+
+
 def _is_torch_cuda(a) -> bool:
     return hasattr(a, "is_cuda") and bool(a.is_cuda)
 
@@ -161,7 +169,7 @@ class Solver:
     def info(self) -> dict:
         i = _lib.Info()
         self._check(self._lib.pdlp_get_info(self._h, C.byref(i)))
-        return {f: getattr(i, f) for f, _ in _lib.Info._fields_}
+        return _info_dict(i)
 
     def time_iterations(self, iters):
         a, b = C.c_double(), C.c_double()
@@ -256,13 +264,25 @@ class BatchSolver:
             out.append(d)
         return out
 
+    def restarts(self, lp):
+        """Iteration counts at which LP `lp` restarted in the last solve (the first 256)."""
+        cnt = self._lib.pdlp_batch_get_restarts(self._h, int(lp), None, 0)
+        if cnt < 0:
+            raise SolverError(cnt, self._lib.pdlp_last_error(self._h).decode())
+        buf = np.zeros(max(cnt, 1), dtype=np.int64)
+        got = self._lib.pdlp_batch_get_restarts(self._h, int(lp), buf.ctypes.data, cnt)
+        if got < 0:
+            raise SolverError(got, self._lib.pdlp_last_error(self._h).decode())
+        return buf[: min(cnt, 256)]
+
     def info(self) -> dict:
-        """Layout sizes, and the team size and resident mode of the last solve."""
+        """Layout sizes, the team size and resident mode of the last solve, and what the
+        online autotuner timed (batch_tuned candidates: tune_team, tune_resident, tune_gbs)."""
         i = _lib.Info()
         rc = self._lib.pdlp_get_info(self._h, C.byref(i))
         if rc < 0:
             raise SolverError(rc, self._lib.pdlp_last_error(self._h).decode())
-        return {f: getattr(i, f) for f, _ in _lib.Info._fields_}
+        return _info_dict(i)
 
     def spmv(self, v, transpose=False):
         """Block-diagonal K v (or K' v) of the whole batch."""

@@ -22,7 +22,8 @@ class Params(C.Structure):
                 ("spmv_batch", C.c_int32), ("precision", C.c_int32),
                 ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32),
                 ("step_rule", C.c_int32), ("engine", C.c_int32), ("batch_tail_iters", C.c_int64),
-                ("host_layout", C.c_int32)]
+                ("host_layout", C.c_int32), ("spmv_stage", C.c_int32),
+                ("batch_tune", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -53,7 +54,9 @@ class Info(C.Structure):
                 ("batch_team", C.c_int32), ("batch_resident", C.c_int32),
                 ("wide_rows_K", C.c_int32), ("batch_resumed", C.c_int32),
                 ("setup_validate_ms", C.c_double), ("setup_layout_ms", C.c_double),
-                ("setup_device_ms", C.c_double), ("setup_tune_ms", C.c_double), ("setup_step_ms", C.c_double)]
+                ("setup_device_ms", C.c_double), ("setup_tune_ms", C.c_double), ("setup_step_ms", C.c_double),
+                ("spmv_stage_K", C.c_int32), ("spmv_stage_Kt", C.c_int32), ("batch_tuned", C.c_int32),
+                ("tune_team", C.c_int32 * 8), ("tune_resident", C.c_int32 * 8), ("tune_gbs", C.c_double * 8)]
 
 
 # every function declared in include/pdlp.h: name -> (restype, argtypes)
@@ -76,6 +79,7 @@ SIGNATURES = {
     "pdlp_batch_setup": (C.c_int, [C.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                    C.POINTER(Params)]),
     "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pdlp_batch_get_restarts": (C.c_int64, [_vp, _i64, _vp, _i64]),
     "pdlp_tc_gemm": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
     "pdlp_mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _i32, _i32, _i32]),
     "pdlp_mlp_free": (None, [_vp]),

@@ -23,6 +23,7 @@
 #include <cstring>
 #include <limits>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "batch_kernel.cuh"
@@ -30,6 +31,7 @@
 #include "layout.h"
 #include "layout_kernels.cuh"
 #include "pdlp.h"
+#include "spmv_stage.cuh"
 
 namespace pdlp {
 
@@ -66,6 +68,7 @@ struct DevSell {
   int32_t nwide = 0;
   int32_t ntasks = 0;
   int32_t tile = 0, tchunks = 0, batch = 8;
+  int32_t staged = 0;   // FP64 products: 0 plain loads, 1 / 2 stream staged by bulk copies (2 / 3 buffers)
   int64_t rows = 0, rows_pad = 0, nchunks = 0, slots = 0, split = 0;
   SellView view() const { return SellView{chunk_ptr, col, val, val32, tasks, ntasks, (int32_t)nchunks, gpart, cnt}; }
 };
@@ -110,6 +113,8 @@ struct pdlp_ctx {
   DevParams dp_host{};
   double eta = 1.0, omega0 = 1.0, normK = 0.0, qnorm = 0.0, cnorm = 0.0;
   std::string err;
+  int* d_err = nullptr;   // set by a staged SpMV kernel whose bounded wait gave up
+  bool broken = false;    // after such a failure the handle refuses further calls
   int64_t last_ncheck = 0, last_nrestart = 0;
   bool solved = false;
   cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
@@ -138,6 +143,18 @@ struct pdlp_ctx {
   double *xg = nullptr, *yg = nullptr;      // global iterates (allocated on first use)
   float *xg32 = nullptr, *yg32 = nullptr;
   int64_t last_resumed = 0;  // LPs continued in the second stage of the last solve
+  int64_t last_launches = 0; // batched launches of the last solve
+  int32_t* count2 = nullptr; // device-side length of the second queue
+  cudaGraphExec_t bgraph = nullptr;   // the device part of a batched solve (see batch_solve_impl)
+  bool last_graph = false;
+  bool last_tuned = false;   // the last solve ran the online autotuner
+  long long* brestarts = nullptr;   // batches: kBatchRestartCap restart iterations per LP
+  // online autotuner of the batched launch: the kept choice and what the tuning timed
+  bool tuned = false;
+  int tuned_team = 0, tuned_resident = 0;
+  int32_t tune_candidates = 0;
+  double tune_rates[8] = {};
+  int tune_team[8] = {}, tune_res[8] = {};
   double setup_ms[5] = {};   // setup phases (pdlp_info)
   std::vector<int32_t> hk_cptr, ht_cptr;  // host copies of the chunk pointers of K and K'
   int dev_smem_optin = 0;
@@ -193,11 +210,65 @@ static void dfree(pdlp_ctx* h, void* p) {
   }
 }
 
+// Staged-stream SpMV shapes: kStageSB slots per buffer, 2 or 3 buffers per warp.
+constexpr int kStageSB = 8;
+using StageA = StageShape<kStageSB, 2>;
+using StageB = StageShape<kStageSB, 3>;
+
 template <class Op, class Epi>
 static void launch_rows(pdlp_ctx* h, const DevSell& S, const typename Epi::T* xg, Epi epi, const DevState* st) {
   const int blocks = (S.ntasks + 7) / 8;
+  if constexpr (std::is_same<Op, OpSpmv>::value && std::is_same<typename Epi::T, double>::value) {
+    if (S.staged == 1) {
+      if (S.batch == 4)
+        sell_rows_staged_kernel<Op, Epi, 4, kStageSB, 2><<<blocks, 256, StageA::kCtaBytes, h->s>>>(S.view(), xg, epi, st, h->d_err);
+      else
+        sell_rows_staged_kernel<Op, Epi, 8, kStageSB, 2><<<blocks, 256, StageA::kCtaBytes, h->s>>>(S.view(), xg, epi, st, h->d_err);
+      return;
+    }
+    if (S.staged == 2) {
+      if (S.batch == 4)
+        sell_rows_staged_kernel<Op, Epi, 4, kStageSB, 3><<<blocks, 256, StageB::kCtaBytes, h->s>>>(S.view(), xg, epi, st, h->d_err);
+      else
+        sell_rows_staged_kernel<Op, Epi, 8, kStageSB, 3><<<blocks, 256, StageB::kCtaBytes, h->s>>>(S.view(), xg, epi, st, h->d_err);
+      return;
+    }
+  }
   if (S.batch == 4) sell_rows_kernel<Op, Epi, 4><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
   else sell_rows_kernel<Op, Epi, 8><<<blocks, 256, 0, h->s>>>(S.view(), xg, epi, st);
+}
+
+// Opt-in shared memory of every staged SpMV instantiation (on the current device).
+template <class Epi>
+static void stage_attrs_for() {
+  CK(cudaFuncSetAttribute(sell_rows_staged_kernel<OpSpmv, Epi, 4, kStageSB, 2>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, StageA::kCtaBytes));
+  CK(cudaFuncSetAttribute(sell_rows_staged_kernel<OpSpmv, Epi, 8, kStageSB, 2>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, StageA::kCtaBytes));
+  CK(cudaFuncSetAttribute(sell_rows_staged_kernel<OpSpmv, Epi, 4, kStageSB, 3>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, StageB::kCtaBytes));
+  CK(cudaFuncSetAttribute(sell_rows_staged_kernel<OpSpmv, Epi, 8, kStageSB, 3>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, StageB::kCtaBytes));
+}
+static void stage_attrs() {
+  stage_attrs_for<EpiStore>();
+  stage_attrs_for<EpiPrimal>();
+  stage_attrs_for<EpiDual>();
+  stage_attrs_for<EpiPrimalA>();
+  stage_attrs_for<EpiDualA>();
+}
+
+// A staged SpMV kernel sets *d_err when a bounded wait gave up; the handle's device
+// state is then undefined, so the handle refuses every later call.
+static void check_stage_err(pdlp_ctx* h) {
+  if (!h->d_err) return;
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (e) {
+    h->broken = true;
+    throw Failure{PDLP_ETIMEOUT, "a bounded wait of the staged SpMV kernel gave up; free this handle"};
+  }
 }
 
 // The caller's matrix on the device, with what the device layout builder derives from
@@ -496,6 +567,7 @@ static void destroy(pdlp_ctx* h) {
   if (h->gm_rem) cudaGraphExecDestroy(h->gm_rem);
   if (h->ga_full) cudaGraphExecDestroy(h->ga_full);
   if (h->ga_rem) cudaGraphExecDestroy(h->ga_rem);
+  if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -514,8 +586,11 @@ static void destroy(pdlp_ctx* h) {
 
 // Chooses (tile_slots, tile_chunks, batch) for one layout by timing the production
 // iteration kernel (fused epilogue included) on the handle's own buffers, which the
-// next pdlp_solve re-initialises; tau = sigma = 0 so the iterate does not move.
-static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
+// next pdlp_solve re-initialises; tau = sigma = 0 so the iterate does not move.  Then,
+// for that plan, the kernels whose value / index stream is staged in shared memory by
+// bulk copies (two or three buffers per warp, both batch sizes) compete with it, unless
+// stage_fixed >= 0 fixes the kind (0 plain loads, 1 / 2 staged).
+static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal, int stage_fixed) {
   static const int32_t tiles[] = {32, 64};
   static const int32_t chunks[] = {1, 2, 4, 8};
   static const int32_t batches[] = {4, 8};
@@ -524,25 +599,30 @@ static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  auto time_plan = [&]() {
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) CK(cudaEventRecord(e0, h->s));
+      if (primal)
+        launch_rows<OpSpmv>(h, D, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
+      else
+        launch_rows<OpSpmv>(h, D, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, h->st_tmp);
+    }
+    CK(cudaEventRecord(e1, h->s));
+    CKL("autotune launch");
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&tot, e0, e1));
+    return tot;
+  };
   float best = 1e30f;
-  int32_t bt = D.tile, bc = D.tchunks, bb = D.batch;
+  int32_t bt = D.tile, bc = D.tchunks, bb = D.batch, bs = 0;
+  D.staged = stage_fixed > 0 ? stage_fixed : 0;
   for (int32_t t : tiles)
     for (int32_t c : chunks) {
       TaskPlan P = plan_tasks(S, t, c);
       for (int32_t b : batches) {
         set_plan(h, D, P, t, c, b);
-        float tot = 0.f;
-        for (int rep = 0; rep < 4; ++rep) {
-          if (rep == 1) CK(cudaEventRecord(e0, h->s));
-          if (primal)
-            launch_rows<OpSpmv>(h, D, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
-          else
-            launch_rows<OpSpmv>(h, D, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, h->st_tmp);
-        }
-        CK(cudaEventRecord(e1, h->s));
-        CKL("autotune launch");
-        CK(cudaEventSynchronize(e1));
-        CK(cudaEventElapsedTime(&tot, e0, e1));
+        const float tot = time_plan();
         if (tot < best) {
           best = tot;
           bt = t;
@@ -551,9 +631,26 @@ static void autotune(pdlp_ctx* h, DevSell& D, const SellHost& S, bool primal) {
         }
       }
     }
+  bs = D.staged;
+  set_plan(h, D, plan_tasks(S, bt, bc), bt, bc, bb);
+  if (stage_fixed < 0) {
+    for (int32_t sg : {1, 2})
+      for (int32_t b : batches) {
+        D.staged = sg;
+        D.batch = b;
+        const float tot = time_plan();
+        if (tot < best) {
+          best = tot;
+          bs = sg;
+          bb = b;
+        }
+      }
+  }
+  D.staged = bs;
+  D.batch = bb;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_plan(h, D, plan_tasks(S, bt, bc), bt, bc, bb);
+  check_stage_err(h);
 }
 
 // ------------------------------------------------------------------ setup
@@ -575,10 +672,13 @@ static void init_handle_resources(pdlp_ctx* h) {
   CK(cudaEventCreate(&h->ev_t1));
   for (auto& e : h->ev_ring) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CK(cudaMallocHost(&h->st_host, sizeof(DevState) * kRing));
+  h->d_err = dalloc<int>(h, 1);
+  stage_attrs();
 }
 
 static void check_params(const pdlp_params& P) {
   if (P.check_every < 1) invalid("check_every must be >= 1");
+  if (P.spmv_stage < 0 || P.spmv_stage > 3) invalid("spmv_stage must be 0, 1, 2 or 3");
   if (!(P.step_scale > 0.0) || P.ruiz_iters < 0 || P.power_iters < 0) invalid("bad scaling/step parameters");
   if (P.cluster_ctas < 0 || P.cluster_ctas > kMaxTeam) invalid("cluster_ctas must be in [0, 16]");
   if (P.resident < 0 || P.resident > 3) invalid("resident must be 0, 1, 2 or 3");
@@ -1015,9 +1115,12 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
 
   // ---- SpMV schedule per layout: explicit parameters, or timed candidates for large K
   const bool auto_tile = P.tile_slots == 0 && P.tile_chunks == 0 && P.spmv_batch == 0;
+  const int stage_fixed = P.spmv_stage - 1;   // -1: chosen by the autotuner (plain below its size)
   if (auto_tile && h->nnz >= kAutotuneMinNnz) {
-    autotune(h, h->Kt, Lo.SKt, true);
-    autotune(h, h->K, Lo.SK, false);
+    autotune(h, h->Kt, Lo.SKt, true, stage_fixed);
+    autotune(h, h->K, Lo.SK, false, stage_fixed);
+  } else if (stage_fixed > 0) {
+    h->K.staged = h->Kt.staged = stage_fixed;
   }
   h->setup_ms[3] = ms_since(tp);
   tp = clk::now();
@@ -1453,6 +1556,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   CK(cudaEventRecord(h->ev_t1, h->s));
   CK(cudaStreamSynchronize(h->s));
   CK(cudaMemcpy(&fin, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  check_stage_err(h);
   float dev_ms = 0.f;
   CK(cudaEventElapsedTime(&dev_ms, h->ev_t0, h->ev_t1));
   h->last_ncheck = fin.ncheck;
@@ -1497,6 +1601,10 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
 template <class F>
 static int guarded(pdlp_ctx* h, F&& f) {
   if (!h) return PDLP_EINVAL;
+  if (h->broken) {
+    h->err = "a bounded device wait gave up earlier on this handle; free it";
+    return PDLP_ETIMEOUT;
+  }
   h->err.clear();
   try {
     DeviceGuard dg(h->dev);
@@ -1809,20 +1917,28 @@ static int batch_team_size(const pdlp_ctx* h, int64_t count, int team_req, bool 
 // One launch of the persistent batched kernel over A.count LPs (A.order): team size,
 // placement of the iterates (shared-memory replicas, with or without resident matrix
 // slices, or global memory) and grid chosen for that count.
+// Device buffers a batched launch may need, allocated before any launch (and so before a
+// graph capture): global iterates, the second queue and its device-side length.
+static void batch_buffers(pdlp_ctx* h, bool glob, bool fp32) {
+  if (glob && !h->xg) {
+    h->xg = dalloc<double>(h, (size_t)h->npad);
+    h->yg = dalloc<double>(h, (size_t)std::max<int64_t>(h->mpad, 1));
+  }
+  if (glob && fp32 && !h->xg32) {
+    h->xg32 = dalloc<float>(h, (size_t)h->npad);
+    h->yg32 = dalloc<float>(h, (size_t)std::max<int64_t>(h->mpad, 1));
+  }
+  if (!h->order2) h->order2 = dalloc<int32_t>(h, (size_t)h->count);
+  if (!h->count2) h->count2 = dalloc<int32_t>(h, 1);
+}
+
 static void launch_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp, int64_t count, int team_req,
                          bool fp32 = false) {
   const bool glob = h->batch_glob || sp.resident == 3;
   const int team = batch_team_size(h, count, team_req, glob);
   BatchArgs A = A0;
+  batch_buffers(h, glob, fp32);
   if (glob) {
-    if (!h->xg) {
-      h->xg = dalloc<double>(h, (size_t)h->npad);
-      h->yg = dalloc<double>(h, (size_t)std::max<int64_t>(h->mpad, 1));
-    }
-    if (fp32 && !h->xg32) {
-      h->xg32 = dalloc<float>(h, (size_t)h->npad);
-      h->yg32 = dalloc<float>(h, (size_t)std::max<int64_t>(h->mpad, 1));
-    }
     A.xs_off = A.ys_off = 0;
     A.red_off = 0;
     A.part_off = kBatchRed;
@@ -1896,6 +2012,118 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp
   void* args[] = {(void*)&A};
   CK(cudaLaunchKernelExC(&cfg, kfn, args));
   CKL("k_batch_solve");
+  h->last_launches++;
+}
+
+constexpr int64_t kBatchRestartCap = 256;   // restart iterations kept per LP of a batch
+
+// LPs of the batch whose last launch suspended them (they continue in a resumed launch).
+static std::vector<int32_t> suspended_lps(pdlp_ctx* h) {
+  CK(cudaMemcpyAsync(h->hstate.data(), h->bstate, sizeof(DevState) * h->count, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  std::vector<int32_t> rest;
+  for (int64_t b = 0; b < h->count; ++b)
+    if (h->hstate[(size_t)b].suspended) rest.push_back((int32_t)b);
+  return rest;
+}
+
+// A resumed launch over the LPs `lps` (uploaded to the second queue).
+static void launch_resumed(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp, const std::vector<int32_t>& lps,
+                           int team_req, long long slice) {
+  batch_buffers(h, h->batch_glob || sp.resident == 3, false);
+  CK(cudaMemcpyAsync(h->order2, lps.data(), sizeof(int32_t) * lps.size(), cudaMemcpyHostToDevice, h->s));
+  BatchArgs A = A0;
+  A.order = h->order2;
+  A.count = (int32_t)lps.size();
+  A.resume = 1;
+  A.slice_iters = slice;
+  launch_batch(h, A, sp, (int64_t)lps.size(), team_req);
+}
+
+// Online autotuner of the batched launch, run by the first solve of a handle whose team
+// size and data placement are automatic (FP64 batches).  The first check_every
+// iterations of every LP run with the rule's choice (they also hold the power
+// iteration); then each candidate (team size x placement: the rule's team, half and
+// twice it; iterates streamed or resident slices where they fit, or global iterates)
+// runs the next check_every iterations of every LP still running, as one resumed
+// launch, and is scored by the work it did (iterations run x stored bytes of one
+// iteration of each LP) per device second.  Tuning stops early once fewer than half of
+// the LPs are still running.  Nothing is repeated: the slices are the solve's own
+// iterations, resumed exactly (up to summation order).  The fastest candidate is kept
+// for the rest of the solve and for later solves of the handle.  Returns the LPs left
+// running after the slices.
+static std::vector<int32_t> tune_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp) {
+  const int64_t count = h->count;
+  const bool glob = h->batch_glob;
+  const int rule = batch_team_size(h, count, 0, glob);
+  const int cap = glob ? kTeamGlobMax : kMaxTeam;
+  struct Cand { int team, resident; };
+  std::vector<Cand> cands;
+  for (int T : {rule, rule / 2, rule * 2}) {
+    if (T < 1 || T > cap) continue;
+    if (T > 1 && h->team_npad_max < (int64_t)T * 64) continue;
+    if (glob) {
+      cands.push_back({T, 3});
+    } else {
+      cands.push_back({T, 1});
+      const long long need = resident_need(h, T);
+      if (h->batch_smem + (size_t)((need + 7) / 8 * 8) <= (size_t)h->dev_smem_optin) cands.push_back({T, 2});
+    }
+  }
+  std::vector<double> w((size_t)count);
+  for (int64_t b = 0; b < count; ++b) {
+    const LpDesc& D = h->hdesc[(size_t)b];
+    const double slots = (double)(h->hk_cptr[(size_t)D.kc1] - h->hk_cptr[(size_t)D.kc0]) +
+                         (double)(h->ht_cptr[(size_t)D.tc1] - h->ht_cptr[(size_t)D.tc0]);
+    w[(size_t)b] = 12.0 * 32.0 * slots + 68.0 * (double)(D.mpad + D.npad);
+  }
+  // slice 0: the rule's choice
+  BatchArgs A = A0;
+  A.slice_iters = sp.check_every;
+  launch_batch(h, A, sp, count, 0);
+  std::vector<int32_t> active = suspended_lps(h);
+  std::vector<long long> kprev((size_t)count);
+  for (int64_t b = 0; b < count; ++b) kprev[(size_t)b] = h->hstate[(size_t)b].k;
+  double best = -1.0;
+  Cand bc = cands.empty() ? Cand{rule, 0} : cands[0];
+  h->tune_candidates = 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (const Cand& c : cands) {
+    if ((int64_t)active.size() * 2 < count) break;
+    pdlp_params sc = sp;
+    sc.resident = c.resident;
+    CK(cudaEventRecord(e0, h->s));
+    launch_resumed(h, A0, sc, active, c.team, sp.check_every);
+    CK(cudaEventRecord(e1, h->s));
+    std::vector<int32_t> next = suspended_lps(h);
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    double work = 0.0;
+    for (int32_t b : active) {
+      work += (double)(h->hstate[(size_t)b].k - kprev[(size_t)b]) * w[(size_t)b];
+      kprev[(size_t)b] = h->hstate[(size_t)b].k;
+    }
+    const double rate = ms > 0.f ? work / (double)ms : 0.0;
+    const int i = h->tune_candidates++;
+    if (i < 8) {
+      h->tune_rates[i] = rate * 1e-6;   // GB/s of stored bytes
+      h->tune_team[i] = c.team;
+      h->tune_res[i] = c.resident;
+    }
+    if (rate > best) {
+      best = rate;
+      bc = c;
+    }
+    active.swap(next);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned = true;
+  h->tuned_team = bc.team;
+  h->tuned_resident = bc.resident;
+  return active;
 }
 
 // single: one LP of a single-LP handle through the persistent engine (omega0_single is
@@ -1909,6 +2137,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   if (sp.resident < 0 || sp.resident > 3) invalid("resident must be 0, 1, 2 or 3");
   if (sp.step_rule != 0) invalid("batches use the constant step (step_rule 0)");
   if (sp.batch_tail_iters < 0) invalid("batch_tail_iters must be >= 0");
+  if (sp.batch_tune < 0 || sp.batch_tune > 2) invalid("batch_tune must be 0, 1 or 2");
   auto t_start = std::chrono::steady_clock::now();
   BatchArgs A;
   A.x0 = nullptr;
@@ -1931,10 +2160,12 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   }
   A.xcur = A.ycur = nullptr;
   A.restarts = nullptr;
+  A.restart_stride = 0;
   A.log = nullptr;
   A.desc = h->desc;
   A.order = h->order;
   A.count = (int32_t)h->count;
+  A.count_dev = nullptr;
   A.next = h->next;
   A.k_cptr = h->K.chunk_ptr;
   A.k_col = h->K.col;
@@ -1955,6 +2186,12 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.P.beta_art = sp.beta_art;
   A.P.theta = sp.omega_theta;
   A.P.max_iter = sp.max_iter;
+  if (!single) {
+    if (!h->brestarts) h->brestarts = dalloc<long long>(h, (size_t)h->count * kBatchRestartCap);
+    A.restarts = h->brestarts;
+    A.restart_stride = kBatchRestartCap;
+    A.P.restart_cap = (int)kBatchRestartCap;
+  }
   A.check_every = sp.check_every;
   A.max_iter = sp.max_iter;
   A.power_iters = h->p.power_iters;
@@ -1985,27 +2222,89 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.slice_iters = (!mixed && sp.batch_tail_iters > 0) ? sp.batch_tail_iters : 0;
   A.resume = 0;
   h->last_resumed = 0;
+  h->last_launches = 0;
   CK(cudaEventRecord(h->ev_t0, h->s));
+  // team size and placement: the caller's, the online autotuner's (timed on the first
+  // solve of the handle, on the solve's own first iterations), or the rule
+  const bool auto_cfg = !single && !mixed && sp.cluster_ctas == 0 && sp.resident == 0 && sp.batch_tune != 1;
+  pdlp_params sp1 = sp;
+  int team1 = sp.cluster_ctas;
+  bool tuned_now = false;
+  std::vector<int32_t> active;
+  h->last_tuned = false;
+  if (auto_cfg && h->count >= 2 && (sp.batch_tune == 2 || !h->tuned)) {
+    active = tune_batch(h, A, sp);
+    tuned_now = true;
+    h->last_tuned = true;
+  }
+  if (auto_cfg && h->tuned) {
+    team1 = h->tuned_team;
+    sp1.resident = h->tuned_resident;
+  }
   // mixed precision: FP32 iterations first; the LPs that leave them unfinished are
-  // suspended with their FP64 state and continue in FP64 (second stage)
-  launch_batch(h, A, sp, h->count, sp.cluster_ctas, mixed);
-  if (A.slice_iters > 0 || mixed) {
-    // second stage: the LPs stopped by the slice continue, with teams sized for their number
-    CK(cudaMemcpyAsync(h->hstate.data(), h->bstate, sizeof(DevState) * h->count, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    std::vector<int32_t> rest;
-    for (int64_t b = 0; b < h->count; ++b)
-      if (h->hstate[(size_t)b].suspended) rest.push_back((int32_t)b);
-    h->last_resumed = (int64_t)rest.size();
-    if (!rest.empty()) {
-      if (!h->order2) h->order2 = dalloc<int32_t>(h, (size_t)h->count);
-      CK(cudaMemcpyAsync(h->order2, rest.data(), sizeof(int32_t) * rest.size(), cudaMemcpyHostToDevice, h->s));
-      BatchArgs A2 = A;
-      A2.order = h->order2;
-      A2.count = (int32_t)rest.size();
-      A2.resume = 1;
-      A2.slice_iters = 0;
-      launch_batch(h, A2, sp, (int64_t)rest.size(), 0);
+  // suspended with their FP64 state and continue in FP64 (second stage).  With
+  // batch_tail_iters the LPs still running after that many iterations continue in a
+  // second stage too.  The second stage runs the largest team the LPs allow.
+  const bool two_stage = A.slice_iters > 0 || mixed;
+  const bool glob1 = h->batch_glob || sp1.resident == 3;
+  const int tail_team = batch_team_size(h, 1, 0, h->batch_glob || sp.resident == 3);
+  h->last_graph = false;
+  if (!tuned_now && !single) {
+    // the device part of the solve as one CUDA graph: the persistent launch and, for a
+    // two-stage solve, the device-side queue of the suspended LPs and the second launch;
+    // instantiated once per handle and updated in place when the arguments change
+    batch_buffers(h, glob1, mixed);
+    batch_buffers(h, h->batch_glob || sp.resident == 3, false);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    try {
+      launch_batch(h, A, sp1, h->count, team1, mixed);
+      if (two_stage) {
+        k_collect_suspended<<<1, 1024, 0, h->s>>>(h->bstate, (int)h->count, h->order2, h->count2);
+        BatchArgs A2 = A;
+        A2.order = h->order2;
+        A2.count_dev = h->count2;
+        A2.resume = 1;
+        A2.slice_iters = 0;
+        launch_batch(h, A2, sp, h->count, tail_team);
+      }
+    } catch (...) {
+      cudaStreamEndCapture(h->s, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    CK(cudaStreamEndCapture(h->s, &g));
+    if (h->bgraph) {
+      cudaGraphExecUpdateResultInfo ui;
+      if (cudaGraphExecUpdate(h->bgraph, g, &ui) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(h->bgraph);
+        h->bgraph = nullptr;
+      }
+    }
+    if (!h->bgraph) {
+      const cudaError_t e = cudaGraphInstantiate(&h->bgraph, g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+    } else {
+      cudaGraphDestroy(g);
+    }
+    CK(cudaGraphLaunch(h->bgraph, h->s));
+    h->last_graph = true;
+    if (two_stage) {
+      int32_t c2 = 0;
+      CK(cudaMemcpyAsync(&c2, h->count2, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      h->last_resumed = c2;
+    }
+  } else if (!tuned_now) {
+    launch_batch(h, A, sp1, h->count, team1, mixed);   // the persistent engine of a single LP
+  } else {
+    if (!active.empty()) launch_resumed(h, A, sp1, active, team1, A.slice_iters);
+    if (two_stage) {
+      std::vector<int32_t> rest = suspended_lps(h);
+      h->last_resumed = (int64_t)rest.size();
+      if (!rest.empty()) launch_resumed(h, A, sp, rest, tail_team, 0);
     }
   }
   CK(cudaEventRecord(h->ev_t1, h->s));
@@ -2041,7 +2340,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
       r.eta = S.eta;
       r.solve_s = wall;
       r.device_ms = dev_ms;
-      r.launches = 1 + (h->last_resumed > 0 ? 1 : 0);
+      r.launches = h->last_launches;
       r.fp32_iters = S.k32;
       r.accepted = S.k;
     }
@@ -2205,6 +2504,7 @@ int pdlp_spmv(pdlp_handle h, int32_t transpose, const double* in, double* out) {
     }
     CKL("pdlp_spmv");
     CK(cudaStreamSynchronize(h->s));
+    check_stage_err(h);
     return PDLP_OK;
   });
 }
@@ -2220,6 +2520,7 @@ int pdlp_bound_duals(pdlp_handle h, const double* y, double* lambda_out) {
     k_unpermute_scale<<<grid_for(h->n), 256, 0, h->s>>>(h->stage_n, h->tn, h->invDc, h->pos_c, h->n);
     copy_out(h, lambda_out, h->stage_n, h->n);
     CK(cudaStreamSynchronize(h->s));
+    check_stage_err(h);
     return PDLP_OK;
   });
 }
@@ -2258,7 +2559,29 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
     info->setup_device_ms = h->setup_ms[2];
     info->setup_tune_ms = h->setup_ms[3];
     info->setup_step_ms = h->setup_ms[4];
+    info->spmv_stage_K = h->K.staged + 1;
+    info->batch_tuned = h->last_tuned ? h->tune_candidates : 0;
+    for (int i = 0; i < 8 && i < h->tune_candidates; ++i) {
+      info->tune_team[i] = h->tune_team[i];
+      info->tune_resident[i] = h->tune_res[i];
+      info->tune_gbs[i] = h->tune_rates[i];
+    }
+    info->spmv_stage_Kt = h->Kt.staged + 1;
     return PDLP_OK;
+  });
+}
+
+int64_t pdlp_batch_get_restarts(pdlp_handle h, int64_t lp, int64_t* iters, int64_t cap) {
+  return guarded(h, [&]() -> int {
+    if (!h->is_batch) invalid("single-LP handle: use pdlp_get_restarts");
+    if (lp < 0 || lp >= h->count) invalid("lp out of range");
+    if (!h->solved) invalid("no solve has run on this handle");
+    const int64_t nr = h->hstate[(size_t)lp].nrestart;
+    const int64_t k = std::min<int64_t>({nr, cap, kBatchRestartCap});
+    if (iters && k > 0)
+      CK(cudaMemcpy(iters, h->brestarts + (size_t)lp * kBatchRestartCap, sizeof(long long) * k,
+                    cudaMemcpyDeviceToHost));
+    return (int)nr;
   });
 }
 
@@ -2301,6 +2624,7 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
         td += b;
       }
     }
+    check_stage_err(h);
     if (ms_primal) *ms_primal = tp / (double)iters;
     if (ms_dual) *ms_dual = td / (double)iters;
     return PDLP_OK;

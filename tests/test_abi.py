@@ -70,7 +70,13 @@ def test_default_params_without_gpu(lib):
 
 
 def test_last_error_null_handle(lib):
+    """With a null handle pdlp_last_error gives the calling thread's last setup error: here
+    that of a setup rejected before any device work (null output handle)."""
     f = lib.pdlp_last_error
     f.restype = C.c_char_p
     f.argtypes = [C.c_void_p]
-    assert f(None) == b""
+    setup = lib.pdlp_setup
+    setup.restype = C.c_int
+    setup.argtypes = [C.c_void_p] + [C.c_int64] * 3 + [C.c_void_p] * 8
+    assert setup(None, 1, 1, 0, None, None, None, None, None, None, None, None) == -1
+    assert f(None) == b"null output handle"
