@@ -206,24 +206,82 @@ def gather_ceiling(nnz, nx):
         return {"error": str(e)[:200]}
 
 
+def cpu_info():
+    """Threads available to this process and the host CPU's model name."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return cores, model
+
+
 def cpu_baseline(lp, seconds=12.0):
-    """The oracle's PDHG step (oracle.pdhg_step, single thread) on the same LP."""
+    """The oracle's PDHG step on the same LP: on every host core (oracle.ThreadedStep,
+    the same arithmetic split over threads, bit-identical to the serial step) for about
+    two thirds of `seconds`, and single-threaded (oracle.pdhg_step) for the rest."""
     import oracle
-    x = np.clip(np.zeros(lp["n"]), lp["l"], lp["u"])
-    y = np.zeros(lp["m"])
+    cores, model = cpu_info()
+    x0 = np.clip(np.zeros(lp["n"]), lp["l"], lp["u"])
+    y0 = np.zeros(lp["m"])
+    # all cores
+    T = oracle.ThreadedStep(lp, cores)
+    x, y = x0.copy(), y0.copy()
+    T.step(x, y, 1e-3, 1.0)                      # untimed: pages the arrays in
     steps, t0 = 0, time.perf_counter()
     while True:
-        x, y = oracle.pdhg_step(lp, x, y, 1e-3, 1.0)
+        T.step(x, y, 1e-3, 1.0)
         steps += 1
         el = time.perf_counter() - t0
-        if el >= seconds or steps >= 200:
+        if el >= seconds * 2 / 3 or steps >= 2000:
             break
-    return {"value": steps / el, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle PDHG steps (orc_pdhg_step: K'y, primal step, K(2x+-x), dual step) "
-                      f"on the full workload, {el:.1f} s"}
+    par = {"value": steps / el, "steps": steps, "s": el}
+    # one thread
+    x, y = x0.copy(), y0.copy()
+    steps1, t0 = 0, time.perf_counter()
+    while True:
+        x, y = oracle.pdhg_step(lp, x, y, 1e-3, 1.0)
+        steps1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= seconds / 3 or steps1 >= 200:
+            break
+    return {"value": par["value"], "unit": "PDHG iter/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": f"{par['steps']} oracle PDHG steps (K'y, primal step, K(2x+-x), dual step; "
+                      f"orc_pdhg_step_par on {cores} threads) on the full workload, {par['s']:.1f} s",
+            "single_thread": {"value": steps1 / el1, "unit": "PDHG iter/s", "cores": 1,
+                              "sample": f"{steps1} orc_pdhg_step steps, {el1:.1f} s"}}
 
 
-FP64_FMA_PER_S = 5.66e11   # measured DFMA rate of a B300 (lane-ops/s): 1.77e10 warp instructions/s x 32
+_FP64_PEAK = None
+
+
+def fp64_peak():
+    """FP64 FMA lane-operations/s of this GPU, measured by the committed microbenchmark
+    (csrc/fp64_peak.cu) once per process: the arithmetic roof of the FP64 kernels."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        from paper_2312_14832_b300 import build as pkbuild
+        try:
+            out = subprocess.check_output([pkbuild.build_fp64_peak()], timeout=120)
+            _FP64_PEAK = json.loads(out.decode().strip().splitlines()[-1])
+        except Exception as e:
+            _FP64_PEAK = {"error": str(e)[:200]}
+    return _FP64_PEAK
+
+
+def fp64_roofline(achieved, note):
+    pk_ = fp64_peak()
+    peak = pk_.get("fma_per_s")
+    return {"bound": "alu", "unit": "FMA/s", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak if peak else None, "peak_kind": "measured by csrc/fp64_peak.cu in this run",
+            "probe": pk_, "note": note}
 
 
 def bench_batched(args):
@@ -242,9 +300,30 @@ def bench_batched(args):
     t0 = time.perf_counter()
     b = pk.BatchSolver.from_lps(lps, scaling=args.batch_scaling)
     setup_s = time.perf_counter() - t0
-    b.solve(tol=1e-4, max_iter=64, want_points=False)      # warm-up launch
+    b.solve(tol=1e-4, max_iter=64, want_points=False, batch_tune=1)      # warm-up launch
     clk = Clocks(0)
+    # the team-size rule alone, then the first solve with the online autotuner (its
+    # timed slices are part of the solve and of its time), then a solve that keeps the
+    # tuned choice (one CUDA graph holding the persistent launch)
+    res_rule = b.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False, batch_tune=1)
+    inf_rule = b.info()
+    res_first = b.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False)
+    inf_tuned = b.info()
     res = b.solve(tol=1e-4, max_iter=args.batch_max_iter, want_points=False)
+    res_again = res
+    k = inf_tuned["batch_tuned"]
+    tuning = {"rule": {"device_s": res_rule[0]["device_ms"] * 1e-3, "team": inf_rule["batch_team"],
+                       "resident": inf_rule["batch_resident"]},
+              "tuned_first_solve": {"device_s": res_first[0]["device_ms"] * 1e-3, "launches": res_first[0]["launches"],
+                                    "note": "the online autotuner's timed slices are this solve's own iterations"},
+              "candidates": [{"team": inf_tuned["tune_team"][i], "resident": inf_tuned["tune_resident"][i],
+                              "stored_gbs": inf_tuned["tune_gbs"][i]} for i in range(min(k, 8))],
+              "kept": {"team": inf_tuned["batch_team"], "resident": inf_tuned["batch_resident"]},
+              "tuned_again": {"device_s": res_again[0]["device_ms"] * 1e-3, "launches": res_again[0]["launches"]},
+              "same_iteration_counts": all(a["iters"] == c["iters"] == d["iters"]
+                                           for a, c, d in zip(res, res_rule, res_first)),
+              "max_rel_obj_diff_vs_rule": max(abs(a["primal_obj"] - c["primal_obj"]) / (1 + abs(c["primal_obj"]))
+                                              for a, c in zip(res, res_rule))}
     one_launch_s = res[0]["device_ms"] * 1e-3
     two_stage = None
     if args.batch_tail > 0:
@@ -319,15 +398,15 @@ def bench_batched(args):
                       "scaling": args.batch_scaling, "total_nnz": int(np.sum(nnz))},
            "batch_device_s": dev_s, "optimal": int(np.sum(status == 0)), "iters_mean": float(iters.mean()),
            "iters_max": int(iters.max()),
-           "roofline": {"bound": "alu", "unit": "FMA/s", "achieved": fma / dev_s, "peak": FP64_FMA_PER_S,
-                        "frac": fma / dev_s / FP64_FMA_PER_S, "note": "FP64 FMAs of both SpMVs per iteration"},
+           "roofline": fp64_roofline(fma / dev_s, "FP64 FMAs of both SpMVs per iteration"),
            "sequential": {"sample": len(sample), "sample_s": seq_s, "sample_iters": seq_it,
                           "estimated_total_s": seq_total, "lps_per_s": args.count / seq_total},
            "speedup_vs_sequential": seq_total / dev_s, "setup_s": setup_s, "generate_s": gen_s,
            "cpu_baseline": {"value": args.count / cpu_total, "unit": "LPs/s to 1e-4", "cores": 1, "kind": "oracle",
                             "sample": f"oracle.solve to 1e-4 on {cpu_n} LPs of the sample ({cpu_s:.1f} s), "
                                       f"scaled to {args.count} LPs"},
-           "one_launch_device_s": one_launch_s, "two_stage": two_stage, "tail": tail, "mixed": mixed,
+           "one_launch_device_s": one_launch_s, "tuning": tuning, "two_stage": two_stage, "tail": tail,
+           "mixed": mixed,
            "clocks": clocks}
     print(json.dumps(out))
 
@@ -364,14 +443,27 @@ def bench_mcf(args):
         ms = e0.elapsed_time(e1)
         mp, md = s.time_iterations(100)
         rt = s.solve(tol=1e-4, time_limit_s=args.mcf_budget)
+        status = ["optimal", "iter_limit", "time_limit", "numerical"]
         out[name] = {"iter_per_s": iters / (ms * 1e-3), "ms_primal": mp, "ms_dual": md,
                      "fp32_iters_in_timed": r["fp32_iters"],
-                     "time_to_1e-4": {"status": ["optimal", "iter_limit", "time_limit", "numerical"][rt["status"]],
+                     "time_to_1e-4": {"status": status[rt["status"]],
                                       "iters": rt["iters"], "fp32_iters": rt["fp32_iters"],
                                       "device_s": rt["device_ms"] * 1e-3, "primal_obj": rt["primal_obj"],
                                       "rel_primal": rt["rel_primal"], "rel_dual": rt["rel_dual"],
                                       "rel_gap": rt["rel_gap"]}}
         out[name + "_x"] = rt["x"]
+        if args.mcf_tol_hi > 0:
+            # high accuracy: in MIXED the FP32 phase hands over to FP64 refinement; the
+            # returned point's three relative tests re-evaluated by the FP64 oracle
+            import oracle
+            rh = s.solve(tol=args.mcf_tol_hi, time_limit_s=args.mcf_budget)
+            orp, ord_, org = oracle.relative_errors(lp, rh["x"], rh["y"])
+            out[name][f"time_to_{args.mcf_tol_hi:g}"] = {
+                "status": status[rh["status"]], "iters": rh["iters"], "fp32_iters": rh["fp32_iters"],
+                "fp32_share": rh["fp32_iters"] / max(rh["iters"], 1), "device_s": rh["device_ms"] * 1e-3,
+                "primal_obj": rh["primal_obj"], "rel_errors_solver": [rh["rel_primal"], rh["rel_dual"], rh["rel_gap"]],
+                "rel_errors_oracle": [orp, ord_, org], "obj_star": lp.get("obj_star")}
+            out[name + "_hi_obj"] = rh["primal_obj"]
         s.close()
     a, b = out["fp64"]["time_to_1e-4"], out["mixed"]["time_to_1e-4"]
     out["mixed_vs_fp64"] = {"iter_speedup": out["mixed"]["iter_per_s"] / out["fp64"]["iter_per_s"],
@@ -380,6 +472,10 @@ def bench_mcf(args):
                             "rel_x_diff": float(np.linalg.norm(out["fp64_x"] - out["mixed_x"]) /
                                                 np.linalg.norm(out["fp64_x"]))}
     del out["fp64_x"], out["mixed_x"]
+    if args.mcf_tol_hi > 0:
+        out["mixed_vs_fp64"][f"rel_obj_diff_at_{args.mcf_tol_hi:g}"] = (
+            abs(out["fp64_hi_obj"] - out["mixed_hi_obj"]) / abs(out["fp64_hi_obj"]))
+        del out["fp64_hi_obj"], out["mixed_hi_obj"]
     import oracle
     x, y, k, t0 = np.zeros(lp["n"]), np.zeros(lp["m"]), 0, time.perf_counter()
     while time.perf_counter() - t0 < args.cpu_seconds:
@@ -605,7 +701,9 @@ def main():
     ap.add_argument("--batch-tail", type=int, default=8192,
                     help="batched: also time the two-stage solve (LPs past this many iterations continue on teams)")
     ap.add_argument("--seq-sample", type=int, default=32)
-    ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-1e-4 solve (mcf)")
+    ap.add_argument("--mcf-budget", type=float, default=60.0, help="seconds per time-to-tolerance solve (mcf)")
+    ap.add_argument("--mcf-tol-hi", type=float, default=1e-8,
+                    help="mcf: also solve to this tolerance (0 = skip), with the same time budget")
     ap.add_argument("--fixed-iters", type=int, default=0, help="teams: one launch of this many iterations")
     ap.add_argument("--team-one", type=int, default=1, help="teams: CTAs per LP for --fixed-iters")
     ap.add_argument("--pr-nodes", type=int, default=1_000_000)
@@ -643,19 +741,35 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        # the reference arm is the CPU oracle, on rank 0 only
+        # the reference arm is the CPU oracle on every host core, on rank 0 only: one step
+        # is one oracle PDHG iteration on the full workload (W untimed, then K timed)
         if rank != 0:
             return
+        import oracle
         lp, desc = workload(args.workload, 0)
-        base = cpu_baseline(lp, seconds=max(3.0, 1.0 * (args.steps + args.warmup)))
-        out = {"metric": METRIC, "value": base["value"], "unit": base["unit"], "n_gpus": 0,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * CHECK_EVERY / base["value"],
+        cores, model = cpu_info()
+        T = oracle.ThreadedStep(lp, cores)
+        x = np.clip(np.zeros(lp["n"]), lp["l"], lp["u"])
+        y = np.zeros(lp["m"])
+        for _ in range(args.warmup):
+            T.step(x, y, 1e-3, 1.0)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            T.step(x, y, 1e-3, 1.0)
+        el = time.perf_counter() - t0
+        rate = args.steps / el
+        base = {"value": rate, "unit": "PDHG iter/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+                "sample": f"{args.steps} oracle PDHG steps (orc_pdhg_step_par on {cores} threads: K'y, primal "
+                          f"step, K(2x+-x), dual step) on the full workload after {args.warmup} untimed, "
+                          f"{el:.1f} s"}
+        out = {"metric": METRIC, "value": rate, "unit": "PDHG iter/s", "n_gpus": 0,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "impl": "reference",
-               "config": {"workload": desc, "check_every": CHECK_EVERY},
+               "config": {"workload": desc, "check_every": CHECK_EVERY, "step": "1 oracle PDHG iteration",
+                          "m": lp["m"], "n": lp["n"], "nnz": int(lp["val"].shape[0])},
                "cpu_baseline": base,
-               "e2e": {"value": base["value"], "unit": base["unit"], "h2d_bytes_per_step": 0,
-                       "d2h_bytes_per_step": 0}}
+               "e2e": {"value": rate, "unit": "PDHG iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
         return
 
@@ -712,7 +826,9 @@ def main():
                 "gather": {"gathers_per_launch": nnz, "achieved_per_s": nnz / (kms * 1e-3),
                            "ceiling_per_s": ceil.get("gathers_per_s"),
                            "frac": (nnz / (kms * 1e-3) / ceil["gathers_per_s"]) if "gathers_per_s" in ceil else None,
-                           "ceiling_run": ceil}}
+                           "ceiling_run": ceil},
+                "fp64": fp64_roofline(nnz / (kms * 1e-3), "one DFMA per stored nonzero of the product "
+                                                         "(the epilogue's FP64 work is not counted)")}
     iter_bytes = info["algorithmic_bytes_per_iter"]
     whole_iter_gbs = iter_bytes * (iters / (ms * 1e-3)) / 1e9
 

@@ -154,14 +154,20 @@ typedef struct {
                               (automatic) and the batch is FP64: 0 = the first solve of the
                               handle runs the online autotuner and later solves keep its
                               choice; 1 = no tuning (the team-size rule above); 2 = tune
-                              again on this solve.  The autotuner times candidate team sizes
-                              (the rule's, half and twice it) and placements (streamed or
-                              resident slices, or global iterates) on the solve's own
-                              iterations: after a first slice of check_every iterations of
-                              every LP, each candidate runs the next slice of every LP still
-                              running as one resumed launch and is scored by bytes of work
-                              per second; the fastest runs the rest.  Results equal the
-                              untuned solve's up to summation order.                      */
+                              again on this solve.  The autotuner times candidates on the
+                              solve's own iterations: after a first slice of check_every
+                              iterations of every LP (the rule's choice), each candidate
+                              runs the next slice of every LP still running as one resumed
+                              launch and is scored by stored bytes of the iterations run
+                              per second.  Candidates: the rule's team size with each
+                              placement that fits (streamed or resident slices; global
+                              iterates when x and y do not fit in shared memory), then
+                              team sizes doubled while the score improves (or halved when
+                              the first doubling loses); at most 8, and only while at
+                              least half of the LPs are still running.  The fastest runs
+                              the rest.  Results equal the untuned solve's up to
+                              summation order.  A solve that keeps a choice (or has fixed
+                              ones) runs its device work as one CUDA graph.              */
 } pdlp_params;
 
 typedef struct {
@@ -406,18 +412,26 @@ int pdlp_mlp_train(pdlp_mlp h, int32_t epochs, int32_t batch, float lr, float we
  *   row_ptr   : int64[m+1] device array, row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz.
  *   col_idx   : int32[nnz] device array, 0 <= col < n;  val: double[nnz] device array.
  *   x         : double[n] device array;  y: double[m] device array (output, overwritten).
+ *               y must not overlap x, row_ptr, col_idx or val: threads write rows of y
+ *               while others still read x (y == x is rejected with PDLP_EINVAL).
  *   stream    : cudaStream_t to run on (NULL = the default stream); the call returns
  *               without waiting, y is ready when the stream reaches that point.
  * Scratch: partial sums of rows that cross thread boundaries live in one fixed 8 MiB
  * device array of the library, which every GPU that uses this call keeps until the
  * process exits.  It limits nnz to 22,369,600; larger inputs return PDLP_EINVAL with a
  * message in pdlp_last_error(NULL), before any device work.  The first call on a device
- * looks up that array's device address (with the device current); make that first call
- * before any stream capture.  Every call on a device shares the array, so calls that
+ * looks up that array's device address (with the device current) and keeps it for the
+ * device: it belongs to the device's primary context, the one the CUDA runtime uses, so
+ * callers must use the runtime's context and must not reset the device
+ * (cudaDeviceReset) between calls; make that first call before any stream capture.  Every call on a device shares the array, so calls that
  * overlap on the GPU (different streams, or different host threads) race and give wrong
  * results; the call writes every scratch entry it later reads, so nothing needs clearing.
  * The same 1e-13 relative agreement with pdlp_spmv holds (summation order differs).
- * Errors: PDLP_EINVAL (sizes, null arrays), PDLP_ECUDA (no device, launch failure). */
+ * Cost: each thread reads 64 consecutive nonzeros, so the loads are not coalesced
+ * across a warp; a row longer than 64 entries is finished by one thread that adds its
+ * ~L/64 run partials one after the other, so a single very long row (L ~ 1e7) makes
+ * the call serial in that row.  pdlp_spmv is the fast path for repeated products.
+ * Errors: PDLP_EINVAL (sizes, null arrays, y == x), PDLP_ECUDA (no device, launch failure). */
 int pdlp_spmv_csr_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
                           const int32_t* col_idx, const double* val, const double* x, double* y,
                           void* stream);

@@ -303,6 +303,55 @@ void orc_pdhg_step(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const in
   free(g); free(w); free(Kw);
 }
 
+/* ---------- the same step on several host threads (CPU baseline timing only) ---------- */
+
+/* K' in CSR by a counting sort of K's entries on their column (stable: each row of K'
+ * lists its entries in increasing row of K).  tp[n + 1], tc[nnz] (row of K), tv[nnz]. */
+void orc_transpose(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                   int64_t* tp, int32_t* tc, double* tv) {
+  for (int64_t j = 0; j <= n; ++j) tp[j] = 0;
+  for (int64_t k = 0; k < rp[m]; ++k) tp[ci[k] + 1] += 1;
+  for (int64_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t j = 0; j < n; ++j) fill[j] = tp[j];
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      int64_t d = fill[ci[k]]++;
+      tc[d] = (int32_t)i;
+      tv[d] = v[k];
+    }
+  free(fill);
+}
+
+/* orc_pdhg_step split over `threads` host threads: the primal update by columns (rows
+ * of K', each column's terms added in increasing row order, as orc_spmv_t adds them),
+ * the dual update by rows.  The arithmetic and its order are orc_pdhg_step's, so the
+ * result is bit-identical; only the CPU baseline's timing uses it. */
+void orc_pdhg_step_par(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t* ci,
+                       const double* v, const int64_t* tp, const int32_t* tc, const double* tv,
+                       const double* c, const double* q, const double* l, const double* u, double eta,
+                       double omega, double* x, double* y, int32_t threads) {
+  double* w = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  if (threads < 1) threads = 1;
+#pragma omp parallel for num_threads(threads) schedule(static)
+  for (int64_t j = 0; j < n; ++j) {
+    double g = 0.0;
+    for (int64_t k = tp[j]; k < tp[j + 1]; ++k) g += tv[k] * y[tc[k]];
+    double xn = proj_box(x[j] - (eta / omega) * (c[j] - g), l[j], u[j]);
+    w[j] = 2.0 * xn - x[j];
+    x[j] = xn;
+  }
+#pragma omp parallel for num_threads(threads) schedule(static)
+  for (int64_t i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * w[ci[k]];
+    double yn = y[i] + (eta * omega) * (q[i] - s);
+    if (i >= m1 && yn < 0.0) yn = 0.0;
+    y[i] = yn;
+  }
+  free(w);
+}
+
 /* ---------- the adaptive step (step_rule = 1) ---------- */
 
 /* One attempt of the adaptive rule from (x, y) with step eta: the candidate goes to

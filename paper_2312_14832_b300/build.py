@@ -38,8 +38,24 @@ def build_ceiling(force: bool = False) -> str:
     return CEIL_BIN
 
 
+PEAK_SRC = os.path.join(HERE, "csrc", "fp64_peak.cu")
+PEAK_BIN = os.path.join(HERE, "fp64_peak")
+
+
+def build_fp64_peak(force: bool = False) -> str:
+    """The FP64 fused multiply-add throughput microbenchmark used by bench.py for the
+    arithmetic roof of the FP64 kernels."""
+    if force or not os.path.exists(PEAK_BIN) or os.path.getmtime(PEAK_BIN) < os.path.getmtime(PEAK_SRC):
+        tmp = PEAK_BIN + f".tmp{os.getpid()}"
+        subprocess.check_call([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
+                               "-o", tmp, PEAK_SRC])
+        os.replace(tmp, PEAK_BIN)
+    return PEAK_BIN
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     build_ceiling(force)
+    build_fp64_peak(force)
     if force or stale():
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [NVCC, *FLAGS, "-o", tmp, *SRC]

@@ -139,6 +139,10 @@ extern "C" int pdlp_spmv_csr_noalloc(int64_t m, int64_t n, int64_t nnz, const in
     pdlp::set_thread_error("pdlp_spmv_csr_noalloc: null array");
     return PDLP_EINVAL;
   }
+  if (static_cast<const void*>(y) == static_cast<const void*>(x)) {
+    pdlp::set_thread_error("pdlp_spmv_csr_noalloc: y must not overlap x (no in-place product)");
+    return PDLP_EINVAL;
+  }
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -147,7 +151,9 @@ extern "C" int pdlp_spmv_csr_noalloc(int64_t m, int64_t n, int64_t nnz, const in
   }
   unsigned char* scratch = nullptr;
   {
-    // once per device, with that device current: the device address of the array
+    // once per device, with that device current: the device address of the array in the
+    // device's primary context (the runtime's); it stays valid until the process exits
+    // unless that context is destroyed (cudaDeviceReset)
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
     if (!g_noalloc_ptr[dev]) {
       void* p = nullptr;

@@ -2043,33 +2043,27 @@ static void launch_resumed(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& 
 // Online autotuner of the batched launch, run by the first solve of a handle whose team
 // size and data placement are automatic (FP64 batches).  The first check_every
 // iterations of every LP run with the rule's choice (they also hold the power
-// iteration); then each candidate (team size x placement: the rule's team, half and
-// twice it; iterates streamed or resident slices where they fit, or global iterates)
-// runs the next check_every iterations of every LP still running, as one resumed
-// launch, and is scored by the work it did (iterations run x stored bytes of one
-// iteration of each LP) per device second.  Tuning stops early once fewer than half of
-// the LPs are still running.  Nothing is repeated: the slices are the solve's own
-// iterations, resumed exactly (up to summation order).  The fastest candidate is kept
-// for the rest of the solve and for later solves of the handle.  Returns the LPs left
-// running after the slices.
+// iteration); then each candidate runs the next check_every iterations of every LP
+// still running, as one resumed launch, and is scored by the work it did (iterations
+// run x stored bytes of one iteration of each LP) per device second.  Candidates: the
+// rule's team size with each placement that fits (iterates streamed from shared-memory
+// replicas or resident matrix slices; global iterates when x and y do not fit), then a
+// climb in team size with the better placement: doubling while the score improves, or
+// halving when the first doubling did not.  At most 8 candidates; tuning stops early
+// once fewer than half of the LPs are still running.  Nothing is repeated: the slices
+// are the solve's own iterations, resumed exactly (up to summation order).  The fastest
+// candidate is kept for the rest of the solve and for later solves of the handle.
+// Returns the LPs left running after the slices.
 static std::vector<int32_t> tune_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp) {
   const int64_t count = h->count;
   const bool glob = h->batch_glob;
   const int rule = batch_team_size(h, count, 0, glob);
   const int cap = glob ? kTeamGlobMax : kMaxTeam;
-  struct Cand { int team, resident; };
-  std::vector<Cand> cands;
-  for (int T : {rule, rule / 2, rule * 2}) {
-    if (T < 1 || T > cap) continue;
-    if (T > 1 && h->team_npad_max < (int64_t)T * 64) continue;
-    if (glob) {
-      cands.push_back({T, 3});
-    } else {
-      cands.push_back({T, 1});
-      const long long need = resident_need(h, T);
-      if (h->batch_smem + (size_t)((need + 7) / 8 * 8) <= (size_t)h->dev_smem_optin) cands.push_back({T, 2});
-    }
-  }
+  auto feasible = [&](int T) { return T >= 1 && T <= cap && (T == 1 || h->team_npad_max >= (int64_t)T * 64); };
+  auto res_fits = [&](int T) {
+    const long long need = resident_need(h, T);
+    return h->batch_smem + (size_t)((need + 7) / 8 * 8) <= (size_t)h->dev_smem_optin;
+  };
   std::vector<double> w((size_t)count);
   for (int64_t b = 0; b < count; ++b) {
     const LpDesc& D = h->hdesc[(size_t)b];
@@ -2084,18 +2078,19 @@ static std::vector<int32_t> tune_batch(pdlp_ctx* h, const BatchArgs& A0, const p
   std::vector<int32_t> active = suspended_lps(h);
   std::vector<long long> kprev((size_t)count);
   for (int64_t b = 0; b < count; ++b) kprev[(size_t)b] = h->hstate[(size_t)b].k;
-  double best = -1.0;
-  Cand bc = cands.empty() ? Cand{rule, 0} : cands[0];
   h->tune_candidates = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (const Cand& c : cands) {
-    if ((int64_t)active.size() * 2 < count) break;
+  double best = -1.0;
+  int best_team = rule, best_res = glob ? 3 : 1;
+  // one timed slice of candidate (team, placement); -1 when tuning has to stop
+  auto eval = [&](int team, int res) -> double {
+    if (h->tune_candidates >= 8 || (int64_t)active.size() * 2 < count) return -1.0;
     pdlp_params sc = sp;
-    sc.resident = c.resident;
+    sc.resident = res;
     CK(cudaEventRecord(e0, h->s));
-    launch_resumed(h, A0, sc, active, c.team, sp.check_every);
+    launch_resumed(h, A0, sc, active, team, sp.check_every);
     CK(cudaEventRecord(e1, h->s));
     std::vector<int32_t> next = suspended_lps(h);
     float ms = 0.f;
@@ -2107,22 +2102,55 @@ static std::vector<int32_t> tune_batch(pdlp_ctx* h, const BatchArgs& A0, const p
     }
     const double rate = ms > 0.f ? work / (double)ms : 0.0;
     const int i = h->tune_candidates++;
-    if (i < 8) {
-      h->tune_rates[i] = rate * 1e-6;   // GB/s of stored bytes
-      h->tune_team[i] = c.team;
-      h->tune_res[i] = c.resident;
-    }
+    h->tune_rates[i] = rate * 1e-6;   // GB/s of stored bytes
+    h->tune_team[i] = team;
+    h->tune_res[i] = res;
     if (rate > best) {
       best = rate;
-      bc = c;
+      best_team = team;
+      best_res = res;
     }
     active.swap(next);
+    return rate;
+  };
+  try {
+    // the rule's team with each placement that fits
+    if (glob) {
+      eval(rule, 3);
+    } else {
+      eval(rule, 1);
+      if (res_fits(rule)) eval(rule, 2);
+    }
+    const int mode = best_res;
+    auto mode_for = [&](int T) { return (mode == 2 && !res_fits(T)) ? 1 : mode; };
+    // climb: double while the score improves; if the first doubling loses, halve instead
+    bool up_won = false;
+    for (int T = rule * 2; feasible(T); T *= 2) {
+      const double before = best;
+      const double r = eval(T, mode_for(T));
+      if (r < 0.0 || r <= before) break;
+      up_won = true;
+    }
+    if (!up_won)
+      for (int T = rule / 2; T >= 1 && feasible(T); T /= 2) {
+        const double before = best;
+        const double r = eval(T, mode_for(T));
+        if (r < 0.0 || r <= before) break;
+      }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->tuned = true;
-  h->tuned_team = bc.team;
-  h->tuned_resident = bc.resident;
+  // a choice needs at least two timed candidates (a solve shorter than the slices
+  // leaves the handle untuned, and the next solve tries again)
+  if (h->tune_candidates >= 2) {
+    h->tuned = true;
+    h->tuned_team = best_team;
+    h->tuned_resident = best_res;
+  }
   return active;
 }
 
@@ -2240,6 +2268,8 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   if (auto_cfg && h->tuned) {
     team1 = h->tuned_team;
     sp1.resident = h->tuned_resident;
+  } else if (tuned_now) {
+    team1 = 0;   // nothing to choose from: the rule
   }
   // mixed precision: FP32 iterations first; the LPs that leave them unfinished are
   // suspended with their FP64 state and continue in FP64 (second stage).  With

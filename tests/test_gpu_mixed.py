@@ -52,6 +52,22 @@ def test_mixed_refines_to_1e8(pk, scaling):
     assert abs(r["primal_obj"] - lp["obj_star"]) <= 1e-6 * abs(lp["obj_star"])
 
 
+def test_mixed_mcf_refines_to_1e8(pk):
+    """The multicommodity-flow family (+-1 incidence entries, capacity rows) at a size the
+    oracle solves to 1e-8 in seconds: an FP32 phase, then the switch to FP64 and the
+    refinement; the point passes the three tests at 1e-8 by the oracle's evaluation and
+    the objective matches the FP64 oracle's solve to 1e-6."""
+    lp = lpgen.mcf(0, nodes=500, arcs=2500)
+    ref = oracle.solve(lp, tol=1e-8, scaling=1)
+    assert ref["status"] == oracle.STATUS_OPTIMAL
+    with pk.Solver.from_lp(lp, scaling=1, precision=pk.MIXED) as s:
+        r = s.solve(tol=1e-8)
+    assert r["status"] == pk.OPTIMAL
+    assert 0 < r["fp32_iters"] < r["iters"]
+    check_point(lp, r["x"], r["y"], 1e-8)
+    assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-6 * abs(ref["primal_obj"])
+
+
 def test_mixed_loose_tolerance_stays_fp32(pk):
     lp = lpgen.planted_small(1)
     with pk.Solver.from_lp(lp, precision=pk.MIXED) as s:

@@ -271,6 +271,32 @@ def test_restart_candidate_strict_rule():
     assert cand(3.0, np.inf) == 0
 
 
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_step_is_the_serial_step(threads):
+    """The CPU baseline's all-core PDHG step (K' built by a counting sort, columns and rows
+    split over threads) performs orc_pdhg_step's operations in the same order: three
+    steps from a random point give the same bits, with empty rows and columns present."""
+    lengths = [0, 1, 31, 32, 33, 0, 5, 200, 1, 64] * 5
+    rp, ci, v = lpgen.random_csr(21, len(lengths), 700, lengths, dist="wide")
+    rng = np.random.default_rng(22)
+    m, n = len(lengths), 700
+    l = np.where(rng.random(n) < 0.5, -np.inf, -1.0)
+    u = np.where(rng.random(n) < 0.5, np.inf, 2.0)
+    lp = dict(m=m, n=n, m1=m // 3, row_ptr=rp, col_idx=ci, val=v, c=rng.standard_normal(n),
+              q=rng.standard_normal(m), l=l, u=u)
+    x = np.clip(rng.standard_normal(n), l, u)
+    y = rng.standard_normal(m)
+    y[m // 3:] = np.abs(y[m // 3:])
+    T = oracle.ThreadedStep(lp, threads)
+    xs, ys = x.copy(), y.copy()
+    xp, yp = x.copy(), y.copy()
+    for _ in range(3):
+        xs, ys = oracle.pdhg_step(lp, xs, ys, 0.4, 1.3)
+        T.step(xp, yp, 0.4, 1.3)
+    np.testing.assert_array_equal(xp, xs)
+    np.testing.assert_array_equal(yp, ys)
+
+
 # ---------------------------------------------------------------- scaling
 
 def test_ruiz_equilibrates():
