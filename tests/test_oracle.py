@@ -529,6 +529,22 @@ def test_adaptive_step_without_rows_grows_by_the_closed_form():
     np.testing.assert_allclose(r["x"], np.where(c > 0, l, u), rtol=0, atol=1e-9)
 
 
+def test_adaptive_first_attempt_by_hand():
+    """The adaptive rule's first attempt on min x s.t. x = 3 (x free), eta = 0.5,
+    omega = 2, from z = 0, worked by hand (reading A1-A2): the attempt is the plain PDHG
+    step, dx = -0.25, dy = 3.5, dy' K dx = -0.875; eta_max = (2 * 0.0625 + 12.25 / 2) /
+    (2 * 0.875) = 25/7 >= 0.5, so the step is kept (s = 1, s + 1 = 2) and the next eta is
+    min((1 - 2^-0.3) * 25/7, (1 + 2^-0.6) * 0.5) = (1 - 2^-0.3) * 25/7 = 0.6705..."""
+    r = oracle.solve(_lp1x1(), tol=1e-12, max_iter=1, check_every=1, eta=0.5, omega0=2.0, scaling=0,
+                     step_rule=1)
+    assert r["accepted"] == 1
+    np.testing.assert_allclose(r["x_cur"], [-0.25], rtol=1e-15)
+    np.testing.assert_allclose(r["y_cur"], [3.5], rtol=1e-15)
+    want = (1.0 - 2.0 ** -0.3) * 25.0 / 7.0
+    assert want < (1.0 + 2.0 ** -0.6) * 0.5
+    assert r["eta"] == pytest.approx(want, rel=1e-14)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_adaptive_tiny_lp_matches_vertex_enumeration(seed):
     lp = lpgen.tiny_lp(seed, n=5, m1=1, m2=3)
