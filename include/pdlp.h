@@ -359,14 +359,26 @@ int64_t pdlp_batch_get_restarts(pdlp_handle h, int64_t lp, int64_t* iters, int64
 
 /* ---------------------------------------------------------------- dense kernels
  * C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], then max(., 0) if relu) on the tcgen05
- * tensor cores: A and B BF16 row-major (K contiguous) device arrays, C FP32 row-major
- * device array, bias FP32 device array or NULL.  M and N multiples of 128, K a multiple
- * of 64.  Used by the learned warm start (an extension: the paper has no
- * learned component); exposed for testing.  Runs on `stream` (NULL = default) and
- * waits for it.  Errors: PDLP_EINVAL (shapes), PDLP_ECUDA, PDLP_ETIMEOUT (an mbarrier
- * wait gave up). */
+ * tensor cores: A and B BF16 row-major (K contiguous) device arrays with 16-byte aligned
+ * bases, C FP32 row-major device array, bias FP32 device array or NULL.  M and N
+ * multiples of 128, K a multiple of 64.  The operand tiles are copied by the tensor
+ * memory accelerator into a 6-stage shared-memory ring that one thread refills while
+ * another issues the MMAs.  Used by the learned warm start (an extension: the paper has
+ * no learned component); exposed for testing.  Runs on `stream` (NULL = default) and
+ * waits for it; allocates no device memory (its error flag is a device variable of the
+ * library).  Errors: PDLP_EINVAL (shapes, alignment), PDLP_ECUDA, PDLP_ETIMEOUT (an
+ * mbarrier wait gave up). */
 int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
                  int32_t relu, void* stream);
+
+/* pdlp_tc_gemm with K cut into `splits` slices (>= 1; fewer when K / 64 does not give
+ * that many non-empty slices), each computed by its own CTAs into the caller's device
+ * array workspace (splits * M * N floats), then added in slice order (+ bias, ReLU) into
+ * C.  For products with few 128 x 128 output tiles and a long K.  The MLP uses this path
+ * internally.  Errors as pdlp_tc_gemm; PDLP_EINVAL also for splits < 1, or a NULL
+ * workspace with splits > 1. */
+int pdlp_tc_gemm_split(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
+                       int32_t relu, int32_t splits, float* workspace, void* stream);
 
 /* ---------------------------------------------------------------- warm-start network
  * A 3-layer MLP for learned warm starts (an extension; the paper has no

@@ -3,12 +3,15 @@
 // BF16 operands on the tcgen05 tensor cores (tc_gemm.cuh) with FP32 accumulation,
 // FP32 master weights, MSE loss and AdamW, forward and backward all on the device.
 // Backward products use explicit BF16 transposes so that every GEMM is A * B'.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -18,53 +21,155 @@
 namespace pdlp {
 void set_thread_error(const std::string& msg);
 
-// Launches k_tc_gemm; returns a CUDA error code (cudaSuccess on success).
+constexpr int kTcMaxDevices = 64;
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a row-major BF16 matrix [rows x K] read in 128-row x 64-column boxes with
+// 128-byte swizzle (the layout the MMA descriptors name).
+static cudaError_t encode_operand(CUtensorMap* tm, const __nv_bfloat16* p, int rows, int K) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcTile};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// The kernel's shared-memory opt-in, once per device (with that device current).
+static cudaError_t tc_gemm_attrs() {
+  static std::once_flag once[kTcMaxDevices];
+  static cudaError_t res[kTcMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kTcMaxDevices) return cudaErrorInvalidDevice;
+  std::call_once(once[dev], [&]() {
+    res[dev] = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemBytes);
+  });
+  return res[dev];
+}
+
+// Slices of K for a product with few output tiles: enough CTAs for about two per SM,
+// at least 8 steps of K per slice, at most max_splits.
+int tc_gemm_splits(int M, int N, int K, int max_splits) {
+  const int tiles = (M / kTcTile) * (N / kTcTile), kt = K / kTcK;
+  if (tiles >= 148 || kt < 16 || max_splits <= 1) return 1;
+  int sp = std::min(std::min(kt / 8, (2 * 148 + tiles - 1) / tiles), max_splits);
+  sp = std::max(sp, 1);
+  const int kps = (kt + sp - 1) / sp;
+  return (kt + kps - 1) / kps;   // no empty slice
+}
+
+// C (FP32, optional) / Cb (BF16, optional) = A B' (+ bias, ReLU) with `splits` slices of K
+// (1: no split; > 1: part holds splits x M x N floats).  Returns a CUDA error code.
 cudaError_t tc_gemm_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, __nv_bfloat16* Cb,
-                           const float* bias, int M, int N, int K, int relu, int* err, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+                           const float* bias, int M, int N, int K, int relu, int splits, float* part, int* err,
+                           cudaStream_t s) {
+  cudaError_t e = tc_gemm_attrs();
+  if (e != cudaSuccess) return e;
+  CUtensorMap ta, tb;
+  e = encode_operand(&ta, A, M, K);
+  if (e == cudaSuccess) e = encode_operand(&tb, B, N, K);
+  if (e != cudaSuccess) return e;
+  const int kt = K / kTcK;
+  if (splits < 1 || !part) splits = 1;
+  const int kps = (kt + splits - 1) / splits;
+  splits = (kt + kps - 1) / kps;
+  TcGemmArgs g{C, Cb, bias, splits > 1 ? part : nullptr, M, N, K, kps, relu, err};
+  dim3 grid(N / kTcTile, M / kTcTile, splits);
+  k_tc_gemm<<<grid, 128, kTmSmemBytes, s>>>(ta, tb, g);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && splits > 1) {
+    const int64_t tot = (int64_t)M * N;
+    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
+    k_tc_splitk_reduce<<<blocks, 256, 0, s>>>(part, splits, M, N, bias, relu, C, Cb);
+    e = cudaGetLastError();
   }
-  TcGemmArgs g{A, B, C, Cb, bias, M, N, K, relu, err};
-  dim3 grid(N / kTcTile, M / kTcTile);
-  k_tc_gemm<<<grid, 128, kTcSmemBytes, s>>>(g);
-  return cudaGetLastError();
+  return e;
+}
+
+// Error flag of the standalone entry points: one device int per GPU, its address looked
+// up once per device.
+__device__ int g_tc_gemm_err;
+static int* tc_err_flag() {
+  static std::mutex mu;
+  static int* addr[kTcMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tc_gemm_err) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<int*>(p);
+  }
+  return addr[dev];
+}
+
+static int tc_gemm_entry(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
+                         int32_t relu, int32_t splits, float* workspace, void* stream, const char* name) {
+  if (M <= 0 || N <= 0 || K <= 0 || M % kTcTile || N % kTcTile || K % kTcK) {
+    set_thread_error(std::string(name) + ": M, N must be positive multiples of 128 and K of 64");
+    return PDLP_EINVAL;
+  }
+  if (!A || !B || !C || (splits > 1 && !workspace) || splits < 1) {
+    set_thread_error(std::string(name) + ": null array or bad split count");
+    return PDLP_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) {
+    set_thread_error(std::string(name) + ": A and B must be 16-byte aligned");
+    return PDLP_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* err = tc_err_flag();
+  if (!err) {
+    set_thread_error(std::string(name) + ": no device error flag");
+    return PDLP_ECUDA;
+  }
+  const int zero = 0;
+  cudaError_t e = cudaMemcpyAsync(err, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = tc_gemm_launch(static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), C, nullptr, bias,
+                       M, N, K, relu, splits, workspace, err, s);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_thread_error(std::string(name) + ": " + cudaGetErrorString(e));
+    return PDLP_ECUDA;
+  }
+  if (herr) {
+    set_thread_error(std::string(name) + ": an mbarrier wait gave up (spin limit)");
+    return PDLP_ETIMEOUT;
+  }
+  return PDLP_OK;
 }
 }  // namespace pdlp
 
 extern "C" int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C,
                             const float* bias, int32_t relu, void* stream) {
-  using namespace pdlp;
-  if (M <= 0 || N <= 0 || K <= 0 || M % kTcTile || N % kTcTile || K % kTcK) {
-    set_thread_error("pdlp_tc_gemm: M, N must be positive multiples of 128 and K of 64");
-    return PDLP_EINVAL;
-  }
-  if (!A || !B || !C) {
-    set_thread_error("pdlp_tc_gemm: null array");
-    return PDLP_EINVAL;
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int* err = nullptr;
-  cudaError_t e = cudaMallocAsync(&err, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
-  if (e == cudaSuccess)
-    e = tc_gemm_launch(static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), C, nullptr, bias,
-                       M, N, K, relu, err, s);
-  int herr = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (err) cudaFreeAsync(err, s);
-  if (e != cudaSuccess) {
-    set_thread_error(std::string("pdlp_tc_gemm: ") + cudaGetErrorString(e));
-    return PDLP_ECUDA;
-  }
-  if (herr) {
-    set_thread_error("pdlp_tc_gemm: an mbarrier wait gave up (spin limit)");
-    return PDLP_ETIMEOUT;
-  }
-  return PDLP_OK;
+  return pdlp::tc_gemm_entry(M, N, K, A, B, C, bias, relu, 1, nullptr, stream, "pdlp_tc_gemm");
+}
+
+extern "C" int pdlp_tc_gemm_split(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C,
+                                  const float* bias, int32_t relu, int32_t splits, float* workspace, void* stream) {
+  return pdlp::tc_gemm_entry(M, N, K, A, B, C, bias, relu, splits, workspace, stream, "pdlp_tc_gemm_split");
 }
 
 // ------------------------------------------------------------------ MLP kernels
@@ -181,6 +286,8 @@ struct pdlp_mlp_ctx {
   float *H1, *H2, *Y, *dY, *dH2, *dZ2, *dH1, *dZ1;
   double* part;
   int* err;
+  float* gemm_ws = nullptr;   // partial products of GEMMs split along K
+  int64_t gemm_ws_floats = 0;
   int* idx;          // batch row indices into the dataset
   float *dataX = nullptr, *dataT = nullptr;
   int64_t ndata = 0;
@@ -208,9 +315,13 @@ static void mlp_ck(cudaError_t e, const char* what) {
 
 static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 148 * 8); }
 
+constexpr int kMlpMaxSplits = 32;
+
 static void gemm(pdlp_mlp_ctx* h, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, __nv_bfloat16* Cb,
                  const float* bias, int M, int N, int K, int relu) {
-  mlp_ck(tc_gemm_launch(A, B, C, Cb, bias, M, N, K, relu, h->err, h->s), "tc_gemm");
+  int sp = tc_gemm_splits(M, N, K, kMlpMaxSplits);
+  if ((int64_t)sp * M * N > h->gemm_ws_floats) sp = 1;
+  mlp_ck(tc_gemm_launch(A, B, C, Cb, bias, M, N, K, relu, sp, h->gemm_ws, h->err, h->s), "tc_gemm");
 }
 
 static void transpose(pdlp_mlp_ctx* h, __nv_bfloat16* dst, const __nv_bfloat16* src, int R, int C) {
@@ -333,6 +444,15 @@ int pdlp_mlp_create(pdlp_mlp* out, int32_t n_in, int32_t hidden, int32_t n_out, 
     h->dY = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
     h->part = mlp_alloc<double>(h, 148);
     h->err = mlp_alloc<int>(h, 1);
+    // the split-K workspace of the largest split product of a training step
+    const int shapes[8][3] = {{h->bp, h->hid, h->in_p},  {h->bp, h->hid, h->hid},  {h->bp, h->out_p, h->hid},
+                              {h->out_p, h->hid, h->bp}, {h->bp, h->hid, h->out_p}, {h->hid, h->hid, h->bp},
+                              {h->bp, h->hid, h->hid},   {h->hid, h->in_p, h->bp}};
+    for (const auto& sh : shapes) {
+      const int sp = tc_gemm_splits(sh[0], sh[1], sh[2], kMlpMaxSplits);
+      if (sp > 1) h->gemm_ws_floats = std::max<int64_t>(h->gemm_ws_floats, (int64_t)sp * sh[0] * sh[1]);
+    }
+    if (h->gemm_ws_floats > 0) h->gemm_ws = mlp_alloc<float>(h, (size_t)h->gemm_ws_floats);
     h->idx = mlp_alloc<int>(h, h->bp);
     mlp_ck(cudaStreamSynchronize(h->s), "create");
   } catch (const std::string& m) {

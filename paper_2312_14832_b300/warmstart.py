@@ -6,9 +6,13 @@ maps the parameters of an LP of the family (for the transportation family: suppl
 and demands) to a starting point x0, y0 and an initial primal weight omega0.  It is
 trained on solutions the batched solver computes, and used through the batched
 solver's warm start.  The KKT error decides: for each LP the prediction is used only
-if its KKT_omega (Section 2, restart criteria; on the scaled LP, each point with the
-primal weight its solve starts with, measured by the solver at iteration 0) is below
-the cold start's; otherwise that LP starts cold.
+if its largest relative error (the three termination tests of Section 2, measured by
+the solver at iteration 0) is below the cold start's; otherwise that LP starts cold.
+KKT_omega (Section 2, restart criteria) is not the judge: its gap term is not
+normalised, and the cold start of a transportation LP, (0, 0), has a zero dual
+residual and a zero gap, so KKT_omega(cold) = omega ||b|| is below that of any
+approximate prediction, whose gap |q'y - c'x| is on the scale of the objective.
+evaluate reports how many predictions each judge would take.
 
 Normalisation is per component: parameters and targets are standardised with the
 training set's mean and standard deviation (floor 1e-6); omega is learned in log
@@ -92,9 +96,9 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
     inference (host wall time of predict, transfers included), the two iteration-0
     launches of the KKT judge (device time), the warm-started solve (device time) and,
     with an iteration budget, the cold re-solve of every LP that did not converge within
-    it (device time of one batched launch over those LPs).  The judge compares KKT_omega
-    of the prediction with that of the cold start; the largest relative error of the
-    three tests is reported beside it.
+    it (device time of one batched launch over those LPs).  The judge compares the
+    largest relative error of the three tests for the prediction and the cold start; the
+    count KKT_omega would accept is reported beside it.
 
     budget: iteration budget of a warm-started solve; an LP that has not converged
     within it falls back to a cold start, and its count is the budget plus the cold
@@ -114,7 +118,7 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
         k_pred = np.array([r["kkt_omega"] for r in p0])
         e_cold = np.array([max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) for r in c0])
         e_pred = np.array([max(r["rel_primal"], r["rel_dual"], r["rel_gap"]) for r in p0])
-        use = k_pred < k_cold
+        use = e_pred < e_cold
         xs = [x0[i] if use[i] else np.zeros(lp["n"]) for i, lp in enumerate(lps)]
         ys = [y0[i] if use[i] else np.zeros(lp["m"]) for i, lp in enumerate(lps)]
         ws = np.where(use, w0, 0.0)
@@ -149,7 +153,7 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
                 warm_fewer_iters=int(np.sum(wi < ci)), warm_more_iters=int(np.sum(wi > ci)),
                 fell_back_after_budget=int(over.sum()))
     out["used_prediction"] = int(use.sum())
-    out["used_prediction_by_max_rel_error"] = int(np.sum(e_pred < e_cold))
+    out["used_prediction_by_kkt_omega"] = int(np.sum(k_pred < k_cold))
     out["initial_kkt_omega_cold_median"] = float(np.median(k_cold))
     out["initial_kkt_omega_pred_median"] = float(np.median(k_pred))
     out["initial_err_cold_median"] = float(np.median(e_cold))
