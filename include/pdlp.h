@@ -166,8 +166,9 @@ typedef struct {
                               the first doubling loses); at most 8, and only while at
                               least half of the LPs are still running.  The fastest runs
                               the rest.  Results equal the untuned solve's up to
-                              summation order.  A solve that keeps a choice (or has fixed
-                              ones) runs its device work as one CUDA graph.              */
+                              summation order.  An FP64 one-stage solve that keeps a choice
+                              (or has fixed ones) runs its persistent launch as a CUDA
+                              graph.                                                     */
 } pdlp_params;
 
 typedef struct {

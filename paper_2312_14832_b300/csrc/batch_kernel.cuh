@@ -36,8 +36,6 @@ struct BatchArgs {
   const LpDesc* desc;
   const int32_t* order;      // LPs in the order the queue hands them out
   int32_t count;
-  const int32_t* count_dev;  // if not null, the queue length is read from here (set on the
-                             // device by k_collect_suspended) instead of `count`
   int32_t* next;             // queue position (left at zero after the launch)
   const int32_t* k_cptr;     // K: chunk_ptr, col, val (rows)
   const int32_t* k_col;
@@ -1239,7 +1237,7 @@ __global__ void __launch_bounds__(256, (kGlob && !kCl) ? PDLP_BATCH32_GLOB_MIN_B
   Team<kCl> T;
   T.init();
   const int teams = (int)gridDim.x / T.size;
-  const int count = A.count_dev ? *A.count_dev : A.count;
+  const int count = A.count;
   for (;;) {
     if (T.rank == 0 && threadIdx.x == 0) {
       const int v = atomicAdd(A.next, 1);
@@ -1262,7 +1260,7 @@ __global__ void __launch_bounds__(256, kCl ? (kGlob ? PDLP_BATCH_CL_GLOB_MIN_BLO
   Team<kCl> T;
   T.init();
   const int teams = (int)gridDim.x / T.size;
-  const int count = A.count_dev ? *A.count_dev : A.count;
+  const int count = A.count;
   for (;;) {
     if (T.rank == 0 && threadIdx.x == 0) {
       const int v = atomicAdd(A.next, 1);
@@ -1275,35 +1273,6 @@ __global__ void __launch_bounds__(256, kCl ? (kGlob ? PDLP_BATCH_CL_GLOB_MIN_BLO
     if (v >= count) break;
     batch_solve_one<kCl, kRes, kGlob>(A, A.order[v], T);
   }
-}
-
-// The LPs a launch left suspended, in batch order, as the queue of the next launch:
-// order2[0 .. *count2) (one CTA; a block-wide prefix count per 1024 LPs).
-__global__ void __launch_bounds__(1024) k_collect_suspended(const DevState* __restrict__ st, int count,
-                                                            int32_t* __restrict__ order2, int32_t* count2) {
-  __shared__ int warp_tot[32];
-  __shared__ int base;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) base = 0;
-  __syncthreads();
-  for (int b0 = 0; b0 < count; b0 += 1024) {
-    const int b = b0 + tid;
-    const int f = (b < count && st[b].suspended) ? 1 : 0;
-    const unsigned mask = __ballot_sync(0xffffffffu, f);
-    const int in_warp = __popc(mask & ((1u << lane) - 1u));
-    if (lane == 0) warp_tot[wid] = __popc(mask);
-    __syncthreads();
-    int before = 0, tot = 0;
-    for (int w = 0; w < 32; ++w) {
-      if (w < wid) before += warp_tot[w];
-      tot += warp_tot[w];
-    }
-    if (f) order2[base + before + in_warp] = b;
-    __syncthreads();
-    if (tid == 0) base += tot;
-    __syncthreads();
-  }
-  if (tid == 0) *count2 = base;
 }
 
 }  // namespace pdlp

@@ -144,7 +144,6 @@ struct pdlp_ctx {
   float *xg32 = nullptr, *yg32 = nullptr;
   int64_t last_resumed = 0;  // LPs continued in the second stage of the last solve
   int64_t last_launches = 0; // batched launches of the last solve
-  int32_t* count2 = nullptr; // device-side length of the second queue
   cudaGraphExec_t bgraph = nullptr;   // the device part of a batched solve (see batch_solve_impl)
   bool last_graph = false;
   bool last_tuned = false;   // the last solve ran the online autotuner
@@ -1918,7 +1917,7 @@ static int batch_team_size(const pdlp_ctx* h, int64_t count, int team_req, bool 
 // placement of the iterates (shared-memory replicas, with or without resident matrix
 // slices, or global memory) and grid chosen for that count.
 // Device buffers a batched launch may need, allocated before any launch (and so before a
-// graph capture): global iterates, the second queue and its device-side length.
+// graph capture): global iterates and the second queue.
 static void batch_buffers(pdlp_ctx* h, bool glob, bool fp32) {
   if (glob && !h->xg) {
     h->xg = dalloc<double>(h, (size_t)h->npad);
@@ -1929,7 +1928,6 @@ static void batch_buffers(pdlp_ctx* h, bool glob, bool fp32) {
     h->yg32 = dalloc<float>(h, (size_t)std::max<int64_t>(h->mpad, 1));
   }
   if (!h->order2) h->order2 = dalloc<int32_t>(h, (size_t)h->count);
-  if (!h->count2) h->count2 = dalloc<int32_t>(h, 1);
 }
 
 static void launch_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp, int64_t count, int team_req,
@@ -2193,7 +2191,6 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   A.desc = h->desc;
   A.order = h->order;
   A.count = (int32_t)h->count;
-  A.count_dev = nullptr;
   A.next = h->next;
   A.k_cptr = h->K.chunk_ptr;
   A.k_col = h->K.col;
@@ -2274,30 +2271,17 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
   // mixed precision: FP32 iterations first; the LPs that leave them unfinished are
   // suspended with their FP64 state and continue in FP64 (second stage).  With
   // batch_tail_iters the LPs still running after that many iterations continue in a
-  // second stage too.  The second stage runs the largest team the LPs allow.
+  // second stage too, with teams sized for their number.
   const bool two_stage = A.slice_iters > 0 || mixed;
-  const bool glob1 = h->batch_glob || sp1.resident == 3;
-  const int tail_team = batch_team_size(h, 1, 0, h->batch_glob || sp.resident == 3);
   h->last_graph = false;
-  if (!tuned_now && !single) {
-    // the device part of the solve as one CUDA graph: the persistent launch and, for a
-    // two-stage solve, the device-side queue of the suspended LPs and the second launch;
-    // instantiated once per handle and updated in place when the arguments change
-    batch_buffers(h, glob1, mixed);
-    batch_buffers(h, h->batch_glob || sp.resident == 3, false);
+  if (!tuned_now && !single && !two_stage) {
+    // a one-stage solve: its persistent launch as a CUDA graph, instantiated once per
+    // handle and updated in place when the arguments change
+    batch_buffers(h, h->batch_glob || sp1.resident == 3, false);
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
     try {
-      launch_batch(h, A, sp1, h->count, team1, mixed);
-      if (two_stage) {
-        k_collect_suspended<<<1, 1024, 0, h->s>>>(h->bstate, (int)h->count, h->order2, h->count2);
-        BatchArgs A2 = A;
-        A2.order = h->order2;
-        A2.count_dev = h->count2;
-        A2.resume = 1;
-        A2.slice_iters = 0;
-        launch_batch(h, A2, sp, h->count, tail_team);
-      }
+      launch_batch(h, A, sp1, h->count, team1, false);
     } catch (...) {
       cudaStreamEndCapture(h->s, &g);
       if (g) cudaGraphDestroy(g);
@@ -2321,20 +2305,13 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
     }
     CK(cudaGraphLaunch(h->bgraph, h->s));
     h->last_graph = true;
-    if (two_stage) {
-      int32_t c2 = 0;
-      CK(cudaMemcpyAsync(&c2, h->count2, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s));
-      CK(cudaStreamSynchronize(h->s));
-      h->last_resumed = c2;
-    }
-  } else if (!tuned_now) {
-    launch_batch(h, A, sp1, h->count, team1, mixed);   // the persistent engine of a single LP
   } else {
-    if (!active.empty()) launch_resumed(h, A, sp1, active, team1, A.slice_iters);
+    if (!tuned_now) launch_batch(h, A, sp1, h->count, team1, mixed);
+    else if (!active.empty()) launch_resumed(h, A, sp1, active, team1, A.slice_iters);
     if (two_stage) {
       std::vector<int32_t> rest = suspended_lps(h);
       h->last_resumed = (int64_t)rest.size();
-      if (!rest.empty()) launch_resumed(h, A, sp, rest, tail_team, 0);
+      if (!rest.empty()) launch_resumed(h, A, sp, rest, 0, 0);
     }
   }
   CK(cudaEventRecord(h->ev_t1, h->s));
