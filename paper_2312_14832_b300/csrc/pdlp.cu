@@ -145,6 +145,9 @@ struct pdlp_ctx {
   int64_t last_resumed = 0;  // LPs continued in the second stage of the last solve
   int64_t last_launches = 0; // batched launches of the last solve
   cudaGraphExec_t bgraph = nullptr;   // the device part of a batched solve (see batch_solve_impl)
+  long long bgraph_key = -1;          // its launch configuration
+  int last_grid = 0;                  // grid and shared memory of the last batched launch
+  size_t last_smem = 0;
   bool last_graph = false;
   bool last_tuned = false;   // the last solve ran the online autotuner
   long long* brestarts = nullptr;   // batches: kBatchRestartCap restart iterations per LP
@@ -2004,6 +2007,8 @@ static void launch_batch(pdlp_ctx* h, const BatchArgs& A0, const pdlp_params& sp
     grid = (int)std::min<int64_t>((int64_t)nc, count) * team;
   }
   cfg.gridDim = dim3((unsigned)grid);
+  h->last_grid = grid;
+  h->last_smem = smem;
   h->last_team = team;
   h->last_resident = resident;
   h->last_glob = glob;
@@ -2288,6 +2293,14 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
       throw;
     }
     CK(cudaStreamEndCapture(h->s, &g));
+    // an in-place update only for the same launch configuration (kernel, team size, grid,
+    // shared memory); another configuration gets a new executable graph
+    const long long key = ((long long)h->last_grid << 24) ^ ((long long)h->last_smem << 8) ^
+                          ((long long)h->last_team << 2) ^ ((long long)h->last_resident << 1) ^ (long long)h->last_glob;
+    if (h->bgraph && key != h->bgraph_key) {
+      cudaGraphExecDestroy(h->bgraph);
+      h->bgraph = nullptr;
+    }
     if (h->bgraph) {
       cudaGraphExecUpdateResultInfo ui;
       if (cudaGraphExecUpdate(h->bgraph, g, &ui) != cudaSuccess) {
@@ -2296,6 +2309,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
         h->bgraph = nullptr;
       }
     }
+    h->bgraph_key = key;
     if (!h->bgraph) {
       const cudaError_t e = cudaGraphInstantiate(&h->bgraph, g, 0);
       cudaGraphDestroy(g);

@@ -137,6 +137,20 @@ def test_batch_autotuner_keeps_the_result(pk):
         close_rel(b2["x"], c["x"], 1e-10)
 
 
+def test_batch_team_sizes_on_one_handle(pk):
+    """Solves of one handle with different team sizes (each a CUDA graph of its own
+    launch configuration) and back: every solve runs its iterations and gives the same
+    point up to summation order."""
+    lps = fixed_iteration_batch()[:6]
+    with pk.BatchSolver.from_lps(lps) as b:
+        runs = [b.solve(tol=0.0, max_iter=300, cluster_ctas=t) for t in (1, 2, 4, 2, 1)]
+    for r in runs:
+        assert all(x["iters"] == 300 for x in r)
+        for a, c in zip(r, runs[0]):
+            close_rel(a["x"], c["x"], 1e-10)
+            close_rel(a["y"], c["y"], 1e-10)
+
+
 def test_batch_ragged_iteration_limit_and_zero(pk):
     lps = fixed_iteration_batch()[:4]
     with pk.BatchSolver.from_lps(lps) as b:
