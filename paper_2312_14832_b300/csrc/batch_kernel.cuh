@@ -284,6 +284,87 @@ __device__ __forceinline__ void batch_rows_p(const int32_t* __restrict__ cptr, c
   }
 }
 
+// batch_rows_p for short chunks (a few slots each, such as K' of a transportation LP,
+// two entries per column): a warp takes kG consecutive chunks at once, loads the slots
+// of all of them two at a time, then gathers, then adds each row's products in slot
+// order (the per-row order of batch_rows_p, so the sums are bit-identical), and
+// finishes the kG rows' epilogues.  This keeps kG times more loads in flight per warp and
+// drops the predicated-off lanes of an 8-slot batch on a 2-slot chunk.
+constexpr int kGrp = 4;
+template <int SRC, class Pre, class F>
+__device__ __forceinline__ void batch_rows_pg(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
+                                              const double* __restrict__ val, int c0, int c1, int cbase,
+                                              int64_t base, const double* gsrc, const BatchArgs& A, Pre pre, F epi) {
+  extern __shared__ double bsm[];
+  constexpr int kB = 2;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* xs = bsm + A.xs_off;
+  const double* ys = bsm + A.ys_off;
+  using PV = decltype(pre(0));
+  for (int ch0 = c0 + wid * kGrp; ch0 < c1; ch0 += nw * kGrp) {
+    int s[kGrp], len[kGrp];
+    PV pv[kGrp];
+    double acc[kGrp];
+    int lmax = 0;
+#pragma unroll
+    for (int g = 0; g < kGrp; ++g) {
+      const int ch = ch0 + g;
+      s[g] = 0;
+      len[g] = 0;
+      acc[g] = 0.0;
+      if (ch < c1) {
+        s[g] = cptr[ch];
+        len[g] = cptr[ch + 1] - s[g];
+        pv[g] = pre((ch - cbase) * 32 + lane);
+        lmax = max(lmax, len[g]);
+      }
+    }
+    if (PDLP_BATCH_L2PF && lane == 0) {
+      const int n0 = ch0 + nw * kGrp;
+      if (n0 < c1) {
+        const int n1 = min(n0 + kGrp, c1);
+        const int a = cptr[n0], b = cptr[n1];
+        if (b > a) {
+          const uint32_t ns = (uint32_t)min(b - a, kPfSlots);
+          l2_prefetch(val + (size_t)a * 32, ns * 256u);
+          l2_prefetch(col + (size_t)a * 32, ns * 128u);
+        }
+      }
+    }
+    for (int k = 0; k < lmax; k += kB) {
+      double v[kGrp][kB], xv[kGrp][kB];
+      int ci[kGrp][kB];
+#pragma unroll
+      for (int g = 0; g < kGrp; ++g)
+#pragma unroll
+        for (int j = 0; j < kB; ++j)
+          if (k + j < len[g]) {
+            v[g][j] = __ldcs(val + (size_t)(s[g] + k + j) * 32 + lane);
+            ci[g][j] = __ldcs(col + (size_t)(s[g] + k + j) * 32 + lane) - (int)base;
+          }
+#pragma unroll
+      for (int g = 0; g < kGrp; ++g)
+#pragma unroll
+        for (int j = 0; j < kB; ++j) {
+          xv[g][j] = 0.0;
+          if (k + j < len[g]) {
+            if (SRC == kSrcSmemX) xv[g][j] = xs[ci[g][j]];
+            else if (SRC == kSrcSmemY) xv[g][j] = ys[ci[g][j]];
+            else xv[g][j] = __ldcg(gsrc + ci[g][j]);
+          }
+        }
+#pragma unroll
+      for (int g = 0; g < kGrp; ++g)
+#pragma unroll
+        for (int j = 0; j < kB; ++j)
+          if (k + j < len[g]) acc[g] = fma(v[g][j], xv[g][j], acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < kGrp; ++g)
+      if (ch0 + g < c1) epi((ch0 + g - cbase) * 32 + lane, acc[g], pv[g]);
+  }
+}
+
 // Rows of this CTA's resident slice of a SELL matrix (shared memory): chunk ch spans
 // elements [cp[ch], cp[ch + 1]) of val / goff (32 per slot, lane = row), goff holds
 // the byte offset of each entry's gathered element within src.  Same summation order
@@ -717,6 +798,10 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   }
 
   // ---- iterations (Section 2: primal step, dual step with extrapolation) and checks
+  // short chunks (at most 4 slots on average over this CTA's range) go through the
+  // grouped row loop (global iterates only)
+  const bool short_t = kGlob && (A.t_cptr[tr1] - A.t_cptr[tr0]) <= 4 * (tr1 - tr0);
+  const bool short_k = kGlob && (A.k_cptr[kr1] - A.k_cptr[kr0]) <= 4 * (kr1 - kr0);
   long long k = S.k, t = S.t;
   const long long k_start = k;
   int until_check = A.check_every;
@@ -738,7 +823,10 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       if constexpr (kRes)
         Tmul(true, nullptr, [&](int j, double gsum) { epi_p(j, gsum, pre_p(j)); });
       else if constexpr (kGlob)
-        batch_rows_p<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
+        if (short_t)
+          batch_rows_pg<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
+        else
+          batch_rows_p<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
       else
         batch_rows_p<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A, pre_p, epi_p);
       T.sync();
@@ -759,7 +847,10 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
       if constexpr (kRes)
         Kmul(true, nullptr, [&](int i, double v) { epi_d(i, v, pre_d(i)); });
       else if constexpr (kGlob)
-        batch_rows_p<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
+        if (short_k)
+          batch_rows_pg<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
+        else
+          batch_rows_p<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
       else
         batch_rows_p<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A, pre_d, epi_d);
       T.sync();

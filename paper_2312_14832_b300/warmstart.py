@@ -108,9 +108,10 @@ def evaluate(model, lps, P, tols=(1e-4, 1e-8), budget=None, **params):
     predict_s = time.perf_counter() - t0
     out = {"predict_wall_s": predict_s}
     with BatchSolver.from_lps(lps, **params) as b:
-        # an untimed cold solve lets the batched solver's online autotuner choose its
-        # launch configuration, so that both timed paths run with the same one
-        b.solve(tol=max(tols), want_points=False)
+        # an untimed cold run of 640 iterations (the autotuner's first slice and up to
+        # eight timed ones) lets the batched solver choose its launch configuration, so
+        # that both timed paths run with the same one
+        b.solve(tol=0.0, max_iter=640, want_points=False)
         c0 = b.solve(tol=0.0, max_iter=0, want_points=False)
         p0 = b.solve(tol=0.0, max_iter=0, want_points=False, x0=list(x0), y0=list(y0), omega0=w0)
         judge_s = (c0[0]["device_ms"] + p0[0]["device_ms"]) * 1e-3
