@@ -493,14 +493,9 @@ def bench_mcf(args):
         out["mixed_vs_fp64"][f"rel_obj_diff_at_{args.mcf_tol_hi:g}"] = (
             abs(out["fp64_hi_obj"] - out["mixed_hi_obj"]) / abs(out["fp64_hi_obj"]))
         del out["fp64_hi_obj"], out["mixed_hi_obj"]
-    import oracle
-    x, y, k, t0 = np.zeros(lp["n"]), np.zeros(lp["m"]), 0, time.perf_counter()
-    while time.perf_counter() - t0 < args.cpu_seconds:
-        x, y = oracle.pdhg_step(lp, x, y, 1e-3, 1.0)
-        k += 1
-    el = time.perf_counter() - t0
-    out["cpu_baseline"] = {"value": k / el, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle",
-                           "sample": f"{k} oracle PDHG steps (FP64) on the same LP, {el:.1f} s"}
+    base = cpu_baseline(lp, seconds=args.cpu_seconds)
+    base["sample"] = base["sample"].replace("full workload", "same LP (FP64)")
+    out["cpu_baseline"] = base
     out["value"] = out["mixed"]["iter_per_s"]
     out["dtype"] = "f32 iterations / f64 checks"
     print(json.dumps(out))
