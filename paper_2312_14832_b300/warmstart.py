@@ -38,21 +38,25 @@ def _init_params(n_in, hidden, n_out, seed):
 
 
 def solve_family(lps, tol, chunk=4096, **params):
-    """Solves LPs with the batched solver, `chunk` per launch.  Returns x (N x n),
-    y (N x m), omega (N,), iterations (N,), status (N,) and the device seconds."""
-    xs, ys, ws, its, sts, dev = [], [], [], [], [], 0.0
-    for s in range(0, len(lps), chunk):
+    """Solves LPs of one family (all of the same sizes) with the batched solver, `chunk`
+    per launch.  Returns x (N x n) and y (N x m) as float32 training targets, omega (N,),
+    iterations (N,), status (N,) and the device seconds."""
+    N = len(lps)
+    X = np.empty((N, lps[0]["n"]), dtype=np.float32)
+    Y = np.empty((N, lps[0]["m"]), dtype=np.float32)
+    ws, its, sts, dev = [], [], [], 0.0
+    for s in range(0, N, chunk):
         part = lps[s:s + chunk]
         with BatchSolver.from_lps(part, **params) as b:
             res = b.solve(tol=tol)
         dev += res[0]["device_ms"] * 1e-3
-        for r in res:
-            xs.append(r["x"])
-            ys.append(r["y"])
+        for i, r in enumerate(res):
+            X[s + i] = r["x"]
+            Y[s + i] = r["y"]
             ws.append(r["omega"])
             its.append(r["iters"])
             sts.append(r["status"])
-    return (np.array(xs), np.array(ys), np.array(ws), np.array(its), np.array(sts), dev)
+    return (X, Y, np.array(ws), np.array(its), np.array(sts), dev)
 
 
 class WarmStart:
@@ -62,14 +66,33 @@ class WarmStart:
         self.net.set_params(_init_params(n_params, hidden, n + m + 1, seed))
         self.max_batch = max_batch
 
-    def _targets(self, X, Y, W):
-        return np.concatenate([X, Y, np.log(np.maximum(W, 1e-300))[:, None]], axis=1)
+    def _targets(self, X, Y, W, a, b):
+        """Rows a..b of the targets (x, y, log omega) in float64."""
+        return np.concatenate([np.asarray(X[a:b], np.float64), np.asarray(Y[a:b], np.float64),
+                               np.log(np.maximum(W[a:b], 1e-300))[:, None]], axis=1)
 
-    def fit(self, P, X, Y, W, epochs=30, batch=256, lr=1e-3, weight_decay=0.0, seed=0):
-        T = self._targets(X, Y, W)
+    def fit(self, P, X, Y, W, epochs=30, batch=256, lr=1e-3, weight_decay=0.0, seed=0, block=2048):
+        """Standardises parameters and targets with the training set's column means and
+        standard deviations (two float64 passes over blocks of `block` rows, so that no
+        float64 copy of the whole target matrix is made), then trains."""
+        N = len(W)
         self.p_mu, self.p_sd = P.mean(0), np.maximum(P.std(0), 1e-6)
-        self.t_mu, self.t_sd = T.mean(0), np.maximum(T.std(0), 1e-6)
-        self.net.load_data((P - self.p_mu) / self.p_sd, (T - self.t_mu) / self.t_sd)
+        cols = self.n + self.m + 1
+        s1 = np.zeros(cols)
+        for a in range(0, N, block):
+            s1 += self._targets(X, Y, W, a, min(a + block, N)).sum(0)
+        self.t_mu = s1 / N
+        s2 = np.zeros(cols)
+        for a in range(0, N, block):
+            d = self._targets(X, Y, W, a, min(a + block, N)) - self.t_mu
+            s2 += (d * d).sum(0)
+        self.t_sd = np.maximum(np.sqrt(s2 / N), 1e-6)
+        Tn = np.empty((N, cols), dtype=np.float32)
+        for a in range(0, N, block):
+            b = min(a + block, N)
+            Tn[a:b] = (self._targets(X, Y, W, a, b) - self.t_mu) / self.t_sd
+        self.net.load_data(((P - self.p_mu) / self.p_sd).astype(np.float32), Tn)
+        del Tn
         t0 = time.perf_counter()
         losses, ms = self.net.train(epochs, min(batch, self.max_batch), lr, weight_decay, seed)
         return dict(losses=losses, train_device_s=ms * 1e-3, train_wall_s=time.perf_counter() - t0)
