@@ -132,7 +132,11 @@ __device__ __forceinline__ int split_point(const int32_t* __restrict__ cptr, int
 }
 
 // Gather source of a batched SpMV: the shared-memory x or y, or a global vector.
-enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal };
+// Where a product gathers its vector from: the shared-memory replicas of x or y, a global
+// vector read through L2 only (ld.global.cg: a team's other CTAs write it), or a global
+// vector read through L1 as well (one CTA per LP: only this CTA writes the vector, and
+// __syncthreads makes its own writes visible to its later loads).
+enum BatchSrc { kSrcSmemX, kSrcSmemY, kSrcGlobal, kSrcGlobalL1 };
 
 // Rows in chunks [c0, c1) of a SELL matrix (in global memory, or a slice staged in
 // shared memory: kMatS); warp w of the CTA takes chunks c0+w,
@@ -213,6 +217,7 @@ __device__ __forceinline__ void batch_rows(const int32_t* __restrict__ cptr, con
         if (j < nb) {
           if (SRC == kSrcSmemX) xv[j] = xs[ci[j]];
           else if (SRC == kSrcSmemY) xv[j] = ys[ci[j]];
+          else if (SRC == kSrcGlobalL1) xv[j] = gsrc[ci[j]];
           else xv[j] = __ldcg(gsrc + ci[j]);
         }
       }
@@ -271,6 +276,7 @@ __device__ __forceinline__ void batch_rows_p(const int32_t* __restrict__ cptr, c
         if (j < nb) {
           if (SRC == kSrcSmemX) xv[j] = xs[ci[j]];
           else if (SRC == kSrcSmemY) xv[j] = ys[ci[j]];
+          else if (SRC == kSrcGlobalL1) xv[j] = gsrc[ci[j]];
           else xv[j] = __ldcg(gsrc + ci[j]);
         }
       }
@@ -350,6 +356,7 @@ __device__ __forceinline__ void batch_rows_pg(const int32_t* __restrict__ cptr, 
           if (k + j < len[g]) {
             if (SRC == kSrcSmemX) xv[g][j] = xs[ci[g][j]];
             else if (SRC == kSrcSmemY) xv[g][j] = ys[ci[g][j]];
+            else if (SRC == kSrcGlobalL1) xv[g][j] = gsrc[ci[g][j]];
             else xv[g][j] = __ldcg(gsrc + ci[g][j]);
           }
         }
@@ -802,6 +809,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
   // grouped row loop (global iterates only)
   const bool short_t = kGlob && (A.t_cptr[tr1] - A.t_cptr[tr0]) <= 4 * (tr1 - tr0);
   const bool short_k = kGlob && (A.k_cptr[kr1] - A.k_cptr[kr0]) <= 4 * (kr1 - kr0);
+  // the iterations' gathers from global iterates: through L1 when this CTA is the LP's
+  // only writer
+  constexpr int kGSrc = kCl ? kSrcGlobal : kSrcGlobalL1;
   long long k = S.k, t = S.t;
   const long long k_start = k;
   int until_check = A.check_every;
@@ -824,9 +834,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
         Tmul(true, nullptr, [&](int j, double gsum) { epi_p(j, gsum, pre_p(j)); });
       else if constexpr (kGlob)
         if (short_t)
-          batch_rows_pg<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
+          batch_rows_pg<kGSrc>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
         else
-          batch_rows_p<kSrcGlobal>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
+          batch_rows_p<kGSrc>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, ys, A, pre_p, epi_p);
       else
         batch_rows_p<kSrcSmemY>(A.t_cptr, A.t_col, A.t_val, tr0, tr1, D.tc0, D.r0, nullptr, A, pre_p, epi_p);
       T.sync();
@@ -848,9 +858,9 @@ __device__ void batch_solve_one(const BatchArgs& A, int b, const Team<kCl>& T) {
         Kmul(true, nullptr, [&](int i, double v) { epi_d(i, v, pre_d(i)); });
       else if constexpr (kGlob)
         if (short_k)
-          batch_rows_pg<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
+          batch_rows_pg<kGSrc>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
         else
-          batch_rows_p<kSrcGlobal>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
+          batch_rows_p<kGSrc>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, xs, A, pre_d, epi_d);
       else
         batch_rows_p<kSrcSmemX>(A.k_cptr, A.k_col, A.k_val, kr0, kr1, D.kc0, D.c0, nullptr, A, pre_d, epi_d);
       T.sync();
