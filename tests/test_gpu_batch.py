@@ -81,10 +81,10 @@ def test_batch_iterates_after_1000(pk, scaling):
             assert r["restarts"] == ref["restarts"]
             assert r["which"] == ref["which"]
         assert abs(r["eta"] - ref["eta"]) <= 1e-12 * ref["eta"]
-        # omega is a function of ||x_c - x_anchor|| between nearly equal iterates, whose
-        # relative rounding grows as the iterates settle; the iterates themselves are
-        # held to 1e-10 below
-        assert abs(r["omega"] - ref["omega"]) <= 1e-6 * ref["omega"]
+        # omega is a function of ||x_c - x_anchor|| between nearly equal iterates: held to
+        # 1e-9 while the run stays above the rounding floor, to 1e-6 for an LP whose later
+        # restarts are decided on noise; the iterates themselves are held to 1e-10 below
+        assert abs(r["omega"] - ref["omega"]) <= (1e-9 if whole else 1e-6) * ref["omega"]
         close_rel(r["x"], ref["x"], 1e-10)
         close_rel(r["y"], ref["y"], 1e-10)
 
