@@ -381,6 +381,15 @@ int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, 
 int pdlp_tc_gemm_split(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
                        int32_t relu, int32_t splits, float* workspace, void* stream);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): one 128 x 128 x 64
+ * tile of pdlp_tc_gemm's kernel (A: 128 x 64 and B: 128 x 64 BF16, C: 128 x 128 FP32,
+ * device arrays) with its operand copies withheld, so the MMA thread's first mbarrier
+ * wait can only give up after spin_limit polls (>= 1).  The kernel then records the
+ * failure, frees its tensor memory and returns; nothing faults and the context stays
+ * usable.  Returns PDLP_ETIMEOUT when the wait gave up (the expected outcome), PDLP_OK
+ * if it did not, PDLP_EINVAL / PDLP_ECUDA otherwise.  C is not written. */
+int pdlp_tc_gemm_wait_selftest(const void* A, const void* B, float* C, int64_t spin_limit, void* stream);
+
 /* ---------------------------------------------------------------- warm-start network
  * A 3-layer MLP for learned warm starts (an extension; the paper has no
  * learned component):  Y = relu(relu(X W1' + b1) W2' + b2) W3' + b3,

@@ -82,6 +82,7 @@ SIGNATURES = {
     "pdlp_batch_get_restarts": (C.c_int64, [_vp, _i64, _vp, _i64]),
     "pdlp_tc_gemm": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
     "pdlp_tc_gemm_split": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "pdlp_tc_gemm_wait_selftest": (C.c_int, [_vp, _vp, _vp, _i64, _vp]),
     "pdlp_mlp_create": (C.c_int, [C.POINTER(_vp), _i32, _i32, _i32, _i32]),
     "pdlp_mlp_free": (None, [_vp]),
     "pdlp_mlp_last_error": (C.c_char_p, [_vp]),

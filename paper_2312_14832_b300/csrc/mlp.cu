@@ -81,7 +81,7 @@ int tc_gemm_splits(int M, int N, int K, int max_splits) {
 // (1: no split; > 1: part holds splits x M x N floats).  Returns a CUDA error code.
 cudaError_t tc_gemm_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, __nv_bfloat16* Cb,
                            const float* bias, int M, int N, int K, int relu, int splits, float* part, int* err,
-                           cudaStream_t s) {
+                           cudaStream_t s, long long spin = kSpinLimit, int withhold = 0) {
   cudaError_t e = tc_gemm_attrs();
   if (e != cudaSuccess) return e;
   CUtensorMap ta, tb;
@@ -92,7 +92,7 @@ cudaError_t tc_gemm_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, float
   if (splits < 1 || !part) splits = 1;
   const int kps = (kt + splits - 1) / splits;
   splits = (kt + kps - 1) / kps;
-  TcGemmArgs g{C, Cb, bias, splits > 1 ? part : nullptr, M, N, K, kps, relu, err};
+  TcGemmArgs g{C, Cb, bias, splits > 1 ? part : nullptr, M, N, K, kps, relu, err, spin, withhold};
   dim3 grid(N / kTcTile, M / kTcTile, splits);
   k_tc_gemm<<<grid, 128, kTmSmemBytes, s>>>(ta, tb, g);
   e = cudaGetLastError();
@@ -123,7 +123,8 @@ static int* tc_err_flag() {
 }
 
 static int tc_gemm_entry(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, const float* bias,
-                         int32_t relu, int32_t splits, float* workspace, void* stream, const char* name) {
+                         int32_t relu, int32_t splits, float* workspace, void* stream, const char* name,
+                         long long spin = kSpinLimit, int withhold = 0) {
   if (M <= 0 || N <= 0 || K <= 0 || M % kTcTile || N % kTcTile || K % kTcK) {
     set_thread_error(std::string(name) + ": M, N must be positive multiples of 128 and K of 64");
     return PDLP_EINVAL;
@@ -146,7 +147,7 @@ static int tc_gemm_entry(int32_t M, int32_t N, int32_t K, const void* A, const v
   cudaError_t e = cudaMemcpyAsync(err, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = tc_gemm_launch(static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), C, nullptr, bias,
-                       M, N, K, relu, splits, workspace, err, s);
+                       M, N, K, relu, splits, workspace, err, s, spin, withhold);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -165,6 +166,15 @@ static int tc_gemm_entry(int32_t M, int32_t N, int32_t K, const void* A, const v
 extern "C" int pdlp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C,
                             const float* bias, int32_t relu, void* stream) {
   return pdlp::tc_gemm_entry(M, N, K, A, B, C, bias, relu, 1, nullptr, stream, "pdlp_tc_gemm");
+}
+
+extern "C" int pdlp_tc_gemm_wait_selftest(const void* A, const void* B, float* C, int64_t spin_limit, void* stream) {
+  if (spin_limit < 1) {
+    pdlp::set_thread_error("pdlp_tc_gemm_wait_selftest: spin_limit must be >= 1");
+    return PDLP_EINVAL;
+  }
+  return pdlp::tc_gemm_entry(128, 128, 64, A, B, C, nullptr, 0, 1, nullptr, stream, "pdlp_tc_gemm_wait_selftest",
+                             spin_limit, 1);
 }
 
 extern "C" int pdlp_tc_gemm_split(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* C,

@@ -65,10 +65,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Waits for completion `parity` of the barrier; false after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for completion `parity` of the barrier; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (long long i = 0; i < kSpinLimit; ++i) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -89,6 +89,9 @@ struct TcGemmArgs {
   int ktiles;               // 64-wide steps of K per CTA (blockIdx.z takes steps z * ktiles ...)
   int relu;
   int* err;
+  long long spin;           // poll limit of every mbarrier wait (kSpinLimit)
+  int withhold;             // self-test of the bounded waits: issue no copy, so the first
+                            // wait of the MMA thread can only give up
 };
 
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
@@ -133,9 +136,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   if (threadIdx.x == 0) {
     // producer: stage s = i % kTmStages; use i of a stage waits for the MMAs of use i - kTmStages
     int i = 0;
-    for (; i < nk; ++i) {
+    for (; i < nk && !g.withhold; ++i) {
       const int s = i % kTmStages;
-      if (i >= kTmStages && !mbar_wait(&empty[s], (uint32_t)(((i / kTmStages) - 1) & 1))) {
+      if (i >= kTmStages && !mbar_wait(&empty[s], (uint32_t)(((i / kTmStages) - 1) & 1), g.spin)) {
         *vfailed = 1;
         break;
       }
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     int i = 0;
     for (; i < nk; ++i) {
       const int s = i % kTmStages;
-      if (!mbar_wait(&full[s], (uint32_t)((i / kTmStages) & 1))) {
+      if (!mbar_wait(&full[s], (uint32_t)((i / kTmStages) & 1), g.spin)) {
         *vfailed = 1;
         break;
       }
@@ -193,11 +196,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   __syncthreads();
   const int consumed = consumed_sh, issued = issued_sh;
   bool ok = !*vfailed && consumed == nk && nk > 0;
-  if (consumed > 0 && !mbar_wait(&done, 0)) ok = false;
+  if (consumed > 0 && !mbar_wait(&done, 0, g.spin)) ok = false;
   if (!ok && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     // no copy may land after the CTA has left: wait (bounded) for the unconsumed ones
-    for (int i = consumed; i < issued; ++i) mbar_wait(&full[i % kTmStages], (uint32_t)((i / kTmStages) & 1));
+    for (int i = consumed; i < issued; ++i)
+      mbar_wait(&full[i % kTmStages], (uint32_t)((i / kTmStages) & 1), g.spin);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {

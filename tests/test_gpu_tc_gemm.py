@@ -107,3 +107,23 @@ def test_tc_gemm_rejects_bad_shapes(env):
     lib, torch = env
     assert lib.pdlp_tc_gemm(100, 128, 64, None, None, None, None, 0, None) == -1
     assert lib.pdlp_tc_gemm(128, 128, 48, None, None, None, None, 0, None) == -1
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(env):
+    """The MMA thread's first mbarrier wait with every operand copy withheld: it gives up
+    after the poll limit, the call returns PDLP_ETIMEOUT (-4) without writing C, the kernel
+    frees its tensor memory, and the next GEMM on the same context is correct."""
+    lib, torch = env
+    A, B, bias = _operands(torch, 128, 128, 64, seed=11)
+    dA, dB = A.cuda(), B.cuda()
+    out = torch.full((128, 128), -7.0, device="cuda")
+    assert lib.pdlp_tc_gemm_wait_selftest(dA.data_ptr(), dB.data_ptr(), out.data_ptr(), 0, None) == -1
+    rc = lib.pdlp_tc_gemm_wait_selftest(dA.data_ptr(), dB.data_ptr(), out.data_ptr(), 2000, None)
+    assert rc == -4, lib.pdlp_last_error(None)
+    assert b"gave up" in lib.pdlp_last_error(None)
+    assert torch.all(out == -7.0)
+    torch.cuda.synchronize()
+    rc = lib.pdlp_tc_gemm(128, 128, 64, dA.data_ptr(), dB.data_ptr(), out.data_ptr(), None, 0, None)
+    assert rc == 0, lib.pdlp_last_error(None)
+    ref, scale = _reference(A, B, torch.zeros(128), False)
+    assert np.all(np.abs(out.cpu().double().numpy() - ref) <= 1e-5 * scale + 1e-30)
