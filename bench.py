@@ -431,7 +431,9 @@ def bench_mcf(args):
     """Mixed precision on the multicommodity-flow LP (lpgen.mcf: 8 commodities, 2e5 nodes,
     1e6 arcs, n = 8e6, m = 2.6e6, nnz = 2.4e7, Ruiz + Pock-Chambolle scaling): PDHG
     iterations/s and time to 1e-4 for FP64 and for MIXED (FP32 iterations, FP64
-    checks and refinement), and the relative objective difference between the two."""
+    checks and refinement) with the +-1 entries stored as sign bits ("mixed", the
+    automatic choice) and as FP32 value copies ("mixed_values"), and the relative
+    objective difference between FP64 and MIXED."""
     import torch
     import lpgen
     import paper_2312_14832_b300 as pk
@@ -445,8 +447,16 @@ def bench_mcf(args):
                                   "planted feasible flow; Ruiz(10)+Pock-Chambolle scaling",
                       "check_every": CHECK_EVERY}}
     iters = args.steps * CHECK_EVERY
-    for name, prec in (("fp64", pk.FP64), ("mixed", pk.MIXED)):
-        s = pk.Solver.from_lp(lp, scaling=1, precision=prec, stream=stream.cuda_stream)
+    nnz, mn = lp["row_ptr"][-1], lp["m"] + lp["n"]
+    # unique bytes of one iteration's two products (values + indices, the vectors each
+    # step reads and writes, the gathered vector once): FP64 24 nnz + 68 (m + n); FP32
+    # value copies 16 nnz + 32 (m + n); sign bits 8 nnz + 36 (m + n) (D_c^2, D_r^2 read
+    # by the steps)
+    model = {0: 24.0 * nnz + 68.0 * mn, 1: 16.0 * nnz + 32.0 * mn, 2: 8.0 * nnz + 36.0 * mn}
+    variants = (("fp64", pk.FP64, {}), ("mixed", pk.MIXED, {}), ("mixed_values", pk.MIXED, {"mixed_values": 1}))
+    for name, prec, extra in variants:
+        s = pk.Solver.from_lp(lp, scaling=1, precision=prec, stream=stream.cuda_stream, **extra)
+        storage = s.info()["mixed_values"]
         s.solve(tol=0.0, max_iter=max(args.warmup, 1) * CHECK_EVERY, want_point=False,
                 mixed_switch_tol=1e-30)
         torch.cuda.synchronize()
@@ -461,6 +471,9 @@ def bench_mcf(args):
         rt = s.solve(tol=1e-4, time_limit_s=args.mcf_budget)
         status = ["optimal", "iter_limit", "time_limit", "numerical"]
         out[name] = {"iter_per_s": iters / (ms * 1e-3), "ms_primal": mp, "ms_dual": md,
+                     "fp32_storage": ["none (fp64)", "fp32 value copies", "sign bits"][storage],
+                     "bytes_per_iter_model": model[storage],
+                     "kernels_gbs": model[storage] / ((mp + md) * 1e-3) / 1e9,
                      "fp32_iters_in_timed": r["fp32_iters"],
                      "time_to_1e-4": {"status": status[rt["status"]],
                                       "iters": rt["iters"], "fp32_iters": rt["fp32_iters"],
@@ -468,7 +481,7 @@ def bench_mcf(args):
                                       "rel_primal": rt["rel_primal"], "rel_dual": rt["rel_dual"],
                                       "rel_gap": rt["rel_gap"]}}
         out[name + "_x"] = rt["x"]
-        if args.mcf_tol_hi > 0:
+        if args.mcf_tol_hi > 0 and name != "mixed_values":
             # high accuracy: in MIXED the FP32 phase hands over to FP64 refinement; the
             # returned point's three relative tests re-evaluated by the FP64 oracle
             import oracle
@@ -488,7 +501,14 @@ def bench_mcf(args):
                             "rel_obj_diff": abs(a["primal_obj"] - b["primal_obj"]) / abs(a["primal_obj"]),
                             "rel_x_diff": float(np.linalg.norm(out["fp64_x"] - out["mixed_x"]) /
                                                 np.linalg.norm(out["fp64_x"]))}
-    del out["fp64_x"], out["mixed_x"]
+    c = out["mixed_values"]
+    out["sign_bits_vs_value_copies"] = {
+        "iter_speedup": out["mixed"]["iter_per_s"] / c["iter_per_s"],
+        "kernel_speedup": (c["ms_primal"] + c["ms_dual"]) / (out["mixed"]["ms_primal"] + out["mixed"]["ms_dual"]),
+        "time_to_1e-4_speedup": c["time_to_1e-4"]["device_s"] / max(b["device_s"], 1e-9),
+        "rel_x_diff": float(np.linalg.norm(out["mixed_values_x"] - out["mixed_x"]) /
+                            np.linalg.norm(out["mixed_values_x"]))}
+    del out["fp64_x"], out["mixed_x"], out["mixed_values_x"]
     if args.mcf_tol_hi > 0:
         out["mixed_vs_fp64"][f"rel_obj_diff_at_{args.mcf_tol_hi:g}"] = (
             abs(out["fp64_hi_obj"] - out["mixed_hi_obj"]) / abs(out["fp64_hi_obj"]))

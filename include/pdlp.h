@@ -169,6 +169,17 @@ typedef struct {
                               summation order.  An FP64 one-stage solve that keeps a choice
                               (or has fixed ones) runs its persistent launch as a CUDA
                               graph.                                                     */
+  int32_t mixed_values;    /* PDLP_MIXED, single-LP handles: how the FP32 products read K.
+                              0 = automatic: when every entry of the caller's K is +1, -1
+                              (or 0), no values are stored for them: each column index
+                              carries the entry's sign in its top bit, and the FP32
+                              iterations run in the unscaled variables (D_c x, D_r y for
+                              K = D_r K0 D_c), where the scaling is a per-row factor
+                              D_c^2 (D_r^2) of the step; otherwise FP32 copies of the
+                              scaled values.  1 = FP32 value copies always.  2 = sign bits
+                              (PDLP_EINVAL when an entry is not +1, -1 or 0).  The FP64
+                              checks and the FP64 refinement use the FP64 values in every
+                              case.                                                      */
 } pdlp_params;
 
 typedef struct {
@@ -235,6 +246,8 @@ typedef struct {
   int32_t tune_resident[8];    /*   placement (1 streamed, 2 resident slices, 3 global)    */
   double tune_gbs[8];          /*   score: stored bytes of the iterations run per second,
                                     in GB/s                                                */
+  int32_t mixed_values;        /* how the FP32 products read K: 0 FP64 handle (no FP32
+                                  products), 1 FP32 value copies, 2 sign bits (pdlp_params) */
 } pdlp_info;
 
 /* Fills p with the defaults listed above. */

@@ -23,7 +23,7 @@ class Params(C.Structure):
                 ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32),
                 ("step_rule", C.c_int32), ("engine", C.c_int32), ("batch_tail_iters", C.c_int64),
                 ("host_layout", C.c_int32), ("spmv_stage", C.c_int32),
-                ("batch_tune", C.c_int32)]
+                ("batch_tune", C.c_int32), ("mixed_values", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -56,7 +56,8 @@ class Info(C.Structure):
                 ("setup_validate_ms", C.c_double), ("setup_layout_ms", C.c_double),
                 ("setup_device_ms", C.c_double), ("setup_tune_ms", C.c_double), ("setup_step_ms", C.c_double),
                 ("spmv_stage_K", C.c_int32), ("spmv_stage_Kt", C.c_int32), ("batch_tuned", C.c_int32),
-                ("tune_team", C.c_int32 * 8), ("tune_resident", C.c_int32 * 8), ("tune_gbs", C.c_double * 8)]
+                ("tune_team", C.c_int32 * 8), ("tune_resident", C.c_int32 * 8), ("tune_gbs", C.c_double * 8),
+                ("mixed_values", C.c_int32)]
 
 
 # every function declared in include/pdlp.h: name -> (restype, argtypes)

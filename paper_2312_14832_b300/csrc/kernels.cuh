@@ -13,6 +13,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "layout.h"
 
 namespace pdlp {
@@ -111,6 +113,10 @@ struct SellView {
   int32_t nchunks;
   double* gpart;   // ntasks * 32 partial sums of split-chunk pieces
   int32_t* cnt;    // arrival counters (index: first piece task), zero between launches
+  // K with entries +-1 only (mixed precision): per slot, the column index in bits 0..30
+  // and the sign of the entry in bit 31; padding slots hold the index of an entry of the
+  // gathered vector that stays zero.  Null otherwise.
+  const int32_t* __restrict__ ucol;
 };
 
 // Row-sum operations: SpMV (gathered), and the infinity / 1-norms used by scaling.
@@ -138,6 +144,11 @@ struct OpSpmvF {
   static constexpr bool kGather = true;
   __device__ static float step(float acc, float v, float x) { return fmaf(v, x, acc); }
 };
+// FP32 row sums of the unscaled signs of a K whose entries are all +-1 (SellView::ucol):
+// sum_j s_ij x_j, with x_j taken with its sign flipped where s_ij = -1 (exact).
+struct OpUnitF {
+  static constexpr bool kGather = true;
+};
 
 // Combination of split-chunk partial sums (kept in FP64 for every value type).
 template <class Op> __device__ __forceinline__ double join_of(double a, double b) { return a + b; }
@@ -147,11 +158,40 @@ template <class T> __device__ __forceinline__ const T* sell_values(const SellVie
 template <> __device__ __forceinline__ const double* sell_values<double>(const SellView& A) { return A.val; }
 template <> __device__ __forceinline__ const float* sell_values<float>(const SellView& A) { return A.val32; }
 
+// OpUnitF's sum of slots [s, e) of one chunk for this lane's row: only the 4-byte
+// column words are streamed; the batching is chunk_sum's.
+template <int kBatch>
+__device__ __forceinline__ float chunk_sum_unit(const SellView& A, const float* __restrict__ xg, int s, int e,
+                                                int lane) {
+  const int32_t* cp = A.ucol + (size_t)s * 32 + lane;
+  float acc = 0.0f;
+  for (int k = s; k < e; k += kBatch) {
+    const int nb = min(kBatch, e - k);
+    uint32_t w[kBatch];
+    float xv[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      w[j] = 0u;
+      if (j < nb) w[j] = (uint32_t)__ldcs(cp + 32 * j);
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      xv[j] = 0.0f;
+      if (j < nb) xv[j] = __ldg(xg + (w[j] & 0x7fffffffu));
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+      if (j < nb) acc += __uint_as_float(__float_as_uint(xv[j]) ^ (w[j] & 0x80000000u));
+    cp += 32 * kBatch;
+  }
+  return acc;
+}
+
 // Sum of slots [s, e) of one chunk for this lane's row.  Loads of a batch of up to
 // kBatch slots are issued before any of its FMAs; `nb` is warp-uniform, so the
 // guards do not diverge and no FP64 instruction is spent on a missing slot.
 template <class T, class Op, int kBatch>
-__device__ __forceinline__ T chunk_sum(const SellView& A, const T* __restrict__ xg, int s, int e, int lane) {
+__device__ __forceinline__ T chunk_sum_vals(const SellView& A, const T* __restrict__ xg, int s, int e, int lane) {
   const int32_t* cp = A.col + (size_t)s * 32 + lane;
   const T* vp = sell_values<T>(A) + (size_t)s * 32 + lane;
   T acc = T(0);
@@ -178,6 +218,14 @@ __device__ __forceinline__ T chunk_sum(const SellView& A, const T* __restrict__ 
     cp += 32 * kBatch;
   }
   return acc;
+}
+
+template <class T, class Op, int kBatch>
+__device__ __forceinline__ T chunk_sum(const SellView& A, const T* __restrict__ xg, int s, int e, int lane) {
+  if constexpr (std::is_same<Op, OpUnitF>::value)
+    return chunk_sum_unit<kBatch>(A, xg, s, e, lane);
+  else
+    return chunk_sum_vals<T, Op, kBatch>(A, xg, s, e, lane);
 }
 
 // A wide chunk's row sum: the lanes' partial sums combined by a fixed butterfly, the
@@ -536,35 +584,136 @@ struct EpiDual32 {
   __device__ void task_end(int, int) {}
 };
 
+// Mixed precision with the +-1 entries of K stored as sign bits (OpUnitF).  The FP32
+// iterations then run in the unscaled variables: for the scaled LP (K = D_r K0 D_c,
+// c = D_c c0, q = D_r q0, bounds l0 / D_c, u0 / D_c) and xu = D_c x, yu = D_r y, the
+// steps of Section 2 become
+//   xu <- proj_[l0,u0](xu - tau D_c^2 (c0 - K0' yu)),
+//   yu <- yu + sigma D_r^2 (q0 - 2 K0 xu_new + K0 xu_old), yu_i >= 0 for i >= m1,
+// so the products gather the iterates themselves and the scaling costs one per-row
+// factor (D_c^2, D_r^2) instead of a stored value per entry.  kxp holds K0 xu_old.
+struct EpiPrimal32U {
+  using T = float;
+  float* __restrict__ x;
+  float* __restrict__ sx;
+  const float* __restrict__ c;
+  const float* __restrict__ l;
+  const float* __restrict__ u;
+  const float* __restrict__ d2;   // D_c^2
+  float tau;
+  struct Pre { float xo, c, l, u, sx, d2; };
+  __device__ void prepare(const DevState* st) { tau = (float)st->tau; }
+  __device__ Pre load(int j) const { return Pre{x[j], c[j], l[j], u[j], sx[j], d2[j]}; }
+  __device__ void finish(int j, float g, const Pre& p) {
+    float xn = fmaf(-(tau * p.d2), p.c - g, p.xo);
+    xn = fminf(fmaxf(xn, p.l), p.u);
+    x[j] = xn;
+    sx[j] = p.sx + xn;
+  }
+  __device__ void task_end(int, int) {}
+};
+struct EpiDual32U {
+  using T = float;
+  float* __restrict__ y;
+  float* __restrict__ sy;
+  float* __restrict__ kxp;
+  const float* __restrict__ q;
+  const float* __restrict__ d2;   // D_r^2
+  int m1;
+  float sigma;
+  struct Pre { float q, kxp, y, sy, d2; };
+  __device__ void prepare(const DevState* st) { sigma = (float)st->sigma; }
+  __device__ Pre load(int i) const { return Pre{q[i], kxp[i], y[i], sy[i], d2[i]}; }
+  __device__ void finish(int i, float v, const Pre& p) {
+    float yn = fmaf(sigma * p.d2, fmaf(-2.0f, v, p.q + p.kxp), p.y);
+    if (i >= m1) yn = fmaxf(yn, 0.0f);
+    y[i] = yn;
+    sy[i] = p.sy + yn;
+    kxp[i] = v;
+  }
+  __device__ void task_end(int, int) {}
+};
+
+// FP32 problem data of the unscaled variables: c0 = c / D_c, l0 = l D_c, u0 = u D_c,
+// D_c^2 (columns, n entries) and q0 = q / D_r, D_r^2 (rows, m entries).
+__global__ void k_unit_vectors(float* c0, float* l0, float* u0, float* dc2, const double* c, const double* l,
+                               const double* u, const double* Dc, const double* invDc, int64_t n, float* q0,
+                               float* dr2, const double* q, const double* Dr, const double* invDr, int64_t m) {
+  const int64_t tot = n > m ? n : m;
+  PDLP_GRID_STRIDE(i, tot) {
+    if (i < n) {
+      c0[i] = (float)(c[i] * invDc[i]);
+      l0[i] = (float)(l[i] * Dc[i]);
+      u0[i] = (float)(u[i] * Dc[i]);
+      dc2[i] = (float)(Dc[i] * Dc[i]);
+    }
+    if (i < m) {
+      q0[i] = (float)(q[i] * invDr[i]);
+      dr2[i] = (float)(Dr[i] * Dr[i]);
+    }
+  }
+}
+
+// Entries of K (a layout's value array, padding included) that are neither 0 nor +-1.
+__global__ void k_count_nonunit(const double* val, int64_t n, unsigned long long* count) {
+  unsigned long long c = 0;
+  PDLP_GRID_STRIDE(i, n) {
+    const double v = val[i];
+    if (v != 0.0 && fabs(v) != 1.0) ++c;
+  }
+  if (c) atomicAdd(count, c);
+}
+// Sign-bit column words of a layout whose entries are all +-1 after positive scaling:
+// val[i] < 0 sets bit 31, a zero value (padding) points at index `zero`.
+__global__ void k_unit_cols(int32_t* ucol, const int32_t* col, const double* val, int64_t n, int32_t zero) {
+  PDLP_GRID_STRIDE(i, n) {
+    const double v = val[i];
+    ucol[i] = v == 0.0 ? zero : (v < 0.0 ? (int32_t)((uint32_t)col[i] | 0x80000000u) : col[i]);
+  }
+}
+
+// Scale factors between the FP32 iterates and the FP64 (scaled) ones: all null when
+// the FP32 iterates are the scaled ones; with sign-bit storage x = xu / D_c, y = yu / D_r
+// and K x = D_r (K0 xu).
+struct MixedScale {
+  const double* Dc;
+  const double* invDc;
+  const double* Dr;
+  const double* invDr;
+};
+
 // Check in mixed precision: FP64 copies of the FP32 iterates, interval sums folded
 // into the FP64 sums and cleared.
 __global__ void k_mixed_to64(double* x, double* sx, const float* x32, float* sx32, int64_t npad, double* y,
-                             double* sy, const float* y32, float* sy32, int64_t mpad, const DevState* st) {
+                             double* sy, const float* y32, float* sy32, int64_t mpad, const DevState* st,
+                             MixedScale ms) {
   if (st->done) return;
   const int64_t tot = npad > mpad ? npad : mpad;
   PDLP_GRID_STRIDE(i, tot) {
     if (i < npad) {
-      x[i] = (double)x32[i];
-      sx[i] += (double)sx32[i];
+      const double f = ms.invDc ? ms.invDc[i] : 1.0;
+      x[i] = (double)x32[i] * f;
+      sx[i] += (double)sx32[i] * f;
       sx32[i] = 0.0f;
     }
     if (i < mpad) {
-      y[i] = (double)y32[i];
-      sy[i] += (double)sy32[i];
+      const double f = ms.invDr ? ms.invDr[i] : 1.0;
+      y[i] = (double)y32[i] * f;
+      sy[i] += (double)sy32[i] * f;
       sy32[i] = 0.0f;
     }
   }
 }
 // After the check (and a restart, if one happened): FP32 iterates from the FP64 ones.
 __global__ void k_mixed_to32(float* x32, const double* x, int64_t npad, float* y32, const double* y,
-                             float* kxp32, const double* kxp, int64_t mpad, const DevState* st) {
+                             float* kxp32, const double* kxp, int64_t mpad, const DevState* st, MixedScale ms) {
   if (st->done) return;
   const int64_t tot = npad > mpad ? npad : mpad;
   PDLP_GRID_STRIDE(i, tot) {
-    if (i < npad) x32[i] = (float)x[i];
+    if (i < npad) x32[i] = (float)(ms.Dc ? x[i] * ms.Dc[i] : x[i]);
     if (i < mpad) {
-      y32[i] = (float)y[i];
-      kxp32[i] = (float)kxp[i];
+      y32[i] = (float)(ms.Dr ? y[i] * ms.Dr[i] : y[i]);
+      kxp32[i] = (float)(ms.invDr ? kxp[i] * ms.invDr[i] : kxp[i]);
     }
   }
 }

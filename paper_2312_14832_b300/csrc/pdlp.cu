@@ -61,6 +61,7 @@ struct DevSell {
   int32_t* col = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;   // mixed precision only
+  int32_t* ucol = nullptr;  // mixed precision, K with +-1 entries: sign-bit column words
   SellTask* tasks = nullptr;
   double* gpart = nullptr;
   int32_t* cnt = nullptr;
@@ -70,7 +71,9 @@ struct DevSell {
   int32_t tile = 0, tchunks = 0, batch = 8;
   int32_t staged = 0;   // FP64 products: 0 plain loads, 1 / 2 stream staged by bulk copies (2 / 3 buffers)
   int64_t rows = 0, rows_pad = 0, nchunks = 0, slots = 0, split = 0;
-  SellView view() const { return SellView{chunk_ptr, col, val, val32, tasks, ntasks, (int32_t)nchunks, gpart, cnt}; }
+  SellView view() const {
+    return SellView{chunk_ptr, col, val, val32, tasks, ntasks, (int32_t)nchunks, gpart, cnt, ucol};
+  }
 };
 
 constexpr int kRing = 4;        // pinned status records in flight
@@ -166,6 +169,11 @@ struct pdlp_ctx {
   // mixed precision (params.precision = 1): FP32 iterates, values and problem vectors
   float *x32 = nullptr, *y32 = nullptr, *sx32 = nullptr, *sy32 = nullptr, *kxp32 = nullptr;
   float *c32 = nullptr, *l32 = nullptr, *u32 = nullptr, *q32 = nullptr;
+  // +-1 entries as sign bits (mixed_values): the FP32 iterates are D_c x and D_r y;
+  // D_c^2 and D_r^2 in FP32 (c32, l32, u32, q32 then hold the unscaled data)
+  float *dc2 = nullptr, *dr2 = nullptr;
+  bool unit_ok = false;     // every entry of K is +-1 (checked at setup when mixed_values != 1)
+  int32_t mixed_values = 0; // 0 FP64 handle, 1 FP32 value copies, 2 sign bits
   cudaGraphExec_t gm_full = nullptr, gm_rem = nullptr;
   int gm_full_len = -1, gm_rem_len = -1;
   int64_t fp32_iters = 0;   // iterations of the last solve run in FP32
@@ -439,9 +447,28 @@ static void enqueue_attempt(pdlp_ctx* h, DevState* st) {
       h->x, h->xb, h->npad, h->y, h->yb, h->kxp, h->kxb, h->mpad, st);
 }
 
+static void launch_primal32(pdlp_ctx* h, const DevState* st) {
+  if (h->mixed_values == 2)
+    launch_rows<OpUnitF>(h, h->Kt, h->y32, EpiPrimal32U{h->x32, h->sx32, h->c32, h->l32, h->u32, h->dc2, 0.f}, st);
+  else
+    launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, st);
+}
+static void launch_dual32(pdlp_ctx* h, const DevState* st) {
+  if (h->mixed_values == 2)
+    launch_rows<OpUnitF>(h, h->K, h->x32, EpiDual32U{h->y32, h->sy32, h->kxp32, h->q32, h->dr2, (int)h->m1_int, 0.f},
+                         st);
+  else
+    launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1_int, 0.f}, st);
+}
+
 static void enqueue_iteration32(pdlp_ctx* h, const DevState* st) {
-  launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, st);
-  launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1_int, 0.f}, st);
+  launch_primal32(h, st);
+  launch_dual32(h, st);
+}
+
+static MixedScale mixed_scale(pdlp_ctx* h) {
+  if (h->mixed_values != 2) return MixedScale{nullptr, nullptr, nullptr, nullptr};
+  return MixedScale{h->Dc, h->invDc, h->Dr, h->invDr};
 }
 
 static KktInputs kkt_inputs(pdlp_ctx* h) {
@@ -476,11 +503,13 @@ static void enqueue_check(pdlp_ctx* h, int len, int final_check, bool adaptive =
 // FP64 check, FP32 iterates back from the (possibly restarted) FP64 ones (launches: 12).
 static void enqueue_check_mixed(pdlp_ctx* h, int len, int final_check) {
   k_mixed_to64<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x, h->sx, h->x32, h->sx32, h->npad, h->y,
-                                                                       h->sy, h->y32, h->sy32, h->mpad, h->st);
+                                                                       h->sy, h->y32, h->sy32, h->mpad, h->st,
+                                                                       mixed_scale(h));
   launch_rows<OpSpmv>(h, h->K, h->x, EpiStore{h->kxp, 0, 1.0}, h->st);
   enqueue_check(h, len, final_check);
   k_mixed_to32<<<grid_for(std::max(h->npad, h->mpad)), 256, 0, h->s>>>(h->x32, h->x, h->npad, h->y32, h->y,
-                                                                       h->kxp32, h->kxp, h->mpad, h->st);
+                                                                       h->kxp32, h->kxp, h->mpad, h->st,
+                                                                       mixed_scale(h));
 }
 
 enum { kModeFp64 = 0, kModeMixed = 1, kModeAdaptive = 2 };
@@ -687,6 +716,7 @@ static void check_params(const pdlp_params& P) {
   if (P.step_rule < 0 || P.step_rule > 1) invalid("step_rule must be 0 or 1");
   if (P.engine < 0 || P.engine > 2) invalid("engine must be 0, 1 or 2");
   if (P.host_layout < 0 || P.host_layout > 1) invalid("host_layout must be 0 or 1");
+  if (P.mixed_values < 0 || P.mixed_values > 2) invalid("mixed_values must be 0, 1 or 2");
 }
 
 // True when pred(i) holds for every i in [0, n) (checked in parallel ranges).
@@ -1159,19 +1189,39 @@ static void setup_impl(pdlp_ctx* h, int64_t m, int64_t n, int64_t m1, const int6
   h->setup_ms[4] = ms_since(tp);
 }
 
-// FP32 copies of the scaled matrix values and problem vectors, FP32 iterates.
+// FP32 iterates and problem vectors; FP32 copies of the scaled matrix values, or, for a
+// K with +-1 entries, sign-bit column words with the unscaled problem data and D_c^2,
+// D_r^2 (the iterations then run in the unscaled variables).
 static void setup_mixed(pdlp_ctx* h) {
   const int64_t np = h->npad, mp = h->mpad;
-  for (DevSell* S : {&h->K, &h->Kt}) {
-    S->val32 = dalloc<float>(h, (size_t)S->slots * 32);
-    k_to_float<<<grid_for(S->slots * 32), 256, 0, h->s>>>(S->val32, S->val, S->slots * 32);
+  // the iterates get 32 more entries: with sign-bit storage entry np (mp) stays zero and
+  // is what the padding slots of K (K') point at
+  for (float** v : {&h->x32, &h->sx32, &h->c32, &h->l32, &h->u32}) *v = dalloc<float>(h, np + 32);
+  for (float** v : {&h->y32, &h->sy32, &h->kxp32, &h->q32}) *v = dalloc<float>(h, mp + 32);
+  if (h->unit_ok) {
+    h->K.ucol = dalloc<int32_t>(h, (size_t)h->K.slots * 32);
+    k_unit_cols<<<grid_for(h->K.slots * 32), 256, 0, h->s>>>(h->K.ucol, h->K.col, h->K.val, h->K.slots * 32,
+                                                             (int32_t)np);
+    h->Kt.ucol = dalloc<int32_t>(h, (size_t)h->Kt.slots * 32);
+    k_unit_cols<<<grid_for(h->Kt.slots * 32), 256, 0, h->s>>>(h->Kt.ucol, h->Kt.col, h->Kt.val, h->Kt.slots * 32,
+                                                              (int32_t)mp);
+    h->dc2 = dalloc<float>(h, np);
+    h->dr2 = dalloc<float>(h, mp);
+    k_unit_vectors<<<grid_for(std::max(np, mp)), 256, 0, h->s>>>(h->c32, h->l32, h->u32, h->dc2, h->c, h->l, h->u,
+                                                                h->Dc, h->invDc, np, h->q32, h->dr2, h->q, h->Dr,
+                                                                h->invDr, mp);
+    h->mixed_values = 2;
+  } else {
+    for (DevSell* S : {&h->K, &h->Kt}) {
+      S->val32 = dalloc<float>(h, (size_t)S->slots * 32);
+      k_to_float<<<grid_for(S->slots * 32), 256, 0, h->s>>>(S->val32, S->val, S->slots * 32);
+    }
+    k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->c32, h->c, np);
+    k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->l32, h->l, np);
+    k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->u32, h->u, np);
+    k_to_float<<<grid_for(mp), 256, 0, h->s>>>(h->q32, h->q, mp);
+    h->mixed_values = 1;
   }
-  for (float** v : {&h->x32, &h->sx32, &h->c32, &h->l32, &h->u32}) *v = dalloc<float>(h, np);
-  for (float** v : {&h->y32, &h->sy32, &h->kxp32, &h->q32}) *v = dalloc<float>(h, mp);
-  k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->c32, h->c, np);
-  k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->l32, h->l, np);
-  k_to_float<<<grid_for(np), 256, 0, h->s>>>(h->u32, h->u, np);
-  k_to_float<<<grid_for(mp), 256, 0, h->s>>>(h->q32, h->q, mp);
   CKL("mixed setup");
   CK(cudaStreamSynchronize(h->s));
 }
@@ -1201,6 +1251,23 @@ static void device_setup_common(pdlp_ctx* h, Layout& Lo, const DevCsr* dc, const
     build_device_sell(h, h->K, Lo.SK, PK, d_val);
     build_device_sell(h, h->Kt, Lo.SKt, PKt, d_val);
     dfree(h, d_val);
+  }
+  // mixed precision: are the (unscaled) entries all +-1?  Then the FP32 products keep
+  // signs instead of values (mixed_values); the gathered vectors' zero entry np (mp)
+  // must be a valid 31-bit index
+  h->unit_ok = false;
+  if (!h->is_batch && P.precision == PDLP_MIXED && P.mixed_values != 1) {
+    unsigned long long* cnt = dalloc<unsigned long long>(h, 1);
+    k_count_nonunit<<<grid_for(h->K.slots * 32), 256, 0, h->s>>>(h->K.val, h->K.slots * 32, cnt);
+    CKL("entry check");
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, cnt, sizeof(bad), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    dfree(h, cnt);
+    const int64_t lim = ((int64_t)1 << 31) - 64;
+    h->unit_ok = bad == 0 && Lo.npad < lim && Lo.mpad < lim;
+    if (P.mixed_values == 2 && !h->unit_ok)
+      invalid("mixed_values = 2 needs every entry of K to be +1 or -1 (and fewer than 2^31 - 64 rows and columns)");
   }
 
   const int64_t mp = h->mpad, np = h->npad;
@@ -1475,7 +1542,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     CK(cudaMemsetAsync(h->sx32, 0, sizeof(float) * np, h->s));
     CK(cudaMemsetAsync(h->sy32, 0, sizeof(float) * mp, h->s));
     k_mixed_to32<<<grid_for(std::max(np, mp)), 256, 0, h->s>>>(h->x32, h->x, np, h->y32, h->y, h->kxp32, h->kxp, mp,
-                                                                 h->st);
+                                                                 h->st, mixed_scale(h));
     launches += 1;
   }
   CKL("solve init");
@@ -2588,6 +2655,7 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info) {
       info->tune_gbs[i] = h->tune_rates[i];
     }
     info->spmv_stage_Kt = h->Kt.staged + 1;
+    info->mixed_values = h->mixed_values;
     return PDLP_OK;
   });
 }
@@ -2625,12 +2693,12 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
       CK(cudaEventRecord(ev[0], h->s));
       for (int64_t i = 0; i < cnt; ++i) {
         if (h->p.precision == PDLP_MIXED)
-          launch_rows<OpSpmvF>(h, h->Kt, h->y32, EpiPrimal32{h->x32, h->sx32, h->c32, h->l32, h->u32, 0.f}, h->st_tmp);
+          launch_primal32(h, h->st_tmp);
         else
           launch_rows<OpSpmv>(h, h->Kt, h->y, EpiPrimal{h->x, h->sx, h->c, h->l, h->u, 0.0}, h->st_tmp);
         CK(cudaEventRecord(ev[2 * i + 1], h->s));
         if (h->p.precision == PDLP_MIXED)
-          launch_rows<OpSpmvF>(h, h->K, h->x32, EpiDual32{h->y32, h->sy32, h->kxp32, h->q32, (int)h->m1_int, 0.f}, h->st_tmp);
+          launch_dual32(h, h->st_tmp);
         else
           launch_rows<OpSpmv>(h, h->K, h->x, EpiDual{h->y, h->sy, h->kxp, h->q, (int)h->m1_int, 0.0}, h->st_tmp);
         CK(cudaEventRecord(ev[2 * i + 2], h->s));

@@ -85,3 +85,60 @@ def test_mixed_iteration_limit(pk):
         r = s.solve(tol=0.0, max_iter=300)
     assert r["iters"] == 300 and r["status"] == pk.ITER_LIMIT
     assert np.all(np.isfinite(r["x"])) and np.all(np.isfinite(r["y"]))
+
+
+def _solve_mixed(pk, lp, scaling, values, **kw):
+    with pk.Solver.from_lp(lp, scaling=scaling, precision=pk.MIXED, mixed_values=values) as s:
+        r = s.solve(**kw)
+        info = s.info()
+    return r, info
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_sign_bit_products_follow_the_fp64_oracle(pk, scaling):
+    """K with +-1 entries stored as sign bits (mixed_values 0 picks it for the MCF LP, 2
+    forces it): 192 FP32 iterations (three check intervals, tolerance 0) stay within the
+    FP32 rounding of the FP64 oracle's iterates, element by element, like the FP32 value
+    copies do.  A wrong sign, a scale applied twice or a padding slot that gathers a
+    nonzero entry would move the iterates by O(1)."""
+    lp = lpgen.mcf(1, nodes=500, arcs=2500)
+    ref = oracle.solve(lp, tol=0.0, max_iter=192, scaling=scaling)
+    got = {}
+    for values in (0, 1, 2):
+        r, info = _solve_mixed(pk, lp, scaling, values, tol=0.0, max_iter=192)
+        assert info["mixed_values"] == (1 if values == 1 else 2)
+        assert r["iters"] == 192 and r["fp32_iters"] == 192
+        assert r["restarts"] == ref["restarts"]
+        got[values] = r
+        for key in ("x", "y"):
+            want = ref[key]
+            err = np.max(np.abs(r[key] - want)) / max(1.0, np.max(np.abs(want)))
+            assert err <= 1e-4, (values, key, err)
+    # automatic and forced sign bits run the same kernels on the same data: identical
+    assert np.array_equal(got[0]["x"], got[2]["x"]) and np.array_equal(got[0]["y"], got[2]["y"])
+
+
+def test_sign_bits_only_for_unit_entries(pk):
+    """An LP with entries other than +-1 keeps FP32 value copies under automatic choice
+    and is refused when sign bits are forced; FP64 handles report no FP32 products."""
+    lp = lpgen.planted_small(0)
+    with pk.Solver.from_lp(lp, precision=pk.MIXED) as s:
+        assert s.info()["mixed_values"] == 1
+    with pytest.raises(pk.SolverError) as e:
+        pk.Solver.from_lp(lp, precision=pk.MIXED, mixed_values=2)
+    assert e.value.code == -1 and "+1 or -1" in str(e.value)
+    with pk.Solver.from_lp(lpgen.mcf(0, nodes=200, arcs=1000)) as s:
+        assert s.info()["mixed_values"] == 0
+
+
+@pytest.mark.parametrize("values", [1, 2])
+def test_mcf_to_1e4_with_either_storage(pk, values):
+    """Both storages of the FP32 products solve the MCF LP to 1e-4 (oracle's evaluation)
+    with objectives within 1e-3 of the FP64 oracle's."""
+    lp = lpgen.mcf(2, nodes=2000, arcs=10000)
+    ref = oracle.solve(lp, tol=1e-4, scaling=1)
+    r, info = _solve_mixed(pk, lp, 1, values, tol=1e-4)
+    assert info["mixed_values"] == values
+    assert r["status"] == pk.OPTIMAL and r["fp32_iters"] == r["iters"]
+    check_point(lp, r["x"], r["y"], 1e-4)
+    assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-3 * abs(ref["primal_obj"])
