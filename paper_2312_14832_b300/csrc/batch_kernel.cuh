@@ -295,8 +295,13 @@ __device__ __forceinline__ void batch_rows_p(const int32_t* __restrict__ cptr, c
 // of all of them two at a time, then gathers, then adds each row's products in slot
 // order (the per-row order of batch_rows_p, so the sums are bit-identical), and
 // finishes the kG rows' epilogues.  This keeps kG times more loads in flight per warp and
-// drops the predicated-off lanes of an 8-slot batch on a 2-slot chunk.
-constexpr int kGrp = 4;
+// drops the predicated-off lanes of an 8-slot batch on a 2-slot chunk.  The kernels with
+// global iterates spill at their 64 registers, and more chunks per group means more
+// spilling: on 300 / 1000 transportation LPs (200 x 300, one CTA per LP) two chunks take
+// 0.904 / 2.12 ms per iteration against 0.925 / 2.31 ms with four; batches of 8 or 16
+// slots in the long-row loop, or loading the next group's chunk bounds ahead, were
+// slower (0.95-0.98 / 2.15-2.74 ms).
+constexpr int kGrp = 2;
 template <int SRC, class Pre, class F>
 __device__ __forceinline__ void batch_rows_pg(const int32_t* __restrict__ cptr, const int32_t* __restrict__ col,
                                               const double* __restrict__ val, int c0, int c1, int cbase,
