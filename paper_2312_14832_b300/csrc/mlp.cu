@@ -61,15 +61,26 @@ static cudaError_t tc_gemm_attrs() {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kTcMaxDevices) return cudaErrorInvalidDevice;
   std::call_once(once[dev], [&]() {
-    res[dev] = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemBytes);
+    res[dev] = cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<1>::kSmem);
+    if (res[dev] == cudaSuccess)
+      res[dev] = cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<2>::kSmem);
   });
   return res[dev];
+}
+
+// Row tiles per CTA: two 128-row tiles share each B stage when M allows it and the
+// product has enough such blocks to fill the GPU, or a long K (where B, streamed once per
+// block row, is most of the traffic and the split along K supplies the CTAs).
+static int tc_gemm_mtiles(int M, int N, int K) {
+  if (M % (2 * kTcTile)) return 1;
+  const int blocks = (M / (2 * kTcTile)) * (N / kTcTile);
+  return (blocks >= 148 || K / kTcK >= 64) ? 2 : 1;
 }
 
 // Slices of K for a product with few output tiles: enough CTAs for about two per SM,
 // at least 8 steps of K per slice, at most max_splits.
 int tc_gemm_splits(int M, int N, int K, int max_splits) {
-  const int tiles = (M / kTcTile) * (N / kTcTile), kt = K / kTcK;
+  const int tiles = (M / (kTcTile * tc_gemm_mtiles(M, N, K))) * (N / kTcTile), kt = K / kTcK;
   if (tiles >= 148 || kt < 16 || max_splits <= 1) return 1;
   int sp = std::min(std::min(kt / 8, (2 * 148 + tiles - 1) / tiles), max_splits);
   sp = std::max(sp, 1);
@@ -93,8 +104,10 @@ cudaError_t tc_gemm_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, float
   const int kps = (kt + splits - 1) / splits;
   splits = (kt + kps - 1) / kps;
   TcGemmArgs g{C, Cb, bias, splits > 1 ? part : nullptr, M, N, K, kps, relu, err, spin, withhold};
-  dim3 grid(N / kTcTile, M / kTcTile, splits);
-  k_tc_gemm<<<grid, 128, kTmSmemBytes, s>>>(ta, tb, g);
+  const int mt = tc_gemm_mtiles(M, N, K);
+  dim3 grid(N / kTcTile, M / (kTcTile * mt), splits);
+  if (mt == 2) k_tc_gemm<2><<<grid, 128, TcShape<2>::kSmem, s>>>(ta, tb, g);
+  else k_tc_gemm<1><<<grid, 128, TcShape<1>::kSmem, s>>>(ta, tb, g);
   e = cudaGetLastError();
   if (e == cudaSuccess && splits > 1) {
     const int64_t tot = (int64_t)M * N;

@@ -2,27 +2,32 @@
 // with FP32 accumulation in tensor memory.  Used by the warm-start MLP (a dense
 // contraction, unlike the LP's SpMV).
 //
-// One CTA of 128 threads computes one 128 x 128 tile of C over a range of K (all of K,
-// or one slice of it when the product is split along K).  The roles are split:
+// One CTA of 128 threads computes a (128 kMT) x 128 block of C (kMT = 1 or 2 tiles of 128
+// rows) over a range of K (all of K, or one slice of it when the product is split along
+// K).  The roles are split:
 //   - thread 0 is the producer: for each 64-wide step of K it waits until the MMAs have
-//     released a stage of the ring, then has the tensor memory accelerator copy the
-//     128 x 64 tiles of A and B into it (two-dimensional tiled copies with 128-byte
-//     swizzle, the K-major layout the MMA descriptors name), completing on the stage's
-//     "full" mbarrier;
+//     released a stage of the ring, then has the tensor memory accelerator copy the kMT
+//     128 x 64 tiles of A and the 128 x 64 tile of B into it (two-dimensional tiled
+//     copies with 128-byte swizzle, the K-major layout the MMA descriptors name),
+//     completing on the stage's "full" mbarrier;
 //   - thread 32 issues the MMAs: it waits for a stage to be full, issues four
-//     128x128x16 tcgen05.mma into the TMEM accumulator, and tcgen05.commit's the stage's
-//     "empty" mbarrier, which hands the stage back to the producer once those MMAs have
-//     read it; after the last step it commits a "done" barrier;
-//   - all four warps then run the epilogue: tcgen05.ld of the accumulator (warp w owns
+//     128x128x16 tcgen05.mma into each of the kMT TMEM accumulators (all reading the
+//     stage's B tile), and tcgen05.commit's the stage's "empty" mbarrier, which hands the
+//     stage back to the producer once those MMAs have read it; after the last step it
+//     commits a "done" barrier;
+//   - all four warps then run the epilogue: tcgen05.ld of each accumulator (warp w owns
 //     TMEM lanes = rows 32w..32w+31), staged through shared memory so that every store
 //     writes 128 consecutive bytes of a row of C, with bias and ReLU (or, for a slice of a
 //     split product, the raw FP32 partial sums, which k_tc_splitk_reduce adds in slice
 //     order).
-// The ring has kTmStages stages of 32 KB (A and B), so up to kTmStages - 1 copies are in
-// flight while the MMAs run.  No multicast: every CTA copies its own tiles.
+// With kMT = 2 each B tile serves 256 rows of C, so B is streamed half as often; that is
+// what bounds the warm-start network's wide products (B a 124 MB weight matrix, M = 256).
+// The ring has 6 stages of 32 KB (kMT = 1) or 4 of 48 KB (kMT = 2), so several copies
+// are in flight while the MMAs run.  No multicast: every CTA copies its own tiles.
 //
-// Requirements (checked by the host launcher): M, N multiples of 128, K a multiple of 64,
-// A and B row-major (K contiguous) with 16-byte aligned rows and bases.
+// Requirements (checked by the host launcher): M a multiple of 128 kMT, N a multiple of
+// 128, K a multiple of 64, A and B row-major (K contiguous) with 16-byte aligned rows and
+// bases.
 // Every wait on an mbarrier gives up after kSpinLimit polls, sets *err and stops the
 // CTA's pipeline; before the CTA leaves, the copies it issued are waited for (bounded)
 // and its TMEM is freed.
@@ -36,8 +41,6 @@ namespace pdlp {
 constexpr int kTcTile = 128;      // M and N of a CTA tile (and of one MMA)
 constexpr int kTcK = 64;          // K per stage (128 bytes of BF16)
 constexpr int kTcStageBytes = kTcTile * kTcK * 2;   // 16 KB per operand per stage
-constexpr int kTmStages = 6;
-constexpr int kTmSmemBytes = kTmStages * 2 * kTcStageBytes + 1024;   // ring + alignment slack
 constexpr long long kSpinLimit = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -94,22 +97,38 @@ struct TcGemmArgs {
                             // wait of the MMA thread can only give up
 };
 
+// Shape of one CTA of k_tc_gemm<kMT>: kMT 128-row tiles of A (kMT accumulators in
+// TMEM, 128 columns each) share every 128 x 64 stage of B, so a CTA computes a
+// (128 kMT) x 128 block of C and B is streamed once per 128 kMT rows of C.
+template <int kMT>
+struct TcShape {
+  static constexpr int kStages = kMT == 2 ? 4 : 6;
+  static constexpr int kABytes = kMT * kTcStageBytes;       // A part of a stage
+  static constexpr int kStageBytes = kABytes + kTcStageBytes;
+  static constexpr int kSmem = kStages * kStageBytes + 1024;  // ring + alignment slack
+  static constexpr int kTmemCols = kMT * kTcTile;
+};
+
+template <int kMT>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, TcGemmArgs g) {
+  using Sh = TcShape<kMT>;
+  constexpr int kSt = Sh::kStages;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kTmStages], empty[kTmStages], done;
+  __shared__ __align__(8) uint64_t full[kSt], empty[kSt], done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int failed, issued_sh, consumed_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcTile, n0 = blockIdx.x * kTcTile;
+  const int m0 = blockIdx.y * (kMT * kTcTile), n0 = blockIdx.x * kTcTile;
   const int kt0 = blockIdx.z * g.ktiles;
   const int nk = min(g.ktiles, g.K / kTcK - kt0);
-  auto sA = [&](int s) { return base + (size_t)s * 2 * kTcStageBytes; };
-  auto sB = [&](int s) { return base + (size_t)s * 2 * kTcStageBytes + kTcStageBytes; };
+  // stage s: A rows m0 + 128 r at sA(s) + r * 16 KB (r < kMT), then B
+  auto sA = [&](int s) { return base + (size_t)s * Sh::kStageBytes; };
+  auto sB = [&](int s) { return base + (size_t)s * Sh::kStageBytes + Sh::kABytes; };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTmStages; ++s) {
+    for (int s = 0; s < kSt; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -123,7 +142,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(kTcTile)
+                 "r"(Sh::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -134,24 +153,26 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   volatile int* vfailed = &failed;
 
   if (threadIdx.x == 0) {
-    // producer: stage s = i % kTmStages; use i of a stage waits for the MMAs of use i - kTmStages
+    // producer: stage s = i % kSt; use i of a stage waits for the MMAs of use i - kSt
     int i = 0;
     for (; i < nk && !g.withhold; ++i) {
-      const int s = i % kTmStages;
-      if (i >= kTmStages && !mbar_wait(&empty[s], (uint32_t)(((i / kTmStages) - 1) & 1), g.spin)) {
+      const int s = i % kSt;
+      if (i >= kSt && !mbar_wait(&empty[s], (uint32_t)(((i / kSt) - 1) & 1), g.spin)) {
         *vfailed = 1;
         break;
       }
       if (*vfailed) break;
       const uint32_t fb = smem_u32(&full[s]);
       const int kx = (kt0 + i) * kTcK;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * kTcStageBytes)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(Sh::kStageBytes)
                    : "memory");
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-          "[%4];" ::"r"(smem_u32(sA(s))),
-          "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kx), "r"(m0), "r"(fb)
-          : "memory");
+#pragma unroll
+      for (int r = 0; r < kMT; ++r)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(smem_u32(sA(s) + r * kTcStageBytes)),
+            "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kx), "r"(m0 + r * kTcTile), "r"(fb)
+            : "memory");
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
           "[%4];" ::"r"(smem_u32(sB(s))),
@@ -160,12 +181,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     }
     issued_sh = i;
   } else if (threadIdx.x == 32) {
-    // MMA issuer
+    // MMA issuer: per stage, four 16-deep steps of K into each of the kMT accumulators
     const uint32_t idesc = tc_idesc();
     int i = 0;
     for (; i < nk; ++i) {
-      const int s = i % kTmStages;
-      if (!mbar_wait(&full[s], (uint32_t)((i / kTmStages) & 1), g.spin)) {
+      const int s = i % kSt;
+      if (!mbar_wait(&full[s], (uint32_t)((i / kSt) & 1), g.spin)) {
         *vfailed = 1;
         break;
       }
@@ -174,13 +195,17 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
       const uint32_t a0 = smem_u32(sA(s)), b0 = smem_u32(sB(s));
 #pragma unroll
       for (int kk = 0; kk < kTcK / 16; ++kk) {
-        const uint64_t ad = tc_desc(a0 + kk * 32), bd = tc_desc(b0 + kk * 32);
+        const uint64_t bd = tc_desc(b0 + kk * 32);
         const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
+#pragma unroll
+        for (int r = 0; r < kMT; ++r) {
+          const uint64_t ad = tc_desc(a0 + r * kTcStageBytes + kk * 32);
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(r * kTcTile)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&empty[s]))
@@ -200,52 +225,55 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   if (!ok && threadIdx.x == 0) {
     atomicExch(g.err, 1);
     // no copy may land after the CTA has left: wait (bounded) for the unconsumed ones
-    for (int i = consumed; i < issued; ++i)
-      mbar_wait(&full[i % kTmStages], (uint32_t)((i / kTmStages) & 1), g.spin);
+    for (int i = consumed; i < issued; ++i) mbar_wait(&full[i % kSt], (uint32_t)((i / kSt) & 1), g.spin);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     // epilogue through shared memory (the ring is free: every copy has been consumed and
-    // every MMA has finished): warp w stages a 32 x 32 block at a time
+    // every MMA has finished): warp w stages a 32 x 32 block at a time; accumulator r
+    // holds rows m0 + 128 r + (TMEM lane)
     float* tile = reinterpret_cast<float*>(base) + warp * 32 * 33;
     const size_t ldc = (size_t)g.N;
-    for (int cb = 0; cb < kTcTile; cb += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int r = 0; r < kMT; ++r) {
+      const int row0 = m0 + r * kTcTile + warp * 32;
+      for (int cb = 0; cb < kTcTile; cb += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * kTcTile + cb);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
-      __syncwarp();
-      const int col = n0 + cb + lane;
-      if (g.part) {
-        float* P = g.part + (size_t)blockIdx.z * g.M * ldc;
-        for (int rr = 0; rr < 32; ++rr) P[(size_t)(m0 + warp * 32 + rr) * ldc + col] = tile[rr * 33 + lane];
-      } else {
-        const float bv = g.bias ? g.bias[col] : 0.0f;
-        for (int rr = 0; rr < 32; ++rr) {
-          float v = tile[rr * 33 + lane] + bv;
-          if (g.relu) v = fmaxf(v, 0.0f);
-          const size_t o = (size_t)(m0 + warp * 32 + rr) * ldc + col;
-          if (g.C) g.C[o] = v;
-          if (g.Cb) g.Cb[o] = __float2bfloat16_rn(v);
+        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int col = n0 + cb + lane;
+        if (g.part) {
+          float* P = g.part + (size_t)blockIdx.z * g.M * ldc;
+          for (int rr = 0; rr < 32; ++rr) P[(size_t)(row0 + rr) * ldc + col] = tile[rr * 33 + lane];
+        } else {
+          const float bv = g.bias ? g.bias[col] : 0.0f;
+          for (int rr = 0; rr < 32; ++rr) {
+            float x = tile[rr * 33 + lane] + bv;
+            if (g.relu) x = fmaxf(x, 0.0f);
+            const size_t o = (size_t)(row0 + rr) * ldc + col;
+            if (g.C) g.C[o] = x;
+            if (g.Cb) g.Cb[o] = __float2bfloat16_rn(x);
+          }
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTile) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::kTmemCols) : "memory");
 }
 
 // C = sum over the splits of the partial products, in split order, + bias, ReLU.

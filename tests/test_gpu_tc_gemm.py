@@ -127,3 +127,26 @@ def test_bounded_wait_gives_up_and_context_stays_usable(env):
     assert rc == 0, lib.pdlp_last_error(None)
     ref, scale = _reference(A, B, torch.zeros(128), False)
     assert np.all(np.abs(out.cpu().double().numpy() - ref) <= 1e-5 * scale + 1e-30)
+
+
+@pytest.mark.parametrize("M,N,K,splits,relu", [(256, 18944, 128, 1, 1), (768, 384, 4096, 1, 0),
+                                                (512, 256, 8192, 4, 1), (256, 1024, 4352, 17, 0)])
+def test_tc_gemm_two_row_tiles(env, M, N, K, splits, relu):
+    """Shapes for which the launcher gives each CTA two 128-row tiles of A sharing every B
+    stage (M a multiple of 256 with at least 148 such blocks, or K of 64 steps or more):
+    unsplit and split along K (17 slices of a 68-step K become 17 of 4 steps), with bias
+    and ReLU."""
+    lib, torch = env
+    A, B, bias = _operands(torch, M, N, K, M + N + K + splits)
+    out = torch.full((M, N), float("nan"), device="cuda")
+    dA, dB, db = A.cuda(), B.cuda(), bias.cuda()
+    if splits == 1:
+        rc = lib.pdlp_tc_gemm(M, N, K, dA.data_ptr(), dB.data_ptr(), out.data_ptr(), db.data_ptr(), relu, None)
+    else:
+        ws = torch.empty(splits * M * N, device="cuda")
+        rc = lib.pdlp_tc_gemm_split(M, N, K, dA.data_ptr(), dB.data_ptr(), out.data_ptr(), db.data_ptr(), relu,
+                                    splits, ws.data_ptr(), None)
+    assert rc == 0, lib.pdlp_last_error(None)
+    ref, mag = _reference(A, B, bias, relu)
+    tol = max(1e-5, K * 2.0 ** -24)
+    assert np.all(np.abs(out.cpu().double().numpy() - ref) <= tol * mag + 1e-6)
