@@ -52,6 +52,35 @@ static cudaError_t encode_operand(CUtensorMap* tm, const __nv_bfloat16* p, int r
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Stages of the ring for products of few K steps per CTA (at most kTcShortK1 with one row
+// tile, kTcShortK2 with two): a ring small enough for two CTAs per SM (97 KB), so that one
+// CTA's epilogue overlaps another's loads.  Measured on the warm-start network's shapes:
+// the output layer's weight gradient (60544 x 1024 x 256, one row tile) 0.217 -> 0.132 ms,
+// its forward product (256 x 60544 x 1024, two row tiles) 0.097 -> 0.083 ms; the
+// hidden-layer products (16 steps, one row tile) gain nothing from the smaller ring.
+#ifndef PDLP_TC_SHORT_K1
+#define PDLP_TC_SHORT_K1 4
+#endif
+#ifndef PDLP_TC_SHORT_K2
+#define PDLP_TC_SHORT_K2 16
+#endif
+#ifndef PDLP_TC_SHORT_STAGES1
+#define PDLP_TC_SHORT_STAGES1 3
+#endif
+#ifndef PDLP_TC_SHORT_STAGES2
+#define PDLP_TC_SHORT_STAGES2 2
+#endif
+constexpr int kTcShortK1 = PDLP_TC_SHORT_K1;
+constexpr int kTcShortK2 = PDLP_TC_SHORT_K2;
+constexpr int kTcShortStages1 = PDLP_TC_SHORT_STAGES1;
+constexpr int kTcShortStages2 = PDLP_TC_SHORT_STAGES2;
+
+template <int kMT, int kSt>
+static cudaError_t tc_gemm_attr() {
+  return cudaFuncSetAttribute(k_tc_gemm<kMT, kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TcShape<kMT, kSt>::kSmem);
+}
+
 // The kernel's shared-memory opt-in, once per device (with that device current).
 static cudaError_t tc_gemm_attrs() {
   static std::once_flag once[kTcMaxDevices];
@@ -61,9 +90,10 @@ static cudaError_t tc_gemm_attrs() {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kTcMaxDevices) return cudaErrorInvalidDevice;
   std::call_once(once[dev], [&]() {
-    res[dev] = cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<1>::kSmem);
-    if (res[dev] == cudaSuccess)
-      res[dev] = cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<2>::kSmem);
+    res[dev] = tc_gemm_attr<1, 6>();
+    if (res[dev] == cudaSuccess) res[dev] = tc_gemm_attr<2, 4>();
+    if (res[dev] == cudaSuccess) res[dev] = tc_gemm_attr<1, kTcShortStages1>();
+    if (res[dev] == cudaSuccess) res[dev] = tc_gemm_attr<2, kTcShortStages2>();
   });
   return res[dev];
 }
@@ -106,8 +136,15 @@ cudaError_t tc_gemm_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, float
   TcGemmArgs g{C, Cb, bias, splits > 1 ? part : nullptr, M, N, K, kps, relu, err, spin, withhold};
   const int mt = tc_gemm_mtiles(M, N, K);
   dim3 grid(N / kTcTile, M / (kTcTile * mt), splits);
-  if (mt == 2) k_tc_gemm<2><<<grid, 128, TcShape<2>::kSmem, s>>>(ta, tb, g);
-  else k_tc_gemm<1><<<grid, 128, TcShape<1>::kSmem, s>>>(ta, tb, g);
+  const bool short_k = kps <= (mt == 2 ? kTcShortK2 : kTcShortK1);
+  if (mt == 2 && short_k)
+    k_tc_gemm<2, kTcShortStages2><<<grid, 128, TcShape<2, kTcShortStages2>::kSmem, s>>>(ta, tb, g);
+  else if (mt == 2)
+    k_tc_gemm<2, 4><<<grid, 128, TcShape<2, 4>::kSmem, s>>>(ta, tb, g);
+  else if (short_k)
+    k_tc_gemm<1, kTcShortStages1><<<grid, 128, TcShape<1, kTcShortStages1>::kSmem, s>>>(ta, tb, g);
+  else
+    k_tc_gemm<1, 6><<<grid, 128, TcShape<1, 6>::kSmem, s>>>(ta, tb, g);
   e = cudaGetLastError();
   if (e == cudaSuccess && splits > 1) {
     const int64_t tot = (int64_t)M * N;

@@ -22,8 +22,10 @@
 //     order).
 // With kMT = 2 each B tile serves 256 rows of C, so B is streamed half as often; that is
 // what bounds the warm-start network's wide products (B a 124 MB weight matrix, M = 256).
-// The ring has 6 stages of 32 KB (kMT = 1) or 4 of 48 KB (kMT = 2), so several copies
-// are in flight while the MMAs run.  No multicast: every CTA copies its own tiles.
+// The ring has kSt stages of 32 KB (kMT = 1) or 48 KB (kMT = 2): 6 or 4 (one CTA per SM,
+// several copies in flight while the MMAs run), or, for few K steps per CTA, 3 or 2 (two
+// CTAs per SM, one's epilogue overlapping the other's loads).  No multicast: every CTA
+// copies its own tiles.
 //
 // Requirements (checked by the host launcher): M a multiple of 128 kMT, N a multiple of
 // 128, K a multiple of 64, A and B row-major (K contiguous) with 16-byte aligned rows and
@@ -100,20 +102,19 @@ struct TcGemmArgs {
 // Shape of one CTA of k_tc_gemm<kMT>: kMT 128-row tiles of A (kMT accumulators in
 // TMEM, 128 columns each) share every 128 x 64 stage of B, so a CTA computes a
 // (128 kMT) x 128 block of C and B is streamed once per 128 kMT rows of C.
-template <int kMT>
+template <int kMT, int kSt>
 struct TcShape {
-  static constexpr int kStages = kMT == 2 ? 4 : 6;
+  static constexpr int kStages = kSt;
   static constexpr int kABytes = kMT * kTcStageBytes;       // A part of a stage
   static constexpr int kStageBytes = kABytes + kTcStageBytes;
   static constexpr int kSmem = kStages * kStageBytes + 1024;  // ring + alignment slack
   static constexpr int kTmemCols = kMT * kTcTile;
 };
 
-template <int kMT>
+template <int kMT, int kSt>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, TcGemmArgs g) {
-  using Sh = TcShape<kMT>;
-  constexpr int kSt = Sh::kStages;
+  using Sh = TcShape<kMT, kSt>;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[kSt], empty[kSt], done;
