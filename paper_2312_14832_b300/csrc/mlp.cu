@@ -315,17 +315,29 @@ __global__ void k_mlp_colsum(float* db, const float* dZ, int R, int C) {
 }
 
 // AdamW on one tensor: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
-// w -= lr (m_hat / (sqrt(v_hat) + eps) + wd w).
+// w -= lr (m_hat / (sqrt(v_hat) + eps) + wd w); wb (if not null) receives the BF16 copy
+// of the new w that the next forward products read.
 __global__ void k_mlp_adamw(float* w, float* m, float* v, const float* g, int64_t n, float lr, float wd, float b1,
-                            float b2, float c1, float c2, float eps) {
+                            float b2, float c1, float c2, float eps, __nv_bfloat16* wb) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+    const float wn = w[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+    w[i] = wn;
+    if (wb) wb[i] = __float2bfloat16_rn(wn);
   }
+}
+
+// Loss of one minibatch from the per-block partial sums of k_mlp_loss_grad, added in
+// block order: out = sum(part[0..nb)) / denom, denom = 2 rows n_out.
+__global__ void k_mlp_loss_total(const double* part, int nb, double denom, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < nb; ++i) s += part[i];
+  *out = s / denom;
 }
 
 }  // namespace pdlp
@@ -389,11 +401,16 @@ static void transpose(pdlp_mlp_ctx* h, __nv_bfloat16* dst, const __nv_bfloat16* 
   k_mlp_transpose_bf16<<<grid, block, 0, h->s>>>(dst, src, R, C);
 }
 
-// BF16 copies of the weights (and transposes of W2, W3 for the backward products).
-static void refresh_bf16(pdlp_mlp_ctx* h) {
-  for (int l = 0; l < 3; ++l) k_mlp_fill_bf16_from_f32<<<gridn(h->wsz[l]), 256, 0, h->s>>>(h->Wb[l], h->W[l], h->wsz[l]);
+// Transposes of the BF16 W2, W3 for the backward products.
+static void refresh_transposes(pdlp_mlp_ctx* h) {
   transpose(h, h->WTb[1], h->Wb[1], h->hid, h->hid);
   transpose(h, h->WTb[2], h->Wb[2], h->out_p, h->hid);
+}
+
+// BF16 copies of the weights and the transposes.
+static void refresh_bf16(pdlp_mlp_ctx* h) {
+  for (int l = 0; l < 3; ++l) k_mlp_fill_bf16_from_f32<<<gridn(h->wsz[l]), 256, 0, h->s>>>(h->Wb[l], h->W[l], h->wsz[l]);
+  refresh_transposes(h);
 }
 
 // Forward on rows idx[0..rows) of X (device, n_in columns), outputs in h->Y.
@@ -404,10 +421,13 @@ static void forward(pdlp_mlp_ctx* h, const float* X, const int* idx, int rows) {
   gemm(h, h->H2b, h->Wb[2], h->Y, nullptr, h->b[2], h->bp, h->out_p, h->hid, 0);
 }
 
+constexpr int kLossBlocks = 148;
+
 // Backward of the MSE loss against rows idx of T (device, n_out columns); gradients
-// in h->gW / h->gb; returns the loss (sum of squares / (2 rows n_out)).
-static double backward(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows) {
-  const int nb = 148;
+// in h->gW / h->gb; the loss (sum of squares / (2 rows n_out)) goes to the device
+// double *loss_dev.  Nothing is waited for.
+static void backward_async(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows, double* loss_dev) {
+  const int nb = kLossBlocks;
   k_mlp_loss_grad<<<nb, 256, 0, h->s>>>(h->Y, h->bp, h->out_p, T, h->n_out, idx, rows, h->dY, h->dYb, h->part);
   transpose(h, h->dYTb, h->dYb, h->bp, h->out_p);
   transpose(h, h->H2Tb, h->H2b, h->bp, h->hid);
@@ -430,13 +450,17 @@ static double backward(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows
   transpose(h, h->dZ1Tb, h->dZ1b, h->bp, h->hid);
   gemm(h, h->dZ1Tb, h->XTb, h->gW[0], nullptr, nullptr, h->hid, h->in_p, h->bp, 0);
   k_mlp_colsum<<<(h->hid + 255) / 256, 256, 0, h->s>>>(h->gb[0], h->dZ1, h->bp, h->hid);
+  k_mlp_loss_total<<<1, 32, 0, h->s>>>(h->part, nb, 2.0 * rows * h->n_out, loss_dev);
   mlp_ck(cudaGetLastError(), "backward");
-  std::vector<double> part(nb);
-  mlp_ck(cudaMemcpyAsync(part.data(), h->part, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->s), "loss copy");
+}
+
+// backward_async, then the loss read back (one wait).
+static double backward(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows) {
+  backward_async(h, T, idx, rows, h->part + kLossBlocks);
+  double L = 0.0;
+  mlp_ck(cudaMemcpyAsync(&L, h->part + kLossBlocks, sizeof(double), cudaMemcpyDeviceToHost, h->s), "loss copy");
   mlp_ck(cudaStreamSynchronize(h->s), "backward sync");
-  double s = 0.0;
-  for (double v : part) s += v;
-  return s / (2.0 * rows * h->n_out);
+  return L;
 }
 
 static void check_err(pdlp_mlp_ctx* h) {
@@ -502,7 +526,7 @@ int pdlp_mlp_create(pdlp_mlp* out, int32_t n_in, int32_t hidden, int32_t n_out, 
     for (float** p : {&h->H1, &h->H2, &h->dH2, &h->dZ2, &h->dH1, &h->dZ1}) *p = mlp_alloc<float>(h, bh);
     h->Y = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
     h->dY = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
-    h->part = mlp_alloc<double>(h, 148);
+    h->part = mlp_alloc<double>(h, kLossBlocks + 1);   // per-block loss sums, then the loss
     h->err = mlp_alloc<int>(h, 1);
     // the split-K workspace of the largest split product of a training step
     const int shapes[8][3] = {{h->bp, h->hid, h->in_p},  {h->bp, h->hid, h->hid},  {h->bp, h->out_p, h->hid},
@@ -663,34 +687,64 @@ int pdlp_mlp_train(pdlp_mlp h, int32_t epochs, int32_t batch, float lr, float we
     mlp_ck(cudaEventCreate(&e0), "event");
     mlp_ck(cudaEventCreate(&e1), "event");
     float total_ms = 0.f;
-    for (int ep = 0; ep < epochs; ++ep) {
-      for (int64_t i = 0; i < N; ++i) perm[(size_t)i] = (int)i;
-      for (int64_t i = N - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(rnd() % (uint64_t)(i + 1))]);
-      double lsum = 0.0;
-      int64_t nb = 0;
-      mlp_ck(cudaEventRecord(e0, h->s), "event");
-      for (int64_t off = 0; off + batch <= N; off += batch, ++nb) {
-        mlp_ck(cudaMemcpyAsync(h->idx, perm.data() + off, sizeof(int) * batch, cudaMemcpyHostToDevice, h->s), "idx");
-        forward(h, h->dataX, h->idx, batch);
-        lsum += backward(h, h->dataT, h->idx, batch);
-        h->step += 1;
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
-        for (int l = 0; l < 3; ++l) {
-          k_mlp_adamw<<<gridn(h->wsz[l]), 256, 0, h->s>>>(h->W[l], h->mW[l], h->vW[l], h->gW[l], h->wsz[l], lr,
-                                                           weight_decay, b1, b2, c1, c2, 1e-8f);
-          k_mlp_adamw<<<gridn(h->bsz[l]), 256, 0, h->s>>>(h->b[l], h->mb[l], h->vb[l], h->gb[l], h->bsz[l], lr, 0.f,
-                                                           b1, b2, c1, c2, 1e-8f);
-        }
-        refresh_bf16(h);
-      }
-      mlp_ck(cudaEventRecord(e1, h->s), "event");
-      mlp_ck(cudaEventSynchronize(e1), "event");
-      float ms = 0.f;
-      mlp_ck(cudaEventElapsedTime(&ms, e0, e1), "event");
-      total_ms += ms;
-      if (epoch_loss) epoch_loss[ep] = nb ? lsum / nb : 0.0;
+    // the epoch's order and the minibatch losses stay on the device, so the steps of an
+    // epoch are queued without waiting for one another
+    const int64_t steps = N / batch;
+    int* perm_dev = nullptr;
+    double* loss_dev = nullptr;
+    cudaError_t ae = cudaMalloc(&perm_dev, sizeof(int) * (size_t)std::max<int64_t>(N, 1));
+    if (ae == cudaSuccess) ae = cudaMalloc(&loss_dev, sizeof(double) * (size_t)std::max<int64_t>(steps, 1));
+    if (ae != cudaSuccess) {
+      cudaFree(perm_dev);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw std::string("cudaMalloc: ") + cudaGetErrorString(ae);
     }
+    std::vector<double> losses((size_t)std::max<int64_t>(steps, 1));
+    try {
+      for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = 0; i < N; ++i) perm[(size_t)i] = (int)i;
+        for (int64_t i = N - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(rnd() % (uint64_t)(i + 1))]);
+        mlp_ck(cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, h->s), "perm");
+        mlp_ck(cudaEventRecord(e0, h->s), "event");
+        for (int64_t st_i = 0; st_i < steps; ++st_i) {
+          const int* idx = perm_dev + st_i * batch;
+          forward(h, h->dataX, idx, batch);
+          backward_async(h, h->dataT, idx, batch, loss_dev + st_i);
+          h->step += 1;
+          const float b1 = 0.9f, b2 = 0.999f;
+          const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+          for (int l = 0; l < 3; ++l) {
+            k_mlp_adamw<<<gridn(h->wsz[l]), 256, 0, h->s>>>(h->W[l], h->mW[l], h->vW[l], h->gW[l], h->wsz[l], lr,
+                                                             weight_decay, b1, b2, c1, c2, 1e-8f, h->Wb[l]);
+            k_mlp_adamw<<<gridn(h->bsz[l]), 256, 0, h->s>>>(h->b[l], h->mb[l], h->vb[l], h->gb[l], h->bsz[l], lr,
+                                                             0.f, b1, b2, c1, c2, 1e-8f, nullptr);
+          }
+          refresh_transposes(h);
+        }
+        mlp_ck(cudaGetLastError(), "train step");
+        mlp_ck(cudaEventRecord(e1, h->s), "event");
+        mlp_ck(cudaEventSynchronize(e1), "event");
+        float ms = 0.f;
+        mlp_ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+        total_ms += ms;
+        double lsum = 0.0;
+        if (steps > 0) {
+          mlp_ck(cudaMemcpy(losses.data(), loss_dev, sizeof(double) * (size_t)steps, cudaMemcpyDeviceToHost),
+                 "losses");
+          for (int64_t i = 0; i < steps; ++i) lsum += losses[(size_t)i];
+        }
+        if (epoch_loss) epoch_loss[ep] = steps ? lsum / steps : 0.0;
+      }
+    } catch (...) {
+      cudaFree(perm_dev);
+      cudaFree(loss_dev);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaFree(perm_dev);
+    cudaFree(loss_dev);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     check_err(h);
