@@ -268,32 +268,66 @@ __global__ void k_mlp_transpose_bf16(__nv_bfloat16* dst, const __nv_bfloat16* sr
   }
 }
 
+// dst[C x R] = src[R x C]^T for R a multiple of 16 and C of 64, without shared memory:
+// warp w takes rows 16 (w / (C/64)) .. + 16 and columns 64 (w % (C/64)) .. + 64; lane l
+// loads the column pair (2l, 2l + 1) of its 16 rows (4 bytes per row, 128 bytes per warp
+// and row) and writes the two 32-byte output rows of that pair.
+__global__ void k_mlp_transpose_bf16_w(__nv_bfloat16* dst, const __nv_bfloat16* src, int R, int C) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int cbs = C / 64;
+  if (w >= (int64_t)(R / 16) * cbs) return;
+  const int r0 = (int)(w / cbs) * 16, c0 = (int)(w % cbs) * 64 + 2 * lane;
+  uint32_t v[16];
+  const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = s32[((int64_t)(r0 + k) * C + c0) >> 1];
+  uint4 lo[2], hi[2];
+  uint32_t* l32 = reinterpret_cast<uint32_t*>(lo);
+  uint32_t* h32 = reinterpret_cast<uint32_t*>(hi);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    l32[j] = __byte_perm(v[2 * j], v[2 * j + 1], 0x5410);   // column c0: low halves of rows 2j, 2j+1
+    h32[j] = __byte_perm(v[2 * j], v[2 * j + 1], 0x7632);   // column c0 + 1: high halves
+  }
+  uint4* d0 = reinterpret_cast<uint4*>(dst + (int64_t)c0 * R + r0);
+  uint4* d1 = reinterpret_cast<uint4*>(dst + (int64_t)(c0 + 1) * R + r0);
+  d0[0] = lo[0];
+  d0[1] = lo[1];
+  d1[0] = hi[0];
+  d1[1] = hi[1];
+}
+
 // dY = (Y - T) / (rows * n_out) on the valid block, 0 elsewhere; BF16 copy; per-block
-// partial sums of (Y - T)^2 for the loss.
-__global__ void k_mlp_loss_grad(const float* Y, int Bp, int Op, const float* T, int n_out, const int* idx, int rows,
-                                float* dY, __nv_bfloat16* dYb, double* part) {
-  const double inv = 1.0 / ((double)rows * n_out);
-  double acc = 0.0;
-  const int64_t tot = (int64_t)Bp * Op;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / Op), c = (int)(i % Op);
+// partial sums of (Y - T)^2 for the loss.  Block (x, y) covers row y, columns x * 256 +
+// threadIdx.x + k * 256 gridDim.x; a thread adds its squares in FP32, the block its
+// threads' sums in FP64 in a fixed order; part[y * gridDim.x + x] = the block's sum.
+__global__ void k_mlp_loss_grad(const float* Y, int Op, const float* T, int n_out, const int* idx, int rows,
+                                float inv, float* dY, __nv_bfloat16* dYb, double* part) {
+  const int r = blockIdx.y;
+  const float* yr = Y + (size_t)r * Op;
+  float* dyr = dY + (size_t)r * Op;
+  __nv_bfloat16* dybr = dYb + (size_t)r * Op;
+  const float* tr = r < rows ? T + (size_t)idx[r] * n_out : nullptr;
+  float acc = 0.f;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < Op; c += gridDim.x * blockDim.x) {
     float g = 0.f;
-    if (r < rows && c < n_out) {
-      const float d = Y[i] - T[(int64_t)idx[r] * n_out + c];
-      acc += (double)d * d;
-      g = (float)(d * inv);
+    if (tr && c < n_out) {
+      const float d = yr[c] - tr[c];
+      acc = fmaf(d, d, acc);
+      g = d * inv;
     }
-    dY[i] = g;
-    dYb[i] = __float2bfloat16_rn(g);
+    dyr[c] = g;
+    dybr[c] = __float2bfloat16_rn(g);
   }
   __shared__ double sh[256];
-  sh[threadIdx.x] = acc;
+  sh[threadIdx.x] = (double)acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
 }
 
 // dZ = dH * (H > 0), FP32 and BF16.
@@ -314,30 +348,20 @@ __global__ void k_mlp_colsum(float* db, const float* dZ, int R, int C) {
   db[c] = s;
 }
 
-// AdamW on one tensor: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
-// w -= lr (m_hat / (sqrt(v_hat) + eps) + wd w); wb (if not null) receives the BF16 copy
-// of the new w that the next forward products read.
-__global__ void k_mlp_adamw(float* w, float* m, float* v, const float* g, int64_t n, float lr, float wd, float b1,
-                            float b2, float c1, float c2, float eps, __nv_bfloat16* wb) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wn = w[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
-    w[i] = wn;
-    if (wb) wb[i] = __float2bfloat16_rn(wn);
-  }
-}
-
-// Loss of one minibatch from the per-block partial sums of k_mlp_loss_grad, added in
-// block order: out = sum(part[0..nb)) / denom, denom = 2 rows n_out.
+// Loss of one minibatch from the per-block partial sums of k_mlp_loss_grad (one block of
+// 256 threads: thread t adds part[t], part[t + 256], ... in order, then a fixed tree):
+// out = sum(part[0..nb)) / denom, denom = 2 rows n_out.
 __global__ void k_mlp_loss_total(const double* part, int nb, double denom, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double sh[256];
   double s = 0.0;
-  for (int i = 0; i < nb; ++i) s += part[i];
-  *out = s / denom;
+  for (int i = threadIdx.x; i < nb; i += 256) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0] / denom;
 }
 
 }  // namespace pdlp
@@ -397,6 +421,11 @@ static void gemm(pdlp_mlp_ctx* h, const __nv_bfloat16* A, const __nv_bfloat16* B
 }
 
 static void transpose(pdlp_mlp_ctx* h, __nv_bfloat16* dst, const __nv_bfloat16* src, int R, int C) {
+  if (R % 16 == 0 && C % 64 == 0 && ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+    const int64_t warps = (int64_t)(R / 16) * (C / 64);
+    k_mlp_transpose_bf16_w<<<(unsigned)((warps + 7) / 8), 256, 0, h->s>>>(dst, src, R, C);
+    return;
+  }
   dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
   k_mlp_transpose_bf16<<<grid, block, 0, h->s>>>(dst, src, R, C);
 }
@@ -421,14 +450,16 @@ static void forward(pdlp_mlp_ctx* h, const float* X, const int* idx, int rows) {
   gemm(h, h->H2b, h->Wb[2], h->Y, nullptr, h->b[2], h->bp, h->out_p, h->hid, 0);
 }
 
-constexpr int kLossBlocks = 148;
+constexpr int kLossColBlocks = 8;   // column blocks of k_mlp_loss_grad per row
 
 // Backward of the MSE loss against rows idx of T (device, n_out columns); gradients
 // in h->gW / h->gb; the loss (sum of squares / (2 rows n_out)) goes to the device
 // double *loss_dev.  Nothing is waited for.
 static void backward_async(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows, double* loss_dev) {
-  const int nb = kLossBlocks;
-  k_mlp_loss_grad<<<nb, 256, 0, h->s>>>(h->Y, h->bp, h->out_p, T, h->n_out, idx, rows, h->dY, h->dYb, h->part);
+  const int nb = kLossColBlocks * h->bp;
+  const float inv = (float)(1.0 / ((double)rows * h->n_out));
+  k_mlp_loss_grad<<<dim3(kLossColBlocks, h->bp), 256, 0, h->s>>>(h->Y, h->out_p, T, h->n_out, idx, rows, inv, h->dY,
+                                                                 h->dYb, h->part);
   transpose(h, h->dYTb, h->dYb, h->bp, h->out_p);
   transpose(h, h->H2Tb, h->H2b, h->bp, h->hid);
   transpose(h, h->H1Tb, h->H1b, h->bp, h->hid);
@@ -450,15 +481,16 @@ static void backward_async(pdlp_mlp_ctx* h, const float* T, const int* idx, int 
   transpose(h, h->dZ1Tb, h->dZ1b, h->bp, h->hid);
   gemm(h, h->dZ1Tb, h->XTb, h->gW[0], nullptr, nullptr, h->hid, h->in_p, h->bp, 0);
   k_mlp_colsum<<<(h->hid + 255) / 256, 256, 0, h->s>>>(h->gb[0], h->dZ1, h->bp, h->hid);
-  k_mlp_loss_total<<<1, 32, 0, h->s>>>(h->part, nb, 2.0 * rows * h->n_out, loss_dev);
+  k_mlp_loss_total<<<1, 256, 0, h->s>>>(h->part, nb, 2.0 * rows * h->n_out, loss_dev);
   mlp_ck(cudaGetLastError(), "backward");
 }
 
 // backward_async, then the loss read back (one wait).
 static double backward(pdlp_mlp_ctx* h, const float* T, const int* idx, int rows) {
-  backward_async(h, T, idx, rows, h->part + kLossBlocks);
+  double* slot = h->part + (size_t)kLossColBlocks * h->bp;
+  backward_async(h, T, idx, rows, slot);
   double L = 0.0;
-  mlp_ck(cudaMemcpyAsync(&L, h->part + kLossBlocks, sizeof(double), cudaMemcpyDeviceToHost, h->s), "loss copy");
+  mlp_ck(cudaMemcpyAsync(&L, slot, sizeof(double), cudaMemcpyDeviceToHost, h->s), "loss copy");
   mlp_ck(cudaStreamSynchronize(h->s), "backward sync");
   return L;
 }
@@ -526,7 +558,7 @@ int pdlp_mlp_create(pdlp_mlp* out, int32_t n_in, int32_t hidden, int32_t n_out, 
     for (float** p : {&h->H1, &h->H2, &h->dH2, &h->dZ2, &h->dH1, &h->dZ1}) *p = mlp_alloc<float>(h, bh);
     h->Y = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
     h->dY = mlp_alloc<float>(h, (int64_t)h->bp * h->out_p);
-    h->part = mlp_alloc<double>(h, kLossBlocks + 1);   // per-block loss sums, then the loss
+    h->part = mlp_alloc<double>(h, (size_t)kLossColBlocks * h->bp + 1);   // per-block loss sums, then the loss
     h->err = mlp_alloc<int>(h, 1);
     // the split-K workspace of the largest split product of a training step
     const int shapes[8][3] = {{h->bp, h->hid, h->in_p},  {h->bp, h->hid, h->hid},  {h->bp, h->out_p, h->hid},
