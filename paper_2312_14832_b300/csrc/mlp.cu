@@ -348,6 +348,23 @@ __global__ void k_mlp_colsum(float* db, const float* dZ, int R, int C) {
   db[c] = s;
 }
 
+// AdamW on one tensor: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// w -= lr (m_hat / (sqrt(v_hat) + eps) + wd w); wb (if not null) receives the BF16 copy
+// of the new w that the next forward products read.
+__global__ void k_mlp_adamw(float* w, float* m, float* v, const float* g, int64_t n, float lr, float wd, float b1,
+                            float b2, float c1, float c2, float eps, __nv_bfloat16* wb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wn = w[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+    w[i] = wn;
+    if (wb) wb[i] = __float2bfloat16_rn(wn);
+  }
+}
+
 // Loss of one minibatch from the per-block partial sums of k_mlp_loss_grad (one block of
 // 256 threads: thread t adds part[t], part[t + 256], ... in order, then a fixed tree):
 // out = sum(part[0..nb)) / denom, denom = 2 rows n_out.
