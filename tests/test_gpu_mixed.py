@@ -142,3 +142,43 @@ def test_mcf_to_1e4_with_either_storage(pk, values):
     assert r["status"] == pk.OPTIMAL and r["fp32_iters"] == r["iters"]
     check_point(lp, r["x"], r["y"], 1e-4)
     assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-3 * abs(ref["primal_obj"])
+
+
+def test_sign_bits_box_only(pk):
+    """An LP with no rows has no entry other than +-1: sign bits are chosen, and the FP32
+    iterations solve the box LP like the oracle."""
+    lp = lpgen.box_only(3, n=100, free_frac=0.2)
+    ref = oracle.solve(lp, tol=1e-6, max_iter=100000)
+    with pk.Solver.from_lp(lp, precision=pk.MIXED) as s:
+        assert s.info()["mixed_values"] == 2
+        r = s.solve(tol=1e-6, max_iter=100000)
+    assert r["status"] == pk.OPTIMAL
+    err = np.max(np.abs(r["x"] - ref["x"])) / max(1.0, np.max(np.abs(ref["x"])))
+    assert err <= 1e-5
+
+
+def test_sign_bits_with_explicit_zero_entries(pk):
+    """Explicit zero entries (stored pairs with value 0) leave the LP unchanged and still
+    qualify for sign bits: a padding-like slot that gathers a zero.  The MCF LP with 500
+    such entries added solves to 1e-4 by the oracle's evaluation, objective within 1e-3
+    of the oracle's solve of the same stored LP."""
+    base = lpgen.mcf(3, nodes=1000, arcs=5000)
+    m, n = base["m"], base["n"]
+    rp, ci, v = base["row_ptr"], base["col_idx"], base["val"]
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp))
+    rng = np.random.default_rng(0)
+    zr, zc = rng.integers(0, m, 500), rng.integers(0, n, 500)
+    present = set(zip(rows.tolist(), ci.tolist()))
+    keep = np.array([(a, b) not in present for a, b in zip(zr.tolist(), zc.tolist())])
+    zr, zc = zr[keep], zc[keep]
+    lp = dict(base)
+    lp["row_ptr"], lp["col_idx"], lp["val"] = lpgen.csr_from_coo(
+        m, n, np.concatenate([rows, zr]), np.concatenate([ci.astype(np.int64), zc]),
+        np.concatenate([v, np.zeros(zr.shape[0])]))
+    assert lp["row_ptr"][-1] == rp[-1] + zr.shape[0] and np.count_nonzero(lp["val"] == 0.0) == zr.shape[0]
+    ref = oracle.solve(lp, tol=1e-4, scaling=1)
+    r, info = _solve_mixed(pk, lp, 1, 0, tol=1e-4)
+    assert info["mixed_values"] == 2
+    assert r["status"] == pk.OPTIMAL
+    check_point(lp, r["x"], r["y"], 1e-4)
+    assert abs(r["primal_obj"] - ref["primal_obj"]) <= 1e-3 * abs(ref["primal_obj"])
