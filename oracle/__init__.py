@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("scaling", C.c_int32), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
                 ("beta_art", C.c_double), ("step_scale", C.c_double), ("omega_theta", C.c_double),
                 ("ruiz_iters", C.c_int32), ("power_iters", C.c_int32), ("eta", C.c_double),
-                ("omega0", C.c_double), ("step_rule", C.c_int32), ("pad0", C.c_int32)]
+                ("omega0", C.c_double), ("step_rule", C.c_int32), ("reject_cap", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -107,7 +107,7 @@ def lib():
 def default_params(**kw) -> Params:
     p = Params(tol=1e-4, max_iter=100_000_000, check_every=64, scaling=0, beta_suff=0.2,
                beta_nec=0.8, beta_art=0.36, step_scale=0.9, omega_theta=0.5, ruiz_iters=10,
-               power_iters=100, eta=0.0, omega0=0.0)
+               power_iters=100, eta=0.0, omega0=0.0, reject_cap=64)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

@@ -30,7 +30,9 @@
  *    (eta_max = +inf when dy' K dx = 0), and either way the next eta is
  *      min((1 - (s+1)^-0.3) eta_max, (1 + (s+1)^-0.6) eta),
  *    s = 1 + the number of steps accepted so far.  A rejected attempt leaves the
- *    point unchanged; after 64 rejections in a row the attempt is accepted.  The
+ *    point unchanged; after reject_cap rejections in a row (64 by default; a
+ *    safeguard of this implementation, the cited rule has none) the attempt is
+ *    accepted.  The
  *    first eta is 1 / max_ij |K_ij| (of the scaled K; 1 when K = 0).  The average
  *    of an inner loop is weighted by the accepted steps' eta.  Iteration counts
  *    (k, t, max_iter, check_every) count attempts.
@@ -74,7 +76,9 @@ typedef struct {
   double eta;          /* > 0: use this step size instead of the power-iteration rule */
   double omega0;       /* > 0: use this initial primal weight */
   int32_t step_rule;   /* 0 constant eta, 1 adaptive (PDLP) */
-  int32_t pad0;
+  int32_t reject_cap;  /* adaptive rule: an attempt is kept after this many rejections in a
+                          row (a safeguard of this implementation, 64 by default; 0 keeps
+                          every attempt) */
 } orc_params;
 
 typedef struct {
@@ -465,7 +469,7 @@ int orc_solve(int64_t m, int64_t n, int64_t m1, const int64_t* rp, const int32_t
         double sidx = (double)(accepted + 2);   /* s + 1, s = accepted + 1 */
         double e1 = (1.0 - pow(sidx, -0.3)) * emax, e2 = (1.0 + pow(sidx, -0.6)) * eta;
         double enext = e1 < e2 ? e1 : e2;
-        if (eta <= emax || rejects >= 64) {
+        if (eta <= emax || rejects >= P->reject_cap) {
           memcpy(x, xn, nb);
           memcpy(y, yn, mb);
           for (int64_t j = 0; j < n; ++j) sx[j] += eta * x[j];

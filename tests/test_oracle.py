@@ -545,6 +545,32 @@ def test_adaptive_first_attempt_by_hand():
     assert r["eta"] == pytest.approx(want, rel=1e-14)
 
 
+def test_adaptive_rejection_and_cap_by_hand():
+    """The rejection branch and the rejection cap on min x s.t. x = 3 (x free), worked by
+    hand from the warm start x = 5, y = 0 with omega = 1 and eta = 3 (tau = sigma = 3):
+    the attempt is x' = 5 - 3 * 1 = 2, y' = 3 * (3 - (2 * 2 - 5)) = 12, so dx = -3,
+    dy = 12, dy' K dx = -36 and eta_max = (9 + 144) / 72 = 2.125 < 3.  With the default
+    cap (64) the attempt is rejected: the point stays (5, 0), nothing is accepted, and the
+    next eta is min((1 - 2^-0.3) * 2.125, (1 + 2^-0.6) * 3) = (1 - 2^-0.3) * 2.125 (s = 1,
+    no step accepted yet).  With cap 0 the same attempt is kept: the point is (2, 12).
+    This fails if a rejection moves the point, if the cap comparison is inverted or
+    compares against the wrong count, or if the step size after a rejection is taken
+    from the wrong branch."""
+    kw = dict(tol=1e-12, max_iter=1, check_every=1, eta=3.0, omega0=1.0, scaling=0, step_rule=1)
+    r = oracle.solve(_lp1x1(), x0=[5.0], y0=[0.0], **kw)
+    assert r["accepted"] == 0
+    np.testing.assert_array_equal(r["x_cur"], [5.0])
+    np.testing.assert_array_equal(r["y_cur"], [0.0])
+    want = (1.0 - 2.0 ** -0.3) * 2.125
+    assert want < (1.0 + 2.0 ** -0.6) * 3.0
+    assert r["eta"] == pytest.approx(want, rel=1e-14)
+    r0 = oracle.solve(_lp1x1(), x0=[5.0], y0=[0.0], reject_cap=0, **kw)
+    assert r0["accepted"] == 1
+    np.testing.assert_allclose(r0["x_cur"], [2.0], rtol=1e-15)
+    np.testing.assert_allclose(r0["y_cur"], [12.0], rtol=1e-15)
+    assert r0["eta"] == pytest.approx(want, rel=1e-14)   # the next step size is the same either way
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_adaptive_tiny_lp_matches_vertex_enumeration(seed):
     lp = lpgen.tiny_lp(seed, n=5, m1=1, m2=3)
