@@ -119,8 +119,8 @@ typedef struct {
                               eta <= (omega |dx|^2 + |dy|^2 / omega) / (2 |dy' K dx|), and
                               the next eta is min((1 - (s+1)^-0.3) eta_max,
                               (1 + (s+1)^-0.6) eta), s = 1 + steps accepted; a rejected
-                              attempt leaves the point unchanged (after 64 rejections in a
-                              row the attempt is kept); first eta = 1 / max |K_ij| of the
+                              attempt leaves the point unchanged (after adaptive_reject_cap
+                              rejections in a row the attempt is kept); first eta = 1 / max |K_ij| of the
                               scaled K (or params.eta); averages are weighted by the kept
                               steps' eta; iteration counts (max_iter, check_every, iters)
                               count attempts.  Not with PDLP_MIXED; not for batches.       */
@@ -180,6 +180,10 @@ typedef struct {
                               (PDLP_EINVAL when an entry is not +1, -1 or 0).  The FP64
                               checks and the FP64 refinement use the FP64 values in every
                               case.                                                      */
+  int32_t adaptive_reject_cap; /* step_rule 1: an attempt is kept after this many rejections
+                              in a row (default 64; a safeguard of this implementation, the
+                              cited rule has none; 0 keeps every attempt).  Read by
+                              pdlp_solve from its params.                                */
 } pdlp_params;
 
 typedef struct {

@@ -23,7 +23,7 @@ class Params(C.Structure):
                 ("mixed_switch_tol", C.c_double), ("cluster_ctas", C.c_int32), ("resident", C.c_int32),
                 ("step_rule", C.c_int32), ("engine", C.c_int32), ("batch_tail_iters", C.c_int64),
                 ("host_layout", C.c_int32), ("spmv_stage", C.c_int32),
-                ("batch_tune", C.c_int32), ("mixed_values", C.c_int32)]
+                ("batch_tune", C.c_int32), ("mixed_values", C.c_int32), ("adaptive_reject_cap", C.c_int32)]
 
 
 class Result(C.Structure):

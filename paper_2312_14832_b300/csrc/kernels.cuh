@@ -38,7 +38,7 @@ struct DevState {
   int rejects, accept;
   double p3, p6;   // (s+1)^-0.3 and (s+1)^-0.6 for the next acceptance decision
   int suspended;   // batched solver: stopped at a check by its iteration slice, resumable
-  int pad_s;
+  int reject_cap;  // adaptive step rule: an attempt is kept after this many rejections in a row
   long long k32;   // batched mixed precision: iterations run in FP32
 };
 
@@ -470,7 +470,8 @@ __global__ void __launch_bounds__(256) k_step_partial(const double* __restrict__
 // Acceptance test and next step size of the adaptive rule, after one attempt (one warp,
 // the kStepParts block sums added in a fixed order):
 //   eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy'K dx|)   (+inf when 0),
-//   accept when eta <= eta_max (or after 64 rejections in a row),
+//   accept when eta <= eta_max (or after reject_cap rejections in a row, 64 by default:
+//   a safeguard of this implementation, the cited rule has none),
 //   next eta = min((1 - (s+1)^-0.3) eta_max, (1 + (s+1)^-0.6) eta), s = accepted + 1.
 __global__ void __launch_bounds__(32) k_step_decide(const double* __restrict__ parts, DevState* st) {
   if (st->done) return;
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(32) k_step_decide(const double* __restrict__ p
                                    : (w * dx2 + dy2 / w) / (2.0 * fabs(inter));
   const double e1 = (1.0 - st->p3) * emax, e2 = (1.0 + st->p6) * eta;
   const double enext = e1 < e2 ? e1 : e2;
-  const bool acc = eta <= emax || st->rejects >= 64;
+  const bool acc = eta <= emax || st->rejects >= st->reject_cap;
   st->accept = acc ? 1 : 0;
   if (acc) {
     st->pw = eta;

@@ -717,6 +717,7 @@ static void check_params(const pdlp_params& P) {
   if (P.engine < 0 || P.engine > 2) invalid("engine must be 0, 1 or 2");
   if (P.host_layout < 0 || P.host_layout > 1) invalid("host_layout must be 0 or 1");
   if (P.mixed_values < 0 || P.mixed_values > 2) invalid("mixed_values must be 0, 1 or 2");
+  if (P.adaptive_reject_cap < 0) invalid("adaptive_reject_cap must be >= 0");
 }
 
 // True when pred(i) holds for every i in [0, n) (checked in parallel ranges).
@@ -1465,6 +1466,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
                       pdlp_result* res, double* x_out, double* y_out) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   if (sp.step_rule < 0 || sp.step_rule > 1) invalid("step_rule must be 0 or 1");
+  if (sp.adaptive_reject_cap < 0) invalid("adaptive_reject_cap must be >= 0");
   const bool adaptive = sp.step_rule == 1;
   if (adaptive && h->p.precision == PDLP_MIXED) invalid("the adaptive step rule runs in FP64 only");
   if (adaptive) ensure_adaptive_buffers(h);
@@ -1527,6 +1529,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   s0.tau = eta0 / w0;
   s0.sigma = eta0 * w0;
   s0.kkt_prev = std::numeric_limits<double>::infinity();
+  s0.reject_cap = sp.adaptive_reject_cap;
   CK(cudaMemcpyAsync(h->st, &s0, sizeof(DevState), cudaMemcpyHostToDevice, h->s));
   launch_rows<OpSpmv>(h, h->K, h->x, EpiStore{h->kxp, 0, 1.0}, h->st);
   launch_rows<OpSpmv>(h, h->Kt, h->y, EpiStore{h->g_c, 0, 1.0}, h->st);
@@ -2474,6 +2477,7 @@ void pdlp_default_params(pdlp_params* p) {
   p->spmv_batch = 0;
   p->precision = PDLP_FP64;
   p->mixed_switch_tol = 0.0;
+  p->adaptive_reject_cap = 64;
 }
 
 int pdlp_setup(pdlp_handle* out, int64_t m, int64_t n, int64_t m1, const int64_t* row_ptr,

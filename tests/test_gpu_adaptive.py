@@ -111,3 +111,44 @@ def test_adaptive_rejects_mixed_precision(pk):
     with pk.Solver.from_lp(lp, precision=pk.MIXED) as s:
         with pytest.raises(pk.SolverError):
             s.solve(tol=1e-4, step_rule=1)
+
+
+def _lp1x1():
+    """min x  s.t.  x = 3, x free."""
+    return dict(m=1, n=1, m1=1, row_ptr=np.array([0, 1]), col_idx=np.array([0], dtype=np.int32),
+                val=np.array([1.0]), c=np.array([1.0]), q=np.array([3.0]), l=np.array([-np.inf]),
+                u=np.array([np.inf]))
+
+
+@pytest.mark.parametrize("cap", [64, 0])
+def test_rejection_cap_on_the_worked_case(pk, cap):
+    """The oracle's hand-worked rejected attempt (x = 5, y = 0, eta = 3, omega = 1 on
+    min x s.t. x = 3: eta_max = 2.125 < 3): rejected with the default cap (point
+    unchanged), kept with cap 0 (point (2, 12)); the same on the GPU, with the next eta."""
+    lp = _lp1x1()
+    ref = oracle.solve(lp, x0=[5.0], y0=[0.0], tol=1e-12, max_iter=1, check_every=1, eta=3.0, omega0=1.0,
+                       scaling=0, step_rule=1, reject_cap=cap)
+    with pk.Solver.from_lp(lp, step_rule=1, eta=3.0, check_every=1, engine=1) as s:
+        r = s.solve(x0=np.array([5.0]), y0=np.array([0.0]), omega0=1.0, tol=1e-12, max_iter=1,
+                    adaptive_reject_cap=cap)
+        xc, yc = s.iterate(0)
+    assert r["accepted"] == ref["accepted"] == (1 if cap == 0 else 0)
+    np.testing.assert_array_equal(xc, ref["x_cur"])
+    np.testing.assert_array_equal(yc, ref["y_cur"])
+    assert r["eta"] == pytest.approx(ref["eta"], rel=1e-14)
+
+
+@pytest.mark.parametrize("cap", [0, 1, 2])
+def test_small_rejection_caps_follow_the_oracle(pk, cap):
+    """Caps small enough to be reached on an LP that rejects attempts: 64 attempts with
+    the same kept steps and restarts as the oracle and the point within 1e-10."""
+    lp = lpgen.planted_small(2)
+    ref = oracle.solve(lp, tol=0.0, max_iter=64, scaling=1, step_rule=1, reject_cap=cap)
+    with pk.Solver.from_lp(lp, scaling=1, step_rule=1) as s:
+        r = s.solve(tol=0.0, max_iter=64, adaptive_reject_cap=cap)
+    assert r["accepted"] == ref["accepted"]
+    if cap == 0:
+        assert r["accepted"] == 64
+    assert r["restarts"] == ref["restarts"]
+    close_rel(r["x"], ref["x"], 1e-10)
+    close_rel(r["y"], ref["y"], 1e-10)

@@ -16,7 +16,8 @@ launched per iteration as CUDA graphs).
 
 The other full-size workloads, each in the configuration bench.py times:
   * the multicommodity-flow LP (n = 8e6, 2.4e7 nonzeros): one check interval in FP64
-    element by element against the oracle; MIXED (FP32 iterations, FP64 checks) to 1e-4,
+    element by element against the oracle (1e-10), and in FP32 with the +-1 entries as
+    sign bits and as value copies (1e-4); MIXED (FP32 iterations, FP64 checks) to 1e-4,
     the returned point re-checked by the oracle's KKT routine, the objective within 1e-6
     of the FP64 solve;
   * the 4096-LP batch (5.5e8 nonzeros): the FP64 two-stage solve and the MIXED solve to
@@ -133,6 +134,16 @@ def test_fullsize_mcf(pk):
         xc, yc = s.iterate(0)
     for got, want in ((xc, ref["x_cur"]), (yc, ref["y_cur"])):
         assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    # the FP32 iterations over the same interval, with the +-1 entries as sign bits (the
+    # automatic choice here) and as FP32 value copies: within FP32 rounding of the oracle
+    for values, storage in ((0, 2), (1, 1)):
+        with pk.Solver.from_lp(lp, scaling=1, eta=ETA, precision=pk.MIXED, mixed_values=values) as s:
+            assert s.info()["mixed_values"] == storage
+            r = s.solve(tol=0.0, max_iter=iters, mixed_switch_tol=1e-30)
+            assert r["fp32_iters"] == iters
+            xc, yc = s.iterate(0)
+        for got, want in ((xc, ref["x_cur"]), (yc, ref["y_cur"])):
+            assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max(), (storage, np.abs(got - want).max())
     with pk.Solver.from_lp(lp, scaling=1) as s:
         r64 = s.solve(tol=1e-4)
     with pk.Solver.from_lp(lp, scaling=1, precision=pk.MIXED) as s:
