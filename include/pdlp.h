@@ -330,6 +330,35 @@ int pdlp_get_info(pdlp_handle h, pdlp_info* info);
  * on the handle's stream around every launch. */
 int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double* ms_dual);
 
+/* ---------------------------------------------------------------- checkpoint / resume
+ * (no counterpart in the paper).  A single-LP FP64 solve that ran the kernels per
+ * iteration (engine 1, or engine 0 when the persistent engine was not chosen) can be saved
+ * after it returns and continued later, on this handle or on another handle set up from
+ * the same LP with the same setup parameters:
+ *   pdlp_state_size(h)              bytes of the state of h's last solve (< 0: error code);
+ *   pdlp_get_state(h, buf, size)    copies it into the caller's host buffer (size must be
+ *                                   pdlp_state_size(h)); opaque, for this build only;
+ *   pdlp_solve_resume(h, p, state, size, res, x_out, y_out)
+ *                                   loads `state` (host bytes from pdlp_get_state; NULL:
+ *                                   continue from h's own last solve), repeats the check that
+ *                                   ended it as an ordinary check (restart rule and primal
+ *                                   weight of Section 2), then runs check intervals until
+ *                                   p->max_iter iterations in total or termination; results as
+ *                                   pdlp_solve.  The state holds x, y, their running sums, the
+ *                                   restart anchor, K x and the scalar state (k, t, omega, eta,
+ *                                   KKT anchors, counters, the adaptive rule's state), the
+ *                                   restart iterations and the per-check records.
+ * A solve that stopped at an iteration limit that is a multiple of check_every, resumed
+ * with the same parameters and a larger max_iter, gives the uninterrupted solve's iterates
+ * bit for bit (the same SpMV schedule on both handles).  A solve stopped by its time limit
+ * is repeated-checked once more on resume, so it continues correctly but not bit for bit.
+ * Errors: PDLP_EINVAL for batch handles, MIXED handles, a last solve on the persistent
+ * engine, engine 2, a buffer of the wrong size, or a state of other LP sizes.  */
+int64_t pdlp_state_size(pdlp_handle h);
+int pdlp_get_state(pdlp_handle h, void* buf, int64_t size);
+int pdlp_solve_resume(pdlp_handle h, const pdlp_params* p, const void* state, int64_t size, pdlp_result* res,
+                      double* x_out, double* y_out);
+
 /* ---------------------------------------------------------------- batches
  * Many independent LPs solved by one persistent kernel launch: each team of the launch
  * (one CTA, or a thread-block cluster of up to 16 CTAs that split the LP's rows and

@@ -130,6 +130,34 @@ class Solver:
         out["x"], out["y"] = x, y
         return out
 
+    def get_state(self) -> bytes:
+        """The state of the last solve (pdlp_get_state): opaque bytes for resume()."""
+        size = self._lib.pdlp_state_size(self._h)
+        self._check(size)
+        buf = C.create_string_buffer(int(size))
+        self._check(self._lib.pdlp_get_state(self._h, buf, int(size)))
+        return buf.raw
+
+    def resume(self, state=None, want_point=True, **overrides) -> dict:
+        """Continues the last solve of this handle, or the one saved in `state`
+        (pdlp_solve_resume), until max_iter iterations in total or termination."""
+        p = _lib.Params()
+        C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
+        for k, v in overrides.items():
+            if not hasattr(p, k):
+                raise KeyError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        buf = C.create_string_buffer(bytes(state), len(state)) if state is not None else None
+        x = self._out(self.n) if want_point else None
+        y = self._out(self.m) if want_point else None
+        r = _lib.Result()
+        self._check(self._lib.pdlp_solve_resume(self._h, C.byref(p), buf, len(state) if state is not None else 0,
+                                                C.byref(r), self._ptr(x),
+                                                self._ptr(y) if y is not None and self.m else None))
+        out = {f: getattr(r, f) for f, _ in _lib.Result._fields_}
+        out["x"], out["y"] = x, y
+        return out
+
     def iterate(self, which=0):
         """which: 0 current iterate, 1 average of the inner loop, 2 restart anchor."""
         x, y = self._out(self.n), self._out(self.m)

@@ -81,6 +81,9 @@ SIGNATURES = {
                                    C.POINTER(Params)]),
     "pdlp_batch_solve": (C.c_int, [_vp, C.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _vp]),
     "pdlp_batch_get_restarts": (C.c_int64, [_vp, _i64, _vp, _i64]),
+    "pdlp_state_size": (C.c_int64, [_vp]),
+    "pdlp_get_state": (C.c_int, [_vp, _vp, _i64]),
+    "pdlp_solve_resume": (C.c_int, [_vp, C.POINTER(Params), _vp, _i64, C.POINTER(Result), _vp, _vp]),
     "pdlp_tc_gemm": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
     "pdlp_tc_gemm_split": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "pdlp_tc_gemm_wait_selftest": (C.c_int, [_vp, _vp, _vp, _i64, _vp]),

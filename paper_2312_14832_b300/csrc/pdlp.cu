@@ -120,6 +120,7 @@ struct pdlp_ctx {
   bool broken = false;    // after such a failure the handle refuses further calls
   int64_t last_ncheck = 0, last_nrestart = 0;
   bool solved = false;
+  bool resumable = false;   // the last solve ran the FP64 kernels per iteration (pdlp_get_state)
   cudaGraphExec_t g_full = nullptr, g_rem = nullptr;
   int g_full_len = -1, g_rem_len = -1;
   std::vector<cudaEvent_t> timing_events;
@@ -1462,8 +1463,19 @@ static void ensure_adaptive_buffers(pdlp_ctx* h) {
   h->part_s = dalloc<double>(h, 3 * kStepParts);
 }
 
+// Continuing a solve (pdlp_solve_resume): the handle's device state is the one its last
+// solve ended with, or one loaded by load_state; the check that ended it is repeated as
+// an ordinary check, then the intervals go on from its iteration count.
+__global__ void k_resume_state(DevState* st, int reject_cap) {
+  st->done = 0;
+  st->status = 0;
+  st->final_force = 0;
+  if (st->ncheck > 0) st->ncheck -= 1;
+  st->reject_cap = reject_cap;
+}
+
 static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, const double* y0, double omega0,
-                      pdlp_result* res, double* x_out, double* y_out) {
+                      pdlp_result* res, double* x_out, double* y_out, bool resume = false) {
   if (sp.check_every < 1 || sp.max_iter < 0 || !(sp.tol >= 0.0)) invalid("bad solve parameters");
   if (sp.step_rule < 0 || sp.step_rule > 1) invalid("step_rule must be 0 or 1");
   if (sp.adaptive_reject_cap < 0) invalid("adaptive_reject_cap must be >= 0");
@@ -1475,8 +1487,8 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   {
     // the persistent engine: automatic for a small LP with the constant step in FP64 and
     // no time limit, or when asked for
-    const bool can = h->small_engine && !adaptive && h->p.precision == PDLP_FP64;
-    if (sp.engine == 2 && !can) invalid("engine 2 needs a small FP64 LP with the constant step");
+    const bool can = h->small_engine && !adaptive && h->p.precision == PDLP_FP64 && !resume;
+    if (sp.engine == 2 && !can) invalid("engine 2 needs a small FP64 LP with the constant step (and no resume)");
     if (can && (sp.engine == 2 || (sp.engine == 0 && !std::isfinite(sp.time_limit_s)))) {
       pdlp_params bp = sp;
       bp.resident = 0;
@@ -1502,6 +1514,20 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   h->dp_host.restart_cap = h->restart_cap;
   CK(cudaMemcpyAsync(h->dp, &h->dp_host, sizeof(DevParams), cudaMemcpyHostToDevice, h->s));
 
+  int64_t k0 = 0;   // iterations already done (resume)
+  const bool mixed = h->p.precision == PDLP_MIXED;
+  if (resume) {
+    if (mixed) invalid("resume: FP64 handles only");
+    CK(cudaEventRecord(h->ev_t0, h->s));
+    k_resume_state<<<1, 1, 0, h->s>>>(h->st, sp.adaptive_reject_cap);
+    DevState cur{};
+    CK(cudaMemcpyAsync(&cur, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    k0 = cur.k;
+    enqueue_check(h, 0, k0 >= sp.max_iter ? 1 : 0, adaptive);
+    launches += adaptive ? 10 : 9;
+    CKL("resume check");
+  } else {
   // initial point (Section 2: x in X, y in Y), anchor z^{0,0} = (x0, y0)
   const double* xs = nullptr;
   const double* ys = nullptr;
@@ -1540,7 +1566,6 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   k_kkt_partials<<<h->nb_rows + h->nb_cols, 256, 0, h->s>>>(kkt_inputs(h), h->st, h->part);
   k_decide<<<1, 256, 0, h->s>>>(h->part, h->nb_rows, h->nb_cols, h->st, h->dp, h->log, h->restarts, 1, 0);
   launches += 9;
-  const bool mixed = h->p.precision == PDLP_MIXED;
   if (mixed) {
     CK(cudaMemsetAsync(h->sx32, 0, sizeof(float) * np, h->s));
     CK(cudaMemsetAsync(h->sy32, 0, sizeof(float) * mp, h->s));
@@ -1549,14 +1574,18 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
     launches += 1;
   }
   CKL("solve init");
+  }
 
   const int L = sp.check_every;
-  const int64_t nfull = sp.max_iter / L;
-  const int rem = (int)(sp.max_iter % L);
+  const int64_t todo = std::max<int64_t>(0, sp.max_iter - k0);
+  const int64_t nfull = todo / L;
+  const int rem = (int)(todo % L);
   const int64_t nint = nfull + (rem > 0 ? 1 : 0);
   bool timed_out = false;
   DevState fin{};
-  if (nint == 0) {
+  if (nint == 0 && resume) {
+    // the repeated check was the last one
+  } else if (nint == 0) {
     enqueue_check(h, 0, 1, adaptive);
     launches += adaptive ? 9 : 8;
     CKL("final check");
@@ -1634,6 +1663,7 @@ static int solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0, cons
   h->last_ncheck = fin.ncheck;
   h->last_nrestart = fin.nrestart;
   h->solved = true;
+  h->resumable = !mixed;
 
   // returned point
   if (x_out || y_out) {
@@ -2444,6 +2474,7 @@ static int batch_solve_impl(pdlp_ctx* h, const pdlp_params& sp, const double* x0
     h->last_nrestart = h->hstate[0].nrestart;
   }
   h->solved = true;
+  h->resumable = false;
   return PDLP_OK;
 }
 
@@ -2522,6 +2553,128 @@ int pdlp_solve(pdlp_handle h, const pdlp_params* p, const double* x0, const doub
     if (h->is_batch) invalid("batch handle: use pdlp_batch_solve");
     pdlp_params sp = p ? *p : h->p;
     return solve_impl(h, sp, x0, y0, omega0, res, x_out, y_out);
+  });
+}
+
+// ------------------------------------------------------------------ solve state
+
+namespace pdlp {
+
+// Layout of a saved solve state (host bytes, this build only): the header, the device
+// state record, x, y, their running sums, the restart anchor and K x (internal order,
+// scaled, padded lengths), then the restart iterations and the per-check records kept.
+struct StateHeader {
+  char magic[8];
+  int64_t version, m, n, npad, mpad, nnz, state_bytes, nrestart, nlog;
+};
+constexpr char kStateMagic[8] = {'P', 'D', 'L', 'P', 'S', 'T', 'A', 'T'};
+constexpr int64_t kStateVersion = 1;
+
+static int64_t state_size(const pdlp_ctx* h, int64_t nrestart, int64_t nlog) {
+  return (int64_t)sizeof(StateHeader) + (int64_t)sizeof(DevState) + 8 * (3 * h->npad + 4 * h->mpad) +
+         8 * nrestart + (int64_t)sizeof(CheckRecord) * nlog;
+}
+
+static void state_counts(const pdlp_ctx* h, int64_t* nrestart, int64_t* nlog) {
+  *nrestart = std::min<int64_t>(h->last_nrestart, h->restart_cap);
+  *nlog = std::min<int64_t>(h->last_ncheck, h->log_cap);
+}
+
+// The vectors of a state in their order in the blob, with their lengths.
+static std::vector<std::pair<double*, int64_t>> state_vectors(pdlp_ctx* h) {
+  return {{h->x, h->npad}, {h->sx, h->npad}, {h->xa, h->npad}, {h->y, h->mpad},
+          {h->sy, h->mpad}, {h->ya, h->mpad}, {h->kxp, h->mpad}};
+}
+
+static void load_state(pdlp_ctx* h, const void* state, int64_t size) {
+  if (!state || size < (int64_t)sizeof(StateHeader)) invalid("resume: state too small");
+  StateHeader hd;
+  std::memcpy(&hd, state, sizeof(hd));
+  if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != kStateVersion)
+    invalid("resume: not a solve state of this library");
+  if (hd.m != h->m || hd.n != h->n || hd.npad != h->npad || hd.mpad != h->mpad || hd.nnz != h->nnz ||
+      hd.state_bytes != (int64_t)sizeof(DevState))
+    invalid("resume: the state belongs to an LP of other sizes");
+  if (hd.nrestart < 0 || hd.nrestart > h->restart_cap || hd.nlog < 0 || hd.nlog > h->log_cap)
+    invalid("resume: restart or log counts out of range for this handle");
+  if (size != state_size(h, hd.nrestart, hd.nlog)) invalid("resume: state size does not match its header");
+  const char* p = static_cast<const char*>(state) + sizeof(StateHeader);
+  CK(cudaMemcpyAsync(h->st, p, sizeof(DevState), cudaMemcpyHostToDevice, h->s));
+  p += sizeof(DevState);
+  for (auto& v : state_vectors(h)) {
+    CK(cudaMemcpyAsync(v.first, p, 8 * (size_t)v.second, cudaMemcpyHostToDevice, h->s));
+    p += 8 * v.second;
+  }
+  if (hd.nrestart > 0) CK(cudaMemcpyAsync(h->restarts, p, 8 * (size_t)hd.nrestart, cudaMemcpyHostToDevice, h->s));
+  p += 8 * hd.nrestart;
+  if (hd.nlog > 0) CK(cudaMemcpyAsync(h->log, p, sizeof(CheckRecord) * (size_t)hd.nlog, cudaMemcpyHostToDevice, h->s));
+  CK(cudaStreamSynchronize(h->s));   // the caller's buffer may be released after return
+}
+
+}  // namespace pdlp
+
+int64_t pdlp_state_size(pdlp_handle h) {
+  if (!h) return PDLP_EINVAL;
+  int64_t out = 0;
+  const int rc = guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle");
+    if (!h->solved || !h->resumable) invalid("no resumable solve on this handle (FP64, engine 1)");
+    int64_t nr = 0, nl = 0;
+    state_counts(h, &nr, &nl);
+    out = state_size(h, nr, nl);
+    return PDLP_OK;
+  });
+  return rc == PDLP_OK ? out : rc;
+}
+
+int pdlp_get_state(pdlp_handle h, void* buf, int64_t size) {
+  return guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle");
+    if (!h->solved || !h->resumable) invalid("no resumable solve on this handle (FP64, engine 1)");
+    int64_t nr = 0, nl = 0;
+    state_counts(h, &nr, &nl);
+    if (!buf || size != state_size(h, nr, nl)) invalid("buffer size must be pdlp_state_size(h)");
+    StateHeader hd;
+    std::memcpy(hd.magic, kStateMagic, 8);
+    hd.version = kStateVersion;
+    hd.m = h->m;
+    hd.n = h->n;
+    hd.npad = h->npad;
+    hd.mpad = h->mpad;
+    hd.nnz = h->nnz;
+    hd.state_bytes = (int64_t)sizeof(DevState);
+    hd.nrestart = nr;
+    hd.nlog = nl;
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    CK(cudaMemcpyAsync(p, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->s));
+    p += sizeof(DevState);
+    for (auto& v : state_vectors(h)) {
+      CK(cudaMemcpyAsync(p, v.first, 8 * (size_t)v.second, cudaMemcpyDeviceToHost, h->s));
+      p += 8 * v.second;
+    }
+    if (nr > 0) CK(cudaMemcpyAsync(p, h->restarts, 8 * (size_t)nr, cudaMemcpyDeviceToHost, h->s));
+    p += 8 * nr;
+    if (nl > 0) CK(cudaMemcpyAsync(p, h->log, sizeof(CheckRecord) * (size_t)nl, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return PDLP_OK;
+  });
+}
+
+int pdlp_solve_resume(pdlp_handle h, const pdlp_params* p, const void* state, int64_t size, pdlp_result* res,
+                      double* x_out, double* y_out) {
+  return guarded(h, [&]() {
+    if (h->is_batch) invalid("batch handle");
+    pdlp_params sp = p ? *p : h->p;
+    if (sp.engine == 2) invalid("resume runs the kernels per iteration (engine 0 or 1)");
+    if (h->p.precision != PDLP_FP64) invalid("resume: FP64 handles only");
+    if (state) {
+      load_state(h, state, size);
+    } else if (!h->solved || !h->resumable) {
+      invalid("no resumable solve on this handle (FP64, engine 1) and no state given");
+    }
+    return solve_impl(h, sp, nullptr, nullptr, 0.0, res, x_out, y_out, true);
   });
 }
 
