@@ -2,7 +2,7 @@
 // device allocation (declaration and contract in include/pdlp.h).
 //
 // Each thread takes a fixed run of kNoallocPerThread consecutive nonzeros and
-// accumulates them with FMA.  A row that ends inside the run and also started
+// accumulates them with FMA (read through shared memory, see k_noalloc_runs).  A row that ends inside the run and also started
 // inside it is written straight to y.  A row that crosses a run boundary leaves
 // partial sums: the run where it starts (or any run it passes through) keeps a
 // "tail" partial, the run where it ends keeps a "head" partial.  A second kernel
@@ -59,33 +59,87 @@ __device__ inline int64_t row_of(const int64_t* row_ptr, int64_t m, int64_t a) {
   return lo;
 }
 
-__global__ void k_noalloc_runs(int64_t m, int64_t nnz, const int64_t* __restrict__ row_ptr,
-                               const int32_t* __restrict__ col, const double* __restrict__ val,
-                               const double* __restrict__ x, double* __restrict__ y, unsigned char* scratch,
-                               int64_t runs) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= runs) return;
-  RunCarry cv = carry_view(scratch, runs);
+// One block of kRunsPerBlock threads takes kRunsPerBlock consecutive runs (a contiguous
+// range of nonzeros).  The range is read in kPhases phases of kPhaseLen nonzeros per run:
+// first the whole block loads the phase's values and column indices (each run's piece is
+// kPhaseLen consecutive entries, so a warp's loads cover whole 32-byte sectors) and
+// gathers x at those columns, every load independent of the others, into shared memory;
+// then each thread walks its own piece in order, with the FMAs and row bookkeeping of a
+// sequential run.  The arithmetic per run (one FMA per nonzero in index order) is the
+// same as walking the run straight from global memory.
+constexpr int kRunsPerBlock = 256;
+constexpr int kPhaseLen = 8;
+constexpr int kPhases = (int)(kNoallocPerThread / kPhaseLen);
+constexpr int kPieceStride = kPhaseLen + 1;   // shared-memory stride of a run's piece (no bank conflicts)
+
+__global__ void __launch_bounds__(kRunsPerBlock) k_noalloc_runs(int64_t m, int64_t nnz,
+                                                                const int64_t* __restrict__ row_ptr,
+                                                                const int32_t* __restrict__ col,
+                                                                const double* __restrict__ val,
+                                                                const double* __restrict__ x,
+                                                                double* __restrict__ y, unsigned char* scratch,
+                                                                int64_t runs) {
+  __shared__ double sv[kRunsPerBlock * kPieceStride];
+  __shared__ double sx[kRunsPerBlock * kPieceStride];
+  const int64_t run0 = (int64_t)blockIdx.x * kRunsPerBlock;
+  const int64_t t = run0 + threadIdx.x;
+  const bool active = t < runs;
   const int64_t a = t * kNoallocPerThread;
-  const int64_t b = (a + kNoallocPerThread < nnz) ? a + kNoallocPerThread : nnz;
+  const int64_t b = active ? ((a + kNoallocPerThread < nnz) ? a + kNoallocPerThread : nnz) : a;
   int32_t head_row = -1, tail_row = -1;
   double head_val = 0.0, tail_val = 0.0;
-  int64_t r = row_of(row_ptr, m, a);
+  int64_t r = active ? row_of(row_ptr, m, a) : 0;
+  int64_t rend = (active && r < m) ? row_ptr[r + 1] : 0;   // end of row r
   double acc = 0.0;
-  for (int64_t k = a; k < b; ++k) {
-    acc = fma(val[k], x[col[k]], acc);
-    if (r < m && k + 1 == row_ptr[r + 1]) {   // row r ends here
-      if (row_ptr[r] >= a) {
-        y[r] = acc;
-      } else {
-        head_row = (int32_t)r;
-        head_val = acc;
+  for (int ph = 0; ph < kPhases; ++ph) {
+    // stage: entry j of run (run0 + q) in this phase is nonzero run0*64 + 64 q + 8 ph + j
+    int32_t c[kPhaseLen];
+    double v[kPhaseLen];
+#pragma unroll
+    for (int i = 0; i < kPhaseLen; ++i) {
+      const int idx = (int)threadIdx.x + i * kRunsPerBlock;
+      const int q = idx / kPhaseLen, j = idx % kPhaseLen;
+      const int64_t k = (run0 + q) * kNoallocPerThread + (int64_t)ph * kPhaseLen + j;
+      c[i] = -1;
+      v[i] = 0.0;
+      if (k < nnz) {
+        v[i] = __ldcs(val + k);
+        c[i] = __ldcs(col + k);
       }
-      acc = 0.0;
-      ++r;
-      while (r < m && row_ptr[r + 1] <= k + 1) ++r;   // skip empty rows
     }
+#pragma unroll
+    for (int i = 0; i < kPhaseLen; ++i) {
+      const int idx = (int)threadIdx.x + i * kRunsPerBlock;
+      const int q = idx / kPhaseLen, j = idx % kPhaseLen;
+      sv[q * kPieceStride + j] = v[i];
+      sx[q * kPieceStride + j] = c[i] >= 0 ? __ldg(x + c[i]) : 0.0;
+    }
+    __syncthreads();
+    // walk: this thread's nonzeros a + 8 ph + j, j < 8, below b
+    const int64_t k0 = a + (int64_t)ph * kPhaseLen;
+#pragma unroll
+    for (int j = 0; j < kPhaseLen; ++j) {
+      const int64_t k = k0 + j;
+      if (k < b) {
+        acc = fma(sv[threadIdx.x * kPieceStride + j], sx[threadIdx.x * kPieceStride + j], acc);
+        if (r < m && k + 1 == rend) {   // row r ends here
+          if (row_ptr[r] >= a) {
+            y[r] = acc;
+          } else {
+            head_row = (int32_t)r;
+            head_val = acc;
+          }
+          acc = 0.0;
+          ++r;
+          while (r < m && row_ptr[r + 1] <= k + 1) ++r;   // skip empty rows
+          rend = r < m ? row_ptr[r + 1] : 0;
+        }
+      }
+    }
+    __syncthreads();   // the next phase overwrites the staged entries
   }
+  if (!active) return;
+  RunCarry cv = carry_view(scratch, runs);
   if (r < m && b < row_ptr[r + 1] && row_ptr[r] < b) {   // row r continues past the run
     tail_row = (int32_t)r;
     tail_val = acc;
@@ -169,8 +223,8 @@ extern "C" int pdlp_spmv_csr_noalloc(int64_t m, int64_t n, int64_t nnz, const in
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (runs > 0) {
-    const int64_t blocks = (runs + 255) / 256;
-    k_noalloc_runs<<<(unsigned)blocks, 256, 0, s>>>(m, nnz, row_ptr, col_idx, val, x, y, scratch, runs);
+    const int64_t blocks = (runs + kRunsPerBlock - 1) / kRunsPerBlock;
+    k_noalloc_runs<<<(unsigned)blocks, kRunsPerBlock, 0, s>>>(m, nnz, row_ptr, col_idx, val, x, y, scratch, runs);
   }
   int64_t fb = ((runs > m ? runs : m) + 255) / 256;
   if (fb > 148 * 8) fb = 148 * 8;
