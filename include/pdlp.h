@@ -351,7 +351,8 @@ int pdlp_time_iterations(pdlp_handle h, int64_t iters, double* ms_primal, double
  * A solve that stopped at an iteration limit that is a multiple of check_every, resumed
  * with the same parameters and a larger max_iter, gives the uninterrupted solve's iterates
  * bit for bit (the same SpMV schedule on both handles).  A solve stopped by its time limit
- * is repeated-checked once more on resume, so it continues correctly but not bit for bit.
+ * ended with one more (forced) check, so resuming it continues correctly but not bit for
+ * bit.
  * Errors: PDLP_EINVAL for batch handles, MIXED handles, a last solve on the persistent
  * engine, engine 2, a buffer of the wrong size, or a state of other LP sizes.  */
 int64_t pdlp_state_size(pdlp_handle h);
