@@ -71,7 +71,6 @@ constexpr int kRunsPerBlock = 256;
 constexpr int kPhaseLen = 8;
 constexpr int kPhases = (int)(kNoallocPerThread / kPhaseLen);
 constexpr int kPieceStride = kPhaseLen + 1;   // shared-memory stride of a run's piece (no bank conflicts)
-constexpr int kRowWin = 1024;                 // rows whose row_ptr entries a block keeps in shared memory
 
 __global__ void __launch_bounds__(kRunsPerBlock) k_noalloc_runs(int64_t m, int64_t nnz,
                                                                 const int64_t* __restrict__ row_ptr,
@@ -82,40 +81,15 @@ __global__ void __launch_bounds__(kRunsPerBlock) k_noalloc_runs(int64_t m, int64
                                                                 int64_t runs) {
   __shared__ double sv[kRunsPerBlock * kPieceStride];
   __shared__ double sx[kRunsPerBlock * kPieceStride];
-  // row_ptr[rlo .. rlo + kRowWin] (INT64_MAX past row m), rlo = the row of the block's
-  // first nonzero: the runs' start rows and row ends are read here when they fall inside
-  __shared__ int64_t srp[kRowWin + 1];
-  __shared__ int64_t s_rlo;
   const int64_t run0 = (int64_t)blockIdx.x * kRunsPerBlock;
   const int64_t t = run0 + threadIdx.x;
   const bool active = t < runs;
   const int64_t a = t * kNoallocPerThread;
   const int64_t b = active ? ((a + kNoallocPerThread < nnz) ? a + kNoallocPerThread : nnz) : a;
-  if (threadIdx.x == 0) s_rlo = row_of(row_ptr, m, run0 * kNoallocPerThread);
-  __syncthreads();
-  const int64_t rlo = s_rlo;
-  for (int i = (int)threadIdx.x; i <= kRowWin; i += kRunsPerBlock)
-    srp[i] = rlo + i <= m ? row_ptr[rlo + i] : INT64_MAX;
-  __syncthreads();
-  auto rp = [&](int64_t i) -> int64_t { return (uint64_t)(i - rlo) <= (uint64_t)kRowWin ? srp[i - rlo] : row_ptr[i]; };
   int32_t head_row = -1, tail_row = -1;
   double head_val = 0.0, tail_val = 0.0;
-  int64_t r = 0;
-  if (active) {
-    if (srp[kRowWin] > a) {
-      // the last window entry <= a (srp[0] <= a: rlo holds the block's first nonzero)
-      int lo = 0, hi = kRowWin;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (srp[mid] <= a) lo = mid;
-        else hi = mid;
-      }
-      r = rlo + lo;
-    } else {
-      r = row_of(row_ptr, m, a);
-    }
-  }
-  int64_t rend = (active && r < m) ? rp(r + 1) : 0;   // end of row r
+  int64_t r = active ? row_of(row_ptr, m, a) : 0;
+  int64_t rend = (active && r < m) ? row_ptr[r + 1] : 0;   // end of row r
   double acc = 0.0;
   for (int ph = 0; ph < kPhases; ++ph) {
     // stage: entry j of run (run0 + q) in this phase is nonzero run0*64 + 64 q + 8 ph + j
@@ -149,7 +123,7 @@ __global__ void __launch_bounds__(kRunsPerBlock) k_noalloc_runs(int64_t m, int64
       if (k < b) {
         acc = fma(sv[threadIdx.x * kPieceStride + j], sx[threadIdx.x * kPieceStride + j], acc);
         if (r < m && k + 1 == rend) {   // row r ends here
-          if (rp(r) >= a) {
+          if (row_ptr[r] >= a) {
             y[r] = acc;
           } else {
             head_row = (int32_t)r;
@@ -157,8 +131,8 @@ __global__ void __launch_bounds__(kRunsPerBlock) k_noalloc_runs(int64_t m, int64
           }
           acc = 0.0;
           ++r;
-          while (r < m && rp(r + 1) <= k + 1) ++r;   // skip empty rows
-          rend = r < m ? rp(r + 1) : 0;
+          while (r < m && row_ptr[r + 1] <= k + 1) ++r;   // skip empty rows
+          rend = r < m ? row_ptr[r + 1] : 0;
         }
       }
     }
@@ -166,7 +140,7 @@ __global__ void __launch_bounds__(kRunsPerBlock) k_noalloc_runs(int64_t m, int64
   }
   if (!active) return;
   RunCarry cv = carry_view(scratch, runs);
-  if (r < m && b < rp(r + 1) && rp(r) < b) {   // row r continues past the run
+  if (r < m && b < row_ptr[r + 1] && row_ptr[r] < b) {   // row r continues past the run
     tail_row = (int32_t)r;
     tail_val = acc;
   }
