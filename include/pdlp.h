@@ -410,8 +410,9 @@ int64_t pdlp_batch_get_restarts(pdlp_handle h, int64_t lp, int64_t* iters, int64
  * tensor cores: A and B BF16 row-major (K contiguous) device arrays with 16-byte aligned
  * bases, C FP32 row-major device array, bias FP32 device array or NULL.  M and N
  * multiples of 128, K a multiple of 64.  The operand tiles are copied by the tensor
- * memory accelerator into a 6-stage shared-memory ring that one thread refills while
- * another issues the MMAs.  Used by the learned warm start (an extension: the paper has
+ * memory accelerator into a shared-memory ring (2 to 6 stages) that one thread refills
+ * while another issues the MMAs; a CTA computes one or two 128-row tiles of C against
+ * each 128-column tile of B.  Used by the learned warm start (an extension: the paper has
  * no learned component); exposed for testing.  Runs on `stream` (NULL = default) and
  * waits for it; allocates no device memory (its error flag is a device variable of the
  * library).  Errors: PDLP_EINVAL (shapes, alignment), PDLP_ECUDA, PDLP_ETIMEOUT (an
